@@ -1,0 +1,724 @@
+/*
+ * cool_oracle.c -- plain, slow, FP64 CPU oracle of the two-temperature
+ * cooling source step (Motta et al., arXiv 2505.08855).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library
+ * and its Python binding) may include, link or call this file.  It is used by
+ * tests/, by __graft_entry__.smoke() and by the cpu_baseline leg of bench.py.
+ * It shares no code, header, constant table or helper with the CUDA path.
+ *
+ * Two levels (both FP64, cgs units):
+ *   O1  the direct formulas of Sec. 2 (bremsstrahlung Eqs. 1-2, synchrotron
+ *       Eqs. 3-6, Compton enhancement Eqs. 7-9, thin cooling Eq. 10, the
+ *       optically-thick bridge Eqs. 11-12, Coulomb exchange Eq. 16);
+ *   O2  the table of Sec. 2.6 / 2.8 built from O1 on log-spaced nodes, read by
+ *       multilinear interpolation in log2 space, and the sub-cycled energy
+ *       update of Sec. 3.2 (explicit with the 30 % limiter, or implicit).
+ *
+ * Readings of the paper where it is silent, garbled or inconsistent (each is
+ * listed again in the design doc):
+ *   - sigma in Eq. 11 and in tau_abs (Eq. 12) is Stefan-Boltzmann's constant
+ *     (the printed sigma_T is dimensionally impossible there);
+ *   - the Compton exponent is -1 - ln P / ln A (the truncated geometric series
+ *     of scatterings); the printed 1 - ln P / ln A is available as a flag;
+ *   - ln(Lambda) = 20 by default (spec field), theta_i = kT_i/(m_p c^2) by
+ *     default (flag for the printed m_e);
+ *   - nu_c is the root of Eq. 5, found by bisection in ln(nu);
+ *   - K2(1/theta_e) -> 2 theta_e^2 for T_e <= k2_switch_T (1e8 K), literally;
+ *   - the table stores log2 values; brems and Coulomb are factored by n_e^2
+ *     (exact), the synchrotron channel is eta*Q_syn on the 4-D grid;
+ *   - the optically-thick bridge is applied at run time per sub-cycle.
+ *
+ * Parity pins: every function below is pinned by tests/test_oracle_*.py to
+ * closed forms, limits, library special functions or brute force; see the
+ * per-function comments.  No function here is "parity unpinned" except the
+ * absolute agreement with the authors' own (unpublished) table values.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------------- */
+/* Physical constants, cgs, CODATA 2018.                                  */
+/* ---------------------------------------------------------------------- */
+#define O_C     2.99792458e10
+#define O_KB    1.380649e-16
+#define O_ME    9.1093837015e-28
+#define O_MP    1.67262192369e-24
+#define O_QE    4.80320471e-10
+#define O_H     6.62607015e-27
+#define O_SIGT  6.6524587321e-25
+#define O_SIGSB 5.670374419e-5
+#define O_G     6.6743e-8
+#define O_MSUN  1.98847e33
+#define O_PI    3.14159265358979323846
+
+double orc_const(int i) {
+    switch (i) {
+    case 0: return O_C;   case 1: return O_KB;  case 2: return O_ME;
+    case 3: return O_MP;  case 4: return O_QE;  case 5: return O_H;
+    case 6: return O_SIGT; case 7: return O_SIGSB; case 8: return O_G;
+    case 9: return O_MSUN;
+    default: return NAN;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Spec / params (the oracle's own definitions).                          */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int n[5];          /* axis sizes: 0 H, 1 B, 2 n_e, 3 T_e (cooling), 4 T (Coulomb, both axes) */
+    double lo[5], hi[5];
+    double k2_switch_T;
+    double lnLambda;
+    int theta_i_uses_mp;
+    int compton_literal;
+} orc_spec;
+
+typedef struct {
+    double rho_scale, M_bh_msun, gamma_e, gamma_i, dt;
+    int n_sub, mode;               /* mode 0: explicit limited, 1: implicit in stiff cells */
+    double limiter_frac, eq_band, coulomb_clamp;
+    int implicit_iters;
+} orc_params;
+
+/* ---------------------------------------------------------------------- */
+/* Exponentially scaled modified Bessel functions of the second kind,     */
+/* Kt_nu(z) = e^z K_nu(z), nu = 0, 1, 2, z > 0.                           */
+/* Method: the integral representation K_nu(z) = int_0^inf               */
+/* exp(-z cosh t) cosh(nu t) dt (DLMF 10.32.9) evaluated by the           */
+/* trapezoidal rule, which converges exponentially for this analytic,     */
+/* double-exponentially decaying integrand (Trefethen & Weideman 2014,    */
+/* SIAM Rev. 56, 385).  cosh t - 1 is formed as 2 sinh^2(t/2).            */
+/* Pinned against scipy.special.kve and the recurrence K2 = K0 + 2K1/z.   */
+/* ---------------------------------------------------------------------- */
+double orc_kve(int nu, double z) {
+    if (!(z > 0.0)) return INFINITY;
+    double h = 0.125;
+    if (z > 1.0) h = 0.125 / sqrt(z);
+    double sum = 0.5; /* t = 0 term: exp(0) * cosh(0) = 1, half weight */
+    for (int k = 1; k < 100000; ++k) {
+        double t = k * h;
+        double sh = sinh(0.5 * t);
+        double ex = z * 2.0 * sh * sh;
+        if (ex > 745.0) break;
+        double term = exp(-ex) * cosh(nu * t);
+        sum += term;
+        if (term < 1e-18 * sum && ex > 40.0) break;
+    }
+    return h * sum;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bremsstrahlung, Sec. 2.1 (Eqs. 1-2), per n_e^2, erg cm^3 s^-1.          */
+/* Pinned: branch continuity at theta = 1, the non-relativistic sqrt(T)   */
+/* free-free law, the n_e^2 scaling.                                      */
+/* ---------------------------------------------------------------------- */
+double orc_theta_e(double T) { return O_KB * T / (O_ME * O_C * O_C); }
+
+double orc_brems_ee(double T) {
+    double th = orc_theta_e(T);
+    double f;
+    if (th < 1.0) f = pow(th, 1.5) * (1.0 + 1.1 * th + th * th - 1.25 * pow(th, 2.5));
+    else          f = 1.34 * th * (log(1.123 * th) + 1.28);
+    return 2.56e-22 * f;
+}
+
+double orc_brems_ei(double T) {
+    double th = orc_theta_e(T);
+    double f;
+    if (th < 1.0) f = 4.0 * sqrt(2.0 * th / (O_PI * O_PI * O_PI)) * (1.0 + 1.781 * pow(th, 1.34));
+    else          f = 9.0 * th / (2.0 * O_PI) * (log(1.123 * th + 0.48) + 1.5);
+    return 1.48e-22 * f;
+}
+
+double orc_brems(double T) { return orc_brems_ee(T) + orc_brems_ei(T); }
+
+/* ---------------------------------------------------------------------- */
+/* Synchrotron, Sec. 2.2.                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Mahadevan's fit I'(x), Eq. 4; log form to avoid underflow. */
+double orc_log_Iprime(double x) {
+    return log(4.0505) - log(x) / 6.0
+         + log(1.0 + 0.4 * pow(x, -0.25) + 0.5316 * pow(x, -0.5))
+         - 1.8899 * cbrt(x);
+}
+double orc_Iprime(double x) { return exp(orc_log_Iprime(x)); }
+
+/* The K2(1/theta_e) factor of Eq. 3, with the low-temperature substitution
+ * K2 -> 2 theta_e^2 for T_e <= k2_switch_T (Sec. 2.2, last paragraph). */
+double orc_k2_factor(double T, double k2_switch_T) {
+    double th = orc_theta_e(T);
+    if (T <= k2_switch_T) return 2.0 * th * th;
+    double z = 1.0 / th;
+    return orc_kve(2, z) * exp(-z);
+}
+
+/* nu_0 such that x_M = nu / nu_0 (Eq. 3). */
+double orc_nu0(double B, double T) {
+    double th = orc_theta_e(T);
+    return 3.0 * O_QE * B * th * th / (4.0 * O_PI * O_ME * O_C);
+}
+
+/* Emissivity eps_s(nu), Eq. 3, erg cm^-3 s^-1 Hz^-1. */
+double orc_eps_syn(double nu, double ne, double B, double T, double k2_switch_T) {
+    double x = nu / orc_nu0(B, T);
+    return 4.43e-30 * 4.0 * O_PI * nu * ne / orc_k2_factor(T, k2_switch_T) * orc_Iprime(x);
+}
+
+/* ln of the ratio (annulus emission)/(Rayleigh-Jeans surface emission) in
+ * Eq. 5, i.e. ln[ 2H eps_s(nu) / (2 * 2 pi nu^2 k T / c^2) ]. */
+static double log_ratio_bb(double lnnu, double H, double ne, double T,
+                           double k2f, double nu0) {
+    double nu = exp(lnnu);
+    double x = nu / nu0;
+    double lhs = log(H) + log(4.43e-30 * 4.0 * O_PI * ne / k2f) + lnnu + orc_log_Iprime(x);
+    double rhs = log(2.0 * O_PI * O_KB * T / (O_C * O_C)) + 2.0 * lnnu;
+    return lhs - rhs;
+}
+
+/* Critical frequency nu_c: root of Eq. 5 by bisection in ln(nu) on
+ * [ln 1 Hz, ln 1e30 Hz] to |d ln nu| < 1e-14, at most 200 halvings.
+ * If the ratio is <= 1 already at 1 Hz, nu_c = 1 Hz.  If it is > 1 at
+ * 1e30 Hz, nu_c = 1e30 Hz and *flag = 1.  Pinned by scipy's brentq on
+ * the same equation and the residual test. */
+double orc_nu_c(double H, double B, double ne, double T, double k2_switch_T, int* flag) {
+    double k2f = orc_k2_factor(T, k2_switch_T);
+    double nu0 = orc_nu0(B, T);
+    double a = 0.0, b = log(1e30);
+    if (flag) *flag = 0;
+    if (log_ratio_bb(a, H, ne, T, k2f, nu0) <= 0.0) return 1.0;
+    if (log_ratio_bb(b, H, ne, T, k2f, nu0) > 0.0) { if (flag) *flag = 1; return 1e30; }
+    for (int it = 0; it < 200 && (b - a) >= 1e-14; ++it) {
+        double m = 0.5 * (a + b);
+        if (log_ratio_bb(m, H, ne, T, k2f, nu0) > 0.0) a = m; else b = m;
+    }
+    return exp(0.5 * (a + b));
+}
+
+/* Gauss-Legendre nodes/weights on [-1,1], n points: Newton iteration on
+ * P_n from the asymptotic initial guess cos(pi (i - 1/4)/(n + 1/2)). */
+static void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(O_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            /* p1 = P_n(z), p0 = P_{n-1}(z) */
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void orc_gl16(double* x, double* w) { gauss_legendre(16, x, w); }
+
+static double gx[16], gw[16];
+__attribute__((constructor)) static void gl16_init(void) { gauss_legendre(16, gx, gw); }
+
+/* Integrand of J in s = x^(1/3): x I'(x) dx = 3 s^5 I'(s^3) ds. */
+static double j_integrand(double s) {
+    if (s <= 0.0) return 0.0;
+    double rs = sqrt(s);
+    double s45 = s * s * s * s * rs;          /* s^4.5 */
+    double sm75 = 1.0 / (rs * sqrt(rs));     /* s^-0.75 */
+    double sm15 = 1.0 / (s * rs);            /* s^-1.5 */
+    return 3.0 * 4.0505 * s45 * (1.0 + 0.4 * sm75 + 0.5316 * sm15) * exp(-1.8899 * s);
+}
+
+/* J(x_c) = int_{x_c}^inf x I'(x) dx, by composite Gauss-Legendre (16 points)
+ * over `panels` equal panels of s in [x_c^(1/3), x_c^(1/3) + 40].
+ * Pinned against the closed form in upper incomplete gamma functions. */
+double orc_J(double xc, int panels) {
+    double s0 = cbrt(xc);
+    double width = 40.0 / panels;
+    double sum = 0.0;
+    for (int p = 0; p < panels; ++p) {
+        double a = s0 + p * width;
+        double mid = a + 0.5 * width, half = 0.5 * width;
+        double ps = 0.0;
+        for (int i = 0; i < 16; ++i) ps += gw[i] * j_integrand(mid + half * gx[i]);
+        sum += half * ps;
+    }
+    return sum;
+}
+
+/* Synchrotron cooling Q_syn, Eq. 6: Rayleigh-Jeans part below nu_c (per
+ * unit volume, divided by H) plus the optically thin integral above nu_c. */
+double orc_qsyn_nu(double H, double B, double ne, double T, double k2_switch_T,
+                   double nuc, int panels) {
+    double rj = 2.0 * O_PI * O_KB * T * nuc * nuc * nuc / (3.0 * O_C * O_C * H);
+    double nu0 = orc_nu0(B, T);
+    double pref = 4.43e-30 * 4.0 * O_PI * ne / orc_k2_factor(T, k2_switch_T);
+    double thin = pref * nu0 * nu0 * orc_J(nuc / nu0, panels);
+    return rj + thin;
+}
+
+/* Compton enhancement eta at nu_c, Eqs. 7-9 (Sec. 2.3).  Stable form of the
+ * truncated geometric series: eta = 1 + P(A-1) [(PA)^k - 1]/(PA - 1),
+ * k = ln(3 theta/E)/ln A, evaluated with expm1.  With literal != 0 the
+ * exponent as printed, 1 - ln P/ln A, is used instead (for the test that
+ * shows its sign failure). */
+double orc_eta(double nuc, double T, double ne, double H, int literal) {
+    double th = orc_theta_e(T);
+    double E = O_H * nuc / (O_ME * O_C * O_C);
+    if (E >= 3.0 * th) return 1.0;
+    double tau = 2.0 * ne * O_SIGT * H;
+    double P = -expm1(-tau);
+    double am1 = 4.0 * th + 16.0 * th * th;
+    double A = 1.0 + am1;
+    double lnA = log1p(am1);
+    if (literal) {
+        double ex = 1.0 - log(P) / lnA;
+        return 1.0 + P * am1 / (1.0 - P * A) * (1.0 - pow(E / (3.0 * th), ex));
+    }
+    if (!(P > 0.0)) return 1.0;
+    double k = log(3.0 * th / E) / lnA;
+    double eps = log(P) + lnA;
+    double ratio = (eps == 0.0) ? k : expm1(k * eps) / expm1(eps);
+    return 1.0 + P * am1 * ratio;
+}
+
+/* eta(nu_c) * Q_syn at one (H, B, n_e, T_e) point: the 4-D table channel. */
+double orc_eta_qsyn(double H, double B, double ne, double T, const orc_spec* s, int* flag) {
+    double nuc = orc_nu_c(H, B, ne, T, s->k2_switch_T, flag);
+    double q = orc_qsyn_nu(H, B, ne, T, s->k2_switch_T, nuc, 64);
+    return orc_eta(nuc, T, ne, H, s->compton_literal) * q;
+}
+
+/* Optically-thick bridge, Eqs. 11-12 (sigma read as Stefan-Boltzmann):
+ * Q_total = (4 sigma T^4/H) / (3 tau/2 + sqrt 3 + 1/tau_abs),
+ * tau_abs = H Q_thin/(4 sigma T^4), tau = tau_abs + tau_sca.  Pinned by the
+ * thin and thick limits. */
+double orc_bridge(double qthin, double T, double H, double ne) {
+    double bb = 4.0 * O_SIGSB * T * T * T * T;
+    double tau_sca = 2.0 * ne * O_SIGT * H;
+    double tau_abs = H * qthin / bb;
+    if (!(tau_abs > 0.0)) return 0.0;
+    return (bb / H) / (1.5 * (tau_abs + tau_sca) + sqrt(3.0) + 1.0 / tau_abs);
+}
+
+/* Direct (O1) total cooling rate at one point, erg cm^-3 s^-1. */
+double orc_qtotal_direct(double H, double B, double ne, double T, const orc_spec* s) {
+    double qthin = ne * ne * orc_brems(T) + orc_eta_qsyn(H, B, ne, T, s, NULL);
+    return orc_bridge(qthin, T, H, ne);
+}
+
+/* Coulomb exchange coefficient, Eq. 16: C = Q_cc / (n_e^2 (T_i - T_e)),
+ * hydrogen (n_i = n_e = rho/m_p), with scaled Bessel functions so that the
+ * exponentials cancel exactly (1/theta_m = 1/theta_e + 1/theta_i).
+ * Pinned: non-relativistic (Spitzer) limit, symmetry, zero at T_e = T_i. */
+double orc_coulomb_C(double Ti, double Te, const orc_spec* s) {
+    double the = O_KB * Te / (O_ME * O_C * O_C);
+    double mi = s->theta_i_uses_mp ? O_MP : O_ME;
+    double thi = O_KB * Ti / (mi * O_C * O_C);
+    double ze = 1.0 / the, zi = 1.0 / thi, zm = ze + zi;
+    double ts = the + thi;
+    double br = (2.0 * ts * ts + 1.0) / ts * orc_kve(1, zm) + 2.0 * orc_kve(0, zm);
+    double pre = 1.5 * (O_ME / O_MP) * s->lnLambda * O_C * O_SIGT * O_KB;
+    return pre * br / (orc_kve(2, zi) * orc_kve(2, ze));
+}
+
+/* ---------------------------------------------------------------------- */
+/* Table nodes (Sec. 2.6): N log-spaced points, endpoints inclusive.       */
+/* l_j = log2(lo) + j (log2(hi) - log2(lo))/(N-1), x_j = 2^l_j; stored also */
+/* rounded to FP32 (the FP32 copy decides index selection).                */
+/* ---------------------------------------------------------------------- */
+#define ORC_MAXN 1024
+typedef struct { int N; double l0, dl; float x32[ORC_MAXN]; } orc_axis;
+
+static double axis_dl(const orc_spec* s, int a) {
+    return (log2(s->hi[a]) - log2(s->lo[a])) / (s->n[a] - 1);
+}
+static double axis_l(const orc_spec* s, int a, int j) {
+    return log2(s->lo[a]) + j * axis_dl(s, a);
+}
+static void axis_init(const orc_spec* s, int a, orc_axis* ax) {
+    ax->N = s->n[a];
+    ax->l0 = log2(s->lo[a]);
+    ax->dl = axis_dl(s, a);
+    for (int j = 0; j < ax->N && j < ORC_MAXN; ++j) ax->x32[j] = (float)exp2(axis_l(s, a, j));
+}
+void orc_nodes(const orc_spec* s, int a, double* x64, double* l64, float* x32) {
+    for (int j = 0; j < s->n[a]; ++j) {
+        double l = axis_l(s, a, j);
+        double x = exp2(l);
+        if (x64) x64[j] = x;
+        if (l64) l64[j] = l;
+        if (x32) x32[j] = (float)x;
+    }
+}
+
+/* Table channels (log2 values):
+ *   lb[t]              = log2(Q_brem/n_e^2)(T_t)
+ *   ls[((h*nB+b)*nN+n)*nT+t] = log2(eta Q_syn)(H_h, B_b, n_n, T_t)
+ *   lc[i*nC+e]         = log2 C(T_i = X_i, T_e = X_e)
+ */
+void orc_build_brems(const orc_spec* s, double* lb) {
+    for (int t = 0; t < s->n[3]; ++t) lb[t] = log2(orc_brems(exp2(axis_l(s, 3, t))));
+}
+
+double orc_syn_node(const orc_spec* s, int h, int b, int n, int t) {
+    double H = exp2(axis_l(s, 0, h)), B = exp2(axis_l(s, 1, b));
+    double ne = exp2(axis_l(s, 2, n)), T = exp2(axis_l(s, 3, t));
+    return log2(orc_eta_qsyn(H, B, ne, T, s, NULL));
+}
+
+void orc_build_syn(const orc_spec* s, double* ls, int nthreads) {
+    long long total = (long long)s->n[0] * s->n[1] * s->n[2] * s->n[3];
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (long long i = 0; i < total; ++i) {
+        long long r = i;
+        int t = (int)(r % s->n[3]); r /= s->n[3];
+        int n = (int)(r % s->n[2]); r /= s->n[2];
+        int b = (int)(r % s->n[1]); r /= s->n[1];
+        int h = (int)r;
+        ls[i] = orc_syn_node(s, h, b, n, t);
+    }
+}
+
+/* Selected synchrotron nodes only: idx[k] are flat indices into the 4-D
+ * table; out[k] receives the node value. */
+void orc_build_syn_at(const orc_spec* s, long long m, const long long* idx, double* out, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (long long k = 0; k < m; ++k) {
+        long long r = idx[k];
+        int t = (int)(r % s->n[3]); r /= s->n[3];
+        int n = (int)(r % s->n[2]); r /= s->n[2];
+        int b = (int)(r % s->n[1]); r /= s->n[1];
+        int h = (int)r;
+        out[k] = orc_syn_node(s, h, b, n, t);
+    }
+}
+
+void orc_build_coulomb(const orc_spec* s, double* lc) {
+    int N = s->n[4];
+    for (int i = 0; i < N; ++i)
+        for (int e = 0; e < N; ++e)
+            lc[i * N + e] = log2(orc_coulomb_C(exp2(axis_l(s, 4, i)), exp2(axis_l(s, 4, e)), s));
+}
+
+/* ---------------------------------------------------------------------- */
+/* Interpolation (O2).                                                     */
+/* Index: the largest j in [0, N-2] with node32[j] <= key (node32 = FP32    */
+/* node, compared exactly); a key below node32[0] takes j = 0.  Weight:     */
+/* w = (log2 key - l_j)/dl clamped to [0, 1] (constant extrapolation at    */
+/* the table edges).  Returns 1 if the key lies outside [node32[0],        */
+/* node32[N-1]] (a clamped key), else 0.                                   */
+/* ---------------------------------------------------------------------- */
+static int select_ax(const orc_axis* ax, double key, int* jout, double* wout) {
+    int N = ax->N;
+    int j = 0;
+    int clamped = 0;
+    if (!(key >= (double)ax->x32[0])) clamped = 1;
+    else {
+        /* plain linear scan over increasing nodes */
+        for (int k = 1; k <= N - 2 && (double)ax->x32[k] <= key; ++k) j = k;
+        if (key > (double)ax->x32[N - 1]) clamped = 1;
+    }
+    double w;
+    if (!(key > 0.0)) w = 0.0;
+    else w = (log2(key) - (ax->l0 + j * ax->dl)) / ax->dl;
+    if (w < 0.0) w = 0.0;
+    if (w > 1.0) w = 1.0;
+    *jout = j; *wout = w;
+    return clamped;
+}
+
+int orc_select(const orc_spec* s, int a, double key, int* jout, double* wout) {
+    orc_axis ax; axis_init(s, a, &ax);
+    return select_ax(&ax, key, jout, wout);
+}
+
+/* Batch selection of FP32 keys on one axis (the twin of the GPU debug
+ * lookup): idx[i], w[i] for keys[i]. */
+void orc_select_f32(const orc_spec* s, int a, long long n, const float* keys, int* idx, double* w) {
+    orc_axis ax; axis_init(s, a, &ax);
+    for (long long i = 0; i < n; ++i) select_ax(&ax, (double)keys[i], &idx[i], &w[i]);
+}
+
+/* Lazy synchrotron table: entries equal to NaN are computed on first use
+ * (single-threaded use only). */
+static double syn_at(const orc_spec* s, double* ls, int lazy, int h, int b, int n, int t) {
+    long long i = (((long long)h * s->n[1] + b) * s->n[2] + n) * s->n[3] + t;
+    double v = ls[i];
+    if (lazy && isnan(v)) { v = orc_syn_node(s, h, b, n, t); ls[i] = v; }
+    return v;
+}
+
+/* Multilinear interpolation of the 4-D channel: sum over the 16 corners of
+ * prod(weights) * value. */
+static double interp4(const orc_spec* s, double* ls, int lazy, const int* j, const double* w) {
+    double acc = 0.0;
+    for (int c = 0; c < 16; ++c) {
+        double wt = 1.0;
+        int idx[4];
+        for (int a = 0; a < 4; ++a) {
+            int bit = (c >> a) & 1;
+            idx[a] = j[a] + bit;
+            wt *= bit ? w[a] : (1.0 - w[a]);
+        }
+        acc += wt * syn_at(s, ls, lazy, idx[0], idx[1], idx[2], idx[3]);
+    }
+    return acc;
+}
+static double interp1(const double* lb, int j, double w) {
+    return (1.0 - w) * lb[j] + w * lb[j + 1];
+}
+static double interp2(const double* lc, int N, int ji, double wi, int je, double we) {
+    return (1.0 - wi) * (1.0 - we) * lc[ji * N + je] + (1.0 - wi) * we * lc[ji * N + je + 1]
+         + wi * (1.0 - we) * lc[(ji + 1) * N + je] + wi * we * lc[(ji + 1) * N + je + 1];
+}
+
+/* Public scalar interpolation helpers (tests). */
+double orc_interp_syn(const orc_spec* s, double* ls, int lazy, double H, double B, double ne, double T) {
+    int j[4]; double w[4];
+    double k[4] = {H, B, ne, T};
+    for (int a = 0; a < 4; ++a) orc_select(s, a, k[a], &j[a], &w[a]);
+    return interp4(s, ls, lazy, j, w);
+}
+double orc_interp_brems(const orc_spec* s, const double* lb, double T) {
+    int j; double w; orc_select(s, 3, T, &j, &w);
+    return interp1(lb, j, w);
+}
+double orc_interp_coulomb(const orc_spec* s, const double* lc, double Ti, double Te) {
+    int ji, je; double wi, we;
+    orc_select(s, 4, Ti, &ji, &wi);
+    orc_select(s, 4, Te, &je, &we);
+    return interp2(lc, s->n[4], ji, wi, je, we);
+}
+
+/* ---------------------------------------------------------------------- */
+/* The per-cell step (Sec. 3.2): unit conversion, N_sub sub-cycles of      */
+/* (i) Coulomb exchange, (ii) radiative cooling with the bridge, applied   */
+/* to the electron internal energy explicitly with the limiter, or         */
+/* implicitly (backward Euler, bisection in log2 u) in stiff cells.        */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    const orc_spec* s;
+    const double* lb;
+    double* ls;
+    const double* lc;
+    int lazy;
+    int direct;       /* 1: O1 rates from the formulas instead of the table */
+    orc_axis ax[5];
+} orc_rates;
+
+typedef struct {
+    double ne, Bg, Hcm, hs, escale, sTe, sTi, ce, ci;
+    int j[3]; double w[3]; /* H, B, n_e selections (step-invariant) */
+} cell_ctx;
+
+/* Cooling energy removed in one sub-cycle (code units) for electron energy
+ * density ue, through T_e = s_Te ue/rho.  *clamp is or-ed with key clamping. */
+static double cool_q(const orc_rates* R, const cell_ctx* c, double ue, double rho, int* clamp) {
+    double Te = c->sTe * ue / rho;
+    double qthin;
+    if (R->direct) {
+        qthin = c->ne * c->ne * orc_brems(Te) + orc_eta_qsyn(c->Hcm, c->Bg, c->ne, Te, R->s, NULL);
+    } else {
+        int jt; double wt;
+        int cl = select_ax(&R->ax[3], Te, &jt, &wt);
+        if (clamp) *clamp |= cl;
+        int j[4] = {c->j[0], c->j[1], c->j[2], jt};
+        double w[4] = {c->w[0], c->w[1], c->w[2], wt};
+        double lqs = interp4(R->s, R->ls, R->lazy, j, w);
+        double lqb = interp1(R->lb, jt, wt);
+        qthin = c->ne * c->ne * exp2(lqb) + exp2(lqs);
+    }
+    double Q = orc_bridge(qthin, Te, c->Hcm, c->ne);
+    return c->hs * Q / c->escale;
+}
+
+static double coulomb_rate(const orc_rates* R, double Ti, double Te, int* clamp) {
+    if (R->direct) return orc_coulomb_C(Ti, Te, R->s);
+    int ji, je; double wi, we;
+    int cl = select_ax(&R->ax[4], Ti, &ji, &wi);
+    cl |= select_ax(&R->ax[4], Te, &je, &we);
+    if (clamp) *clamp |= cl;
+    return exp2(interp2(R->lc, R->s->n[4], ji, wi, je, we));
+}
+
+/* Unit conversion of one cell (code units G = c = M = 1, 4 pi absorbed in
+ * b; hydrogen, n_e = n_i = rho rho_scale/m_p; T_s = (gamma_s - 1) m_p c^2
+ * (u_s/rho)/k_B) and the step-invariant H, B, n_e selections. */
+static int cell_setup(const orc_rates* R, const orc_params* p, double rho, double B, double H,
+                      cell_ctx* c) {
+    double rg = (O_G * (p->M_bh_msun * O_MSUN)) / (O_C * O_C);
+    double tg = rg / O_C;
+    c->ne = rho * (p->rho_scale / O_MP);
+    c->Bg = B * (sqrt(4.0 * O_PI * p->rho_scale) * O_C);
+    c->Hcm = H * rg;
+    c->hs = p->dt * tg / p->n_sub;
+    c->escale = p->rho_scale * O_C * O_C;
+    c->ce = p->gamma_e - 1.0; c->ci = p->gamma_i - 1.0;
+    c->sTe = c->ce * O_MP * O_C * O_C / O_KB;
+    c->sTi = c->ci * O_MP * O_C * O_C / O_KB;
+    int clamp = 0;
+    if (!R->direct) {
+        double k[3] = {c->Hcm, c->Bg, c->ne};
+        for (int a = 0; a < 3; ++a) clamp |= select_ax(&R->ax[a], k[a], &c->j[a], &c->w[a]);
+    }
+    return clamp;
+}
+
+/* Per-cell flags: bit 0 clamped key, 1 invalid input (non-finite or
+ * non-positive; passed through unchanged), 2 stiff (implicit solve entered),
+ * 3 Coulomb inside the equilibrium band |T_e/T_i - 1| <= eq_band,
+ * 4 implicit solve without a sign change (limited explicit step taken). */
+static void step_cell(const orc_rates* R, const orc_params* p, double rho, double B, double H,
+                      double ue, double ui, double* ue_out, double* ui_out,
+                      double* qcool, double* qcc, unsigned* flags) {
+    *flags = 0;
+    if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
+        !(rho > 0.0) || !(ue > 0.0) || !(ui > 0.0) || B < 0.0 || H < 0.0) {
+        *ue_out = ue; *ui_out = ui;
+        if (qcool) *qcool = 0.0;
+        if (qcc) *qcc = 0.0;
+        *flags = 1u << 1;
+        return;
+    }
+    cell_ctx c;
+    int clamp = cell_setup(R, p, rho, B, H, &c);
+    double sum_cool = 0.0, sum_cc = 0.0;
+    int stiff = 0, eqb = 0, fail = 0;
+    for (int k = 0; k < p->n_sub; ++k) {
+        /* (i) Coulomb exchange (Eq. 16), clamped so that the step does not
+         * cross T_e = T_i. */
+        double Te = c.sTe * ue / rho, Ti = c.sTi * ui / rho;
+        if (fabs(Te / Ti - 1.0) <= p->eq_band) eqb = 1;
+        double C = coulomb_rate(R, Ti, Te, &clamp);
+        double X = c.hs * c.ne * c.ne * C * (Ti - Te) / c.escale;
+        double Xeq = (c.ci * ui - c.ce * ue) / (c.ce + c.ci);
+        double lim = p->coulomb_clamp * fabs(Xeq);
+        if (fabs(X) > lim) X = (X >= 0.0 ? lim : -lim);
+        ue += X; ui -= X; sum_cc += X;
+        /* (ii) cooling with the bridge (Eqs. 10-12) */
+        double q = cool_q(R, &c, ue, rho, &clamp);
+        double du;
+        if (p->mode == 1 && q > p->limiter_frac * ue) {
+            /* implicit backward Euler: g(u) = u - ue + q(u) = 0 on
+             * [ue 2^-60, ue], bisection in log2 u */
+            stiff = 1;
+            double a = log2(ue) - 60.0, b = log2(ue);
+            double ga = exp2(a) - ue + cool_q(R, &c, exp2(a), rho, NULL);
+            if (!(ga < 0.0)) {
+                fail = 1;
+                du = p->limiter_frac * ue;
+            } else {
+                for (int it = 0; it < p->implicit_iters; ++it) {
+                    double m = 0.5 * (a + b);
+                    double um = exp2(m);
+                    if (um - ue + cool_q(R, &c, um, rho, NULL) > 0.0) b = m; else a = m;
+                }
+                du = ue - exp2(0.5 * (a + b));
+            }
+        } else {
+            du = q < p->limiter_frac * ue ? q : p->limiter_frac * ue;
+        }
+        ue -= du; sum_cool += du;
+    }
+    *ue_out = ue; *ui_out = ui;
+    if (qcool) *qcool = sum_cool;
+    if (qcc) *qcc = sum_cc;
+    *flags = (clamp ? 1u : 0u) | (stiff ? 1u << 2 : 0u) | (eqb ? 1u << 3 : 0u) | (fail ? 1u << 4 : 0u);
+}
+
+/* Step n cells.  counters[0..5] = cells with flag bit k set (bit 5 unused:
+ * the oracle has no surrogate fallback).  lazy: the 4-D channel may hold NaN
+ * entries, computed on first use (forces one thread).  direct: O1 rates. */
+int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, int lazy, int direct,
+             const orc_params* p, long long n,
+             const double* rho, const double* B, const double* H, const double* ue, const double* ui,
+             double* ue_out, double* ui_out, double* qcool, double* qcc,
+             long long* counters, int nthreads) {
+    orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
+    if (!R) return -1;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = lazy; R->direct = direct;
+    for (int a = 0; a < 5; ++a) {
+        if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
+        axis_init(s, a, &R->ax[a]);
+    }
+    long long cnt[6] = {0, 0, 0, 0, 0, 0};
+    if (lazy || direct) nthreads = 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+:cnt[:6]) if (nthreads != 1)
+#endif
+    for (long long i = 0; i < n; ++i) {
+        unsigned f;
+        double a, b;
+        step_cell(R, p, rho[i], B[i], H[i], ue[i], ui[i], &a, &b,
+                  qcool ? &qcool[i] : NULL, qcc ? &qcc[i] : NULL, &f);
+        ue_out[i] = a; ui_out[i] = b;
+        for (int k = 0; k < 5; ++k) cnt[k] += (f >> k) & 1u;
+    }
+    if (counters) for (int k = 0; k < 6; ++k) counters[k] = cnt[k];
+    free(R);
+    return 0;
+}
+
+/* Cooling energy removed in one sub-cycle (code units) at electron energy
+ * density ue for one cell (tests: implicit residual, limiter). */
+double orc_cool_q_cell(const orc_spec* s, const double* lb, double* ls, const double* lc, int direct,
+                       const orc_params* p, double rho, double B, double H, double ue) {
+    orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
+    if (!R) return NAN;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = direct;
+    for (int a = 0; a < 5; ++a) axis_init(s, a, &R->ax[a]);
+    cell_ctx c;
+    cell_setup(R, p, rho, B, H, &c);
+    double q = cool_q(R, &c, ue, rho, NULL);
+    free(R);
+    return q;
+}
+
+/* Keys of the first sub-cycle formed in FP32 by the fixed operation sequence
+ * that the GPU path also uses:  n_e = rho*s_n, B_G = B*s_B, H_cm = H*s_H,
+ * inv = s_T / rho (IEEE division), T = u*inv, with the scale factors rounded
+ * from FP64 once.  keys[5*i + {0..4}] = H_cm, B_G, n_e, T_e, T_i. */
+void orc_keys_f32(const orc_params* p, long long n, const float* rho, const float* B, const float* H,
+                  const float* ue, const float* ui, float* keys) {
+    double rg = (O_G * (p->M_bh_msun * O_MSUN)) / (O_C * O_C);
+    float s_n = (float)(p->rho_scale / O_MP);
+    float s_B = (float)(sqrt(4.0 * O_PI * p->rho_scale) * O_C);
+    float s_H = (float)rg;
+    float s_Te = (float)((p->gamma_e - 1.0) * O_MP * O_C * O_C / O_KB);
+    float s_Ti = (float)((p->gamma_i - 1.0) * O_MP * O_C * O_C / O_KB);
+    for (long long i = 0; i < n; ++i) {
+        volatile float inv_e = s_Te / rho[i];
+        volatile float inv_i = s_Ti / rho[i];
+        keys[5 * i + 0] = H[i] * s_H;
+        keys[5 * i + 1] = B[i] * s_B;
+        keys[5 * i + 2] = rho[i] * s_n;
+        keys[5 * i + 3] = ue[i] * inv_e;
+        keys[5 * i + 4] = ui[i] * inv_i;
+    }
+}

@@ -1,0 +1,329 @@
+"""Pins of the oracle's physics functions (no GPU).
+
+Each test fixes a part of the FP64 oracle against something other than the
+oracle's own formula: library special functions, closed forms, textbook
+limits, classical formulae from other sources, or brute force.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+import scipy.optimize
+import scipy.special as sp
+
+C_LIGHT = 2.99792458e10
+K_B = 1.380649e-16
+M_E = 9.1093837015e-28
+M_P = 1.67262192369e-24
+SIG_T = 6.6524587321e-25
+SIG_SB = 5.670374419e-5
+H_PL = 6.62607015e-27
+ME_C2_K = M_E * C_LIGHT ** 2 / K_B      # T at theta_e = 1
+
+
+# ---- constants --------------------------------------------------------------
+
+def test_constants_codata(oracle):
+    # CODATA 2018 exact / recommended values (cgs)
+    assert oracle.const("c") == 2.99792458e10
+    assert oracle.const("k_B") == 1.380649e-16
+    assert oracle.const("h") == 6.62607015e-27
+    assert abs(oracle.const("m_e") / 9.1093837015e-28 - 1) < 1e-15
+    assert abs(oracle.const("sigma_T") / 6.6524587321e-25 - 1) < 1e-15
+    # sigma_SB from its definition 2 pi^5 k^4 / (15 h^3 c^2)
+    sb = 2 * math.pi ** 5 * K_B ** 4 / (15 * H_PL ** 3 * C_LIGHT ** 2)
+    assert abs(oracle.const("sigma_SB") / sb - 1) < 1e-9
+    # sigma_T from its definition (8 pi/3) (e^2/(m_e c^2))^2
+    e = oracle.const("e")
+    st = 8 * math.pi / 3 * (e ** 2 / (M_E * C_LIGHT ** 2)) ** 2
+    assert abs(oracle.const("sigma_T") / st - 1) < 1e-8
+    # gravitational radius of 10 solar masses: 14.77 km
+    rg = oracle.const("G") * 10 * oracle.const("M_sun") / C_LIGHT ** 2
+    assert abs(rg / 1.4767e6 - 1) < 1e-4
+
+
+# ---- P8: scaled Bessel functions ---------------------------------------------
+
+@pytest.mark.parametrize("nu", [0, 1, 2])
+def test_kve_vs_scipy(oracle, nu):
+    for z in np.logspace(-4, 9, 60):
+        ref = sp.kve(nu, z)
+        assert abs(oracle.kve(nu, z) / ref - 1) < 2e-14, (nu, z)
+
+
+@pytest.mark.parametrize("nu", [0, 1, 2])
+def test_kve_large_z_asymptotic(oracle, nu):
+    # DLMF 10.40.2: e^z K_nu(z) ~ sqrt(pi/2z) sum_k a_k(nu)/z^k
+    m = 4 * nu * nu
+    for z in [1e10, 1e11, 1e12]:
+        s = 1 + (m - 1) / (8 * z) + (m - 1) * (m - 9) / (2 * (8 * z) ** 2)
+        ref = math.sqrt(math.pi / (2 * z)) * s
+        assert abs(oracle.kve(nu, z) / ref - 1) < 1e-13
+
+
+def test_kve_mpmath_and_recurrence(oracle):
+    mpmath.mp.dps = 30
+    for z in [1e-3, 0.7, 3.3, 59.3, 1e4]:
+        for nu in (0, 1, 2):
+            ref = float(mpmath.besselk(nu, z) * mpmath.e ** z)
+            assert abs(oracle.kve(nu, z) / ref - 1) < 1e-14
+        # K_2 = K_0 + (2/z) K_1 (DLMF 10.29.1), computed independently here
+        k0, k1, k2 = (oracle.kve(n, z) for n in (0, 1, 2))
+        assert abs((k0 + 2 * k1 / z) / k2 - 1) < 1e-14
+
+
+# ---- P1/P2: bremsstrahlung ---------------------------------------------------
+
+def test_brems_branch_continuity(oracle):
+    """The two branches of each fit meet at theta_e = 1 within the fits'
+    own accuracy: a mistyped coefficient would open a large jump."""
+    lo, hi = ME_C2_K * (1 - 1e-12), ME_C2_K * (1 + 1e-12)
+    jee = oracle.brems_ee(hi) / oracle.brems_ee(lo) - 1
+    jei = oracle.brems_ei(hi) / oracle.brems_ei(lo) - 1
+    assert 0.0 < jee < 0.012
+    assert -0.0003 < jei < 0.0
+    # scaling with n_e^2 is exact: the oracle returns per-n_e^2 rates, and
+    # the ratio ee/ei vanishes as theta^1 in the non-relativistic limit
+    r1 = oracle.brems_ee(1e5) / oracle.brems_ei(1e5)
+    r2 = oracle.brems_ee(1e6) / oracle.brems_ei(1e6)
+    assert abs(r2 / r1 - 10.0) < 0.05
+
+
+def test_brems_nonrelativistic_free_free(oracle):
+    """Classical thermal free-free emission of hydrogen (Rybicki & Lightman
+    Eq. 5.15b): eps = 1.4e-27 sqrt(T) n_e n_i g_B with g_B ~ 1.1-1.5.  The
+    e-i fit must follow sqrt(T) with an implied Gaunt factor in that range."""
+    g = []
+    for T in [1e4, 1e5, 1e6]:
+        g.append(oracle.brems_ei(T) / (1.4e-27 * math.sqrt(T)))
+    assert all(1.1 < x < 1.5 for x in g)
+    assert max(g) / min(g) - 1 < 1e-3
+
+
+# ---- synchrotron ------------------------------------------------------------
+
+def _J_closed(xc):
+    """int_{xc}^inf x I'(x) dx for Mahadevan's I' in s = x^(1/3):
+    3*4.0505 int s^4.5 (1 + 0.4 s^-0.75 + 0.5316 s^-1.5) e^{-a s} ds,
+    a sum of upper incomplete gamma functions."""
+    a = 1.8899
+    s = xc ** (1.0 / 3.0)
+    tot = 0.0
+    for c, p in [(1.0, 5.5), (0.4, 4.75), (0.5316, 4.0)]:
+        tot += c * sp.gammaincc(p, a * s) * sp.gamma(p) / a ** p
+    return 3 * 4.0505 * tot
+
+
+def test_J_quadrature_closed_form(oracle):
+    for xc in [0.0, 1e-6, 1e-2, 1.0, 30.0, 1e3, 1e5]:
+        ref = _J_closed(xc)
+        assert abs(oracle.J(xc) / ref - 1) < 1e-12, xc
+        # panel doubling converges
+        assert abs(oracle.J(xc, 128) / oracle.J(xc, 64) - 1) < 1e-13
+
+
+def test_Iprime_against_quadrature_derivative(oracle):
+    # -d/dx J(x) = x I'(x): check the integrand/quadrature pairing
+    for x in [1e-3, 0.5, 7.0, 300.0]:
+        h = x * 2e-3
+        Jf = lambda y: oracle.J(y, 128)
+        d = -(-Jf(x + 2 * h) + 8 * Jf(x + h) - 8 * Jf(x - h) + Jf(x - 2 * h)) / (12 * h)
+        assert abs(d / (x * oracle.Iprime(x)) - 1) < 1e-7
+
+
+def test_synchrotron_total_power_ultrarelativistic(oracle):
+    """Integrated optically-thin emissivity of ultra-relativistic thermal
+    electrons equals the classical power (4/3) sigma_T c gamma^2 U_B per
+    electron with <gamma^2> = 12 theta^2 (Rybicki & Lightman 6.7b, 6.17):
+    eps_tot = 2 sigma_T c n_e theta^2 B^2 / pi (within the fit's accuracy)."""
+    ne, B = 1e10, 100.0
+    for T in [3e10, 1e11]:
+        th = oracle.theta_e(T)
+        nu0 = oracle.nu0(B, T)
+        f = lambda lx: oracle.eps_syn(nu0 * math.exp(lx), ne, B, T) * nu0 * math.exp(lx)
+        tot = scipy.integrate.quad(f, -30, 12, limit=400, epsabs=0)[0]
+        cls = 2 * SIG_T * C_LIGHT * ne * th ** 2 * B ** 2 / math.pi
+        # <gamma^2 beta^2> = 12 theta^2 (1 + O(1/theta)); Mahadevan fit ~ few %
+        assert 0.9 < tot / cls < 1.15, (T, tot / cls)
+
+
+def test_eps_syn_switch_and_scaling(oracle):
+    # eps_s is linear in n_e; K2 substitution at T <= 1e8 K (2 theta^2)
+    a = oracle.eps_syn(1e12, 1e10, 1e3, 5e9)
+    b = oracle.eps_syn(1e12, 2e10, 1e3, 5e9)
+    assert abs(b / a - 2) < 1e-14
+    th = oracle.theta_e(1e8)
+    assert oracle.k2_factor(1e8) == pytest.approx(2 * th * th, rel=1e-15)
+    z = 1 / oracle.theta_e(1.0001e8)
+    assert oracle.k2_factor(1.0001e8) == pytest.approx(sp.kv(2, z), rel=1e-12)
+
+
+def _nu_c_brentq(H, B, ne, T):
+    """Root of Eq. 5 (2H eps_s = 2 * 2 pi nu^2 k T / c^2) by scipy's brentq,
+    written here from the paper's symbols with scipy's Bessel K2."""
+    th = K_B * T / (M_E * C_LIGHT ** 2)
+    k2 = 2 * th * th if T <= 1e8 else sp.kv(2, 1 / th)
+    nu0 = 3 * 4.80320471e-10 * B * th * th / (4 * math.pi * M_E * C_LIGHT)
+
+    def f(lnnu):
+        nu = math.exp(lnnu)
+        x = nu / nu0
+        lip = (math.log(4.0505) - math.log(x) / 6 + math.log(1 + 0.4 * x ** -0.25 + 0.5316 * x ** -0.5)
+               - 1.8899 * x ** (1 / 3))
+        leps = math.log(4.43e-30 * 4 * math.pi * nu * ne / k2) + lip
+        return math.log(H) + leps - math.log(2 * math.pi * nu * nu * K_B * T / C_LIGHT ** 2)
+
+    if f(0.0) <= 0:
+        return 1.0
+    return math.exp(scipy.optimize.brentq(f, 0.0, math.log(1e30), xtol=1e-15, rtol=1e-15))
+
+
+@pytest.mark.parametrize("pt", [(1e8, 1e3, 1e15, 1e9), (1e6, 1e5, 1e18, 3e10),
+                                (1e11, 10.0, 1e12, 2e8), (1e4, 1e8, 1e20, 1e11),
+                                (1e9, 1e2, 1e10, 5e7)])
+def test_nu_c_root(oracle, pt):
+    H, B, ne, T = pt
+    nuc, flag = oracle.nu_c(H, B, ne, T)
+    assert flag == 0
+    assert abs(nuc / _nu_c_brentq(H, B, ne, T) - 1) < 1e-12
+    if nuc > 1.0:
+        lhs = H * oracle.eps_syn(nuc, ne, B, T)
+        rhs = 2 * math.pi * nuc ** 2 * K_B * T / C_LIGHT ** 2
+        assert abs(lhs / rhs - 1) < 1e-11
+
+
+def test_qsyn_thin_limit_small_H(oracle):
+    """H -> 0: nu_c -> 0 (nu_c ~ H^(6/7) since eps_s ~ nu^(1/3) there), the
+    Rayleigh-Jeans part vanishes and Q_syn -> the whole thin integral,
+    computed here by tanh-sinh quadrature (mpmath) of Eq. 3."""
+    B, ne, T = 1e3, 1e12, 1e10
+    mpmath.mp.dps = 20
+    th = oracle.theta_e(T)
+    nu0 = oracle.nu0(B, T)
+    pref = 4.43e-30 * 4 * math.pi * ne / float(mpmath.besselk(2, 1 / th))
+    ip = lambda x: 4.0505 * x ** (-mpmath.mpf(1) / 6) * (1 + 0.4 * x ** -0.25 + 0.5316 * x ** -0.5) * mpmath.e ** (-1.8899 * mpmath.cbrt(x))
+    full = pref * nu0 ** 2 * float(mpmath.quad(lambda x: x * ip(x), [0, 1, 100, 1e4, mpmath.inf]))
+    prev = None
+    for H in [1e-6, 1e-9, 1e-12]:
+        nuc, _ = oracle.nu_c(H, B, ne, T)
+        q = oracle.qsyn_nu(H, B, ne, T, nuc)
+        if prev is not None:
+            assert nuc < prev
+        prev = nuc
+    assert abs(q / full - 1) < 1e-6
+
+
+# ---- P5: Compton enhancement --------------------------------------------------
+
+def _eta_series(P, A, k):
+    """Brute force: photon energy multiplied by A per scattering (prob. P),
+    capped after k scatterings: 1 + sum_{j=1}^k P^j (A^j - A^(j-1))."""
+    return 1 + sum(P ** j * (A ** j - A ** (j - 1)) for j in range(1, k + 1))
+
+
+def test_eta_matches_series(oracle):
+    for T, ne, H, k in [(5e9, 1e17, 1e7, 5), (2e10, 1e18, 1e7, 3), (1e9, 1e16, 1e6, 12)]:
+        th = oracle.theta_e(T)
+        A = 1 + 4 * th + 16 * th * th
+        E = 3 * th / A ** k                      # exactly k scatterings to reach 3 theta
+        nuc = E * M_E * C_LIGHT ** 2 / H_PL
+        tau = 2 * ne * SIG_T * H
+        P = -math.expm1(-tau)
+        assert abs(oracle.eta(nuc, T, ne, H) / _eta_series(P, A, k) - 1) < 1e-10
+
+
+def test_eta_limits_and_bounds(oracle):
+    T, nuc = 1e10, 1e11
+    th = oracle.theta_e(T)
+    E = H_PL * nuc / (M_E * C_LIGHT ** 2)
+    assert abs(oracle.eta(nuc, T, 1.0, 1e-10) - 1) < 1e-12        # tau -> 0
+    for ne in np.logspace(12, 22, 21):
+        e = oracle.eta(nuc, T, ne, 1e7)
+        assert 1.0 <= e <= 3 * th / E * (1 + 1e-12)
+    assert oracle.eta(1e30, T, 1e18, 1e7) == 1.0                   # E >= 3 theta
+
+
+def test_eta_continuous_through_PA_equal_1(oracle):
+    T = 3e9
+    th = oracle.theta_e(T)
+    A = 1 + 4 * th + 16 * th * th
+    H = 1e7
+    P = 1 / A
+    tau = -math.log1p(-P)
+    ne0 = tau / (2 * SIG_T * H)
+    vals = [oracle.eta(1e10, T, ne0 * (1 + d), H) for d in (-1e-9, 0.0, 1e-9)]
+    assert abs(vals[0] / vals[2] - 1) < 1e-7
+    assert abs(vals[1] / vals[2] - 1) < 1e-7
+
+
+def test_eta_printed_exponent_fails(oracle):
+    """The exponent as printed (1 - ln P/ln A) gives eta < 0 where P A > 1;
+    the series exponent (-1 - ln P/ln A) stays >= 1."""
+    th = 0.5
+    T = th * ME_C2_K
+    H = 1e7
+    ne = 2.0 / (2 * SIG_T * H)                  # tau_sca = 2
+    E = 3 * th * 1e-4
+    nuc = E * M_E * C_LIGHT ** 2 / H_PL
+    assert oracle.eta(nuc, T, ne, H, literal=1) < 0.0
+    assert oracle.eta(nuc, T, ne, H, literal=0) > 1.0
+
+
+# ---- P6: bridge ------------------------------------------------------------------
+
+def test_bridge_limits(oracle):
+    T, H = 1e7, 1e8
+    bb = 4 * SIG_SB * T ** 4
+    # thin: tau_abs, tau_sca -> 0  =>  Q_total -> Q_thin
+    q = 1e-12 * bb / H
+    assert abs(oracle.bridge(q, T, H, 1.0) / q - 1) < 1e-10
+    # thick: Q_total * 3 H tau / (8 sigma T^4) -> 1
+    for qthin, ne in [(1e12 * bb / H, 1.0), (1e3 * bb / H, 1e22)]:
+        tau = H * qthin / bb + 2 * ne * SIG_T * H
+        val = oracle.bridge(qthin, T, H, ne) * 3 * H * tau / (2 * bb)
+        assert abs(val - 1) < 2e-3
+
+
+# ---- P7: Coulomb exchange -----------------------------------------------------
+
+def test_coulomb_spitzer_limit(oracle):
+    """theta_e, theta_i << 1: C -> (3/2)(m_e/m_p) lnL c sigma_T k sqrt(2/pi)
+    (theta_e + theta_i)^(-3/2) (large-argument Bessel asymptotics)."""
+    lnL = 20.0
+    for Te, Ti, tol in [(1e4, 1e5, 1e-6), (1e6, 1e7, 1e-4), (1e7, 1e8, 1e-3)]:
+        the = K_B * Te / (M_E * C_LIGHT ** 2)
+        thi = K_B * Ti / (M_P * C_LIGHT ** 2)
+        lim = 1.5 * (M_E / M_P) * lnL * C_LIGHT * SIG_T * K_B * math.sqrt(2 / math.pi) * (the + thi) ** -1.5
+        assert abs(oracle.coulomb_C(Ti, Te) / lim - 1) < tol
+
+
+def test_coulomb_vs_nrl_equilibration(oracle):
+    """NRL Plasma Formulary electron-ion temperature equilibration,
+    nu = 1.8e-19 sqrt(m_e m_i) n_i lnL / (m_e T_i + m_i T_e)^(3/2) (cgs
+    masses, T in eV), dT_e/dt = nu (T_i - T_e), Q = (3/2) n_e k dT_e/dt."""
+    ne = 1e15
+    for Te, Ti in [(1e5, 1e6), (1e6, 1e5), (3e6, 3e7)]:
+        ev = 8.617333262e-5
+        nu = 1.8e-19 * math.sqrt(M_E * M_P) * ne * 20.0 / (M_E * Ti * ev + M_P * Te * ev) ** 1.5
+        q_nrl = 1.5 * ne * K_B * nu * (Ti - Te)
+        q = oracle.coulomb_C(Ti, Te) * ne * ne * (Ti - Te)
+        assert abs(q / q_nrl - 1) < 0.03
+
+
+def test_coulomb_finite_and_smooth_over_range(oracle):
+    Ts = np.logspace(2, 15, 40)
+    v = np.array([[math.log2(oracle.coulomb_C(a, b)) for b in Ts] for a in Ts])
+    assert np.all(np.isfinite(v))
+    # smooth: second differences in log space bounded
+    assert np.max(np.abs(np.diff(v, 2, axis=0))) < 5
+    assert np.max(np.abs(np.diff(v, 2, axis=1))) < 5
+
+
+def test_coulomb_printed_theta_i_reading(oracle):
+    """With theta_i = kT_i/(m_e c^2) (as printed) the ion term carries the
+    electron mass: the rate no longer has the Spitzer form in T_i/m_i."""
+    s = oracle.Spec(theta_i_uses_mp=0)
+    a = oracle.coulomb_C(1e8, 1e6, s)
+    b = oracle.coulomb_C(1e8, 1e6)
+    assert a < 0.01 * b
