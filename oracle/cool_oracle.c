@@ -309,14 +309,16 @@ double orc_eta_qsyn(double H, double B, double ne, double T, const orc_spec* s, 
 
 /* Optically-thick bridge, Eqs. 11-12 (sigma read as Stefan-Boltzmann):
  * Q_total = (4 sigma T^4/H) / (3 tau/2 + sqrt 3 + 1/tau_abs),
- * tau_abs = H Q_thin/(4 sigma T^4), tau = tau_abs + tau_sca.  Pinned by the
- * thin and thick limits. */
+ * tau_abs = H Q_thin/(4 sigma T^4), tau = tau_abs + tau_sca, written with
+ * numerator and denominator multiplied by tau_abs,
+ * Q_total = Q_thin / (1 + tau_abs (sqrt 3 + 1.5 (tau_abs + tau_sca))),
+ * which is the same function and keeps its tau_abs -> 0 limit (Q_thin) at
+ * H = 0 or Q_thin = 0.  Pinned by the thin and thick limits. */
 double orc_bridge(double qthin, double T, double H, double ne) {
     double bb = 4.0 * O_SIGSB * T * T * T * T;
     double tau_sca = 2.0 * ne * O_SIGT * H;
     double tau_abs = H * qthin / bb;
-    if (!(tau_abs > 0.0)) return 0.0;
-    return (bb / H) / (1.5 * (tau_abs + tau_sca) + sqrt(3.0) + 1.0 / tau_abs);
+    return qthin / (1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca)));
 }
 
 /* Direct (O1) total cooling rate at one point, erg cm^-3 s^-1. */
