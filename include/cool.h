@@ -1,0 +1,199 @@
+/*
+ * cool.h -- C ABI of libcool, a B300-native (sm_103a) implementation of the
+ * per-cell two-temperature radiative cooling source step of Motta et al.,
+ * "Black hole spectral states revealed in GRMHD simulations with texture
+ * memory accelerated cooling" (arXiv 2505.08855).
+ *
+ * What the library computes (paper sections / equations):
+ *   - a log-space rate table (Sec. 2.6; Coulomb table Sec. 2.8) built on the
+ *     GPU in FP64 from the cooling formulas of Sec. 2: bremsstrahlung
+ *     (Eqs. 1-2), self-absorbed thermal synchrotron (Eqs. 3-6) with the
+ *     low-temperature K2 substitution, the local Compton enhancement
+ *     (Eqs. 7-9), thin cooling (Eq. 10), and the Coulomb exchange (Eq. 16);
+ *   - the per-cell step: multilinear interpolation of the table, the
+ *     optically-thick bridge (Eqs. 11-12, applied per sub-cycle), the
+ *     Coulomb exchange, and the sub-cycled update of the electron and ion
+ *     internal energies, explicit with the 30 % limiter or implicit in stiff
+ *     cells (Sec. 3.2.1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named "device" are CUDA device (or managed) pointers; pointers
+ *     named "host" are host memory.  The caller owns every field array; the
+ *     library owns cool_table objects (freed by cool_table_free).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Entry points that launch work are asynchronous on `stream`
+ *     unless stated otherwise; they return after enqueueing.
+ *   - Errors are returned as cool_status, never as exceptions, traps or
+ *     device asserts.  Invalid arguments are detected on the host before any
+ *     launch; nothing is written to outputs in that case.  A CUDA error is
+ *     reported as COOL_ECUDA; cool_last_cuda_error() gives its code.
+ *   - Field units are the paper's code units (G = c = M = 1, the 4 pi factor
+ *     absorbed in b, Sec. 3.2): rho (rest-mass density; rho = 1 maps to
+ *     rho_scale g/cm^3), B = |b|, H (thermal scale height in r_g), u_e, u_i
+ *     (internal energy densities).  Hydrogen composition (n_e = n_i).
+ */
+#ifndef COOL_H
+#define COOL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    COOL_OK = 0,
+    COOL_EINVAL = 1,        /* an argument is out of its documented range */
+    COOL_ENULL = 2,         /* a required pointer is NULL */
+    COOL_EALIGN = 3,        /* a field pointer is not 16-byte aligned (vector path) */
+    COOL_ECUDA = 4,         /* a CUDA runtime call failed (see cool_last_cuda_error) */
+    COOL_ENOMEM = 5,        /* device or host allocation failed */
+    COOL_ESTATE = 6,        /* the object is in the wrong state (e.g. freed table) */
+    COOL_EUNSUPPORTED = 7,  /* the combination of options is not implemented */
+    COOL_EIO = 8            /* file could not be read/written or is malformed */
+} cool_status;
+
+typedef enum { COOL_F32 = 0, COOL_BF16 = 1, COOL_F16 = 2, COOL_F64 = 3 } cool_dtype;
+
+/* Energy update of Sec. 3.2.1: (i) explicit with the limiter, (ii) implicit. */
+typedef enum { COOL_EXPLICIT_LIMITED = 0, COOL_IMPLICIT_STIFF = 1 } cool_mode;
+
+/* How the 4-D synchrotron channel is read.  L2WINDOW: global memory kept
+ * L2-resident by a persisting access-policy window. */
+typedef enum {
+    COOL_PATH_L2WINDOW = 0,
+    COOL_PATH_TMA_SMEM = 1,
+    COOL_PATH_TEXTURE_POINT = 2,
+    COOL_PATH_TEXTURE_HWLERP = 3,
+    COOL_PATH_SURROGATE = 4
+} cool_path;
+
+/* Table specification.  Axis nodes are log-spaced with inclusive endpoints
+ * (Sec. 2.6): l_j = log2(min) + j (log2(max) - log2(min))/(n - 1), x_j = 2^l_j.
+ * Channels: log2(Q_brem/n_e^2)(T_e) [n_Te], log2(eta Q_syn)(H, B, n_e, T_e)
+ * [n_H x n_B x n_ne x n_Te, T_e fastest], log2 C(T_i, T_e) with
+ * Q_cc = n_e^2 (T_i - T_e) C [n_Tc x n_Tc, T_e fastest].  Ranges in cgs.
+ * Limits: 2 <= n <= 512 per axis, n_Tc <= 128; 0 < min < max. */
+typedef struct {
+    int n_H, n_B, n_ne, n_Te, n_Tc;
+    double H_min, H_max;      /* cm   (paper: 1e3 .. 1e12) */
+    double B_min, B_max;      /* G    (paper: 1 .. 1e10)   */
+    double ne_min, ne_max;    /* cm^-3 (paper: 1e2 .. 1e25) */
+    double T_min, T_max;      /* K    (paper: 1e2 .. 1e15), T_e and Coulomb axes */
+    cool_dtype dtype;         /* storage of the 4-D channel: COOL_F32 (others: not yet) */
+    int row_scaled;           /* reserved for reduced-precision storage; must be 0 for F32 */
+    double k2_switch_T;       /* K2(1/theta) -> 2 theta^2 at T_e <= this (paper: 1e8 K) */
+    double lnLambda;          /* Coulomb logarithm (default 20) */
+    int theta_i_uses_mp;      /* 1: theta_i = kT_i/(m_p c^2) (default); 0: m_e as printed */
+    int compton_literal;      /* 1: Compton exponent 1 - lnP/lnA as printed; 0: -1 - lnP/lnA */
+} cool_table_spec;
+
+/* Step parameters. */
+typedef struct {
+    double rho_scale;         /* g/cm^3 of rho = 1 (paper: 3e-7 .. 1e-9) */
+    double M_bh_msun;         /* black-hole mass in solar masses (paper: 10) */
+    double gamma_e, gamma_i;  /* adiabatic indices (paper: 5/3) */
+    double dt;                /* step in code time units (r_g/c) */
+    int n_sub;                /* sub-cycles per step, 1 .. 64 */
+    cool_mode mode;
+    double limiter_frac;      /* explicit cap on the electron energy removed per sub-cycle (0.3) */
+    double eq_band;           /* equilibrium band |T_e - T_i| <= eq_band T_i (0.1), where T_i - T_e cancels */
+    double coulomb_clamp;     /* the exchange may move at most this fraction of the way to T_e = T_i (1) */
+    int implicit_iters;       /* bisection halvings of the implicit solve, 1 .. 200 (60) */
+    cool_path path;           /* COOL_PATH_L2WINDOW (others: not yet) */
+    int band_fp64;            /* FP32 fields: 0 (default) forms (gamma_i-1) u_i - (gamma_e-1) u_e
+                                 with an error-free FP32 product transformation in every cell;
+                                 1 evaluates the exchange in FP64 inside the equilibrium band */
+} cool_params;
+
+/* Per-call diagnostics, accumulated (atomically) into a caller-owned device
+ * struct when a pointer is given; counts are cells (not sub-cycles). */
+typedef struct {
+    unsigned long long n_clamped;        /* a table key outside the table range (edge value used) */
+    unsigned long long n_nonfinite;      /* invalid cell (non-finite or non-positive rho/u, negative B/H): passed through */
+    unsigned long long n_stiff;          /* implicit solve entered (mode IMPLICIT) */
+    unsigned long long n_fp64_coulomb;   /* Coulomb exchange inside the equilibrium band in some sub-cycle
+                                            (FP64 there when band_fp64 = 1; FP64 fields: always FP64) */
+    unsigned long long n_implicit_fail;  /* implicit bracket without sign change: limited explicit step taken */
+    unsigned long long n_fallback;       /* reserved (surrogate fallback) */
+} cool_counters;
+
+typedef struct cool_table cool_table;    /* opaque; owns device memory */
+
+/* Human-readable name of a status. */
+const char* cool_strerror(cool_status s);
+
+/* The cudaError_t of the last COOL_ECUDA returned on this thread (0 if none). */
+int cool_last_cuda_error(void);
+
+/* Fill *spec with the paper's ranges (Sec. 2.6, 2.8), 64 points per axis,
+ * FP32 storage, k2_switch_T = 1e8 K, lnLambda = 20, theta_i with m_p. */
+cool_status cool_table_spec_default(cool_table_spec* spec);
+
+/* Fill *p with rho_scale 3e-7, M = 10 Msun, gamma 5/3, dt 1e-2, n_sub 8,
+ * explicit mode, limiter 0.3, eq_band 0.1, clamp 1, 60 iterations, L2 path. */
+cool_status cool_params_default(cool_params* p);
+
+/* Build the table on the device in FP64 (Sec. 2.6: every node evaluates the
+ * formulas of Sec. 2, including the nu_c root of Eq. 5 and the integral of
+ * Eq. 6), then pack it for the step.  Synchronous: returns when the table is
+ * ready (the build takes seconds for 64^4 nodes).  `stream` orders the work.
+ * On success *out owns device memory until cool_table_free. */
+cool_status cool_build_table(const cool_table_spec* spec, void* stream, cool_table** out);
+
+/* Release a table (NULL is a no-op). */
+cool_status cool_table_free(cool_table* t);
+
+/* The spec a table was built with. */
+cool_status cool_table_get_spec(const cool_table* t, cool_table_spec* spec);
+
+/* Copy the FP64 log2 values of one channel to host memory.
+ * channel 0: brems [n_Te]; 1: synchrotron [n_H*n_B*n_ne*n_Te]; 2: Coulomb
+ * [n_Tc*n_Tc].  host_out must hold that many doubles.  Synchronous. */
+cool_status cool_table_export(const cool_table* t, int channel, double* host_out, long long count);
+
+/* FP32 node coordinates of one axis (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T)
+ * to host memory (host_out holds n floats).  Synchronous. */
+cool_status cool_table_nodes(const cool_table* t, int axis, float* host_out, int n);
+
+/* Save / load a table (spec + FP64 channel values, binary, with a spec hash).
+ * load rebuilds the packed device table from the stored values without
+ * re-evaluating the formulas.  Synchronous. */
+cool_status cool_table_save(const cool_table* t, const char* path);
+cool_status cool_table_load(const char* path, void* stream, cool_table** out);
+
+/* One cooling step over n_cells cells (Sec. 3.2): per cell, N_sub sub-cycles
+ * of (i) Coulomb exchange (Eq. 16; FP64 inside the equilibrium band) and
+ * (ii) radiative cooling from the table with the bridge of Eq. 11, applied
+ * to u_e explicitly (min(h Q, limiter_frac u_e)) or, in mode IMPLICIT for
+ * stiff cells (h Q > limiter_frac u_e), by backward Euler.
+ *   field_dtype: COOL_F32 or COOL_F64 (all seven field arrays of that type).
+ *   rho, B, H, u_e_in, u_i_in: device inputs, n_cells each.
+ *   u_e_out, u_i_out: device outputs (may alias u_e_in / u_i_in).
+ *   q_cool_out (nullable): electron energy removed by cooling during the step.
+ *   q_cc_out (nullable): energy moved from ions to electrons by Coulomb.
+ *     (u_e_out = u_e_in + q_cc - q_cool, u_i_out = u_i_in - q_cc.)
+ *   counters (nullable, device): accumulated with atomics.
+ * Invalid cells are copied through unchanged.  Out-of-range keys use the
+ * table edge.  n_cells = 0 is a no-op.  Non-NULL pointers are required for
+ * every non-nullable array when n_cells > 0.  For COOL_F32, arrays that are
+ * 16-byte aligned use 128-bit loads; unaligned arrays take a scalar path. */
+cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cells,
+                      cool_dtype field_dtype,
+                      const void* rho, const void* B, const void* H,
+                      const void* u_e_in, const void* u_i_in,
+                      void* u_e_out, void* u_i_out,
+                      void* q_cool_out, void* q_cc_out,
+                      cool_counters* counters, void* stream);
+
+/* Index/weight selection of the table interpolation on one axis, for FP32
+ * keys in the axis' physical unit (device arrays of n): idx = the largest j
+ * in [0, N-2] with node32[j] <= key (0 below the first node), w = log2(key /
+ * x_j) / dl clamped to [0, 1].  The same rule the step uses. */
+cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
+                              int* idx, float* w, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COOL_H */

@@ -1,0 +1,204 @@
+"""B300-native two-temperature cooling step (arXiv 2505.08855).
+
+Python front end of libcool (include/cool.h):
+
+    import paper_2505_08855_b300 as cool
+    tab = cool.Table(cool.TableSpec(n=(64, 64, 64, 64, 64)))     # built on the GPU in FP64
+    ue, ui = cool.step(tab, cool.Params(n_sub=8), rho, B, H, ue, ui)
+
+Fields are CUDA torch tensors (float32 or float64, contiguous).  Every
+computation runs in the library's CUDA kernels on the tensors' device and
+the current torch stream; this module only marshals arguments.
+"""
+import ctypes as C
+import dataclasses
+
+from . import binding as _b
+
+F32, BF16, F16, F64 = _b.COOL_F32, _b.COOL_BF16, _b.COOL_F16, _b.COOL_F64
+EXPLICIT, IMPLICIT = _b.COOL_EXPLICIT_LIMITED, _b.COOL_IMPLICIT_STIFF
+CoolError = _b.CoolError
+
+# Axis order of the table: 0 H [cm], 1 |B| [G], 2 n_e [cm^-3], 3 T_e [K],
+# 4 Coulomb T [K].  Ranges: the paper's Sec. 2.6 and 2.8.
+PAPER_LO = (1e3, 1.0, 1e2, 1e2, 1e2)
+PAPER_HI = (1e12, 1e10, 1e25, 1e15, 1e15)
+
+
+@dataclasses.dataclass
+class TableSpec:
+    n: tuple = (64, 64, 64, 64, 64)
+    lo: tuple = PAPER_LO
+    hi: tuple = PAPER_HI
+    dtype: int = F32
+    row_scaled: int = 0
+    k2_switch_T: float = 1e8
+    lnLambda: float = 20.0
+    theta_i_uses_mp: int = 1
+    compton_literal: int = 0
+
+    def c(self):
+        if tuple(self.lo[3:4]) != tuple(self.lo[4:5]) or tuple(self.hi[3:4]) != tuple(self.hi[4:5]):
+            raise ValueError("the T_e and Coulomb T axes share one range")
+        return _b.cool_table_spec(*self.n, self.lo[0], self.hi[0], self.lo[1], self.hi[1],
+                                  self.lo[2], self.hi[2], self.lo[3], self.hi[3], self.dtype,
+                                  self.row_scaled, self.k2_switch_T, self.lnLambda,
+                                  self.theta_i_uses_mp, self.compton_literal)
+
+
+@dataclasses.dataclass
+class Params:
+    rho_scale: float = 3e-7
+    M_bh_msun: float = 10.0
+    gamma_e: float = 5.0 / 3.0
+    gamma_i: float = 5.0 / 3.0
+    dt: float = 1e-2
+    n_sub: int = 8
+    mode: int = EXPLICIT
+    limiter_frac: float = 0.3
+    eq_band: float = 0.1
+    coulomb_clamp: float = 1.0
+    implicit_iters: int = 60
+    path: int = _b.COOL_PATH_L2WINDOW
+    band_fp64: int = 0
+
+    def c(self):
+        return _b.cool_params(self.rho_scale, self.M_bh_msun, self.gamma_e, self.gamma_i,
+                              self.dt, self.n_sub, self.mode, self.limiter_frac, self.eq_band,
+                              self.coulomb_clamp, self.implicit_iters, self.path, self.band_fp64)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Table:
+    """A cooling/Coulomb rate table on the current CUDA device."""
+
+    def __init__(self, spec=None, _handle=None):
+        self.spec = spec if spec is not None else TableSpec()
+        if _handle is not None:
+            self._h = _handle
+            return
+        L = _b.lib()
+        h = C.c_void_p()
+        cs = self.spec.c()
+        _b.check(L.cool_build_table(_b.ref(cs), _stream_ptr(), _b.ref(h)), "cool_build_table")
+        self._h = h
+
+    @classmethod
+    def load(cls, path):
+        L = _b.lib()
+        h = C.c_void_p()
+        _b.check(L.cool_table_load(path.encode(), _stream_ptr(), _b.ref(h)), "cool_table_load")
+        s = _b.cool_table_spec()
+        _b.check(L.cool_table_get_spec(h, _b.ref(s)), "cool_table_get_spec")
+        spec = TableSpec(n=(s.n_H, s.n_B, s.n_ne, s.n_Te, s.n_Tc),
+                         lo=(s.H_min, s.B_min, s.ne_min, s.T_min, s.T_min),
+                         hi=(s.H_max, s.B_max, s.ne_max, s.T_max, s.T_max), dtype=s.dtype,
+                         row_scaled=s.row_scaled, k2_switch_T=s.k2_switch_T, lnLambda=s.lnLambda,
+                         theta_i_uses_mp=s.theta_i_uses_mp, compton_literal=s.compton_literal)
+        return cls(spec, _handle=h)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise _b.CoolError(_b.COOL_ESTATE, "table already freed")
+        return self._h
+
+    def save(self, path):
+        _b.check(_b.lib().cool_table_save(self.handle, path.encode()), "cool_table_save")
+
+    def export(self, channel):
+        """FP64 log2 values of channel 0 (brems), 1 (synchrotron) or 2 (Coulomb) as numpy."""
+        import numpy as np
+        n = self.spec.n
+        count = {0: n[3], 1: n[0] * n[1] * n[2] * n[3], 2: n[4] * n[4]}[channel]
+        out = np.zeros(count, np.float64)
+        _b.check(_b.lib().cool_table_export(self.handle, channel, out.ctypes.data_as(C.c_void_p),
+                                            count), "cool_table_export")
+        return out
+
+    def nodes(self, axis):
+        import numpy as np
+        out = np.zeros(self.spec.n[axis], np.float32)
+        _b.check(_b.lib().cool_table_nodes(self.handle, axis, out.ctypes.data_as(C.c_void_p),
+                                           out.size), "cool_table_nodes")
+        return out
+
+    def free(self):
+        if self._h is not None:
+            _b.check(_b.lib().cool_table_free(self._h), "cool_table_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None and _b._LIB is not None:
+                _b._LIB.cool_table_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"fields must be float32 or float64, got {t.dtype}")
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def new_counters(device=None):
+    """A zeroed device counter block (int64 x 6) for step(..., counters=)."""
+    import torch
+    return torch.zeros(6, dtype=torch.int64, device=device or "cuda")
+
+
+COUNTER_NAMES = ("clamped", "nonfinite", "stiff", "fp64_coulomb", "implicit_fail", "fallback")
+
+
+def counters_dict(c):
+    return dict(zip(COUNTER_NAMES, c.tolist()))
+
+
+def step(table, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None, q_cc=None,
+         counters=None, stream=None):
+    """One cooling step (cool_step).  Returns (ue_out, ui_out); outputs are
+    allocated when not given (pass ue_out=ue for in place).  q_cool / q_cc:
+    optional output tensors of the cooled / Coulomb-exchanged energy."""
+    import torch
+    fields = (rho, B, H, ue, ui)
+    code = _dtype_code(rho)
+    n = rho.numel()
+    for f in fields:
+        if f.dtype != rho.dtype or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("fields must be contiguous CUDA tensors of one dtype and size")
+    if ue_out is None:
+        ue_out = torch.empty_like(ue)
+    if ui_out is None:
+        ui_out = torch.empty_like(ui)
+    p = params.c()
+    cptr = C.c_void_p(counters.data_ptr()) if counters is not None else C.c_void_p(0)
+    st = _b.lib().cool_step(table.handle, _b.ref(p), n, code, *[_ptr(f) for f in fields],
+                            _ptr(ue_out), _ptr(ui_out), _ptr(q_cool), _ptr(q_cc), cptr,
+                            _stream_ptr(stream))
+    _b.check(st, "cool_step")
+    return ue_out, ui_out
+
+
+def debug_lookup(table, axis, keys, stream=None):
+    """(idx int32, w float32) of the interpolation rule for FP32 keys."""
+    import torch
+    keys = keys.contiguous()
+    idx = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    w = torch.empty(keys.numel(), dtype=torch.float32, device=keys.device)
+    _b.check(_b.lib().cool_debug_lookup(table.handle, axis, keys.numel(), _ptr(keys), _ptr(idx),
+                                        _ptr(w), _stream_ptr(stream)), "cool_debug_lookup")
+    return idx, w

@@ -1,0 +1,110 @@
+"""ctypes binding of libcool (include/cool.h), same entry-point names.
+
+Argument marshalling only: every computation runs in the CUDA library.
+Torch is used for device memory and the current stream.  If libcool.so is
+missing or fails to load, every call raises: there is no CPU fallback.
+"""
+import ctypes as C
+import dataclasses
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcool.so")
+
+COOL_OK, COOL_EINVAL, COOL_ENULL, COOL_EALIGN, COOL_ECUDA, COOL_ENOMEM, COOL_ESTATE, \
+    COOL_EUNSUPPORTED, COOL_EIO = range(9)
+COOL_F32, COOL_BF16, COOL_F16, COOL_F64 = range(4)
+COOL_EXPLICIT_LIMITED, COOL_IMPLICIT_STIFF = 0, 1
+COOL_PATH_L2WINDOW, COOL_PATH_TMA_SMEM, COOL_PATH_TEXTURE_POINT, COOL_PATH_TEXTURE_HWLERP, \
+    COOL_PATH_SURROGATE = range(5)
+
+# Every entry point declared in include/cool.h (checked by the CPU tests).
+EXPORTS = (
+    "cool_strerror", "cool_last_cuda_error", "cool_table_spec_default", "cool_params_default",
+    "cool_build_table", "cool_table_free", "cool_table_get_spec", "cool_table_export",
+    "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
+)
+
+
+class cool_table_spec(C.Structure):
+    _fields_ = [("n_H", C.c_int), ("n_B", C.c_int), ("n_ne", C.c_int), ("n_Te", C.c_int),
+                ("n_Tc", C.c_int),
+                ("H_min", C.c_double), ("H_max", C.c_double), ("B_min", C.c_double),
+                ("B_max", C.c_double), ("ne_min", C.c_double), ("ne_max", C.c_double),
+                ("T_min", C.c_double), ("T_max", C.c_double),
+                ("dtype", C.c_int), ("row_scaled", C.c_int), ("k2_switch_T", C.c_double),
+                ("lnLambda", C.c_double), ("theta_i_uses_mp", C.c_int),
+                ("compton_literal", C.c_int)]
+
+
+class cool_params(C.Structure):
+    _fields_ = [("rho_scale", C.c_double), ("M_bh_msun", C.c_double), ("gamma_e", C.c_double),
+                ("gamma_i", C.c_double), ("dt", C.c_double), ("n_sub", C.c_int), ("mode", C.c_int),
+                ("limiter_frac", C.c_double), ("eq_band", C.c_double),
+                ("coulomb_clamp", C.c_double), ("implicit_iters", C.c_int), ("path", C.c_int),
+                ("band_fp64", C.c_int)]
+
+
+class cool_counters(C.Structure):
+    _fields_ = [(n, C.c_ulonglong) for n in ("n_clamped", "n_nonfinite", "n_stiff",
+                                              "n_fp64_coulomb", "n_implicit_fail", "n_fallback")]
+
+
+class CoolError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib_or_none_strerror(status)
+        extra = ""
+        if status == COOL_ECUDA and _LIB is not None:
+            extra = f" (cudaError {_LIB.cool_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}{extra}")
+        self.status = status
+
+
+_LIB = None
+
+
+def _lib_or_none_strerror(status):
+    if _LIB is None:
+        return f"status {status}"
+    return _LIB.cool_strerror(status).decode()
+
+
+def lib():
+    """Load libcool.so (raises if it is missing: no fallback path exists)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcool.so not built at {LIB_PATH}; run "
+                               "`python -m paper_2505_08855_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, I, LL, D = C.c_void_p, C.c_int, C.c_longlong, C.c_double
+        sig = {
+            "cool_strerror": (C.c_char_p, [I]),
+            "cool_last_cuda_error": (I, []),
+            "cool_table_spec_default": (I, [P]),
+            "cool_params_default": (I, [P]),
+            "cool_build_table": (I, [P, P, P]),
+            "cool_table_free": (I, [P]),
+            "cool_table_get_spec": (I, [P, P]),
+            "cool_table_export": (I, [P, I, P, LL]),
+            "cool_table_nodes": (I, [P, I, P, I]),
+            "cool_table_save": (I, [P, C.c_char_p]),
+            "cool_table_load": (I, [C.c_char_p, P, P]),
+            "cool_step": (I, [P, P, LL, I, P, P, P, P, P, P, P, P, P, P, P]),
+            "cool_debug_lookup": (I, [P, I, LL, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(status, where):
+    if status != COOL_OK:
+        raise CoolError(status, where)
+
+
+def ref(x):
+    return C.cast(C.pointer(x), C.c_void_p)

@@ -1,0 +1,474 @@
+// cool_api.cu -- host side of the libcool C ABI (include/cool.h): argument
+// validation, table construction/packing/persistence, and kernel dispatch.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <unordered_set>
+
+#include "cool_internal.cuh"
+
+namespace cool {
+
+static thread_local int g_last_cuda_error = 0;
+
+cool_status set_cuda_error(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    return COOL_ECUDA;
+}
+
+// Live tables: a handle is valid only while registered, so a freed (or
+// never created) handle is rejected without reading its memory.
+static std::mutex g_tables_mu;
+static std::unordered_set<const cool_table*>& live_tables() {
+    static std::unordered_set<const cool_table*> s;
+    return s;
+}
+static void register_table(const cool_table* t) {
+    std::lock_guard<std::mutex> g(g_tables_mu);
+    live_tables().insert(t);
+}
+static bool unregister_table(const cool_table* t) {
+    std::lock_guard<std::mutex> g(g_tables_mu);
+    return live_tables().erase(t) == 1;
+}
+
+bool table_ok(const cool_table* t) {
+    if (t == nullptr) return false;
+    std::lock_guard<std::mutex> g(g_tables_mu);
+    return live_tables().count(t) == 1 && t->magic == kTableMagic;
+}
+
+long long syn_count(const cool_table_spec& s) {
+    return (long long)s.n_H * s.n_B * s.n_ne * s.n_Te;
+}
+
+namespace {
+
+__global__ void k_pack_f32(const double* src, float* dst, long long n) {
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = (float)src[i];
+}
+
+cool_status validate_spec(const cool_table_spec* s) {
+    if (!s) return COOL_ENULL;
+    int n[5] = {s->n_H, s->n_B, s->n_ne, s->n_Te, s->n_Tc};
+    for (int a = 0; a < 5; ++a)
+        if (n[a] < 2 || n[a] > kMaxAxis) return COOL_EINVAL;
+    if (s->n_Tc > kMaxTc) return COOL_EINVAL;
+    double lo[4] = {s->H_min, s->B_min, s->ne_min, s->T_min};
+    double hi[4] = {s->H_max, s->B_max, s->ne_max, s->T_max};
+    for (int a = 0; a < 4; ++a)
+        if (!(lo[a] > 0.0) || !(hi[a] > lo[a]) || !isfinite(hi[a])) return COOL_EINVAL;
+    if (s->dtype != COOL_F32) return COOL_EUNSUPPORTED;
+    if (s->row_scaled != 0) return COOL_EUNSUPPORTED;
+    if (!(s->k2_switch_T >= 0.0) || !(s->lnLambda > 0.0)) return COOL_EINVAL;
+    if ((s->theta_i_uses_mp != 0 && s->theta_i_uses_mp != 1) ||
+        (s->compton_literal != 0 && s->compton_literal != 1))
+        return COOL_EINVAL;
+    return COOL_OK;
+}
+
+cool_status validate_params(const cool_params* p) {
+    if (!p) return COOL_ENULL;
+    if (!(p->rho_scale > 0.0) || !isfinite(p->rho_scale)) return COOL_EINVAL;
+    if (!(p->M_bh_msun > 0.0) || !isfinite(p->M_bh_msun)) return COOL_EINVAL;
+    if (!(p->gamma_e > 1.0) || !(p->gamma_i > 1.0) || !isfinite(p->gamma_e) || !isfinite(p->gamma_i))
+        return COOL_EINVAL;
+    if (!(p->dt >= 0.0) || !isfinite(p->dt)) return COOL_EINVAL;
+    if (p->n_sub < 1 || p->n_sub > 64) return COOL_EINVAL;
+    if (p->mode != COOL_EXPLICIT_LIMITED && p->mode != COOL_IMPLICIT_STIFF) return COOL_EINVAL;
+    if (!(p->limiter_frac > 0.0 && p->limiter_frac <= 1.0)) return COOL_EINVAL;
+    if (!(p->eq_band >= 0.0 && p->eq_band < 1.0)) return COOL_EINVAL;
+    if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
+    if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
+    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
+    if (p->band_fp64 != 0 && p->band_fp64 != 1) return COOL_EINVAL;
+    return COOL_OK;
+}
+
+// Node arrays of one axis: l_j = log2(min) + j dl, x_j = 2^l_j.
+void axis_nodes(double lo, double hi, int n, double* x64, double* l64) {
+    double l0 = log2(lo);
+    double dl = (log2(hi) - l0) / (n - 1);
+    for (int j = 0; j < n; ++j) {
+        l64[j] = l0 + j * dl;
+        x64[j] = exp2(l64[j]);
+    }
+}
+
+void free_table_memory(cool_table* t) {
+    void* dptrs[] = {t->d_axes, t->d_axes64, t->d_lb, t->d_ls, t->d_lc, t->d_lb64, t->d_ls64, t->d_lc64};
+    for (void* p : dptrs)
+        if (p) cudaFree(p);
+    free(t->h_lb64);
+    free(t->h_ls64);
+    free(t->h_lc64);
+    free(t->h_axes);
+}
+
+// Allocate a table, fill its node arrays; channels left to the caller.
+cool_status table_alloc(const cool_table_spec& s, cool_table** out) {
+    cool_table* t = new (std::nothrow) cool_table;
+    if (!t) return COOL_ENOMEM;
+    memset(t, 0, sizeof(*t));
+    t->spec = s;
+    cudaGetDevice(&t->device);
+    int n[5] = {s.n_H, s.n_B, s.n_ne, s.n_Te, s.n_Tc};
+    double lo[5] = {s.H_min, s.B_min, s.ne_min, s.T_min, s.T_min};
+    double hi[5] = {s.H_max, s.B_max, s.ne_max, s.T_max, s.T_max};
+    int na = 0, na64 = 0;
+    int off64[5];
+    for (int a = 0; a < 5; ++a) {
+        t->dev.n[a] = n[a];
+        t->dev.axis_off[a] = na;
+        off64[a] = na64;
+        na += 3 * n[a];
+        na64 += 2 * n[a];
+    }
+    t->h_axes = (float*)malloc(sizeof(float) * na);
+    double* h64 = (double*)malloc(sizeof(double) * na64);
+    long long nls = syn_count(s);
+    t->h_lb64 = (double*)malloc(sizeof(double) * s.n_Te);
+    t->h_ls64 = (double*)malloc(sizeof(double) * nls);
+    t->h_lc64 = (double*)malloc(sizeof(double) * s.n_Tc * s.n_Tc);
+    if (!t->h_axes || !h64 || !t->h_lb64 || !t->h_ls64 || !t->h_lc64) {
+        free(h64);
+        free_table_memory(t);
+        delete t;
+        return COOL_ENOMEM;
+    }
+    for (int a = 0; a < 5; ++a) {
+        double* x64 = h64 + off64[a];
+        double* l64 = x64 + n[a];
+        axis_nodes(lo[a], hi[a], n[a], x64, l64);
+        float* x = t->h_axes + t->dev.axis_off[a];
+        for (int j = 0; j < n[a]; ++j) {
+            x[j] = (float)x64[j];
+            x[n[a] + j] = (float)(1.0 / x64[j]);
+            x[2 * n[a] + j] = (float)l64[j];
+        }
+        double dl = (log2(hi[a]) - log2(lo[a])) / (n[a] - 1);
+        t->dev.dl64[a] = dl;
+        t->dev.l0_64[a] = log2(lo[a]);
+        t->dev.inv_dl[a] = (float)(1.0 / dl);
+    }
+    cudaError_t e = cudaSuccess;
+    size_t lsb = sizeof(float) * nls;
+    t->ls_bytes = lsb;
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_axes, sizeof(float) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_axes64, sizeof(double) * na64);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_lb, sizeof(float) * s.n_Te);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_ls, lsb);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_lc, sizeof(float) * s.n_Tc * s.n_Tc);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_lb64, sizeof(double) * s.n_Te);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_ls64, sizeof(double) * nls);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_lc64, sizeof(double) * s.n_Tc * s.n_Tc);
+    if (e == cudaSuccess) e = cudaMemcpy(t->d_axes, t->h_axes, sizeof(float) * na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->d_axes64, h64, sizeof(double) * na64, cudaMemcpyHostToDevice);
+    free(h64);
+    if (e != cudaSuccess) {
+        free_table_memory(t);
+        delete t;
+        return e == cudaErrorMemoryAllocation ? COOL_ENOMEM : set_cuda_error(e);
+    }
+    t->dev.axes = (const float*)t->d_axes;
+    t->dev.axes64 = (const double*)t->d_axes64;
+    t->dev.lb = (const float*)t->d_lb;
+    t->dev.ls = (const float*)t->d_ls;
+    t->dev.lc = (const float*)t->d_lc;
+    t->dev.lb64 = (const double*)t->d_lb64;
+    t->dev.ls64 = (const double*)t->d_ls64;
+    t->dev.lc64 = (const double*)t->d_lc64;
+    t->magic = kTableMagic;
+    *out = t;
+    return COOL_OK;
+}
+
+// FP64 device channels -> FP32 packed device channels; FP64 host copies.
+cool_status table_finish(cool_table* t, cudaStream_t st, bool copy_host) {
+    const cool_table_spec& s = t->spec;
+    long long nls = syn_count(s);
+    struct { const void* src; void* dst; long long n; } parts[3] = {
+        {t->d_lb64, t->d_lb, s.n_Te}, {t->d_ls64, t->d_ls, nls}, {t->d_lc64, t->d_lc, (long long)s.n_Tc * s.n_Tc}};
+    for (auto& pt : parts) {
+        long long blocks = (pt.n + 255) / 256;
+        if (blocks > 8192) blocks = 8192;
+        k_pack_f32<<<(int)blocks, 256, 0, st>>>((const double*)pt.src, (float*)pt.dst, pt.n);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && copy_host) {
+        e = cudaMemcpyAsync(t->h_lb64, t->d_lb64, sizeof(double) * s.n_Te, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t->h_ls64, t->d_ls64, sizeof(double) * nls, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t->h_lc64, t->d_lc64, sizeof(double) * s.n_Tc * s.n_Tc,
+                                cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    // Keep the 4-D channel L2-resident: reserve persisting L2 for it (a
+    // per-context limit; the access-policy window is set per launch).
+    int dev = t->device;
+    int maxp = 0;
+    cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    size_t want = t->ls_bytes < (size_t)maxp ? t->ls_bytes : (size_t)maxp;
+    size_t cur = 0;
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (want > cur) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+    cudaGetLastError();  // the limit is an optimisation: ignore failure
+    return COOL_OK;
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
+    const unsigned char* p = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+const char kFileMagic[8] = {'C', 'O', 'O', 'L', 'T', 'A', 'B', '1'};
+
+}  // namespace
+}  // namespace cool
+
+using namespace cool;
+
+extern "C" {
+
+const char* cool_strerror(cool_status s) {
+    switch (s) {
+    case COOL_OK: return "ok";
+    case COOL_EINVAL: return "invalid argument";
+    case COOL_ENULL: return "null pointer";
+    case COOL_EALIGN: return "misaligned pointer";
+    case COOL_ECUDA: return "CUDA error";
+    case COOL_ENOMEM: return "out of memory";
+    case COOL_ESTATE: return "invalid object state";
+    case COOL_EUNSUPPORTED: return "unsupported option";
+    case COOL_EIO: return "I/O error";
+    }
+    return "unknown status";
+}
+
+int cool_last_cuda_error(void) { return g_last_cuda_error; }
+
+cool_status cool_table_spec_default(cool_table_spec* s) {
+    if (!s) return COOL_ENULL;
+    memset(s, 0, sizeof(*s));
+    s->n_H = s->n_B = s->n_ne = s->n_Te = s->n_Tc = 64;
+    s->H_min = 1e3; s->H_max = 1e12;
+    s->B_min = 1.0; s->B_max = 1e10;
+    s->ne_min = 1e2; s->ne_max = 1e25;
+    s->T_min = 1e2; s->T_max = 1e15;
+    s->dtype = COOL_F32;
+    s->row_scaled = 0;
+    s->k2_switch_T = 1e8;
+    s->lnLambda = 20.0;
+    s->theta_i_uses_mp = 1;
+    s->compton_literal = 0;
+    return COOL_OK;
+}
+
+cool_status cool_params_default(cool_params* p) {
+    if (!p) return COOL_ENULL;
+    memset(p, 0, sizeof(*p));
+    p->rho_scale = 3e-7;
+    p->M_bh_msun = 10.0;
+    p->gamma_e = 5.0 / 3.0;
+    p->gamma_i = 5.0 / 3.0;
+    p->dt = 1e-2;
+    p->n_sub = 8;
+    p->mode = COOL_EXPLICIT_LIMITED;
+    p->limiter_frac = 0.3;
+    p->eq_band = 0.1;
+    p->coulomb_clamp = 1.0;
+    p->implicit_iters = 60;
+    p->path = COOL_PATH_L2WINDOW;
+    p->band_fp64 = 0;
+    return COOL_OK;
+}
+
+cool_status cool_build_table(const cool_table_spec* spec, void* stream, cool_table** out) {
+    if (!out) return COOL_ENULL;
+    *out = nullptr;
+    cool_status st = validate_spec(spec);
+    if (st != COOL_OK) return st;
+    cool_table* t = nullptr;
+    st = table_alloc(*spec, &t);
+    if (st != COOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int off64[5], o = 0;
+    for (int a = 0; a < 5; ++a) { off64[a] = o; o += 2 * t->dev.n[a]; }
+    st = build_channels_fp64(*spec, (const double*)t->d_axes64, off64, (double*)t->d_lb64,
+                             (double*)t->d_ls64, (double*)t->d_lc64, s);
+    if (st == COOL_OK) st = table_finish(t, s, true);
+    if (st != COOL_OK) {
+        t->magic = 0;
+        free_table_memory(t);
+        delete t;
+        return st;
+    }
+    register_table(t);
+    *out = t;
+    return COOL_OK;
+}
+
+cool_status cool_table_free(cool_table* t) {
+    if (!t) return COOL_OK;
+    if (!unregister_table(t)) return COOL_ESTATE;
+    t->magic = 0;
+    free_table_memory(t);
+    delete t;
+    return COOL_OK;
+}
+
+cool_status cool_table_get_spec(const cool_table* t, cool_table_spec* spec) {
+    if (!t || !spec) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    *spec = t->spec;
+    return COOL_OK;
+}
+
+cool_status cool_table_export(const cool_table* t, int channel, double* host_out, long long count) {
+    if (!t || !host_out) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    const double* src;
+    long long n;
+    switch (channel) {
+    case 0: src = t->h_lb64; n = t->spec.n_Te; break;
+    case 1: src = t->h_ls64; n = syn_count(t->spec); break;
+    case 2: src = t->h_lc64; n = (long long)t->spec.n_Tc * t->spec.n_Tc; break;
+    default: return COOL_EINVAL;
+    }
+    if (count != n) return COOL_EINVAL;
+    memcpy(host_out, src, sizeof(double) * n);
+    return COOL_OK;
+}
+
+cool_status cool_table_nodes(const cool_table* t, int axis, float* host_out, int n) {
+    if (!t || !host_out) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    if (axis < 0 || axis > 4 || n != t->dev.n[axis]) return COOL_EINVAL;
+    memcpy(host_out, t->h_axes + t->dev.axis_off[axis], sizeof(float) * n);
+    return COOL_OK;
+}
+
+cool_status cool_table_save(const cool_table* t, const char* path) {
+    if (!t || !path) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    FILE* f = fopen(path, "wb");
+    if (!f) return COOL_EIO;
+    const cool_table_spec& s = t->spec;
+    long long n[3] = {s.n_Te, syn_count(s), (long long)s.n_Tc * s.n_Tc};
+    const double* d[3] = {t->h_lb64, t->h_ls64, t->h_lc64};
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(&s, sizeof(s), h);
+    for (int c = 0; c < 3; ++c) h = fnv1a(d[c], sizeof(double) * n[c], h);
+    uint32_t ver = 1, sz = (uint32_t)sizeof(s);
+    bool ok = fwrite(kFileMagic, 1, 8, f) == 8 && fwrite(&ver, 4, 1, f) == 1 && fwrite(&sz, 4, 1, f) == 1 &&
+              fwrite(&s, sizeof(s), 1, f) == 1;
+    for (int c = 0; c < 3 && ok; ++c) ok = fwrite(d[c], sizeof(double), n[c], f) == (size_t)n[c];
+    ok = ok && fwrite(&h, 8, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? COOL_OK : COOL_EIO;
+}
+
+cool_status cool_table_load(const char* path, void* stream, cool_table** out) {
+    if (!path || !out) return COOL_ENULL;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return COOL_EIO;
+    char magic[8];
+    uint32_t ver = 0, sz = 0;
+    cool_table_spec s;
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kFileMagic, 8) != 0 || fread(&ver, 4, 1, f) != 1 ||
+        ver != 1 || fread(&sz, 4, 1, f) != 1 || sz != sizeof(s) || fread(&s, sizeof(s), 1, f) != 1) {
+        fclose(f);
+        return COOL_EIO;
+    }
+    cool_status st = validate_spec(&s);
+    if (st != COOL_OK) { fclose(f); return COOL_EIO; }
+    cool_table* t = nullptr;
+    st = table_alloc(s, &t);
+    if (st != COOL_OK) { fclose(f); return st; }
+    long long n[3] = {s.n_Te, syn_count(s), (long long)s.n_Tc * s.n_Tc};
+    double* d[3] = {t->h_lb64, t->h_ls64, t->h_lc64};
+    bool ok = true;
+    for (int c = 0; c < 3 && ok; ++c) ok = fread(d[c], sizeof(double), n[c], f) == (size_t)n[c];
+    uint64_t hf = 0;
+    ok = ok && fread(&hf, 8, 1, f) == 1;
+    fclose(f);
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(&s, sizeof(s), h);
+    for (int c = 0; c < 3 && ok; ++c) h = fnv1a(d[c], sizeof(double) * n[c], h);
+    if (!ok || h != hf) {
+        t->magic = 0;
+        free_table_memory(t);
+        delete t;
+        return COOL_EIO;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    void* dd[3] = {t->d_lb64, t->d_ls64, t->d_lc64};
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+        e = cudaMemcpyAsync(dd[c], d[c], sizeof(double) * n[c], cudaMemcpyHostToDevice, cs);
+    st = e == cudaSuccess ? table_finish(t, cs, false) : set_cuda_error(e);
+    if (st != COOL_OK) {
+        t->magic = 0;
+        free_table_memory(t);
+        delete t;
+        return st;
+    }
+    register_table(t);
+    *out = t;
+    return COOL_OK;
+}
+
+cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cells, cool_dtype field_dtype,
+                      const void* rho, const void* B, const void* H, const void* u_e_in, const void* u_i_in,
+                      void* u_e_out, void* u_i_out, void* q_cool_out, void* q_cc_out,
+                      cool_counters* counters, void* stream) {
+    if (!t || !p) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    cool_status st = validate_params(p);
+    if (st != COOL_OK) return st;
+    if (n_cells < 0) return COOL_EINVAL;
+    if (field_dtype != COOL_F32 && field_dtype != COOL_F64) return COOL_EUNSUPPORTED;
+    if (n_cells == 0) return COOL_OK;
+    if (!rho || !B || !H || !u_e_in || !u_i_in || !u_e_out || !u_i_out) return COOL_ENULL;
+    size_t esz = field_dtype == COOL_F32 ? 4 : 8;
+    const void* ptrs[] = {rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out, q_cc_out};
+    for (const void* q : ptrs)
+        if ((uintptr_t)q % esz != 0) return COOL_EALIGN;
+    if ((uintptr_t)counters % 8 != 0) return COOL_EALIGN;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return COOL_ESTATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (field_dtype == COOL_F32)
+        return launch_step_f32(t, p, n_cells, (const float*)rho, (const float*)B, (const float*)H,
+                               (const float*)u_e_in, (const float*)u_i_in, (float*)u_e_out,
+                               (float*)u_i_out, (float*)q_cool_out, (float*)q_cc_out, counters, s);
+    return launch_step_f64(t, p, n_cells, (const double*)rho, (const double*)B, (const double*)H,
+                           (const double*)u_e_in, (const double*)u_i_in, (double*)u_e_out,
+                           (double*)u_i_out, (double*)q_cool_out, (double*)q_cc_out, counters, s);
+}
+
+cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys, int* idx,
+                              float* w, void* stream) {
+    if (!t) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    if (axis < 0 || axis > 4 || n < 0) return COOL_EINVAL;
+    if (n == 0) return COOL_OK;
+    if (!keys || !idx || !w) return COOL_ENULL;
+    return launch_debug_lookup(t, axis, n, keys, idx, w, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+// cool_build.cu -- FP64 device evaluation of the cooling-rate table.
+//
+// One thread per table node evaluates the formulas of Sec. 2 of the paper
+// (arXiv 2505.08855) in FP64:
+//   bremsstrahlung e-e and e-i fits (Eqs. 1-2),
+//   thermal synchrotron emissivity (Eq. 3) with Mahadevan's I'(x) (Eq. 4)
+//   and K2(1/theta_e) -> 2 theta_e^2 at T_e <= k2_switch_T,
+//   the self-absorption frequency nu_c from the annulus balance (Eq. 5),
+//   Q_syn = Rayleigh-Jeans part below nu_c + thin integral above (Eq. 6),
+//   the Compton enhancement eta(nu_c) (Eqs. 7-9; exponent -1 - ln P/ln A,
+//   the truncated scattering series -- the printed 1 - ln P/ln A is a flag),
+//   the Coulomb coefficient C = Q_cc / (n_e^2 (T_i - T_e)) (Eq. 16).
+// The table stores log2 values (Sec. 2.6: log-spaced nodes; values in log2
+// so that interpolation spans the 60-decade dynamic range).
+#include <math.h>
+#include <stdio.h>
+
+#include "cool_internal.cuh"
+
+namespace cool {
+namespace {
+
+__constant__ double c_glx[16];
+__constant__ double c_glw[16];
+
+// Gauss-Legendre abscissae/weights on [-1, 1] (16 points): Newton's method
+// on P_16 seeded at the Chebyshev points; P and P' from the three-term
+// recurrence and P'_n = n (x P_n - P_{n-1}) / (x^2 - 1).
+void gl16_host(double* x, double* w) {
+    const int n = 16;
+    for (int i = 0; i < n; ++i) {
+        double r = cos(kPi * (2.0 * i + 1.0) / (2.0 * n));
+        double pn = 0.0, dpn = 1.0;
+        for (int iter = 0; iter < 200; ++iter) {
+            double pm = 1.0, pc = r;
+            for (int k = 1; k < n; ++k) {
+                double pnext = ((2 * k + 1) * r * pc - k * pm) / (k + 1);
+                pm = pc;
+                pc = pnext;
+            }
+            pn = pc;
+            dpn = n * (r * pc - pm) / (r * r - 1.0);
+            double step = pn / dpn;
+            r -= step;
+            if (fabs(step) <= 1e-17) break;
+        }
+        // final derivative at the converged root
+        double pm = 1.0, pc = r;
+        for (int k = 1; k < n; ++k) {
+            double pnext = ((2 * k + 1) * r * pc - k * pm) / (k + 1);
+            pm = pc;
+            pc = pnext;
+        }
+        dpn = n * (r * pc - pm) / (r * r - 1.0);
+        x[i] = r;
+        w[i] = 2.0 / ((1.0 - r * r) * dpn * dpn);
+    }
+}
+
+__device__ __forceinline__ double theta_e(double T) { return T * (kKB / (kME * kC * kC)); }
+
+// Bremsstrahlung per n_e^2 (Eqs. 1-2).
+__device__ double brems_n2(double T) {
+    double th = theta_e(T);
+    double ee, ei;
+    if (th < 1.0) {
+        double th15 = th * sqrt(th);
+        ee = th15 * (1.0 + 1.1 * th + th * th - 1.25 * th * th15);
+        ei = 4.0 * sqrt(2.0 * th / (kPi * kPi * kPi)) * (1.0 + 1.781 * pow(th, 1.34));
+    } else {
+        ee = 1.34 * th * (log(1.123 * th) + 1.28);
+        ei = 9.0 * th / (2.0 * kPi) * (log(1.123 * th + 0.48) + 1.5);
+    }
+    return 2.56e-22 * ee + 1.48e-22 * ei;
+}
+
+// Scaled modified Bessel functions e^z K_nu(z), nu = 0, 1, 2.
+// z <= 2: ascending series (Abramowitz & Stegun 9.6.13 for K_0, 9.6.11 with
+// n = 1 for K_1) and K_2 = K_0 + 2 K_1 / z.
+// z > 2: with cosh t - 1 = 2 s^2 (s = sinh(t/2)) the integral
+// K_nu(z) = int_0^inf exp(-z cosh t) cosh(nu t) dt becomes
+// e^z K_nu(z) = int_0^inf exp(-2 z s^2) c_nu(s) 2/sqrt(1+s^2) ds with
+// c_0 = 1, c_1 = 1 + 2 s^2, c_2 = 1 + 8 s^2 + 8 s^4; the integrand is even
+// and analytic in |Im s| < 1, so the trapezoidal rule converges
+// exponentially (step h = min(0.05, 0.3/sqrt z)).
+__device__ void kve012(double z, double& k0, double& k1, double& k2) {
+    const double euler = 0.57721566490153286061;
+    if (z <= 2.0) {
+        double q = 0.25 * z * z;
+        double lnh = log(0.5 * z);
+        double term0 = 1.0;         // q^k / (k!)^2
+        double term1 = 1.0;         // q^k / (k! (k+1)!)
+        double i0 = 0.0, i1s = 0.0, s0 = 0.0, s1 = 0.0;
+        double hk = 0.0;            // harmonic number H_k
+        double psi1 = -euler;       // psi(k+1)
+        double psi2 = 1.0 - euler;  // psi(k+2)
+        for (int k = 0; k < 60; ++k) {
+            i0 += term0;
+            i1s += term1;
+            s0 += hk * term0;
+            s1 += (psi1 + psi2) * term1;
+            double kk = k + 1.0;
+            term0 *= q / (kk * kk);
+            term1 *= q / (kk * (kk + 1.0));
+            hk += 1.0 / kk;
+            psi1 += 1.0 / kk;
+            psi2 += 1.0 / (kk + 1.0);
+            if (term0 < 1e-18 * i0 && term1 < 1e-18 * i1s) break;
+        }
+        double K0 = -(lnh + euler) * i0 + s0;
+        double I1 = 0.5 * z * i1s;
+        double K1 = 1.0 / z + lnh * I1 - 0.25 * z * s1;
+        double ez = exp(z);
+        k0 = K0 * ez;
+        k1 = K1 * ez;
+        k2 = k0 + 2.0 * k1 / z;
+        return;
+    }
+    double h = fmin(0.05, 0.3 / sqrt(z));
+    double a0 = 0.5, a1 = 0.5, a2 = 0.5;  // s = 0: weights 1/2, c_nu(0) = 1, 2/sqrt(1) = 2 applied below
+    for (int k = 1; k < 4000; ++k) {
+        double s = k * h;
+        double s2 = s * s;
+        double ex = 2.0 * z * s2;
+        if (ex > 745.0) break;
+        double g = exp(-ex) / sqrt(1.0 + s2);
+        a0 += g;
+        a1 += g * (1.0 + 2.0 * s2);
+        a2 += g * (1.0 + 8.0 * s2 + 8.0 * s2 * s2);
+        if (ex > 45.0) break;
+    }
+    k0 = 2.0 * h * a0;
+    k1 = 2.0 * h * a1;
+    k2 = 2.0 * h * a2;
+}
+
+// log of Mahadevan's I'(x) (Eq. 4).
+__device__ double log_iprime(double x) {
+    double rx = 1.0 / sqrt(x);
+    return log(4.0505) - log(x) * (1.0 / 6.0) + log1p(0.4 * sqrt(rx) + 0.5316 * rx) - 1.8899 * cbrt(x);
+}
+
+// Integrand of int x I'(x) dx in s = x^(1/3): 3 s^5 I'(s^3)
+// = 3 * 4.0505 s^4.5 (1 + 0.4 s^-0.75 + 0.5316 s^-1.5) e^(-1.8899 s).
+__device__ double syn_integrand(double s) {
+    if (!(s > 0.0)) return 0.0;
+    double r = sqrt(s);
+    double q = sqrt(r);
+    double s2 = s * s;
+    return 12.1515 * s2 * s2 * r * (1.0 + 0.4 / (r * q) + 0.5316 / (s * r)) * exp(-1.8899 * s);
+}
+
+// J(x_c) = int_{x_c}^inf x I'(x) dx: 16-point Gauss-Legendre on 64 equal
+// panels of s = x^(1/3) over [x_c^(1/3), x_c^(1/3) + 40].
+__device__ double syn_tail_integral(double xc) {
+    const int panels = 64;
+    const double width = 40.0 / panels;
+    double s0 = cbrt(xc);
+    double total = 0.0;
+    for (int p = 0; p < panels; ++p) {
+        double c = s0 + (p + 0.5) * width;
+        double acc = 0.0;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) acc += c_glw[i] * syn_integrand(c + 0.5 * width * c_glx[i]);
+        total += acc;
+    }
+    return 0.5 * width * total;
+}
+
+struct SynOut { double eta_qsyn; int flag; };
+
+// eta(nu_c) * Q_syn at one node (Eqs. 3-9).
+__device__ SynOut eta_qsyn(double H, double B, double ne, double T, double k2_switch_T,
+                           int compton_literal) {
+    double th = theta_e(T);
+    double k2f;
+    if (T <= k2_switch_T) {
+        k2f = 2.0 * th * th;
+    } else {
+        double z = 1.0 / th, a, b, c;
+        kve012(z, a, b, c);
+        k2f = c * exp(-z);
+    }
+    double nu0 = 3.0 * kQE * B * th * th / (4.0 * kPi * kME * kC);
+    double pref = 4.43e-30 * 4.0 * kPi * ne / k2f;       // eps_s = pref * nu * I'(nu/nu0)
+    // Eq. 5 in x = nu/nu0:  ln I'(x) - ln x = ln(2 pi k T / c^2) - ln(H pref / nu0)
+    double L = log(2.0 * kPi * kKB * T / (kC * kC)) - log(H * pref / nu0);
+    double lnnu0 = log(nu0);
+    double a = -lnnu0, b = log(1e30) - lnnu0;             // nu in [1 Hz, 1e30 Hz]
+    double nuc;
+    int flag = 0;
+    if (log_iprime(exp(a)) - a - L <= 0.0) {
+        nuc = 1.0;
+    } else if (log_iprime(exp(b)) - b - L > 0.0) {
+        nuc = 1e30;
+        flag = 1;
+    } else {
+        for (int it = 0; it < 200 && (b - a) >= 1e-14; ++it) {
+            double m = 0.5 * (a + b);
+            if (log_iprime(exp(m)) - m - L > 0.0) a = m; else b = m;
+        }
+        nuc = exp(lnnu0 + 0.5 * (a + b));
+    }
+    // Eq. 6: Rayleigh-Jeans part (per unit volume of the annulus) + thin part
+    double qsyn = 2.0 * kPi * kKB * T * nuc * nuc * nuc / (3.0 * kC * kC * H)
+                + pref * nu0 * nu0 * syn_tail_integral(nuc / nu0);
+    // Eqs. 7-9 at nu_c
+    double E = kHP * nuc / (kME * kC * kC);
+    double eta = 1.0;
+    if (E < 3.0 * th) {
+        double tau = 2.0 * ne * kSigT * H;
+        double P = -expm1(-tau);
+        double am1 = 4.0 * th * (1.0 + 4.0 * th);          // A - 1
+        double lnA = log1p(am1);
+        if (compton_literal) {
+            double ex = 1.0 - log(P) / lnA;
+            eta = 1.0 + P * am1 / (1.0 - P * (1.0 + am1)) * (1.0 - pow(E / (3.0 * th), ex));
+        } else if (P > 0.0) {
+            double kk = log(3.0 * th / E) / lnA;            // scatterings to reach 3 theta
+            double eps = log(P) + lnA;                       // ln(P A)
+            double ratio = (eps == 0.0) ? kk : expm1(kk * eps) / expm1(eps);
+            eta = 1.0 + P * am1 * ratio;
+        }
+    }
+    SynOut o;
+    o.eta_qsyn = eta * qsyn;
+    o.flag = flag;
+    return o;
+}
+
+// Coulomb coefficient (Eq. 16) with scaled Bessel functions; the factors
+// e^(-1/theta) cancel because 1/theta_m = 1/theta_e + 1/theta_i.
+__device__ double coulomb_coeff(double Ti, double Te, double lnLambda, int theta_i_uses_mp) {
+    double the = theta_e(Te);
+    double mi = theta_i_uses_mp ? kMP : kME;
+    double thi = Ti * (kKB / (mi * kC * kC));
+    double ze = 1.0 / the, zi = 1.0 / thi;
+    double zm = ze + zi;
+    double a0, a1, a2, e0, e1, e2, m0, m1, m2;
+    kve012(zi, a0, a1, a2);
+    kve012(ze, e0, e1, e2);
+    kve012(zm, m0, m1, m2);
+    double sum = the + thi;
+    double bracket = (2.0 * sum * sum + 1.0) / sum * m1 + 2.0 * m0;
+    return 1.5 * (kME / kMP) * lnLambda * kC * kSigT * kKB * bracket / (a2 * e2);
+}
+
+struct BuildArgs {
+    const double* x64;  // node coordinates, concatenated per axis
+    int off[5];
+    int n[5];
+    double k2_switch_T, lnLambda;
+    int theta_i_uses_mp, compton_literal;
+};
+
+__global__ void k_build_syn(BuildArgs a, long long first, long long count, double* out,
+                            unsigned int* flags) {
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = first + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < first + count;
+         i += stride) {
+        long long r = i;
+        int t = (int)(r % a.n[3]); r /= a.n[3];
+        int n = (int)(r % a.n[2]); r /= a.n[2];
+        int b = (int)(r % a.n[1]); r /= a.n[1];
+        int h = (int)r;
+        SynOut o = eta_qsyn(a.x64[a.off[0] + h], a.x64[a.off[1] + b], a.x64[a.off[2] + n],
+                            a.x64[a.off[3] + t], a.k2_switch_T, a.compton_literal);
+        out[i] = log2(o.eta_qsyn);
+        if (o.flag) atomicAdd(flags, 1u);
+    }
+}
+
+__global__ void k_build_small(BuildArgs a, double* lb, double* lc) {
+    int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    int nT = a.n[3], nC = a.n[4];
+    if (tid < nT) lb[tid] = log2(brems_n2(a.x64[a.off[3] + tid]));
+    if (tid < nC * nC) {
+        int i = tid / nC, e = tid % nC;
+        lc[tid] = log2(coulomb_coeff(a.x64[a.off[4] + i], a.x64[a.off[4] + e], a.lnLambda,
+                                     a.theta_i_uses_mp));
+    }
+}
+
+}  // namespace
+
+cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64,
+                                const int* axis_off64, double* d_lb64, double* d_ls64,
+                                double* d_lc64, cudaStream_t st) {
+    double gx[16], gw[16];
+    gl16_host(gx, gw);
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    BuildArgs a;
+    a.x64 = d_axes64;
+    int n[5] = {s.n_H, s.n_B, s.n_ne, s.n_Te, s.n_Tc};
+    for (int i = 0; i < 5; ++i) { a.off[i] = axis_off64[i]; a.n[i] = n[i]; }
+    a.k2_switch_T = s.k2_switch_T;
+    a.lnLambda = s.lnLambda;
+    a.theta_i_uses_mp = s.theta_i_uses_mp;
+    a.compton_literal = s.compton_literal;
+    int small = n[3] > n[4] * n[4] ? n[3] : n[4] * n[4];
+    k_build_small<<<(small + 127) / 128, 128, 0, st>>>(a, d_lb64, d_lc64);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_error(e);
+    unsigned int* d_flags = nullptr;
+    e = cudaMallocAsync(&d_flags, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    cudaMemsetAsync(d_flags, 0, sizeof(unsigned int), st);
+    long long total = syn_count(s);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // chunks of ~4M nodes: each launch finishes in well under a second
+    const long long chunk = 1LL << 22;
+    for (long long first = 0; first < total; first += chunk) {
+        long long cnt = total - first < chunk ? total - first : chunk;
+        long long blocks = (cnt + 127) / 128;
+        if (blocks > sms * 16LL) blocks = sms * 16LL;
+        k_build_syn<<<(int)blocks, 128, 0, st>>>(a, first, cnt, d_ls64, d_flags);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { cudaFreeAsync(d_flags, st); return set_cuda_error(e); }
+    }
+    cudaFreeAsync(d_flags, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return COOL_OK;
+}
+
+}  // namespace cool

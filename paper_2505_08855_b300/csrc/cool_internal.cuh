@@ -1,0 +1,98 @@
+// cool_internal.cuh -- shared definitions of libcool's CUDA sources.
+//
+// Physical constants (cgs, CODATA 2018), the device-side table layout and
+// the kernel parameter blocks.  This is the product path: it shares nothing
+// with the CPU oracle used by the tests.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cool.h"
+
+namespace cool {
+
+// ---- constants (cgs) -------------------------------------------------------
+constexpr double kC = 2.99792458e10;        // speed of light
+constexpr double kKB = 1.380649e-16;        // Boltzmann
+constexpr double kME = 9.1093837015e-28;    // electron mass
+constexpr double kMP = 1.67262192369e-24;   // proton mass
+constexpr double kQE = 4.80320471e-10;      // elementary charge (esu)
+constexpr double kHP = 6.62607015e-27;      // Planck
+constexpr double kSigT = 6.6524587321e-25;  // Thomson cross section
+constexpr double kSigSB = 5.670374419e-5;   // Stefan-Boltzmann
+constexpr double kG = 6.6743e-8;            // gravitational constant
+constexpr double kMsun = 1.98847e33;        // solar mass
+constexpr double kPi = 3.141592653589793238;
+
+constexpr int kMaxAxis = 512;
+constexpr int kMaxTc = 128;
+
+// ---- the table --------------------------------------------------------------
+// Axis data on the device, per axis a (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T):
+//   x32[j]  FP32 node (index selection compares keys against it exactly)
+//   rx32[j] FP32 of 1/x_j (weight: log2(key * rx_j) = log2(key/x_j))
+//   lx32[j] FP32 of l_j = log2 x_j
+// stored as axis_off[a] + {0, n, 2n} inside one float array.
+struct DevTable {
+    int n[5];
+    int axis_off[5];
+    float inv_dl[5];        // 1/dl, dl = node spacing in log2
+    double dl64[5];
+    double l0_64[5];
+    const float* axes;      // concatenated axis arrays (x, rx, lx per axis)
+    const double* axes64;   // concatenated FP64 axis arrays (x, lx per axis)
+    const float* lb;        // [n_Te]       log2(Q_brem / n_e^2)
+    const float* ls;        // [nH nB nN nT] log2(eta Q_syn)
+    const float* lc;        // [nTc nTc]    log2 C
+    const double* lb64;     // FP64 copies (FP64 step path, export)
+    const double* ls64;
+    const double* lc64;
+};
+
+}  // namespace cool
+
+// The opaque handle of the C ABI.
+struct cool_table {
+    uint32_t magic;             // kTableMagic while alive
+    int device;
+    cool_table_spec spec;
+    cool::DevTable dev;
+    void* d_axes;               // device allocations owned by the table
+    void* d_axes64;
+    void* d_lb; void* d_ls; void* d_lc;
+    void* d_lb64; void* d_ls64; void* d_lc64;
+    double* h_lb64;             // host FP64 copies of the channels (export / save)
+    double* h_ls64;
+    double* h_lc64;
+    float* h_axes;              // host copy of the FP32 axis arrays
+    size_t ls_bytes;
+};
+
+constexpr uint32_t kTableMagic = 0xC0011AB1u;
+
+namespace cool {
+
+// Host helpers shared by the .cu files of the library.
+cool_status set_cuda_error(cudaError_t e);
+bool table_ok(const cool_table* t);
+long long syn_count(const cool_table_spec& s);
+
+// Builder entry (cool_build.cu): evaluates the FP64 channels on the device.
+cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64,
+                                const int* axis_off64, double* d_lb64, double* d_ls64,
+                                double* d_lc64, cudaStream_t st);
+
+// Step launches (cool_step.cu).
+cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long n,
+                            const float* rho, const float* B, const float* H,
+                            const float* ue, const float* ui, float* ue_o, float* ui_o,
+                            float* qc, float* qx, cool_counters* cnt, cudaStream_t st);
+cool_status launch_step_f64(const cool_table* t, const cool_params* p, long long n,
+                            const double* rho, const double* B, const double* H,
+                            const double* ue, const double* ui, double* ue_o, double* ui_o,
+                            double* qc, double* qx, cool_counters* cnt, cudaStream_t st);
+cool_status launch_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
+                                int* idx, float* w, cudaStream_t st);
+
+}  // namespace cool
