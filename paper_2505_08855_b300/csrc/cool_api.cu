@@ -54,6 +54,21 @@ __global__ void k_pack_f32(const double* src, float* dst, long long n) {
         dst[i] = (float)src[i];
 }
 
+// FP64 [rows][nT] -> FP32 T_e octets [rows][nblk][8], block k = nodes 7k..7k+7.
+__global__ void k_pack_octets(const double* src, float* dst, long long rows, int nT, int nblk) {
+    long long total = rows * nblk * 8;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        int o = (int)(i & 7);
+        long long rb = i >> 3;
+        int k = (int)(rb % nblk);
+        long long r = rb / nblk;
+        int node = 7 * k + o;
+        if (node > nT - 1) node = nT - 1;
+        dst[i] = (float)src[r * nT + node];
+    }
+}
+
 cool_status validate_spec(const cool_table_spec* s) {
     if (!s) return COOL_ENULL;
     int n[5] = {s->n_H, s->n_B, s->n_ne, s->n_Te, s->n_Tc};
@@ -64,6 +79,9 @@ cool_status validate_spec(const cool_table_spec* s) {
     double hi[4] = {s->H_max, s->B_max, s->ne_max, s->T_max};
     for (int a = 0; a < 4; ++a)
         if (!(lo[a] > 0.0) || !(hi[a] > lo[a]) || !isfinite(hi[a])) return COOL_EINVAL;
+    // the step addresses the packed 4-D channel with 32-bit float offsets
+    long long rows = (long long)s->n_H * s->n_B * s->n_ne;
+    if (rows * 8LL * ((s->n_Te - 1 + 6) / 7) >= (1LL << 31)) return COOL_EINVAL;
     if (s->dtype != COOL_F32) return COOL_EUNSUPPORTED;
     if (s->row_scaled != 0) return COOL_EUNSUPPORTED;
     if (!(s->k2_switch_T >= 0.0) || !(s->lnLambda > 0.0)) return COOL_EINVAL;
@@ -158,7 +176,8 @@ cool_status table_alloc(const cool_table_spec& s, cool_table** out) {
         t->dev.inv_dl[a] = (float)(1.0 / dl);
     }
     cudaError_t e = cudaSuccess;
-    size_t lsb = sizeof(float) * nls;
+    t->dev.nblk = (s.n_Te - 1 + 6) / 7;
+    size_t lsb = sizeof(float) * 8 * (size_t)t->dev.nblk * (size_t)(nls / s.n_Te);
     t->ls_bytes = lsb;
     if (e == cudaSuccess) e = cudaMalloc(&t->d_axes, sizeof(float) * na);
     if (e == cudaSuccess) e = cudaMalloc(&t->d_axes64, sizeof(double) * na64);
@@ -179,7 +198,7 @@ cool_status table_alloc(const cool_table_spec& s, cool_table** out) {
     t->dev.axes = (const float*)t->d_axes;
     t->dev.axes64 = (const double*)t->d_axes64;
     t->dev.lb = (const float*)t->d_lb;
-    t->dev.ls = (const float*)t->d_ls;
+    t->dev.ls8 = (const float*)t->d_ls;
     t->dev.lc = (const float*)t->d_lc;
     t->dev.lb64 = (const double*)t->d_lb64;
     t->dev.ls64 = (const double*)t->d_ls64;
@@ -193,12 +212,20 @@ cool_status table_alloc(const cool_table_spec& s, cool_table** out) {
 cool_status table_finish(cool_table* t, cudaStream_t st, bool copy_host) {
     const cool_table_spec& s = t->spec;
     long long nls = syn_count(s);
-    struct { const void* src; void* dst; long long n; } parts[3] = {
-        {t->d_lb64, t->d_lb, s.n_Te}, {t->d_ls64, t->d_ls, nls}, {t->d_lc64, t->d_lc, (long long)s.n_Tc * s.n_Tc}};
+    struct { const void* src; void* dst; long long n; } parts[2] = {
+        {t->d_lb64, t->d_lb, s.n_Te}, {t->d_lc64, t->d_lc, (long long)s.n_Tc * s.n_Tc}};
     for (auto& pt : parts) {
         long long blocks = (pt.n + 255) / 256;
         if (blocks > 8192) blocks = 8192;
         k_pack_f32<<<(int)blocks, 256, 0, st>>>((const double*)pt.src, (float*)pt.dst, pt.n);
+    }
+    {
+        long long rows = nls / s.n_Te;
+        long long total = rows * t->dev.nblk * 8;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 8192) blocks = 8192;
+        k_pack_octets<<<(int)blocks, 256, 0, st>>>((const double*)t->d_ls64, (float*)t->d_ls, rows, s.n_Te,
+                                                   t->dev.nblk);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && copy_host) {

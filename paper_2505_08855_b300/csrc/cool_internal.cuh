@@ -43,7 +43,10 @@ struct DevTable {
     const float* axes;      // concatenated axis arrays (x, rx, lx per axis)
     const double* axes64;   // concatenated FP64 axis arrays (x, lx per axis)
     const float* lb;        // [n_Te]       log2(Q_brem / n_e^2)
-    const float* ls;        // [nH nB nN nT] log2(eta Q_syn)
+    const float* ls8;       // log2(eta Q_syn) in T_e octets: row r = (h nB + b) nN + n holds
+                            // nblk blocks of 8 floats, block k = nodes 7k .. 7k+7 (clamped to
+                            // nT-1), 32-byte aligned; block k serves the intervals 7k .. 7k+6
+    int nblk;               // ceil((nT - 1) / 7)
     const float* lc;        // [nTc nTc]    log2 C
     const double* lb64;     // FP64 copies (FP64 step path, export)
     const double* ls64;

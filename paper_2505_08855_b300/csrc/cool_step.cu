@@ -73,43 +73,23 @@ struct Sel {
 };
 
 // Index selection on an axis (x, rx, lx arrays of n floats at `a`): the
-// largest j in [0, n-2] with x[j] <= key (exact FP32 comparisons; a guess
-// from log2 is corrected by walking), j = 0 below the first node.
+// largest j in [0, n-2] with x[j] <= key, compared exactly in FP32 (j = 0
+// below the first node).  The guess floor((log2 key - l_0)/dl) is within
+// one of that index (lg2.approx is accurate to ~1e-5 absolute, far below
+// one node spacing), so one upward and one downward correction make the
+// selection exact with no data-dependent loop.  The key is clamped when it
+// lies outside [x_0, x_{n-1}].
 __device__ __forceinline__ Sel select_axis(const float* a, int n, float inv_dl, float key,
                                            unsigned& clamp) {
     const float* x = a;
     const float* rx = a + n;
     const float* lx = a + 2 * n;
+    int j = __float2int_rd((lg2a(key) - lx[0]) * inv_dl);
+    j = min(max(j, 0), n - 2);
+    j += (j < n - 2 && x[j + 1] <= key) ? 1 : 0;
+    j -= (j > 0 && x[j] > key) ? 1 : 0;
+    clamp |= (key < x[0] || key > x[n - 1]) ? 1u : 0u;
     Sel s;
-    if (!(key >= x[0])) {
-        clamp = 1u;
-        s.j = 0;
-    } else {
-        int j = __float2int_rz((lg2a(key) - lx[0]) * inv_dl);
-        j = min(max(j, 0), n - 2);
-        while (j < n - 2 && x[j + 1] <= key) ++j;
-        while (j > 0 && x[j] > key) --j;
-        if (key > x[n - 1]) clamp = 1u;
-        s.j = j;
-    }
-    s.r = lg2a(key * rx[s.j]);
-    return s;
-}
-
-// Same, starting the walk from a previous index (keys that move little).
-__device__ __forceinline__ Sel select_from(const float* a, int n, int j, float key,
-                                           unsigned& clamp) {
-    const float* x = a;
-    const float* rx = a + n;
-    Sel s;
-    if (!(key >= x[0])) {
-        clamp = 1u;
-        j = 0;
-    } else {
-        while (j < n - 2 && x[j + 1] <= key) ++j;
-        while (j > 0 && x[j] > key) --j;
-        if (key > x[n - 1]) clamp = 1u;
-    }
     s.j = j;
     s.r = lg2a(key * rx[j]);
     return s;
@@ -117,86 +97,105 @@ __device__ __forceinline__ Sel select_from(const float* a, int n, int j, float k
 
 // Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
 struct CellC {
-    const float* lsp;   // &ls[((jh nB + jb) nN + jn) nT]
-    int oH, oB, oN;     // strides of the H, B, n_e corners
+    const float* row;   // octet row of corner (jh, jb, jn): ls8 + r nblk 8
+    int oH, oB, oN;     // float offsets to the H+1, B+1, n_e+1 corner rows
     float wh, wb, wn;
     float lb_off;       // log2(h n_e^2 / e_scale)
     float ls_off;       // log2(h / e_scale)
     float lbb_off;      // log2(4 sigma_SB h / (H_cm e_scale))
     float tau_sca;      // 2 n_e sigma_T H_cm
-    float inv_e;        // s_Te / rho
 };
 
+// Collapsed synchrotron values of one T_e octet (7 intervals) live in shared
+// memory, node o of thread t at win[o * kThreads + t] (conflict-free).
 struct Cache {
-    int jt;             // T_e interval whose collapsed values are held
-    float s0, s1;       // synchrotron channel at T_e nodes jt, jt+1 (collapsed)
-    float b0, b1;       // bremsstrahlung channel at jt, jt+1
+    int base;           // first node of the held octet (multiple of 7), -8 if none
+    float* win;         // this thread's window column
 };
+
+constexpr int kThreads = 256;
 
 __device__ __forceinline__ float lerpf(float a, float b, float w) { return fmaf(w, b - a, a); }
 
-__device__ __forceinline__ void gather(const CellC& c, const float* lb, int jt, Cache& cc) {
-    const float* p = c.lsp + jt;
-    float v000 = __ldg(p), v000b = __ldg(p + 1);
-    float v001 = __ldg(p + c.oN), v001b = __ldg(p + c.oN + 1);
-    float v010 = __ldg(p + c.oB), v010b = __ldg(p + c.oB + 1);
-    float v011 = __ldg(p + c.oB + c.oN), v011b = __ldg(p + c.oB + c.oN + 1);
+// 256-bit read-only load of one octet (32-byte aligned).
+__device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+}
+
+// Read the 8 corner octets of block kb (one 32-byte sector each) and collapse
+// the H, B, n_e axes: win[o] = trilinear value at T_e node 7 kb + o.
+__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
+    const float* p = c.row + (long long)kb * 8;
+    float a[8], b[8], d[8];
+    ld8(p, a);
+    ld8(p + c.oN, b);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = lerpf(a[t], b[t], c.wn);
+    ld8(p + c.oB, b);
+    ld8(p + c.oB + c.oN, d);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = lerpf(a[t], lerpf(b[t], d[t], c.wn), c.wb);
     const float* q = p + c.oH;
-    float v100 = __ldg(q), v100b = __ldg(q + 1);
-    float v101 = __ldg(q + c.oN), v101b = __ldg(q + c.oN + 1);
-    float v110 = __ldg(q + c.oB), v110b = __ldg(q + c.oB + 1);
-    float v111 = __ldg(q + c.oB + c.oN), v111b = __ldg(q + c.oB + c.oN + 1);
-    float a0 = lerpf(lerpf(v000, v001, c.wn), lerpf(v010, v011, c.wn), c.wb);
-    float a1 = lerpf(lerpf(v100, v101, c.wn), lerpf(v110, v111, c.wn), c.wb);
-    float b0 = lerpf(lerpf(v000b, v001b, c.wn), lerpf(v010b, v011b, c.wn), c.wb);
-    float b1 = lerpf(lerpf(v100b, v101b, c.wn), lerpf(v110b, v111b, c.wn), c.wb);
-    cc.s0 = lerpf(a0, a1, c.wh);
-    cc.s1 = lerpf(b0, b1, c.wh);
-    cc.b0 = lb[jt];
-    cc.b1 = lb[jt + 1];
-    cc.jt = jt;
+    ld8(q, b);
+    ld8(q + c.oN, d);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) b[t] = lerpf(b[t], d[t], c.wn);
+    float e[8];
+    ld8(q + c.oB, d);
+    ld8(q + c.oB + c.oN, e);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        b[t] = lerpf(b[t], lerpf(d[t], e[t], c.wn), c.wb);
+        cc.win[t * kThreads] = lerpf(a[t], b[t], c.wh);
+    }
+    cc.base = 7 * kb;
 }
 
 // Energy (code units) that cooling removes in one sub-cycle at T_e, with
 // the bridge of Eq. 11 evaluated in log2 space:
-//   A = log2 q_thin, B = log2 q_bb (q_bb = h 4 sigma T^4/(H e_scale)),
-//   tau_abs = 2^(A - B), q = q_thin / (1 + tau_abs (sqrt3 + 1.5 (tau_abs + tau_sca))).
+//   A = log2 q_thin = log2(q_brem + q_syn), B = log2 q_bb with
+//   q_bb = h 4 sigma T^4/(H e_scale), tau_abs = 2^(A - B),
+//   q = q_thin / (1 + tau_abs (sqrt3 + 1.5 (tau_abs + tau_sca))).
+// The common path has no range branches: 2^d underflows to 0 where one
+// channel is negligible and tau_abs to 0 where the cell is thin; only
+// tau_abs > 2^60 (where tau_abs^2 would overflow) takes the asymptotic form.
 __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, const CellC& c,
-                                             Cache& cc, float Te, bool walk, unsigned& clamp) {
+                                             Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
     const float* axT = S.ax + k.tab.axis_off[3];
-    Sel s = walk && cc.jt >= 0 ? select_from(axT, nT, cc.jt, Te, clamp)
-                               : select_axis(axT, nT, k.tab.inv_dl[3], Te, clamp);
-    if (s.j != cc.jt) gather(c, S.lb, s.j, cc);
-    float w = __saturatef(s.r * k.tab.inv_dl[3]);
-    float Ls = lerpf(cc.s0, cc.s1, w) + c.ls_off;
-    float Lb = lerpf(cc.b0, cc.b1, w) + c.lb_off;
-    float lT = axT[2 * nT + s.j] + s.r;
-    float M = fmaxf(Ls, Lb), d = fminf(Ls, Lb) - M;
-    float A = d > -40.f ? M + lg2a(1.f + ex2a(d)) : M;
-    float Bb = fmaf(4.f, lT, c.lbb_off);
-    float lt = A - Bb;  // log2 tau_abs
+    Sel s = select_axis(axT, nT, k.tab.inv_dl[3], Te, clamp);
+    const int j = s.j;
+    if ((unsigned)(j - cc.base) > 6u) gather(c, j / 7, cc);
+    const int o = j - cc.base;
+    const float w = __saturatef(s.r * k.tab.inv_dl[3]);
+    const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
+    const float Lb = lerpf(S.lb[j], S.lb[j + 1], w) + c.lb_off;
+    const float lT = axT[2 * nT + j] + s.r;
+    const float M = fmaxf(Ls, Lb);
+    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
+    const float Bb = fmaf(4.f, lT, c.lbb_off);
+    const float lt = A - Bb;  // log2 tau_abs
     float lq;
-    if (lt < -40.f) {
-        lq = A;
-    } else if (lt > 40.f) {
-        // tau_abs > 2^40: q = q_bb / (1.5 (tau_abs + tau_sca)) to 2^-39
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    } else {
-        float tau = ex2a(lt);
-        float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
+    if (lt <= 60.f) {
+        const float tau = ex2a(lt);
+        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
         lq = A - lg2a(D);
+    } else {
+        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
+        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
     }
     return ex2a(fminf(lq, 126.f));
 }
 
 struct Out {
     float ue, ui, qc, qx;
-    unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 fp64 Coulomb, 4 implicit fail
+    unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail
 };
 
-__device__ Out step_cell(const StepK& k, const Smem& S, float rho, float B, float H, float ue,
-                         float ui) {
+__device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* win, float rho, float B,
+                                         float H, float ue, float ui) {
     Out o;
     if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
         !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
@@ -208,7 +207,7 @@ __device__ Out step_cell(const StepK& k, const Smem& S, float rho, float B, floa
     const float ne = rho * k.s_n;
     const float Bg = B * k.s_B;
     const float Hc = H * k.s_H;
-    const float inv_e = k.s_Te / rho;   // IEEE division
+    const float inv_e = k.s_Te / rho;   // IEEE division (the key sequence of the interface)
     const float inv_i = k.s_Ti / rho;
     const float kr = k.s_K / rho;
     CellC c;
@@ -216,10 +215,11 @@ __device__ Out step_cell(const StepK& k, const Smem& S, float rho, float B, floa
         Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
         Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
         Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
-        c.oN = T.n[3];
-        c.oB = T.n[2] * T.n[3];
-        c.oH = T.n[1] * c.oB;
-        c.lsp = T.ls + ((long long)(sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * T.n[3];
+        const int rowf = 8 * T.nblk;                       // floats per n_e row
+        c.oN = rowf;
+        c.oB = rowf * T.n[2];
+        c.oH = c.oB * T.n[1];
+        c.row = T.ls8 + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
         c.wh = __saturatef(sh.r * T.inv_dl[0]);
         c.wb = __saturatef(sb.r * T.inv_dl[1]);
         c.wn = __saturatef(sn.r * T.inv_dl[2]);
@@ -228,30 +228,25 @@ __device__ Out step_cell(const StepK& k, const Smem& S, float rho, float B, floa
         c.lb_off = fmaf(2.f, lne, k.l_hs_e);
         c.lbb_off = k.l_bb - lg2a(Hc);
         c.tau_sca = k.two_sigT * ne * Hc;
-        c.inv_e = inv_e;
     }
     const float lcc_off = c.lb_off;  // log2(h n_e^2 / e_scale)
     const int nC = T.n[4];
     const float* axC = S.ax + T.axis_off[4];
     Cache cc;
-    cc.jt = -1;
-    int jCe = -1, jCi = -1;
+    cc.base = -8;
+    cc.win = win;
     float sum_q = 0.f, sum_x = 0.f;
     for (int sub = 0; sub < k.n_sub; ++sub) {
         // ---- (i) Coulomb exchange --------------------------------------------
-        float Te = ue * inv_e;
-        float Ti = ui * inv_i;
-        Sel se = jCe >= 0 ? select_from(axC, nC, jCe, Te, clamp)
-                          : select_axis(axC, nC, T.inv_dl[4], Te, clamp);
-        Sel si = jCi >= 0 ? select_from(axC, nC, jCi, Ti, clamp)
-                          : select_axis(axC, nC, T.inv_dl[4], Ti, clamp);
-        jCe = se.j;
-        jCi = si.j;
-        float we = __saturatef(se.r * T.inv_dl[4]);
-        float wi = __saturatef(si.r * T.inv_dl[4]);
+        const float Te = ue * inv_e;
+        const float Ti = ui * inv_i;
+        const Sel se = select_axis(axC, nC, T.inv_dl[4], Te, clamp);
+        const Sel si = select_axis(axC, nC, T.inv_dl[4], Ti, clamp);
+        const float we = __saturatef(se.r * T.inv_dl[4]);
+        const float wi = __saturatef(si.r * T.inv_dl[4]);
         const float* row = S.lc + si.j * nC + se.j;
-        float lC = lerpf(lerpf(row[0], row[1], we), lerpf(row[nC], row[nC + 1], we), wi);
-        float rate = ex2a(fminf(lC + lcc_off, 126.f));
+        const float lC = lerpf(lerpf(row[0], row[1], we), lerpf(row[nC], row[nC + 1], we), wi);
+        const float rate = ex2a(fminf(lC + lcc_off, 126.f));
         // D = (gamma_i - 1) u_i - (gamma_e - 1) u_e; T_i - T_e = (s_K/rho) D and
         // the equilibrium point is X_eq = D / (ce + ci).  D cancels as T_e -> T_i:
         // it is formed by an error-free transformation of the product ce*u_e
@@ -269,42 +264,39 @@ __device__ Out step_cell(const StepK& k, const Smem& S, float rho, float B, floa
             ui = (float)((double)ui - Xd);
             X = (float)Xd;
         } else {
-            float pe = k.ce * ue;
-            float ee = fmaf(k.ce, ue, -pe);
-            float D = fmaf(k.ci, ui, -pe) - ee;
+            const float pe = k.ce * ue;
+            const float ee = fmaf(k.ce, ue, -pe);
+            const float D = fmaf(k.ci, ui, -pe) - ee;
             X = rate * (kr * D);
-            float lim = k.clamp * fabsf(D * k.inv_cec);
-            if (fabsf(X) > lim) X = copysignf(lim, X);
+            const float lim = k.clamp * fabsf(D * k.inv_cec);
+            X = fabsf(X) > lim ? copysignf(lim, X) : X;
             ue += X;
             ui -= X;
         }
         sum_x += X;
         // ---- (ii) radiative cooling ----------------------------------------
-        float q = cool_energy(k, S, c, cc, ue * inv_e, true, clamp);
-        float du;
+        const float q = cool_energy(k, S, c, cc, ue * inv_e, clamp);
+        float du = fminf(q, k.limiter * ue);
         if (k.mode == 1 && q > k.limiter * ue) {
             stiff = 1u;
             const float u0 = ue;
             float b = lg2a(u0);
             float a = b - 60.f;
-            float ua = ex2a(a);
+            const float ua = ex2a(a);
             unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
-            float ga = ua - u0 + cool_energy(k, S, c, cc, ua * inv_e, false, trial);
+            const float ga = ua - u0 + cool_energy(k, S, c, cc, ua * inv_e, trial);
             if (!(ga < 0.f)) {
                 fail = 1u;
-                du = k.limiter * u0;
             } else {
                 for (int it = 0; it < k.iters; ++it) {
-                    float m = 0.5f * (a + b);
+                    const float m = 0.5f * (a + b);
                     if (m == a || m == b) break;
-                    float um = ex2a(m);
-                    float g = um - u0 + cool_energy(k, S, c, cc, um * inv_e, false, trial);
+                    const float um = ex2a(m);
+                    const float g = um - u0 + cool_energy(k, S, c, cc, um * inv_e, trial);
                     if (g > 0.f) b = m; else a = m;
                 }
                 du = u0 - ex2a(0.5f * (a + b));
             }
-        } else {
-            du = fminf(q, k.limiter * ue);
         }
         ue -= du;
         sum_q += du;
@@ -344,64 +336,76 @@ __device__ __forceinline__ void count_flags(unsigned f, cool_counters* cnt) {
     }
 }
 
-constexpr int kThreads = 256;
-constexpr int kTile = 4 * kThreads;  // cells per tile: one float4 per thread per field
+constexpr int kWarpCells = 128;          // cells per warp tile: one float4 per lane per field
+constexpr int kWarps = kThreads / 32;
 
-// VEC: fields are 16-byte aligned.  Each block walks tiles of kTile cells:
-// the five input fields are read with 128-bit streaming loads into shared
-// memory, each thread then steps cells t, t+256, t+512, t+768 (conflict-free
-// shared-memory access, one cell's state in registers at a time), and the
-// outputs leave through shared memory with 128-bit streaming stores.  The
-// remainder (and unaligned arrays) take a scalar grid-stride loop.
+// Shared memory of one block: the small table parts (axes, brems, Coulomb),
+// then the per-thread synchrotron windows (8 x kThreads floats), then, for
+// the vector path, one staging tile of 5 x kWarpCells floats per warp.
+__host__ __device__ __forceinline__ int smem_table_floats(const StepK& k) { return (k.smem_floats + 3) & ~3; }
+
+// VEC: all arrays 16-byte aligned.  Each warp walks its own tiles of 128
+// cells: the five input fields arrive by 128-bit streaming loads into the
+// warp's staging area, each lane steps cells lane, lane+32, lane+64, lane+96
+// (one cell's state in registers at a time), the outputs overwrite the
+// staging area and leave by 128-bit streaming stores.  Warps synchronise
+// only with themselves (__syncwarp), so a slow cell delays one warp, not the
+// block.  The remainder (and unaligned arrays) take a scalar loop.
 template <bool VEC>
-__global__ void __launch_bounds__(kThreads) k_step_f32(StepK k, long long n, const float* __restrict__ rho,
-                                                      const float* __restrict__ Bf, const float* __restrict__ Hf,
-                                                      const float* ue_in, const float* ui_in, float* ue_out,
-                                                      float* ui_out, float* qc_out, float* qx_out,
-                                                      cool_counters* cnt) {
+#ifndef COOL_MINB
+#define COOL_MINB 3
+#endif
+__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long long n, const float* __restrict__ rho,
+                                                         const float* __restrict__ Bf, const float* __restrict__ Hf,
+                                                         const float* ue_in, const float* ui_in, float* ue_out,
+                                                         float* ui_out, float* qc_out, float* qx_out,
+                                                         cool_counters* cnt) {
     extern __shared__ float sm[];
     load_smem(k, sm);
     Smem S;
     S.ax = sm;
     S.lb = sm + k.axes_floats;
     S.lc = sm + k.axes_floats + k.tab.n[3];
-    const int t = threadIdx.x;
+    float* win = sm + smem_table_floats(k) + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     long long scalar_start = 0;
     if (VEC) {
-        float* tile = sm + ((k.smem_floats + 3) & ~3);   // 16-byte aligned
-        float4* t4 = reinterpret_cast<float4*>(tile);    // 7 fields x kThreads float4
-        const long long ntiles = n / kTile;
-        for (long long tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
-            const long long q = tb * kThreads + t;       // float4 index
-            t4[0 * kThreads + t] = __ldcs(reinterpret_cast<const float4*>(rho) + q);
-            t4[1 * kThreads + t] = __ldcs(reinterpret_cast<const float4*>(Bf) + q);
-            t4[2 * kThreads + t] = __ldcs(reinterpret_cast<const float4*>(Hf) + q);
-            t4[3 * kThreads + t] = __ldcs(reinterpret_cast<const float4*>(ue_in) + q);
-            t4[4 * kThreads + t] = __ldcs(reinterpret_cast<const float4*>(ui_in) + q);
-            __syncthreads();
+        float* tile = sm + smem_table_floats(k) + 8 * kThreads + warp * 5 * kWarpCells;
+        float4* t4 = reinterpret_cast<float4*>(tile);
+        const long long ntiles = n / kWarpCells;
+        for (long long tw = (long long)blockIdx.x * kWarps + warp; tw < ntiles; tw += (long long)gridDim.x * kWarps) {
+            const long long q = tw * 32 + lane;  // float4 index of this lane
+            t4[0 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rho) + q);
+            t4[1 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(Bf) + q);
+            t4[2 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(Hf) + q);
+            t4[3 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ue_in) + q);
+            t4[4 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ui_in) + q);
+            __syncwarp();
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
-                const int j = c * kThreads + t;
-                Out o = step_cell(k, S, tile[j], tile[kTile + j], tile[2 * kTile + j], tile[3 * kTile + j],
-                                  tile[4 * kTile + j]);
-                tile[3 * kTile + j] = o.ue;
-                tile[4 * kTile + j] = o.ui;
-                tile[5 * kTile + j] = o.qc;
-                tile[6 * kTile + j] = o.qx;
+                const int j = c * 32 + lane;
+                Out o = step_cell(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
+                                  tile[3 * kWarpCells + j], tile[4 * kWarpCells + j]);
+                // inputs of cell j are consumed: outputs reuse its slots
+                tile[3 * kWarpCells + j] = o.ue;
+                tile[4 * kWarpCells + j] = o.ui;
+                tile[0 * kWarpCells + j] = o.qc;
+                tile[1 * kWarpCells + j] = o.qx;
                 if (cnt) count_flags(o.flags, cnt);
             }
-            __syncthreads();
-            __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * kThreads + t]);
-            __stcs(reinterpret_cast<float4*>(ui_out) + q, t4[4 * kThreads + t]);
-            if (qc_out) __stcs(reinterpret_cast<float4*>(qc_out) + q, t4[5 * kThreads + t]);
-            if (qx_out) __stcs(reinterpret_cast<float4*>(qx_out) + q, t4[6 * kThreads + t]);
-            __syncthreads();
+            __syncwarp();
+            __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
+            __stcs(reinterpret_cast<float4*>(ui_out) + q, t4[4 * 32 + lane]);
+            if (qc_out) __stcs(reinterpret_cast<float4*>(qc_out) + q, t4[0 * 32 + lane]);
+            if (qx_out) __stcs(reinterpret_cast<float4*>(qx_out) + q, t4[1 * 32 + lane]);
+            __syncwarp();
         }
-        scalar_start = ntiles * kTile;
+        scalar_start = ntiles * kWarpCells;
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + t; i < n; i += stride) {
-        Out o = step_cell(k, S, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
+    for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Out o = step_cell(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
@@ -603,8 +607,8 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     if (n == 0) return COOL_OK;
     bool vec = ((uintptr_t)rho | (uintptr_t)B | (uintptr_t)H | (uintptr_t)ue | (uintptr_t)ui |
                 (uintptr_t)ue_o | (uintptr_t)ui_o | (uintptr_t)qc | (uintptr_t)qx) % 16 == 0;
-    size_t smem = (size_t)((k.smem_floats + 3) & ~3) * sizeof(float);
-    if (vec) smem += (size_t)7 * kTile * sizeof(float);
+    size_t smem = (size_t)(smem_table_floats(k) + 8 * kThreads) * sizeof(float);
+    if (vec) smem += (size_t)kWarps * 5 * kWarpCells * sizeof(float);
     auto fn = vec ? k_step_f32<true> : k_step_f32<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
@@ -612,7 +616,7 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     if (per_sm < 1) per_sm = 1;
-    long long work = vec ? (n + kTile - 1) / kTile : (n + kThreads - 1) / kThreads;
+    long long work = vec ? (n + kWarps * kWarpCells - 1) / (kWarps * kWarpCells) : (n + kThreads - 1) / kThreads;
     long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
     long long blocks = work < cap ? work : cap;
     if (blocks < 1) blocks = 1;
