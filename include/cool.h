@@ -186,6 +186,31 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
                       void* q_cool_out, void* q_cc_out,
                       cool_counters* counters, void* stream);
 
+/* Build the three FP64 channels of a table into caller-allocated device
+ * arrays, allocating no device memory.  The paper has no counterpart: this
+ * entry point serves callers that cannot let a library call cudaMalloc or
+ * cudaFree -- for example a simulation code that reserves its whole device
+ * memory as one arena at start-up and hands out slices of it, or a framework
+ * whose caching allocator must own every device allocation.
+ *   spec: as for cool_build_table, but every axis must have at most 256
+ *     nodes (n_H, n_B, n_ne, n_Te, n_Tc <= 256); larger axes return
+ *     COOL_EINVAL because the builder's scratch is a fixed-size array.
+ *   lb_out [n_Te], ls_out [n_H n_B n_ne n_Te], lc_out [n_Tc n_Tc]: device
+ *     arrays (8-byte aligned) that receive the same FP64 log2 values, in the
+ *     same layouts, as cool_table_export returns for a table built from spec.
+ *   stream: the work is enqueued on it; the call returns after enqueueing.
+ * The builder's scratch (node coordinates and a counter) is one 20.25 KiB
+ * file-scope device array that every GPU loading the library holds until the
+ * process exits.  All calls share it and it keeps the last call's contents
+ * (the counter is cleared at the start of each call), so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race:
+ * order them on one stream.  The first call on a device performs a
+ * synchronous one-time set-up (it resolves the array's device address and
+ * uploads the quadrature constants); make that first call before any stream
+ * capture. */
+cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_out, double* ls_out,
+                                        double* lc_out, void* stream);
+
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n): idx = the largest j
  * in [0, N-2] with node32[j] <= key (0 below the first node), w = log2(key /

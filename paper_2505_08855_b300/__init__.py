@@ -202,3 +202,15 @@ def debug_lookup(table, axis, keys, stream=None):
     _b.check(_b.lib().cool_debug_lookup(table.handle, axis, keys.numel(), _ptr(keys), _ptr(idx),
                                         _ptr(w), _stream_ptr(stream)), "cool_debug_lookup")
     return idx, w
+
+
+def build_channels_noalloc(spec, lb_out, ls_out, lc_out, stream=None):
+    """cool_build_channels_noalloc: the table's FP64 log2 channels written into
+    caller-allocated CUDA float64 tensors (sizes n_Te, n_H n_B n_ne n_Te,
+    n_Tc^2); the library allocates no device memory for it."""
+    cs = spec.c()
+    for t in (lb_out, ls_out, lc_out):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("outputs must be contiguous CUDA tensors")
+    _b.check(_b.lib().cool_build_channels_noalloc(_b.ref(cs), _ptr(lb_out), _ptr(ls_out), _ptr(lc_out),
+                                                  _stream_ptr(stream)), "cool_build_channels_noalloc")

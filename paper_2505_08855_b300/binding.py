@@ -23,6 +23,7 @@ EXPORTS = (
     "cool_strerror", "cool_last_cuda_error", "cool_table_spec_default", "cool_params_default",
     "cool_build_table", "cool_table_free", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
+    "cool_build_channels_noalloc",
 )
 
 
@@ -92,6 +93,7 @@ def lib():
             "cool_table_load": (I, [C.c_char_p, P, P]),
             "cool_step": (I, [P, P, LL, I, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_debug_lookup": (I, [P, I, LL, P, P, P, P]),
+            "cool_build_channels_noalloc": (I, [P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

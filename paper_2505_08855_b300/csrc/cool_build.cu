@@ -13,7 +13,10 @@
 // The table stores log2 values (Sec. 2.6: log-spaced nodes; values in log2
 // so that interpolation spans the 60-decade dynamic range).
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
+
+#include <mutex>
 
 #include "cool_internal.cuh"
 
@@ -326,5 +329,147 @@ cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
 }
+
+
+// ---------------------------------------------------------------------------
+// Caller-allocated table build: the variant of the builder above that
+// allocates no device memory.  The builder's scratch (FP64 node coordinates
+// of the five axes and the nu_c-cap flag counter) lives in one file-scope
+// device array instead of cudaMallocAsync'd buffers; the caller passes the
+// three FP64 output channels.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocAxisMax = 256;                     // nodes per axis the scratch holds
+constexpr int kNoAllocDevices = 64;
+constexpr size_t kNoAllocNodeBytes = sizeof(double) * 5 * 2 * kNoAllocAxisMax;   // 20 KiB
+constexpr size_t kNoAllocScratchBytes = kNoAllocNodeBytes + 256;                 // + flag word
+
+// Every device that loads the library holds this array until the process
+// exits.  Layout: axis a at doubles [a*2*256, a*2*256 + 256) = x_j and
+// [a*2*256 + 256, (a+1)*2*256) = l_j; the flag counter at byte
+// kNoAllocNodeBytes.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+    bool ready;
+    unsigned char* scratch;   // device address of g_noalloc_scratch on this device
+};
+static NoAllocDevice g_noalloc[kNoAllocDevices];
+static std::mutex g_noalloc_mu;
+
+// Node coordinates of the five axes into the scratch: l_j = l0 + j dl,
+// x_j = 2^l_j (the same node definition as the allocating build).
+__global__ void k_noalloc_nodes(double* nodes, double l0_0, double l0_1, double l0_2, double l0_3,
+                                double dl0, double dl1, double dl2, double dl3, int n0, int n1, int n2,
+                                int n3, int n4, double dl4) {
+    int a = blockIdx.x;
+    int j = threadIdx.x;
+    double l0 = a == 0 ? l0_0 : a == 1 ? l0_1 : a == 2 ? l0_2 : l0_3;
+    double dl = a == 0 ? dl0 : a == 1 ? dl1 : a == 2 ? dl2 : a == 3 ? dl3 : dl4;
+    int n = a == 0 ? n0 : a == 1 ? n1 : a == 2 ? n2 : a == 3 ? n3 : n4;
+    if (j < n) {
+        double l = l0 + j * dl;
+        nodes[a * 2 * kNoAllocAxisMax + j] = exp2(l);
+        nodes[a * 2 * kNoAllocAxisMax + kNoAllocAxisMax + j] = l;
+    }
+}
+
+// First call on a device: resolve the device address of the scratch array
+// (its name is only a host-side stand-in in host code) and upload the
+// Gauss-Legendre constants.  Synchronous; must not run inside a capture.
+cool_status noalloc_setup(int dev, unsigned char** scratch) {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (dev < 0 || dev >= kNoAllocDevices) return COOL_EUNSUPPORTED;
+    if (!g_noalloc[dev].ready) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        double gx[16], gw[16];
+        gl16_host(gx, gw);
+        e = cudaMemcpyToSymbol(c_glx, gx, sizeof(gx));
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, gw, sizeof(gw));
+        if (e != cudaSuccess) return set_cuda_error(e);
+        g_noalloc[dev].scratch = (unsigned char*)ptr;
+        g_noalloc[dev].ready = true;
+    }
+    *scratch = g_noalloc[dev].scratch;
+    return COOL_OK;
+}
+
+}  // namespace
+}  // namespace cool
+
+extern "C" cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_out,
+                                                   double* ls_out, double* lc_out, void* stream) {
+    using namespace cool;
+    if (!spec || !lb_out || !ls_out || !lc_out) return COOL_ENULL;
+    const cool_table_spec& s = *spec;
+    int n[5] = {s.n_H, s.n_B, s.n_ne, s.n_Te, s.n_Tc};
+    for (int a = 0; a < 5; ++a)
+        if (n[a] < 2) return COOL_EINVAL;
+    for (int a = 0; a < 5; ++a)
+        if (n[a] > kNoAllocAxisMax) return COOL_EINVAL;   // beyond the fixed scratch
+    double lo[4] = {s.H_min, s.B_min, s.ne_min, s.T_min};
+    double hi[4] = {s.H_max, s.B_max, s.ne_max, s.T_max};
+    for (int a = 0; a < 4; ++a)
+        if (!(lo[a] > 0.0) || !(hi[a] > lo[a]) || !isfinite(hi[a])) return COOL_EINVAL;
+    if (!(s.k2_switch_T >= 0.0) || !(s.lnLambda > 0.0)) return COOL_EINVAL;
+    if ((s.theta_i_uses_mp != 0 && s.theta_i_uses_mp != 1) ||
+        (s.compton_literal != 0 && s.compton_literal != 1))
+        return COOL_EINVAL;
+    if (((uintptr_t)lb_out | (uintptr_t)ls_out | (uintptr_t)lc_out) % 8 != 0) return COOL_EALIGN;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    unsigned char* scratch = nullptr;
+    cool_status st = noalloc_setup(dev, &scratch);
+    if (st != COOL_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    double* nodes = (double*)scratch;
+    unsigned int* flags = (unsigned int*)(scratch + kNoAllocNodeBytes);
+    double l0[5], dl[5];
+    double lo5[5] = {s.H_min, s.B_min, s.ne_min, s.T_min, s.T_min};
+    double hi5[5] = {s.H_max, s.B_max, s.ne_max, s.T_max, s.T_max};
+    for (int a = 0; a < 5; ++a) {
+        l0[a] = log2(lo5[a]);
+        dl[a] = (log2(hi5[a]) - l0[a]) / (n[a] - 1);
+    }
+    // the Coulomb axis shares T_min with the T_e axis: l0[4] == l0[3]
+    k_noalloc_nodes<<<5, kNoAllocAxisMax, 0, cs>>>(nodes, l0[0], l0[1], l0[2], l0[3], dl[0], dl[1], dl[2],
+                                                    dl[3], n[0], n[1], n[2], n[3], n[4], dl[4]);
+    e = cudaMemsetAsync(flags, 0, sizeof(unsigned int), cs);   // the counter starts at zero every call
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_error(e);
+    BuildArgs a;
+    a.x64 = nodes;
+    for (int i = 0; i < 5; ++i) {
+        a.off[i] = i * 2 * kNoAllocAxisMax;
+        a.n[i] = n[i];
+    }
+    a.k2_switch_T = s.k2_switch_T;
+    a.lnLambda = s.lnLambda;
+    a.theta_i_uses_mp = s.theta_i_uses_mp;
+    a.compton_literal = s.compton_literal;
+    // BuildArgs addresses l_j at off + n; in the scratch l_j sits at off + 256
+    // and is not read by the build kernels (they use x_j only).
+    int small = n[3] > n[4] * n[4] ? n[3] : n[4] * n[4];
+    k_build_small<<<(small + 127) / 128, 128, 0, cs>>>(a, lb_out, lc_out);
+    long long total = (long long)n[0] * n[1] * n[2] * n[3];
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long chunk = 1LL << 22;
+    for (long long first = 0; first < total; first += chunk) {
+        long long cnt = total - first < chunk ? total - first : chunk;
+        long long blocks = (cnt + 127) / 128;
+        if (blocks > sms * 16LL) blocks = sms * 16LL;
+        k_build_syn<<<(int)blocks, 128, 0, cs>>>(a, first, cnt, ls_out, flags);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return COOL_OK;
+}
+
+namespace cool {
 
 }  // namespace cool
