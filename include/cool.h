@@ -80,8 +80,10 @@ typedef struct {
     double B_min, B_max;      /* G    (paper: 1 .. 1e10)   */
     double ne_min, ne_max;    /* cm^-3 (paper: 1e2 .. 1e25) */
     double T_min, T_max;      /* K    (paper: 1e2 .. 1e15), T_e and Coulomb axes */
-    cool_dtype dtype;         /* storage of the 4-D channel: COOL_F32 (others: not yet) */
-    int row_scaled;           /* reserved for reduced-precision storage; must be 0 for F32 */
+    cool_dtype dtype;         /* storage of the 4-D channel: COOL_F32, COOL_BF16 or COOL_F16 */
+    int row_scaled;           /* 16-bit storage only: 1 = each 32-byte block along T_e holds an FP32
+                                 offset and scale and 12 16-bit residuals in [-1, 1]
+                                 (value = offset + scale r); 0 = plain 16-bit log2 values */
     double k2_switch_T;       /* K2(1/theta) -> 2 theta^2 at T_e <= this (paper: 1e8 K) */
     double lnLambda;          /* Coulomb logarithm (default 20) */
     int theta_i_uses_mp;      /* 1: theta_i = kT_i/(m_p c^2) (default); 0: m_e as printed */
@@ -155,6 +157,17 @@ cool_status cool_table_export(const cool_table* t, int channel, double* host_out
 /* FP32 node coordinates of one axis (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T)
  * to host memory (host_out holds n floats).  Synchronous. */
 cool_status cool_table_nodes(const cool_table* t, int axis, float* host_out, int n);
+
+/* The 4-D channel as packed for the step: 32-byte blocks along T_e, row
+ * r = (h n_B + b) n_ne + n holding ceil((n_Te - 1)/S) blocks.  F32: 8 floats
+ * (nodes S k .. S k + 7, S = 7).  BF16/F16 plain: 16 codes (S = 15), node
+ * 2i in the low half of word i.  Row-scaled: words 0, 1 = FP32 offset and
+ * scale, words 2..7 = 12 codes of (v - offset)/scale (S = 11).  Codes are
+ * FP64 -> FP32 -> 16-bit, round to nearest even; nodes past n_Te - 1 repeat
+ * the last node.  packed_bytes gives the size; export copies it to host
+ * memory (synchronous). */
+cool_status cool_table_packed_bytes(const cool_table* t, long long* bytes);
+cool_status cool_table_export_packed(const cool_table* t, void* host_out, long long bytes);
 
 /* Save / load a table (spec + FP64 channel values, binary, with a spec hash).
  * load rebuilds the packed device table from the stored values without

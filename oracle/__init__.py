@@ -125,6 +125,8 @@ def _declare(L):
                           _P, _P, _P, _P, _P, _i]),
         "orc_keys_f32": (None, [_P, _ll, _P, _P, _P, _P, _P, _P]),
         "orc_cool_q_cell": (_d, [_P, _P, _P, _P, _i, _P, _d, _d, _d, _d]),
+        "orc_step_pairs": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P,
+                                _P, _P, _P, _P, _P, _i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -336,6 +338,26 @@ def cool_q_cell(spec, tables, params, rho, B, H, ue, direct=False):
     lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
     return lib().orc_cool_q_cell(_ref(s), _ptr(tables["lb"]), _ptr(tables["ls"]), _ptr(lc),
                                  int(direct), _ref(p), float(rho), float(B), float(H), float(ue))
+
+
+def step_pairs(spec, lb, lsp, lc, params, rho, B, H, ue, ui, nthreads=0):
+    """The O2 step reading the 4-D channel as per-interval node pairs
+    lsp[row, t, 0/1] (see oracle.quant) and the given brems/Coulomb
+    channels.  Returns the same tuple as step()."""
+    f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui)]
+    n = f[0].size
+    outs = [np.zeros(n) for _ in range(4)]
+    cnt = np.zeros(6, np.int64)
+    s = spec.c()
+    p = params.c()
+    lsp = np.ascontiguousarray(lsp, dtype=np.float64)
+    lb = np.ascontiguousarray(lb, dtype=np.float64)
+    lc = np.ascontiguousarray(lc, dtype=np.float64).reshape(-1)
+    rc = lib().orc_step_pairs(_ref(s), _ptr(lb), _ptr(lsp), _ptr(lc), _ref(p), n, *[_ptr(a) for a in f],
+                              *[_ptr(a) for a in outs], _ptr(cnt), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_pairs failed: {rc}")
+    return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
 
 
 def keys_f32(params, rho, B, H, ue, ui):

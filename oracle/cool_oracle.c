@@ -530,6 +530,7 @@ typedef struct {
     const double* lc;
     int lazy;
     int direct;       /* 1: O1 rates from the formulas instead of the table */
+    const double* lsp;  /* optional: per-interval node pairs of the 4-D channel */
     orc_axis ax[5];
 } orc_rates;
 
@@ -537,6 +538,25 @@ typedef struct {
     double ne, Bg, Hcm, hs, escale, sTe, sTi, ce, ci;
     int j[3]; double w[3]; /* H, B, n_e selections (step-invariant) */
 } cell_ctx;
+
+/* Multilinear interpolation of the 4-D channel when the table is given as
+ * per-interval node pairs lsp[((row (nT-1)) + jt) 2 + bt] (a storage format
+ * whose node values may depend on the interval, as a block-quantised table). */
+static double interp4_pairs(const orc_spec* s, const double* lsp, const int* j, const double* w) {
+    double acc = 0.0;
+    for (int c = 0; c < 16; ++c) {
+        double wt = 1.0;
+        int idx[4];
+        for (int a = 0; a < 4; ++a) {
+            int bit = (c >> a) & 1;
+            idx[a] = j[a] + bit;
+            wt *= bit ? w[a] : (1.0 - w[a]);
+        }
+        long long row = ((long long)idx[0] * s->n[1] + idx[1]) * s->n[2] + idx[2];
+        acc += wt * lsp[(row * (s->n[3] - 1) + j[3]) * 2 + ((c >> 3) & 1)];
+    }
+    return acc;
+}
 
 /* Cooling energy removed in one sub-cycle (code units) for electron energy
  * density ue, through T_e = s_Te ue/rho.  *clamp is or-ed with key clamping. */
@@ -551,7 +571,7 @@ static double cool_q(const orc_rates* R, const cell_ctx* c, double ue, double rh
         if (clamp) *clamp |= cl;
         int j[4] = {c->j[0], c->j[1], c->j[2], jt};
         double w[4] = {c->w[0], c->w[1], c->w[2], wt};
-        double lqs = interp4(R->s, R->ls, R->lazy, j, w);
+        double lqs = R->lsp ? interp4_pairs(R->s, R->lsp, j, w) : interp4(R->s, R->ls, R->lazy, j, w);
         double lqb = interp1(R->lb, jt, wt);
         qthin = c->ne * c->ne * exp2(lqb) + exp2(lqs);
     }
@@ -656,14 +676,14 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
 /* Step n cells.  counters[0..5] = cells with flag bit k set (bit 5 unused:
  * the oracle has no surrogate fallback).  lazy: the 4-D channel may hold NaN
  * entries, computed on first use (forces one thread).  direct: O1 rates. */
-int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, int lazy, int direct,
-             const orc_params* p, long long n,
+static int step_impl(const orc_spec* s, const double* lb, double* ls, const double* lc, int lazy, int direct,
+             const double* lsp, const orc_params* p, long long n,
              const double* rho, const double* B, const double* H, const double* ue, const double* ui,
              double* ue_out, double* ui_out, double* qcool, double* qcc,
              long long* counters, int nthreads) {
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return -1;
-    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = lazy; R->direct = direct;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = lazy; R->direct = direct; R->lsp = lsp;
     for (int a = 0; a < 5; ++a) {
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
         axis_init(s, a, &R->ax[a]);
@@ -687,13 +707,33 @@ int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, 
     return 0;
 }
 
+int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, int lazy, int direct,
+             const orc_params* p, long long n,
+             const double* rho, const double* B, const double* H, const double* ue, const double* ui,
+             double* ue_out, double* ui_out, double* qcool, double* qcc,
+             long long* counters, int nthreads) {
+    return step_impl(s, lb, ls, lc, lazy, direct, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool, qcc,
+                     counters, nthreads);
+}
+
+/* The step with the 4-D channel given as per-interval node pairs (the
+ * values a packed storage format yields for each T_e interval). */
+int orc_step_pairs(const orc_spec* s, const double* lb, const double* lsp, const double* lc,
+                   const orc_params* p, long long n,
+                   const double* rho, const double* B, const double* H, const double* ue, const double* ui,
+                   double* ue_out, double* ui_out, double* qcool, double* qcc,
+                   long long* counters, int nthreads) {
+    return step_impl(s, lb, NULL, lc, 0, 0, lsp, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool, qcc,
+                     counters, nthreads);
+}
+
 /* Cooling energy removed in one sub-cycle (code units) at electron energy
  * density ue for one cell (tests: implicit residual, limiter). */
 double orc_cool_q_cell(const orc_spec* s, const double* lb, double* ls, const double* lc, int direct,
                        const orc_params* p, double rho, double B, double H, double ue) {
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return NAN;
-    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = direct;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = direct; R->lsp = NULL;
     for (int a = 0; a < 5; ++a) axis_init(s, a, &R->ax[a]);
     cell_ctx c;
     cell_setup(R, p, rho, B, H, &c);

@@ -121,6 +121,16 @@ class Table:
                                             count), "cool_table_export")
         return out
 
+    def export_packed(self):
+        """The 4-D channel as packed for the step (uint32 words, 8 per block)."""
+        import numpy as np
+        nb = C.c_longlong(0)
+        _b.check(_b.lib().cool_table_packed_bytes(self.handle, _b.ref(nb)), "cool_table_packed_bytes")
+        out = np.zeros(nb.value // 4, np.uint32)
+        _b.check(_b.lib().cool_table_export_packed(self.handle, out.ctypes.data_as(C.c_void_p), nb.value),
+                 "cool_table_export_packed")
+        return out
+
     def nodes(self, axis):
         import numpy as np
         out = np.zeros(self.spec.n[axis], np.float32)

@@ -1,5 +1,7 @@
 // cool_api.cu -- host side of the libcool C ABI (include/cool.h): argument
 // validation, table construction/packing/persistence, and kernel dispatch.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -54,18 +56,53 @@ __global__ void k_pack_f32(const double* src, float* dst, long long n) {
         dst[i] = (float)src[i];
 }
 
-// FP64 [rows][nT] -> FP32 T_e octets [rows][nblk][8], block k = nodes 7k..7k+7.
-__global__ void k_pack_octets(const double* src, float* dst, long long rows, int nT, int nblk) {
-    long long total = rows * nblk * 8;
+// 16-bit codes: FP64 -> FP32 (round to nearest even) -> BF16 or FP16 (RNE).
+__device__ __forceinline__ uint32_t code16(double v, int f16) {
+    float f = (float)v;
+    if (f16) return (uint32_t)__half_as_ushort(__float2half_rn(f));
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// FP64 [rows][nT] -> 32-byte blocks [rows][nblk] of the table format (see
+// DevTable): one thread per block.
+__global__ void k_pack_blocks(const double* src, uint32_t* dst, long long rows, int nT, int nblk, int fmt) {
+    long long total = rows * nblk;
     long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        int o = (int)(i & 7);
-        long long rb = i >> 3;
-        int k = (int)(rb % nblk);
-        long long r = rb / nblk;
-        int node = 7 * k + o;
-        if (node > nT - 1) node = nT - 1;
-        dst[i] = (float)src[r * nT + node];
+        int k = (int)(i % nblk);
+        long long r = i / nblk;
+        const double* row = src + r * nT;
+        uint32_t* out = dst + i * 8;
+        if (fmt == 0) {
+            for (int o = 0; o < 8; ++o) {
+                int node = min(7 * k + o, nT - 1);
+                out[o] = __float_as_uint((float)row[node]);
+            }
+        } else if (fmt == 1 || fmt == 2) {
+            int f16 = fmt == 2;
+            for (int o = 0; o < 8; ++o) {
+                int n0 = min(15 * k + 2 * o, nT - 1), n1 = min(15 * k + 2 * o + 1, nT - 1);
+                out[o] = code16(row[n0], f16) | (code16(row[n1], f16) << 16);
+            }
+        } else {
+            int f16 = fmt == 4;
+            double lo = row[min(11 * k, nT - 1)], hi = lo;
+            for (int o = 1; o < 12; ++o) {
+                double v = row[min(11 * k + o, nT - 1)];
+                lo = fmin(lo, v);
+                hi = fmax(hi, v);
+            }
+            float off = (float)(0.5 * (hi + lo));
+            float sc = (float)(0.5 * (hi - lo));
+            out[0] = __float_as_uint(off);
+            out[1] = __float_as_uint(sc);
+            for (int o = 0; o < 6; ++o) {
+                int n0 = min(11 * k + 2 * o, nT - 1), n1 = min(11 * k + 2 * o + 1, nT - 1);
+                double r0 = sc > 0.f ? (row[n0] - (double)off) / (double)sc : 0.0;
+                double r1 = sc > 0.f ? (row[n1] - (double)off) / (double)sc : 0.0;
+                out[2 + o] = code16(r0, f16) | (code16(r1, f16) << 16);
+            }
+        }
     }
 }
 
@@ -79,11 +116,12 @@ cool_status validate_spec(const cool_table_spec* s) {
     double hi[4] = {s->H_max, s->B_max, s->ne_max, s->T_max};
     for (int a = 0; a < 4; ++a)
         if (!(lo[a] > 0.0) || !(hi[a] > lo[a]) || !isfinite(hi[a])) return COOL_EINVAL;
-    // the step addresses the packed 4-D channel with 32-bit float offsets
+    if (s->dtype != COOL_F32 && s->dtype != COOL_BF16 && s->dtype != COOL_F16) return COOL_EUNSUPPORTED;
+    if (s->row_scaled != 0 && s->row_scaled != 1) return COOL_EINVAL;
+    if (s->dtype == COOL_F32 && s->row_scaled) return COOL_EUNSUPPORTED;
+    // the step addresses the packed 4-D channel with 32-bit word offsets
     long long rows = (long long)s->n_H * s->n_B * s->n_ne;
     if (rows * 8LL * ((s->n_Te - 1 + 6) / 7) >= (1LL << 31)) return COOL_EINVAL;
-    if (s->dtype != COOL_F32) return COOL_EUNSUPPORTED;
-    if (s->row_scaled != 0) return COOL_EUNSUPPORTED;
     if (!(s->k2_switch_T >= 0.0) || !(s->lnLambda > 0.0)) return COOL_EINVAL;
     if ((s->theta_i_uses_mp != 0 && s->theta_i_uses_mp != 1) ||
         (s->compton_literal != 0 && s->compton_literal != 1))
@@ -176,8 +214,12 @@ cool_status table_alloc(const cool_table_spec& s, cool_table** out) {
         t->dev.inv_dl[a] = (float)(1.0 / dl);
     }
     cudaError_t e = cudaSuccess;
-    t->dev.nblk = (s.n_Te - 1 + 6) / 7;
-    size_t lsb = sizeof(float) * 8 * (size_t)t->dev.nblk * (size_t)(nls / s.n_Te);
+    int fmt = s.dtype == COOL_F32 ? 0 : (s.row_scaled ? (s.dtype == COOL_BF16 ? 3 : 4)
+                                                       : (s.dtype == COOL_BF16 ? 1 : 2));
+    t->dev.fmt = fmt;
+    t->dev.blk_stride = fmt == 0 ? 7 : (fmt <= 2 ? 15 : 11);
+    t->dev.nblk = (s.n_Te - 1 + t->dev.blk_stride - 1) / t->dev.blk_stride;
+    size_t lsb = 32 * (size_t)t->dev.nblk * (size_t)(nls / s.n_Te);
     t->ls_bytes = lsb;
     if (e == cudaSuccess) e = cudaMalloc(&t->d_axes, sizeof(float) * na);
     if (e == cudaSuccess) e = cudaMalloc(&t->d_axes64, sizeof(double) * na64);
@@ -198,7 +240,7 @@ cool_status table_alloc(const cool_table_spec& s, cool_table** out) {
     t->dev.axes = (const float*)t->d_axes;
     t->dev.axes64 = (const double*)t->d_axes64;
     t->dev.lb = (const float*)t->d_lb;
-    t->dev.ls8 = (const float*)t->d_ls;
+    t->dev.lsb = (const uint32_t*)t->d_ls;
     t->dev.lc = (const float*)t->d_lc;
     t->dev.lb64 = (const double*)t->d_lb64;
     t->dev.ls64 = (const double*)t->d_ls64;
@@ -221,11 +263,11 @@ cool_status table_finish(cool_table* t, cudaStream_t st, bool copy_host) {
     }
     {
         long long rows = nls / s.n_Te;
-        long long total = rows * t->dev.nblk * 8;
+        long long total = rows * t->dev.nblk;
         long long blocks = (total + 255) / 256;
         if (blocks > 8192) blocks = 8192;
-        k_pack_octets<<<(int)blocks, 256, 0, st>>>((const double*)t->d_ls64, (float*)t->d_ls, rows, s.n_Te,
-                                                   t->dev.nblk);
+        k_pack_blocks<<<(int)blocks, 256, 0, st>>>((const double*)t->d_ls64, (uint32_t*)t->d_ls, rows, s.n_Te,
+                                                   t->dev.nblk, t->dev.fmt);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && copy_host) {
@@ -376,6 +418,22 @@ cool_status cool_table_export(const cool_table* t, int channel, double* host_out
     }
     if (count != n) return COOL_EINVAL;
     memcpy(host_out, src, sizeof(double) * n);
+    return COOL_OK;
+}
+
+cool_status cool_table_export_packed(const cool_table* t, void* host_out, long long bytes) {
+    if (!t || !host_out) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    if (bytes != (long long)t->ls_bytes) return COOL_EINVAL;
+    cudaError_t e = cudaMemcpy(host_out, t->d_ls, t->ls_bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return COOL_OK;
+}
+
+cool_status cool_table_packed_bytes(const cool_table* t, long long* bytes) {
+    if (!t || !bytes) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    *bytes = (long long)t->ls_bytes;
     return COOL_OK;
 }
 

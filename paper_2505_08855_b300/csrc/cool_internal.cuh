@@ -43,10 +43,17 @@ struct DevTable {
     const float* axes;      // concatenated axis arrays (x, rx, lx per axis)
     const double* axes64;   // concatenated FP64 axis arrays (x, lx per axis)
     const float* lb;        // [n_Te]       log2(Q_brem / n_e^2)
-    const float* ls8;       // log2(eta Q_syn) in T_e octets: row r = (h nB + b) nN + n holds
-                            // nblk blocks of 8 floats, block k = nodes 7k .. 7k+7 (clamped to
-                            // nT-1), 32-byte aligned; block k serves the intervals 7k .. 7k+6
-    int nblk;               // ceil((nT - 1) / 7)
+    // log2(eta Q_syn) packed in 32-byte blocks along T_e: row r = (h nB + b) nN + n
+    // holds nblk blocks; block k covers nodes S k .. S k + W - 1 (clamped to nT - 1)
+    // and serves the intervals S k .. S k + S - 1 (S = W - 1):
+    //   fmt 0 (FP32):          8 floats                     W = 8,  S = 7
+    //   fmt 1/2 (BF16/FP16):   16 16-bit values              W = 16, S = 15
+    //   fmt 3/4 (BF16/FP16 block-scaled): float off, float scale, 12 16-bit
+    //                          residuals r, value = off + scale r,   W = 12, S = 11
+    const uint32_t* lsb;
+    int fmt;
+    int blk_stride;         // S
+    int nblk;               // ceil((nT - 1) / S)
     const float* lc;        // [nTc nTc]    log2 C
     const double* lb64;     // FP64 copies (FP64 step path, export)
     const double* ls64;

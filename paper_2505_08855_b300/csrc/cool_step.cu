@@ -26,6 +26,7 @@
 //     so a sub-cycle that stays in its T_e interval reads no table memory;
 //   - the bridge is evaluated in log2 space so that no intermediate
 //     over/underflows FP32 over the table's 60-decade range.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "cool_internal.cuh"
@@ -97,7 +98,7 @@ __device__ __forceinline__ Sel select_axis(const float* a, int n, float inv_dl, 
 
 // Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
 struct CellC {
-    const float* row;   // octet row of corner (jh, jb, jn): ls8 + r nblk 8
+    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words
     int oH, oB, oN;     // float offsets to the H+1, B+1, n_e+1 corner rows
     float wh, wb, wn;
     float lb_off;       // log2(h n_e^2 / e_scale)
@@ -117,40 +118,98 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ float lerpf(float a, float b, float w) { return fmaf(w, b - a, a); }
 
-// 256-bit read-only load of one octet (32-byte aligned).
-__device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+// Packed formats of the 4-D channel (DevTable::fmt): nodes per 32-byte block
+// W and block stride S = W - 1.
+template <int FMT> struct Fmt;
+template <> struct Fmt<0> { static constexpr int W = 8, S = 7; };    // FP32
+template <> struct Fmt<1> { static constexpr int W = 16, S = 15; };  // BF16
+template <> struct Fmt<2> { static constexpr int W = 16, S = 15; };  // FP16
+template <> struct Fmt<3> { static constexpr int W = 12, S = 11; };  // BF16, block-scaled
+template <> struct Fmt<4> { static constexpr int W = 12, S = 11; };  // FP16, block-scaled
+constexpr int kMaxW = 16;
+
+// 256-bit read-only load of one block (32-byte aligned).
+__device__ __forceinline__ void ld8u(const uint32_t* p, uint32_t (&v)[8]) {
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
         : "l"(p));
 }
 
-// Read the 8 corner octets of block kb (one 32-byte sector each) and collapse
-// the H, B, n_e axes: win[o] = trilinear value at T_e node 7 kb + o.
-__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
-    const float* p = c.row + (long long)kb * 8;
-    float a[8], b[8], d[8];
-    ld8(p, a);
-    ld8(p + c.oN, b);
-#pragma unroll
-    for (int t = 0; t < 8; ++t) a[t] = lerpf(a[t], b[t], c.wn);
-    ld8(p + c.oB, b);
-    ld8(p + c.oB + c.oN, d);
-#pragma unroll
-    for (int t = 0; t < 8; ++t) a[t] = lerpf(a[t], lerpf(b[t], d[t], c.wn), c.wb);
-    const float* q = p + c.oH;
-    ld8(q, b);
-    ld8(q + c.oN, d);
-#pragma unroll
-    for (int t = 0; t < 8; ++t) b[t] = lerpf(b[t], d[t], c.wn);
-    float e[8];
-    ld8(q + c.oB, d);
-    ld8(q + c.oB + c.oN, e);
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        b[t] = lerpf(b[t], lerpf(d[t], e[t], c.wn), c.wb);
-        cc.win[t * kThreads] = lerpf(a[t], b[t], c.wh);
+__device__ __forceinline__ float half_bits(uint32_t h16, bool f16) {
+    return f16 ? __half2float(__ushort_as_half((unsigned short)h16)) : __uint_as_float(h16 << 16);
+}
+
+// Value of node t (0 <= t < W) of a block.
+template <int FMT>
+__device__ __forceinline__ float dec(const uint32_t (&r)[8], int t) {
+    if (FMT == 0) return __uint_as_float(r[t]);
+    if (FMT == 1 || FMT == 2) {
+        const uint32_t w = r[t >> 1];
+        return half_bits((t & 1) ? (w >> 16) : (w & 0xffffu), FMT == 2);
     }
-    cc.base = 7 * kb;
+    const uint32_t w = r[2 + (t >> 1)];
+    const float res = half_bits((t & 1) ? (w >> 16) : (w & 0xffffu), FMT == 4);
+    return fmaf(__uint_as_float(r[1]), res, __uint_as_float(r[0]));
+}
+
+// Read the 8 corner blocks of block kb (one 32-byte sector each) and collapse
+// the H, B, n_e axes: win[o] = trilinear value at T_e node S kb + o.
+template <int FMT>
+__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
+    constexpr int W = Fmt<FMT>::W;
+    const uint32_t* p = c.row + (long long)kb * 8;
+    if (FMT == 0) {
+        // FP32: all four (h, b) pairs reduced in registers
+        uint32_t a[8], b[8], d[8], e[8];
+        ld8u(p, a);
+        ld8u(p + c.oN, b);
+        float x[8], y[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = lerpf(dec<0>(a, t), dec<0>(b, t), c.wn);
+        ld8u(p + c.oB, b);
+        ld8u(p + c.oB + c.oN, d);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = lerpf(x[t], lerpf(dec<0>(b, t), dec<0>(d, t), c.wn), c.wb);
+        const uint32_t* q = p + c.oH;
+        ld8u(q, b);
+        ld8u(q + c.oN, d);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) y[t] = lerpf(dec<0>(b, t), dec<0>(d, t), c.wn);
+        ld8u(q + c.oB, d);
+        ld8u(q + c.oB + c.oN, e);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            y[t] = lerpf(y[t], lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
+            cc.win[t * kThreads] = lerpf(x[t], y[t], c.wh);
+        }
+    } else {
+        // 16-bit formats (W = 16 or 12 nodes): the partial sums go through
+        // the window in shared memory to bound register use
+        uint32_t r0[8], r1[8];
+        ld8u(p, r0);
+        ld8u(p + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t) cc.win[t * kThreads] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
+        ld8u(p + c.oB, r0);
+        ld8u(p + c.oB + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t)
+            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
+        const uint32_t* q = p + c.oH;
+        float hb[W];
+        ld8u(q, r0);
+        ld8u(q + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t) hb[t] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
+        ld8u(q + c.oB, r0);
+        ld8u(q + c.oB + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            const float h1 = lerpf(hb[t], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
+            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], h1, c.wh);
+        }
+    }
+    cc.base = Fmt<FMT>::S * kb;
 }
 
 // Energy (code units) that cooling removes in one sub-cycle at T_e, with
@@ -161,13 +220,14 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
 // The common path has no range branches: 2^d underflows to 0 where one
 // channel is negligible and tau_abs to 0 where the cell is thin; only
 // tau_abs > 2^60 (where tau_abs^2 would overflow) takes the asymptotic form.
+template <int FMT>
 __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, const CellC& c,
                                              Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
     const float* axT = S.ax + k.tab.axis_off[3];
     Sel s = select_axis(axT, nT, k.tab.inv_dl[3], Te, clamp);
     const int j = s.j;
-    if ((unsigned)(j - cc.base) > 6u) gather(c, j / 7, cc);
+    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
     const int o = j - cc.base;
     const float w = __saturatef(s.r * k.tab.inv_dl[3]);
     const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
@@ -194,6 +254,7 @@ struct Out {
     unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail
 };
 
+template <int FMT>
 __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* win, float rho, float B,
                                          float H, float ue, float ui) {
     Out o;
@@ -219,7 +280,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         c.oN = rowf;
         c.oB = rowf * T.n[2];
         c.oH = c.oB * T.n[1];
-        c.row = T.ls8 + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
+        c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
         c.wh = __saturatef(sh.r * T.inv_dl[0]);
         c.wb = __saturatef(sb.r * T.inv_dl[1]);
         c.wn = __saturatef(sn.r * T.inv_dl[2]);
@@ -275,7 +336,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         }
         sum_x += X;
         // ---- (ii) radiative cooling ----------------------------------------
-        const float q = cool_energy(k, S, c, cc, ue * inv_e, clamp);
+        const float q = cool_energy<FMT>(k, S, c, cc, ue * inv_e, clamp);
         float du = fminf(q, k.limiter * ue);
         if (k.mode == 1 && q > k.limiter * ue) {
             stiff = 1u;
@@ -284,7 +345,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
             float a = b - 60.f;
             const float ua = ex2a(a);
             unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
-            const float ga = ua - u0 + cool_energy(k, S, c, cc, ua * inv_e, trial);
+            const float ga = ua - u0 + cool_energy<FMT>(k, S, c, cc, ua * inv_e, trial);
             if (!(ga < 0.f)) {
                 fail = 1u;
             } else {
@@ -292,7 +353,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
                     const float m = 0.5f * (a + b);
                     if (m == a || m == b) break;
                     const float um = ex2a(m);
-                    const float g = um - u0 + cool_energy(k, S, c, cc, um * inv_e, trial);
+                    const float g = um - u0 + cool_energy<FMT>(k, S, c, cc, um * inv_e, trial);
                     if (g > 0.f) b = m; else a = m;
                 }
                 du = u0 - ex2a(0.5f * (a + b));
@@ -351,7 +412,7 @@ __host__ __device__ __forceinline__ int smem_table_floats(const StepK& k) { retu
 // staging area and leave by 128-bit streaming stores.  Warps synchronise
 // only with themselves (__syncwarp), so a slow cell delays one warp, not the
 // block.  The remainder (and unaligned arrays) take a scalar loop.
-template <bool VEC>
+template <bool VEC, int FMT>
 #ifndef COOL_MINB
 #define COOL_MINB 3
 #endif
@@ -366,12 +427,12 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     S.ax = sm;
     S.lb = sm + k.axes_floats;
     S.lc = sm + k.axes_floats + k.tab.n[3];
-    float* win = sm + smem_table_floats(k) + threadIdx.x;
+    float* win = sm + smem_table_floats(k) + threadIdx.x;   // kMaxW x kThreads window
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     long long scalar_start = 0;
     if (VEC) {
-        float* tile = sm + smem_table_floats(k) + 8 * kThreads + warp * 5 * kWarpCells;
+        float* tile = sm + smem_table_floats(k) + kMaxW * kThreads + warp * 5 * kWarpCells;
         float4* t4 = reinterpret_cast<float4*>(tile);
         const long long ntiles = n / kWarpCells;
         for (long long tw = (long long)blockIdx.x * kWarps + warp; tw < ntiles; tw += (long long)gridDim.x * kWarps) {
@@ -385,8 +446,8 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                Out o = step_cell(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
-                                  tile[3 * kWarpCells + j], tile[4 * kWarpCells + j]);
+                Out o = step_cell<FMT>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
+                                       tile[3 * kWarpCells + j], tile[4 * kWarpCells + j]);
                 // inputs of cell j are consumed: outputs reuse its slots
                 tile[3 * kWarpCells + j] = o.ue;
                 tile[4 * kWarpCells + j] = o.ui;
@@ -405,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
+        Out o = step_cell<FMT>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
@@ -607,9 +668,17 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     if (n == 0) return COOL_OK;
     bool vec = ((uintptr_t)rho | (uintptr_t)B | (uintptr_t)H | (uintptr_t)ue | (uintptr_t)ui |
                 (uintptr_t)ue_o | (uintptr_t)ui_o | (uintptr_t)qc | (uintptr_t)qx) % 16 == 0;
-    size_t smem = (size_t)(smem_table_floats(k) + 8 * kThreads) * sizeof(float);
+    size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads) * sizeof(float);
     if (vec) smem += (size_t)kWarps * 5 * kWarpCells * sizeof(float);
-    auto fn = vec ? k_step_f32<true> : k_step_f32<false>;
+    using KFn = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
+                         float*, float*, float*, float*, cool_counters*);
+    static const KFn table_v[5] = {k_step_f32<true, 0>, k_step_f32<true, 1>, k_step_f32<true, 2>,
+                                   k_step_f32<true, 3>, k_step_f32<true, 4>};
+    static const KFn table_s[5] = {k_step_f32<false, 0>, k_step_f32<false, 1>, k_step_f32<false, 2>,
+                                   k_step_f32<false, 3>, k_step_f32<false, 4>};
+    const int fmt = t->dev.fmt;
+    if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
+    KFn fn = vec ? table_v[fmt] : table_s[fmt];
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;

@@ -90,7 +90,10 @@ def test_host_validation_without_gpu(L):
     bad.T_max = bad.T_min
     assert L.cool_build_table(b.ref(bad), None, b.ref(h)) == b.COOL_EINVAL
     bad.T_max = 1e15
-    bad.dtype = b.COOL_BF16
+    bad.row_scaled = 1          # block scaling applies to 16-bit storage only
+    assert L.cool_build_table(b.ref(bad), None, b.ref(h)) == b.COOL_EUNSUPPORTED
+    bad.row_scaled = 0
+    bad.dtype = b.COOL_F64      # FP64 storage of the 4-D channel is not a step format
     assert L.cool_build_table(b.ref(bad), None, b.ref(h)) == b.COOL_EUNSUPPORTED
     assert L.cool_build_table(None, None, b.ref(h)) == b.COOL_ENULL
     # a handle that was never created is rejected without being read

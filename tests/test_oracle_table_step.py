@@ -277,3 +277,57 @@ def test_keys_f32_sequence(oracle):
     assert np.array_equal(k[:, 2], (f["rho"] * s_n).astype(np.float32))
     s_B = np.float32(math.sqrt(4 * math.pi * p.rho_scale) * C_LIGHT)
     assert np.array_equal(k[:, 1], (f["B"] * s_B).astype(np.float32))
+
+
+# ---- reduced-precision storage mirror (oracle.quant) -----------------------------
+
+def test_quant_roundings_match_torch():
+    """bf16 / f16 codes are round-to-nearest-even of the FP32 value: checked
+    against torch's CPU conversions (an independent implementation)."""
+    import torch
+    from oracle import quant
+    rng = np.random.default_rng(40)
+    x = np.concatenate([rng.uniform(-200, 200, 100000), rng.uniform(-1, 1, 100000)]).astype(np.float32)
+    tb = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16).astype(np.uint32)
+    assert np.array_equal(quant.bf16_bits(x), tb)
+    th = torch.from_numpy(x).to(torch.float16).view(torch.int16).numpy().view(np.uint16).astype(np.uint32)
+    assert np.array_equal(quant.f16_bits(x), th)
+
+
+def test_quant_pack_layout_and_error(oracle):
+    from oracle import quant
+    rng = np.random.default_rng(41)
+    nT = 40
+    ls = np.cumsum(rng.normal(0, 1.0, (30, nT)), axis=1) - 80.0
+    for fmt in range(5):
+        words, pairs = quant.pack(ls, nT, fmt)
+        W, S = quant.WS[fmt]
+        assert words.shape == (30, (nT - 1 + S - 1) // S, 8)
+        # pairs reproduce the exact values within the format's resolution
+        exact = np.stack([ls[:, :-1], ls[:, 1:]], axis=2)
+        err = np.abs(pairs - exact).max()
+        bound = {0: 2 ** -24 * 128, 1: 2 ** -8 * 128, 2: 2 ** -11 * 128, 3: None, 4: None}[fmt]
+        if bound is not None:
+            assert err <= bound
+        else:
+            half = 0.5 * (ls.max() - ls.min())
+            assert err <= (2 ** -8 if fmt == 3 else 2 ** -11) * half
+        if fmt in (0, 1, 2):
+            # plain formats: the pair values do not depend on the block
+            assert np.array_equal(pairs[:, 1:, 0], pairs[:, :-1, 1])
+    # block scaling is more accurate than plain 16-bit storage of large log2 values
+    assert quant.storage_error(ls, nT, 3) < quant.storage_error(ls, nT, 1)
+    assert quant.storage_error(ls, nT, 4) < quant.storage_error(ls, nT, 2)
+
+
+def test_step_pairs_equals_step_for_exact_pairs(oracle, small):
+    """The paired-table step with exact (unrounded) pairs equals the step."""
+    spec, T = small
+    nT = spec.n[3]
+    ls = T["ls"].reshape(-1, nT)
+    pairs = np.stack([ls[:, :-1], ls[:, 1:]], axis=2)
+    f = inputs.uniform(2000, seed=42)
+    p = oracle.Params(n_sub=4)
+    a = oracle.step(spec, T, p, **f)
+    b = oracle.step_pairs(spec, T["lb"], pairs, T["lc"], p, **f)
+    assert np.allclose(a[0], b[0], rtol=1e-14) and np.allclose(a[1], b[1], rtol=1e-14)
