@@ -103,9 +103,11 @@ typedef struct {
     double coulomb_clamp;     /* the exchange may move at most this fraction of the way to T_e = T_i (1) */
     int implicit_iters;       /* bisection halvings of the implicit solve, 1 .. 200 (60) */
     cool_path path;           /* COOL_PATH_L2WINDOW (others: not yet) */
-    int band_fp64;            /* FP32 fields: 0 (default) forms (gamma_i-1) u_i - (gamma_e-1) u_e
-                                 with an error-free FP32 product transformation in every cell;
-                                 1 evaluates the exchange in FP64 inside the equilibrium band */
+    int fp64_critical;        /* FP32 fields only.  0 (default): the Coulomb difference
+                                 (gamma_i-1) u_i - (gamma_e-1) u_e is formed with an error-free FP32
+                                 product transformation in every cell, and stiff cells are solved in
+                                 FP32.  1: FP64 inside the equilibrium band for the exchange, and the
+                                 implicit solve of stiff cells in FP64 on the FP64 table. */
 } cool_params;
 
 /* Per-call diagnostics, accumulated (atomically) into a caller-owned device
@@ -115,7 +117,7 @@ typedef struct {
     unsigned long long n_nonfinite;      /* invalid cell (non-finite or non-positive rho/u, negative B/H): passed through */
     unsigned long long n_stiff;          /* implicit solve entered (mode IMPLICIT) */
     unsigned long long n_fp64_coulomb;   /* Coulomb exchange inside the equilibrium band in some sub-cycle
-                                            (FP64 there when band_fp64 = 1; FP64 fields: always FP64) */
+                                            (FP64 there when fp64_critical = 1; FP64 fields: always FP64) */
     unsigned long long n_implicit_fail;  /* implicit bracket without sign change: limited explicit step taken */
     unsigned long long n_fallback;       /* reserved (surrogate fallback) */
 } cool_counters;

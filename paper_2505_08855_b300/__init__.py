@@ -60,12 +60,12 @@ class Params:
     coulomb_clamp: float = 1.0
     implicit_iters: int = 60
     path: int = _b.COOL_PATH_L2WINDOW
-    band_fp64: int = 0
+    fp64_critical: int = 0
 
     def c(self):
         return _b.cool_params(self.rho_scale, self.M_bh_msun, self.gamma_e, self.gamma_i,
                               self.dt, self.n_sub, self.mode, self.limiter_frac, self.eq_band,
-                              self.coulomb_clamp, self.implicit_iters, self.path, self.band_fp64)
+                              self.coulomb_clamp, self.implicit_iters, self.path, self.fp64_critical)
 
 
 def _stream_ptr(stream=None):

@@ -43,7 +43,7 @@ class cool_params(C.Structure):
                 ("gamma_i", C.c_double), ("dt", C.c_double), ("n_sub", C.c_int), ("mode", C.c_int),
                 ("limiter_frac", C.c_double), ("eq_band", C.c_double),
                 ("coulomb_clamp", C.c_double), ("implicit_iters", C.c_int), ("path", C.c_int),
-                ("band_fp64", C.c_int)]
+                ("fp64_critical", C.c_int)]
 
 
 class cool_counters(C.Structure):

@@ -143,7 +143,7 @@ cool_status validate_params(const cool_params* p) {
     if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
     if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
     if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
-    if (p->band_fp64 != 0 && p->band_fp64 != 1) return COOL_EINVAL;
+    if (p->fp64_critical != 0 && p->fp64_critical != 1) return COOL_EINVAL;
     return COOL_OK;
 }
 
@@ -360,7 +360,7 @@ cool_status cool_params_default(cool_params* p) {
     p->coulomb_clamp = 1.0;
     p->implicit_iters = 60;
     p->path = COOL_PATH_L2WINDOW;
-    p->band_fp64 = 0;
+    p->fp64_critical = 0;
     return COOL_OK;
 }
 

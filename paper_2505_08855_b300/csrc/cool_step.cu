@@ -45,13 +45,98 @@ __device__ __forceinline__ float lg2a(float x) {
     return y;
 }
 
+
+// Shared-memory view of the small table parts.
+struct Smem {
+    const float* ax;   // concatenated axes (x, rx, lx per axis)
+    const float* lb;
+    const float* lc;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 instantiation: all arithmetic in FP64 on the FP64 table channels
+// (the same algorithm; index selection compares the FP64 key with the FP32
+// nodes, weights from FP64 log2).
+// ---------------------------------------------------------------------------
+struct StepK64 {
+    DevTable tab;
+    double s_n, s_B, s_H, s_Te, s_Ti, ce, ci, hs, escale;
+    double limiter, eq_band, clamp;
+    int n_sub, mode, iters;
+};
+
+__device__ int select64(const DevTable& T, int a, double key, double& w, unsigned& clamp) {
+    const int n = T.n[a];
+    const float* x = T.axes + T.axis_off[a];
+    int j = 0;
+    if (!(key >= (double)x[0])) {
+        clamp = 1u;
+    } else {
+        int lo = 0, hi = n - 2;  // largest j in [0, n-2] with x[j] <= key
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if ((double)x[mid] <= key) lo = mid; else hi = mid - 1;
+        }
+        j = lo;
+        if (key > (double)x[n - 1]) clamp = 1u;
+    }
+    double wl = key > 0.0 ? (log2(key) - (T.l0_64[a] + j * T.dl64[a])) / T.dl64[a] : 0.0;
+    w = fmin(fmax(wl, 0.0), 1.0);
+    return j;
+}
+
+struct Cell64 {
+    int jh, jb, jn;
+    double wh, wb, wn, ne, Hc;
+};
+
+__device__ double cool_q64(const StepK64& k, const Cell64& c, double ue, double rho, unsigned& clamp) {
+    const DevTable& T = k.tab;
+    double Te = k.s_Te * ue / rho;
+    double wt;
+    int jt = select64(T, 3, Te, wt, clamp);
+    const int nB = T.n[1], nN = T.n[2], nT = T.n[3];
+    double ls = 0.0;
+    for (int cidx = 0; cidx < 16; ++cidx) {
+        int bh = cidx & 1, bb = (cidx >> 1) & 1, bn = (cidx >> 2) & 1, bt = (cidx >> 3) & 1;
+        double wgt = (bh ? c.wh : 1.0 - c.wh) * (bb ? c.wb : 1.0 - c.wb) * (bn ? c.wn : 1.0 - c.wn) *
+                     (bt ? wt : 1.0 - wt);
+        long long idx = (((long long)(c.jh + bh) * nB + (c.jb + bb)) * nN + (c.jn + bn)) * nT + jt + bt;
+        ls += wgt * T.ls64[idx];
+    }
+    double lb = (1.0 - wt) * T.lb64[jt] + wt * T.lb64[jt + 1];
+    double qthin = c.ne * c.ne * exp2(lb) + exp2(ls);
+    double bb4 = 4.0 * kSigSB * Te * Te * Te * Te;
+    double tau_sca = 2.0 * c.ne * kSigT * c.Hc;
+    double tau_abs = c.Hc * qthin / bb4;
+    double Q = qthin / (1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca)));
+    return k.hs * Q / k.escale;
+}
+
+// Backward Euler of a stiff cell in FP64 on the FP64 table: bisection in
+// log2 u over [u0 2^-60, u0] (iters halvings).  Returns false when the
+// bracket has no sign change.
+__device__ __noinline__ bool implicit_fp64(const StepK64& k, const Cell64& c, double rho, double u0, double& u_out) {
+    unsigned dummy = 0u;
+    double a = log2(u0) - 60.0, b = log2(u0);
+    if (!(exp2(a) - u0 + cool_q64(k, c, exp2(a), rho, dummy) < 0.0)) return false;
+    for (int it = 0; it < k.iters; ++it) {
+        double m = 0.5 * (a + b);
+        double um = exp2(m);
+        if (um - u0 + cool_q64(k, c, um, rho, dummy) > 0.0) b = m; else a = m;
+    }
+    u_out = exp2(0.5 * (a + b));
+    return true;
+}
+
 struct StepK {
     DevTable tab;
     float s_n, s_B, s_H, s_Te, s_Ti;  // FP32 key scales (rounded once from FP64)
     float ce, ci, inv_cec;            // gamma - 1, 1/(ce + ci)
     double ce64, ci64, inv_cec64;
     float s_K;                        // m_p c^2 / k_B  (T_s = (gamma_s - 1) s_K u_s / rho)
-    int band_fp64;
+    int fp64_critical;
+    StepK64 k64;                      // FP64 constants for stiff cells when fp64_critical
     float l_hs_e;                     // log2(h / e_scale)
     float l_bb;                       // log2(4 sigma_SB h / e_scale)
     float two_sigT;                   // 2 sigma_T
@@ -59,13 +144,6 @@ struct StepK {
     int n_sub, mode, iters;
     int smem_floats;                  // floats of axes + lb + lc in shared memory
     int axes_floats;
-};
-
-// Shared-memory view of the small table parts.
-struct Smem {
-    const float* ax;   // concatenated axes (x, rx, lx per axis)
-    const float* lb;
-    const float* lc;
 };
 
 struct Sel {
@@ -249,12 +327,94 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     return ex2a(fminf(lq, 126.f));
 }
 
+// Backward Euler u' = u0 - q(u') of a stiff cell (q(u0) > limiter u0) in
+// FP32.  Bracket [u0 2^-60, u0]: g(u0) = q(u0) > 0 and g(u0 2^-60) < 0 is
+// checked (false when it fails).  Illinois (modified regula falsi) first on
+// G(x) = log2((2^x + q(2^x))/u0), x = log2 u, which is close to piecewise
+// linear over the 60 octaves, then on g(u) = u + q(u) - u0 in u once the
+// bracket is tight (FP32 x cannot resolve u to better than ~1e-6).  At most
+// implicit_iters evaluations.  Kept out of line: stiff cells are a minority.
+template <int FMT>
+__device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
+                                           float inv_e, float u0, float q0, float& u_out) {
+    const float inv_u0 = 1.f / u0;
+    unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
+    float xb = lg2a(u0);
+    float xa = xb - 60.f;
+    const float ua0 = ex2a(xa);
+    const float qa0 = cool_energy<FMT>(k, S, c, cc, ua0 * inv_e, trial);
+    if (!(ua0 - u0 + qa0 < 0.f)) return false;
+    float Gb = lg2a(fmaf(q0, inv_u0, 1.f));
+    float Ga = lg2a((ua0 + qa0) * inv_u0);
+    int side = 0, it = 0;
+    for (; it < k.iters; ++it) {
+        if (xb - xa < 1e-3f) break;
+        float x = xb - Gb * (xb - xa) / (Gb - Ga);
+        if (!(x > xa && x < xb)) x = 0.5f * (xa + xb);
+        const float u = ex2a(x);
+        const float G = lg2a((u + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
+        if (G > 0.f) {
+            xb = x; Gb = G;
+            if (side == 1) Ga *= 0.5f;
+            side = 1;
+        } else {
+            xa = x; Ga = G;
+            if (side == -1) Gb *= 0.5f;
+            side = -1;
+        }
+    }
+    float a = ex2a(xa), b = ex2a(xb);
+    float ga = a - u0 + cool_energy<FMT>(k, S, c, cc, a * inv_e, trial);
+    float gb = b - u0 + cool_energy<FMT>(k, S, c, cc, b * inv_e, trial);
+    // an end whose residual rounds to the wrong sign is the root to rounding
+    float u = !(ga < 0.f) ? a : (!(gb > 0.f) ? b : 0.5f * (a + b));
+    side = 0;
+    for (; it < k.iters && ga < 0.f && gb > 0.f; ++it) {
+        u = b - gb * (b - a) / (gb - ga);
+        if (!(u > a && u < b)) u = 0.5f * (a + b);
+        if (b - a <= 2.4e-7f * b) break;
+        const float g = u - u0 + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial);
+        if (g > 0.f) {
+            b = u; gb = g;
+            if (side == 1) ga *= 0.5f;
+            side = 1;
+        } else if (g < 0.f) {
+            a = u; ga = g;
+            if (side == -1) gb *= 0.5f;
+            side = -1;
+        } else {
+            break;
+        }
+    }
+    u_out = u;
+    return true;
+}
+
+// The same solve in FP64 on the FP64 table (fp64_critical): the cell's H, B,
+// n_e selections are redone with FP64 keys and implicit_fp64 bisects.
+__device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
+                                                float u0, float& u_out) {
+    Cell64 c64;
+    unsigned dummy = 0u;
+    c64.ne = (double)rho * k.k64.s_n;
+    c64.Hc = (double)H * k.k64.s_H;
+    c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
+    c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
+    c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
+    double u1;
+    if (!implicit_fp64(k.k64, c64, (double)rho, (double)u0, u1)) return false;
+    u_out = (float)u1;
+    return true;
+}
+
 struct Out {
     float ue, ui, qc, qx;
     unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail
 };
 
-template <int FMT>
+// VAR: bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in
+// (the explicit FP32 kernel carries no solver code and no FP64 code).
+template <int FMT, int VAR>
 __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* win, float rho, float B,
                                          float H, float ue, float ui) {
     Out o;
@@ -315,7 +475,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         const bool in_band = fabsf(Te - Ti) <= k.eq_band * Ti;
         band |= in_band ? 1u : 0u;
         float X;
-        if (k.band_fp64 && in_band) {
+        if ((VAR & 2) && in_band) {
             // literal FP64 evaluation inside the band
             double D = k.ci64 * (double)ui - k.ce64 * (double)ue;
             double Xd = (double)rate * ((double)kr * D);
@@ -338,26 +498,13 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         // ---- (ii) radiative cooling ----------------------------------------
         const float q = cool_energy<FMT>(k, S, c, cc, ue * inv_e, clamp);
         float du = fminf(q, k.limiter * ue);
-        if (k.mode == 1 && q > k.limiter * ue) {
+        if ((VAR & 1) && q > k.limiter * ue) {
             stiff = 1u;
-            const float u0 = ue;
-            float b = lg2a(u0);
-            float a = b - 60.f;
-            const float ua = ex2a(a);
-            unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
-            const float ga = ua - u0 + cool_energy<FMT>(k, S, c, cc, ua * inv_e, trial);
-            if (!(ga < 0.f)) {
-                fail = 1u;
-            } else {
-                for (int it = 0; it < k.iters; ++it) {
-                    const float m = 0.5f * (a + b);
-                    if (m == a || m == b) break;
-                    const float um = ex2a(m);
-                    const float g = um - u0 + cool_energy<FMT>(k, S, c, cc, um * inv_e, trial);
-                    if (g > 0.f) b = m; else a = m;
-                }
-                du = u0 - ex2a(0.5f * (a + b));
-            }
+            float u1;
+            const bool ok = (VAR & 2) ? implicit_fp64_cell(k, T, rho, B, H, ue, u1)
+                                      : implicit_fp32<FMT>(k, S, c, cc, inv_e, ue, q, u1);
+            if (ok) du = ue - u1;
+            else fail = 1u;
         }
         ue -= du;
         sum_q += du;
@@ -412,7 +559,7 @@ __host__ __device__ __forceinline__ int smem_table_floats(const StepK& k) { retu
 // staging area and leave by 128-bit streaming stores.  Warps synchronise
 // only with themselves (__syncwarp), so a slow cell delays one warp, not the
 // block.  The remainder (and unaligned arrays) take a scalar loop.
-template <bool VEC, int FMT>
+template <bool VEC, int FMT, int VAR>
 #ifndef COOL_MINB
 #define COOL_MINB 3
 #endif
@@ -446,8 +593,8 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                Out o = step_cell<FMT>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
-                                       tile[3 * kWarpCells + j], tile[4 * kWarpCells + j]);
+                Out o = step_cell<FMT, VAR>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
+                                            tile[3 * kWarpCells + j], tile[4 * kWarpCells + j]);
                 // inputs of cell j are consumed: outputs reuse its slots
                 tile[3 * kWarpCells + j] = o.ue;
                 tile[4 * kWarpCells + j] = o.ui;
@@ -466,73 +613,13 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
+        Out o = step_cell<FMT, VAR>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
         if (qx_out) qx_out[i] = o.qx;
         if (cnt) count_flags(o.flags, cnt);
     }
-}
-
-// ---------------------------------------------------------------------------
-// FP64 instantiation: all arithmetic in FP64 on the FP64 table channels
-// (the same algorithm; index selection compares the FP64 key with the FP32
-// nodes, weights from FP64 log2).
-// ---------------------------------------------------------------------------
-struct StepK64 {
-    DevTable tab;
-    double s_n, s_B, s_H, s_Te, s_Ti, ce, ci, hs, escale;
-    double limiter, eq_band, clamp;
-    int n_sub, mode, iters;
-};
-
-__device__ int select64(const DevTable& T, int a, double key, double& w, unsigned& clamp) {
-    const int n = T.n[a];
-    const float* x = T.axes + T.axis_off[a];
-    int j = 0;
-    if (!(key >= (double)x[0])) {
-        clamp = 1u;
-    } else {
-        int lo = 0, hi = n - 2;  // largest j in [0, n-2] with x[j] <= key
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if ((double)x[mid] <= key) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
-        if (key > (double)x[n - 1]) clamp = 1u;
-    }
-    double wl = key > 0.0 ? (log2(key) - (T.l0_64[a] + j * T.dl64[a])) / T.dl64[a] : 0.0;
-    w = fmin(fmax(wl, 0.0), 1.0);
-    return j;
-}
-
-struct Cell64 {
-    int jh, jb, jn;
-    double wh, wb, wn, ne, Hc;
-};
-
-__device__ double cool_q64(const StepK64& k, const Cell64& c, double ue, double rho, unsigned& clamp) {
-    const DevTable& T = k.tab;
-    double Te = k.s_Te * ue / rho;
-    double wt;
-    int jt = select64(T, 3, Te, wt, clamp);
-    const int nB = T.n[1], nN = T.n[2], nT = T.n[3];
-    double ls = 0.0;
-    for (int cidx = 0; cidx < 16; ++cidx) {
-        int bh = cidx & 1, bb = (cidx >> 1) & 1, bn = (cidx >> 2) & 1, bt = (cidx >> 3) & 1;
-        double wgt = (bh ? c.wh : 1.0 - c.wh) * (bb ? c.wb : 1.0 - c.wb) * (bn ? c.wn : 1.0 - c.wn) *
-                     (bt ? wt : 1.0 - wt);
-        long long idx = (((long long)(c.jh + bh) * nB + (c.jb + bb)) * nN + (c.jn + bn)) * nT + jt + bt;
-        ls += wgt * T.ls64[idx];
-    }
-    double lb = (1.0 - wt) * T.lb64[jt] + wt * T.lb64[jt + 1];
-    double qthin = c.ne * c.ne * exp2(lb) + exp2(ls);
-    double bb4 = 4.0 * kSigSB * Te * Te * Te * Te;
-    double tau_sca = 2.0 * c.ne * kSigT * c.Hc;
-    double tau_abs = c.Hc * qthin / bb4;
-    double Q = qthin / (1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca)));
-    return k.hs * Q / k.escale;
 }
 
 __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const double* Bf,
@@ -631,6 +718,27 @@ int sm_count() {
 
 }  // namespace
 
+void fill_k64(const cool_table* t, const cool_params* p, StepK64& k) {
+    k.tab = t->dev;
+    double rg, hs, escale;
+    fill_common(t, p, rg, hs, escale);
+    k.s_n = p->rho_scale / kMP;
+    k.s_B = sqrt(4.0 * kPi * p->rho_scale) * kC;
+    k.s_H = rg;
+    k.ce = p->gamma_e - 1.0;
+    k.ci = p->gamma_i - 1.0;
+    k.s_Te = k.ce * kMP * kC * kC / kKB;
+    k.s_Ti = k.ci * kMP * kC * kC / kKB;
+    k.hs = hs;
+    k.escale = escale;
+    k.limiter = p->limiter_frac;
+    k.eq_band = p->eq_band;
+    k.clamp = p->coulomb_clamp;
+    k.n_sub = p->n_sub;
+    k.mode = (int)p->mode;
+    k.iters = p->implicit_iters;
+}
+
 cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long n,
                             const float* rho, const float* B, const float* H,
                             const float* ue, const float* ui, float* ue_o, float* ui_o,
@@ -651,7 +759,8 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     k.ci = (float)k.ci64;
     k.inv_cec = (float)k.inv_cec64;
     k.s_K = (float)(kMP * kC * kC / kKB);
-    k.band_fp64 = p->band_fp64;
+    k.fp64_critical = p->fp64_critical;
+    fill_k64(t, p, k.k64);
     k.l_hs_e = (float)log2(hs / escale);
     k.l_bb = (float)log2(4.0 * kSigSB * hs / escale);
     k.two_sigT = (float)(2.0 * kSigT);
@@ -672,13 +781,16 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     if (vec) smem += (size_t)kWarps * 5 * kWarpCells * sizeof(float);
     using KFn = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
                          float*, float*, float*, float*, cool_counters*);
-    static const KFn table_v[5] = {k_step_f32<true, 0>, k_step_f32<true, 1>, k_step_f32<true, 2>,
-                                   k_step_f32<true, 3>, k_step_f32<true, 4>};
-    static const KFn table_s[5] = {k_step_f32<false, 0>, k_step_f32<false, 1>, k_step_f32<false, 2>,
-                                   k_step_f32<false, 3>, k_step_f32<false, 4>};
+#define COOL_KV(V, F) k_step_f32<V, F, 0>, k_step_f32<V, F, 1>, k_step_f32<V, F, 2>, k_step_f32<V, F, 3>
+    static const KFn table_v[5][4] = {{COOL_KV(true, 0)}, {COOL_KV(true, 1)}, {COOL_KV(true, 2)},
+                                      {COOL_KV(true, 3)}, {COOL_KV(true, 4)}};
+    static const KFn table_s[5][4] = {{COOL_KV(false, 0)}, {COOL_KV(false, 1)}, {COOL_KV(false, 2)},
+                                      {COOL_KV(false, 3)}, {COOL_KV(false, 4)}};
+#undef COOL_KV
     const int fmt = t->dev.fmt;
     if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
-    KFn fn = vec ? table_v[fmt] : table_s[fmt];
+    const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0);
+    KFn fn = vec ? table_v[fmt][var] : table_s[fmt][var];
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;

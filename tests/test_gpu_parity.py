@@ -133,15 +133,18 @@ def test_step_fp64_parity(cool, oracle, cfg1, mode, n_sub):
     assert got[4]["nonfinite"] == 0
 
 
+@pytest.mark.parametrize("fp64_critical", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n_sub", [4, 8])
-def test_step_fp32_parity(cool, oracle, cfg1, mode, n_sub):
+def test_step_fp32_parity(cool, oracle, cfg1, mode, n_sub, fp64_critical):
     tab, ospec, OT = cfg1
     f = inputs.make("uniform_32c", dtype=np.float32)
     want = oracle.step(ospec, OT, oracle.Params(n_sub=n_sub, mode=mode), **f)
-    got = run_gpu(cool, tab, cool.Params(n_sub=n_sub, mode=mode), to_dev(f, torch.float32))
+    got = run_gpu(cool, tab, cool.Params(n_sub=n_sub, mode=mode, fp64_critical=fp64_critical),
+                  to_dev(f, torch.float32))
     eu, ei = rel(got[0], want[0]), rel(got[1], want[1])
-    print(f"\nFP32 mode {mode} n_sub {n_sub}: max rel u_e {eu.max():.2e}, u_i {ei.max():.2e}")
+    print(f"\nFP32 mode {mode} n_sub {n_sub} fp64_critical {fp64_critical}: "
+          f"max rel u_e {eu.max():.2e}, u_i {ei.max():.2e}")
     assert eu.max() <= TOL32 and ei.max() <= TOL32
     # diagnostics: conservation identities hold on the GPU outputs
     ue0 = f["ue"].astype(np.float64)
