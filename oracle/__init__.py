@@ -127,6 +127,8 @@ def _declare(L):
         "orc_cool_q_cell": (_d, [_P, _P, _P, _P, _i, _P, _d, _d, _d, _d]),
         "orc_step_pairs": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P,
                                 _P, _P, _P, _P, _P, _i]),
+        "orc_step_bwd": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P,
+                              _P, _P, _P, _P, _P, _P, _i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -358,6 +360,35 @@ def step_pairs(spec, lb, lsp, lc, params, rho, B, H, ue, ui, nthreads=0):
     if rc != 0:
         raise RuntimeError(f"orc_step_pairs failed: {rc}")
     return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
+
+
+def step_bwd(spec, tables, params, rho, B, H, ue, ui, g_ue, g_ui, table_grads=False, nthreads=0):
+    """Adjoint of step(): returns dict with g_rho, g_B, g_H, g_ue, g_ui (per
+    cell), the table adjoints g_lb, g_ls, g_lc (natural layouts) when asked,
+    sig (hash of each cell's discrete decisions) and the forward outputs."""
+    f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui, g_ue, g_ui)]
+    n = f[0].size
+    grads = np.zeros((n, 5))
+    sig = np.zeros(n, np.uint64)
+    ue_o = np.zeros(n)
+    ui_o = np.zeros(n)
+    nH, nB, nN, nT, nC = spec.n
+    g_lb = np.zeros(nT) if table_grads else None
+    g_ls = np.zeros(nH * nB * nN * nT) if table_grads else None
+    g_lc = np.zeros(nC * nC) if table_grads else None
+    s = spec.c()
+    p = params.c()
+    lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
+    rc = lib().orc_step_bwd(_ref(s), _ptr(tables["lb"]), _ptr(tables["ls"]), _ptr(lc), _ref(p), n,
+                            *[_ptr(a) for a in f], _ptr(grads), _ptr(g_lb), _ptr(g_ls), _ptr(g_lc),
+                            _ptr(sig), _ptr(ue_o), _ptr(ui_o), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_bwd failed: {rc}")
+    out = dict(g_rho=grads[:, 0], g_B=grads[:, 1], g_H=grads[:, 2], g_ue=grads[:, 3], g_ui=grads[:, 4],
+               sig=sig, ue=ue_o, ui=ui_o)
+    if table_grads:
+        out.update(g_lb=g_lb, g_ls=g_ls, g_lc=g_lc.reshape(nC, nC))
+    return out
 
 
 def keys_f32(params, rho, B, H, ue, ui):

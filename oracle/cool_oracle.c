@@ -764,3 +764,312 @@ void orc_keys_f32(const orc_params* p, long long n, const float* rho, const floa
         keys[5 * i + 4] = ui[i] * inv_i;
     }
 }
+
+/* ===================================================================== */
+/* Adjoint of the O2 step.                                                */
+/* Reverse sweep over the sub-cycles (states recomputed by a forward pass */
+/* and kept per sub-cycle); inside one sub-cycle the partial derivatives  */
+/* of the Coulomb transfer X and of the cooling energy q come from        */
+/* forward-mode dual numbers carrying d/d(u_e, u_i, rho, B, H) and one    */
+/* seed used for d/d(Q_thin).  The implicit update is differentiated by   */
+/* the implicit-function theorem at the root, not through the bisection.  */
+/* Pinned by kink-aware central finite differences (tests).               */
+/* ===================================================================== */
+#define ND 6
+typedef struct { double v, d[ND]; } dn;
+
+static dn dc(double v) { dn r; r.v = v; for (int k = 0; k < ND; ++k) r.d[k] = 0.0; return r; }
+static dn dvar(double v, int k) { dn r = dc(v); r.d[k] = 1.0; return r; }
+static dn dadd(dn a, dn b) { dn r; r.v = a.v + b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
+static dn dsub(dn a, dn b) { dn r; r.v = a.v - b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
+static dn dmul(dn a, dn b) { dn r; r.v = a.v * b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+static dn ddiv(dn a, dn b) {
+    dn r; r.v = a.v / b.v;
+    for (int k = 0; k < ND; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static dn dscale(dn a, double s) { dn r; r.v = a.v * s; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * s; return r; }
+static dn dshift(dn a, double s) { a.v += s; return a; }
+static dn dlog2(dn a) { dn r; r.v = log2(a.v); for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] / (a.v * log(2.0)); return r; }
+static dn dexp2(dn a) { dn r; r.v = exp2(a.v); for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * r.v * log(2.0); return r; }
+
+/* Selection with a differentiable weight: w = (log2 key - l_j)/dl inside
+ * the cell, constant where the weight is clamped (outside the table). */
+static int sel_dn(const orc_axis* ax, dn key, int* j, dn* w, unsigned long long* sig) {
+    double wv;
+    int cl = select_ax(ax, key.v, j, &wv);
+    double raw = (log2(key.v) - (ax->l0 + *j * ax->dl)) / ax->dl;
+    if (raw < 0.0 || raw > 1.0) *w = dc(wv);
+    else *w = dscale(dshift(dlog2(key), -(ax->l0 + *j * ax->dl)), 1.0 / ax->dl);
+    if (sig) *sig = (*sig ^ (unsigned long long)(*j + 1000 * cl)) * 1099511628211ull;
+    return cl;
+}
+
+typedef struct {
+    double rg, hs, escale, sTe, sTi, ce, ci, s_n, s_B;
+} bwd_const;
+
+static void bwd_consts(const orc_params* p, bwd_const* k) {
+    k->rg = (O_G * (p->M_bh_msun * O_MSUN)) / (O_C * O_C);
+    k->hs = p->dt * (k->rg / O_C) / p->n_sub;
+    k->escale = p->rho_scale * O_C * O_C;
+    k->ce = p->gamma_e - 1.0; k->ci = p->gamma_i - 1.0;
+    k->sTe = k->ce * O_MP * O_C * O_C / O_KB;
+    k->sTi = k->ci * O_MP * O_C * O_C / O_KB;
+    k->s_n = p->rho_scale / O_MP;
+    k->s_B = sqrt(4.0 * O_PI * p->rho_scale) * O_C;
+}
+
+/* Cooling energy of one sub-cycle as a dual number (components 0 u_e,
+ * 2 rho, 3 B, 4 H, 5 = d/dQ_thin), with what the table scatter needs. */
+typedef struct {
+    dn q;
+    int jt; double wt;
+    int j[3]; double w[3];
+    double lqs, lqb, ne;
+} qinfo;
+
+static void q_dn(const orc_rates* R, const bwd_const* K, dn rho, dn B, dn H, dn ue, qinfo* o,
+                 unsigned long long* sig) {
+    dn ne = dscale(rho, K->s_n);
+    dn Bg = dscale(B, K->s_B);
+    dn Hc = dscale(H, K->rg);
+    dn Te = ddiv(dscale(ue, K->sTe), rho);
+    dn w[4];
+    int j[4];
+    sel_dn(&R->ax[0], Hc, &j[0], &w[0], sig);
+    sel_dn(&R->ax[1], Bg, &j[1], &w[1], sig);
+    sel_dn(&R->ax[2], ne, &j[2], &w[2], sig);
+    sel_dn(&R->ax[3], Te, &j[3], &w[3], sig);
+    dn lqs = dc(0.0);
+    for (int c = 0; c < 16; ++c) {
+        dn wt = dc(1.0);
+        int idx[4];
+        for (int a = 0; a < 4; ++a) {
+            int bit = (c >> a) & 1;
+            idx[a] = j[a] + bit;
+            wt = dmul(wt, bit ? w[a] : dsub(dc(1.0), w[a]));
+        }
+        lqs = dadd(lqs, dscale(wt, syn_at(R->s, R->ls, 0, idx[0], idx[1], idx[2], idx[3])));
+    }
+    dn lqb = dadd(dscale(dsub(dc(1.0), w[3]), R->lb[j[3]]), dscale(w[3], R->lb[j[3] + 1]));
+    dn qthin = dadd(dmul(dmul(ne, ne), dexp2(lqb)), dexp2(lqs));
+    qthin.d[5] = 1.0;
+    dn T2 = dmul(Te, Te);
+    dn bb = dscale(dmul(T2, T2), 4.0 * O_SIGSB);
+    dn tau_sca = dscale(dmul(ne, Hc), 2.0 * O_SIGT);
+    dn tau_abs = ddiv(dmul(Hc, qthin), bb);
+    dn den = dadd(dc(1.0), dmul(tau_abs, dadd(dc(sqrt(3.0)), dscale(dadd(tau_abs, tau_sca), 1.5))));
+    o->q = dscale(ddiv(qthin, den), K->hs / K->escale);
+    o->jt = j[3]; o->wt = w[3].v;
+    for (int a = 0; a < 3; ++a) { o->j[a] = j[a]; o->w[a] = w[a].v; }
+    o->lqs = lqs.v; o->lqb = lqb.v; o->ne = ne.v;
+}
+
+/* Coulomb transfer X of one sub-cycle as a dual number (components 0 u_e,
+ * 1 u_i, 2 rho). */
+typedef struct {
+    dn X;
+    int clamped;
+    int ji, je; double wi, we;
+} xinfo;
+
+static void x_dn(const orc_rates* R, const orc_params* p, const bwd_const* K, dn rho, dn ue, dn ui, xinfo* o,
+                 unsigned long long* sig) {
+    dn Te = ddiv(dscale(ue, K->sTe), rho);
+    dn Ti = ddiv(dscale(ui, K->sTi), rho);
+    dn wi, we;
+    sel_dn(&R->ax[4], Ti, &o->ji, &wi, sig);
+    sel_dn(&R->ax[4], Te, &o->je, &we, sig);
+    int N = R->s->n[4];
+    const double* lc = R->lc;
+    dn lC = dadd(dadd(dscale(dmul(dsub(dc(1.0), wi), dsub(dc(1.0), we)), lc[o->ji * N + o->je]),
+                      dscale(dmul(dsub(dc(1.0), wi), we), lc[o->ji * N + o->je + 1])),
+                 dadd(dscale(dmul(wi, dsub(dc(1.0), we)), lc[(o->ji + 1) * N + o->je]),
+                      dscale(dmul(wi, we), lc[(o->ji + 1) * N + o->je + 1])));
+    dn ne = dscale(rho, K->s_n);
+    dn X = dscale(dmul(dmul(dmul(ne, ne), dexp2(lC)), dsub(Ti, Te)), K->hs / K->escale);
+    dn Xeq = dscale(dsub(dscale(ui, K->ci), dscale(ue, K->ce)), 1.0 / (K->ce + K->ci));
+    double lim = p->coulomb_clamp * fabs(Xeq.v);
+    o->clamped = 0;
+    if (fabs(X.v) > lim) {
+        double sgn = (X.v >= 0.0 ? 1.0 : -1.0) * (Xeq.v >= 0.0 ? 1.0 : -1.0);
+        X = dscale(Xeq, p->coulomb_clamp * sgn);
+        o->clamped = 1;
+    }
+    if (sig) *sig = (*sig ^ (unsigned long long)(o->clamped + 7)) * 1099511628211ull;
+    o->X = X;
+    o->wi = wi.v; o->we = we.v;
+}
+
+#define ORC_MAXSUB 64
+typedef struct { double ue, ui, ue1, ustar; int branch; } sub_state;  /* branch: 0 free, 1 limited, 2 implicit */
+
+/* Adjoint of one cell.  g_out_e, g_out_i: adjoints of u_e_out, u_i_out.
+ * Returns the input adjoints; table adjoints are added (atomically) into
+ * g_lb / g_ls / g_lc when given.  *sig hashes every discrete decision. */
+static void cell_bwd(const orc_rates* R, const orc_params* p, double rho, double B, double H, double ue0,
+                     double ui0, double g_out_e, double g_out_i, double* g, double* g_lb, double* g_ls,
+                     double* g_lc, unsigned long long* sig, double* ue_out, double* ui_out) {
+    bwd_const K;
+    bwd_consts(p, &K);
+    sub_state st[ORC_MAXSUB];
+    for (int k = 0; k < 5; ++k) g[k] = 0.0;
+    *sig = 1469598103934665603ull;
+    if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue0) && isfinite(ui0)) ||
+        !(rho > 0.0) || !(ue0 > 0.0) || !(ui0 > 0.0) || B < 0.0 || H < 0.0 || p->n_sub > ORC_MAXSUB) {
+        g[3] = g_out_e; g[4] = g_out_i;   /* pass-through cell */
+        *ue_out = ue0; *ui_out = ui0;
+        return;
+    }
+    dn drho = dc(rho), dB = dc(B), dH = dc(H);
+    double ue = ue0, ui = ui0;
+    /* forward, keeping the per-sub-cycle states and branches */
+    for (int k = 0; k < p->n_sub; ++k) {
+        xinfo xi;
+        x_dn(R, p, &K, drho, dc(ue), dc(ui), &xi, sig);
+        st[k].ue = ue; st[k].ui = ui;
+        ue += xi.X.v; ui -= xi.X.v;
+        st[k].ue1 = ue;
+        qinfo qi;
+        q_dn(R, &K, drho, dB, dH, dc(ue), &qi, sig);
+        double q = qi.q.v, du;
+        if (p->mode == 1 && q > p->limiter_frac * ue) {
+            double a = log2(ue) - 60.0, b = log2(ue);
+            qinfo qa;
+            q_dn(R, &K, drho, dB, dH, dc(exp2(a)), &qa, NULL);
+            if (!(exp2(a) - ue + qa.q.v < 0.0)) {
+                st[k].branch = 1; du = p->limiter_frac * ue;
+            } else {
+                for (int it = 0; it < p->implicit_iters; ++it) {
+                    double m = 0.5 * (a + b);
+                    qinfo qm;
+                    q_dn(R, &K, drho, dB, dH, dc(exp2(m)), &qm, NULL);
+                    if (exp2(m) - ue + qm.q.v > 0.0) b = m; else a = m;
+                }
+                st[k].ustar = exp2(0.5 * (a + b));
+                st[k].branch = 2; du = ue - st[k].ustar;
+            }
+        } else if (q < p->limiter_frac * ue) {
+            st[k].branch = 0; du = q;
+        } else {
+            st[k].branch = 1; du = p->limiter_frac * ue;
+        }
+        *sig = (*sig ^ (unsigned long long)(st[k].branch + 17)) * 1099511628211ull;
+        ue -= du;
+    }
+    *ue_out = ue; *ui_out = ui;
+    /* reverse sweep */
+    double ge = g_out_e, gi = g_out_i;     /* adjoints of (u_e, u_i) after sub-cycle k */
+    double grho = 0.0, gB = 0.0, gH = 0.0;
+    for (int k = p->n_sub - 1; k >= 0; --k) {
+        /* (ii) cooling: u_e' = F(u_e1) */
+        double ge1;
+        if (st[k].branch == 1) {
+            ge1 = (1.0 - p->limiter_frac) * ge;
+        } else {
+            double u = st[k].branch == 2 ? st[k].ustar : st[k].ue1;
+            qinfo qi;
+            q_dn(R, &K, dvar(rho, 2), dvar(B, 3), dvar(H, 4), dvar(u, 0), &qi, NULL);
+            double scale;   /* d u_e' / d q_theta */
+            if (st[k].branch == 2) {
+                double den = 1.0 + qi.q.d[0];
+                ge1 = ge / den;
+                scale = -ge / den;
+            } else {
+                ge1 = ge * (1.0 - qi.q.d[0]);
+                scale = -ge;
+            }
+            grho += scale * qi.q.d[2];
+            gB += scale * qi.q.d[3];
+            gH += scale * qi.q.d[4];
+            /* table entries: dq/dls_c = dq/dQthin ln2 2^lqs W_c, dq/dlb = dq/dQthin ln2 ne^2 2^lqb (1-wt, wt) */
+            double cs = scale * qi.q.d[5] * log(2.0) * exp2(qi.lqs);
+            double cb = scale * qi.q.d[5] * log(2.0) * qi.ne * qi.ne * exp2(qi.lqb);
+            if (g_ls) {
+                for (int c = 0; c < 16; ++c) {
+                    double wt = 1.0;
+                    int idx[4];
+                    for (int a = 0; a < 4; ++a) {
+                        int bit = (c >> a) & 1;
+                        double wa = a < 3 ? qi.w[a] : qi.wt;
+                        int ja = a < 3 ? qi.j[a] : qi.jt;
+                        idx[a] = ja + bit;
+                        wt *= bit ? wa : (1.0 - wa);
+                    }
+                    long long ii = (((long long)idx[0] * R->s->n[1] + idx[1]) * R->s->n[2] + idx[2]) * R->s->n[3] + idx[3];
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                    g_ls[ii] += cs * wt;
+                }
+            }
+            if (g_lb) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                g_lb[qi.jt] += cb * (1.0 - qi.wt);
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                g_lb[qi.jt + 1] += cb * qi.wt;
+            }
+        }
+        /* (i) Coulomb: u_e1 = u_e + X, u_i1 = u_i - X */
+        xinfo xi;
+        x_dn(R, p, &K, dvar(rho, 2), dvar(st[k].ue, 0), dvar(st[k].ui, 1), &xi, NULL);
+        double gX = ge1 - gi;
+        double ge0 = ge1 + gX * xi.X.d[0];
+        double gi0 = gi + gX * xi.X.d[1];
+        grho += gX * xi.X.d[2];
+        if (g_lc && !xi.clamped) {
+            int N = R->s->n[4];
+            double cl = gX * xi.X.v * log(2.0);
+            double ws[4] = {(1.0 - xi.wi) * (1.0 - xi.we), (1.0 - xi.wi) * xi.we, xi.wi * (1.0 - xi.we), xi.wi * xi.we};
+            int ids[4] = {xi.ji * N + xi.je, xi.ji * N + xi.je + 1, (xi.ji + 1) * N + xi.je, (xi.ji + 1) * N + xi.je + 1};
+            for (int c = 0; c < 4; ++c) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                g_lc[ids[c]] += cl * ws[c];
+            }
+        }
+        ge = ge0; gi = gi0;
+    }
+    g[0] = grho; g[1] = gB; g[2] = gH; g[3] = ge; g[4] = gi;
+}
+
+/* Adjoint of orc_step for n cells: grads[5 i + {0..4}] = dL/d(rho, B, H,
+ * u_e_in, u_i_in) for L = sum(g_ue_out u_e_out + g_ui_out u_i_out);
+ * g_lb / g_ls / g_lc (nullable, natural table layouts) accumulate dL/d(table
+ * log2 values); sig (nullable) receives a hash of each cell's discrete
+ * decisions; ue_out / ui_out (nullable) the forward outputs. */
+int orc_step_bwd(const orc_spec* s, const double* lb, double* ls, const double* lc, const orc_params* p,
+                 long long n, const double* rho, const double* B, const double* H, const double* ue,
+                 const double* ui, const double* g_ue_out, const double* g_ui_out, double* grads,
+                 double* g_lb, double* g_ls, double* g_lc, unsigned long long* sig, double* ue_out,
+                 double* ui_out, int nthreads) {
+    orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
+    if (!R) return -1;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = 0; R->lsp = NULL;
+    for (int a = 0; a < 5; ++a) {
+        if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
+        axis_init(s, a, &R->ax[a]);
+    }
+    if (p->n_sub > ORC_MAXSUB) { free(R); return -3; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (long long i = 0; i < n; ++i) {
+        unsigned long long sg;
+        double a, b;
+        cell_bwd(R, p, rho[i], B[i], H[i], ue[i], ui[i], g_ue_out[i], g_ui_out[i], &grads[5 * i], g_lb, g_ls,
+                 g_lc, &sg, &a, &b);
+        if (sig) sig[i] = sg;
+        if (ue_out) ue_out[i] = a;
+        if (ui_out) ui_out[i] = b;
+    }
+    free(R);
+    return 0;
+}
