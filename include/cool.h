@@ -226,6 +226,22 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
 cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_out, double* ls_out,
                                         double* lc_out, void* stream);
 
+/* Adjoint of cool_step (FP32 fields, FP32 table, fp64_critical = 0): for
+ * L = sum(g_u_e_out u_e_out + g_u_i_out u_i_out) over the cells of one
+ * cool_step with the same table, params and inputs, writes dL/d(rho, B, H,
+ * u_e_in, u_i_in) per cell and, when the pointers are given, ADDS dL/d(log2
+ * table values) into g_lb [n_Te], g_ls [n_H n_B n_ne n_Te] (natural layout,
+ * T_e fastest) and g_lc [n_Tc n_Tc] (atomic accumulation: order of the FP32
+ * additions is not deterministic).  The forward sub-cycles are recomputed,
+ * not stored; explicit and limited sub-cycles are differentiated on the
+ * branch taken, implicit ones by the implicit-function theorem at the root.
+ * Invalid cells pass the output adjoints through.  The inputs must not alias
+ * the gradient outputs.  Device pointers, asynchronous on stream; n_sub <= 64. */
+cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
+                          const float* B, const float* H, const float* u_e_in, const float* u_i_in,
+                          const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
+                          float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
+
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n): idx = the largest j
  * in [0, N-2] with node32[j] <= key (0 below the first node), w = log2(key /

@@ -224,3 +224,60 @@ def build_channels_noalloc(spec, lb_out, ls_out, lc_out, stream=None):
             raise ValueError("outputs must be contiguous CUDA tensors")
     _b.check(_b.lib().cool_build_channels_noalloc(_b.ref(cs), _ptr(lb_out), _ptr(ls_out), _ptr(lc_out),
                                                   _stream_ptr(stream)), "cool_build_channels_noalloc")
+
+
+def step_bwd(table, params, rho, B, H, ue, ui, g_ue_out, g_ui_out, table_grads=None, stream=None):
+    """Adjoint of step (cool_step_bwd) for FP32 fields: returns (g_rho, g_B,
+    g_H, g_ue_in, g_ui_in).  table_grads: optional dict of float32 CUDA
+    tensors 'lb' [n_Te], 'ls' [n_H n_B n_ne n_Te], 'lc' [n_Tc^2] into which
+    dL/d(log2 table values) is added."""
+    import torch
+    fields = (rho, B, H, ue, ui, g_ue_out, g_ui_out)
+    n = rho.numel()
+    for f in fields:
+        if f.dtype != torch.float32 or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("step_bwd takes contiguous float32 CUDA tensors of one size")
+    outs = [torch.empty_like(rho) for _ in range(5)]
+    tg = table_grads or {}
+    p = params.c()
+    st = _b.lib().cool_step_bwd(table.handle, _b.ref(p), n, *[_ptr(f) for f in fields], *[_ptr(o) for o in outs],
+                                _ptr(tg.get("lb")), _ptr(tg.get("ls")), _ptr(tg.get("lc")), _stream_ptr(stream))
+    _b.check(st, "cool_step_bwd")
+    return tuple(outs)
+
+
+def _make_autograd():
+    import torch
+
+    class CoolStepFn(torch.autograd.Function):
+        """u_e_out, u_i_out = cool_step(rho, B, H, u_e, u_i) with the adjoint
+        of cool_step_bwd; the forward keeps only its inputs (the backward
+        recomputes the sub-cycles)."""
+
+        @staticmethod
+        def forward(ctx, rho, B, H, ue, ui, table, params, table_grads=None):
+            ue_o, ui_o = step(table, params, rho.detach(), B.detach(), H.detach(), ue.detach(), ui.detach())
+            ctx.save_for_backward(rho, B, H, ue, ui)
+            ctx.table, ctx.params, ctx.table_grads = table, params, table_grads
+            return ue_o, ui_o
+
+        @staticmethod
+        def backward(ctx, g_ue, g_ui):
+            rho, B, H, ue, ui = ctx.saved_tensors
+            g_ue = torch.zeros_like(ue) if g_ue is None else g_ue.contiguous()
+            g_ui = torch.zeros_like(ui) if g_ui is None else g_ui.contiguous()
+            g = step_bwd(ctx.table, ctx.params, rho, B, H, ue, ui, g_ue, g_ui, ctx.table_grads)
+            return g[0], g[1], g[2], g[3], g[4], None, None, None
+
+    return CoolStepFn
+
+
+_CoolStepFn = None
+
+
+def cool_step_fn(rho, B, H, ue, ui, table, params, table_grads=None):
+    """Differentiable cool_step (torch.autograd)."""
+    global _CoolStepFn
+    if _CoolStepFn is None:
+        _CoolStepFn = _make_autograd()
+    return _CoolStepFn.apply(rho, B, H, ue, ui, table, params, table_grads)

@@ -23,7 +23,7 @@ EXPORTS = (
     "cool_strerror", "cool_last_cuda_error", "cool_table_spec_default", "cool_params_default",
     "cool_build_table", "cool_table_free", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
-    "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed",
+    "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
 )
 
 
@@ -95,6 +95,7 @@ def lib():
             "cool_debug_lookup": (I, [P, I, LL, P, P, P, P]),
             "cool_build_channels_noalloc": (I, [P, P, P, P, P]),
             "cool_table_packed_bytes": (I, [P, P]),
+            "cool_step_bwd": (I, [P, P, LL] + [P] * 15 + [P]),
             "cool_table_export_packed": (I, [P, P, LL]),
         }
         for name, (res, args) in sig.items():

@@ -546,6 +546,31 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
                            (double*)u_i_out, (double*)q_cool_out, (double*)q_cc_out, counters, s);
 }
 
+cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
+                          const float* B, const float* H, const float* u_e_in, const float* u_i_in,
+                          const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
+                          float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream) {
+    if (!t || !p) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    cool_status st = validate_params(p);
+    if (st != COOL_OK) return st;
+    if (n_cells < 0) return COOL_EINVAL;
+    if (n_cells == 0) return COOL_OK;
+    const void* req[] = {rho, B, H, u_e_in, u_i_in, g_u_e_out, g_u_i_out, g_rho, g_B, g_H, g_u_e_in, g_u_i_in};
+    for (const void* q : req)
+        if (!q) return COOL_ENULL;
+    for (const void* q : req)
+        if ((uintptr_t)q % 4 != 0) return COOL_EALIGN;
+    const void* opt[] = {g_lb, g_ls, g_lc};
+    for (const void* q : opt)
+        if ((uintptr_t)q % 4 != 0) return COOL_EALIGN;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return COOL_ESTATE;
+    return launch_step_bwd_f32(t, p, n_cells, rho, B, H, u_e_in, u_i_in, g_u_e_out, g_u_i_out, g_rho, g_B, g_H,
+                               g_u_e_in, g_u_i_in, g_lb, g_ls, g_lc, (cudaStream_t)stream);
+}
+
 cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys, int* idx,
                               float* w, void* stream) {
     if (!t) return COOL_ENULL;

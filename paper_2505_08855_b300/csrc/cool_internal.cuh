@@ -102,6 +102,10 @@ cool_status launch_step_f64(const cool_table* t, const cool_params* p, long long
                             const double* rho, const double* B, const double* H,
                             const double* ue, const double* ui, double* ue_o, double* ui_o,
                             double* qc, double* qx, cool_counters* cnt, cudaStream_t st);
+cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                                const float* B, const float* H, const float* ue, const float* ui,
+                                const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
+                                float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st);
 cool_status launch_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
                                 int* idx, float* w, cudaStream_t st);
 

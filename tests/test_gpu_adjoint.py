@@ -1,0 +1,118 @@
+"""GPU adjoint (cool_step_bwd) against the FP64 oracle adjoint.
+
+The oracle adjoint is pinned by finite differences (test_oracle_adjoint).
+Here the GPU gradients of L = sum(a u_e_out + b u_i_out) are compared with
+it cell by cell with the scale-free measure |dg| |x| / |L| <= 2e-4 (FP32
+forward and derivatives; cells whose discrete decisions sit within rounding
+of a kink may take the other branch and are allowed to differ, at most
+0.5 %), and the table adjoints (sums over cells) to 2e-3 of the largest
+entry of each channel.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2505_08855_b300 import inputs  # noqa: E402
+
+N5 = (16, 16, 16, 24, 24)
+
+
+@pytest.fixture(scope="module")
+def env(oracle):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2505_08855_b300 as cool
+    from paper_2505_08855_b300 import build
+    build.build()
+    ospec = oracle.Spec(n=N5)
+    return cool, cool.Table(cool.TableSpec(n=N5)), ospec, oracle.build_tables(ospec, nthreads=0)
+
+
+def _compare(cool, tab, oracle, ospec, OT, f, mode, n_sub=8, table=False):
+    n = f["rho"].size
+    rng = np.random.default_rng(77)
+    a = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    b = rng.uniform(-1.0, 1.0, n).astype(np.float32)
+    p = cool.Params(n_sub=n_sub, mode=mode)
+    tf = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
+    tg = None
+    if table:
+        tg = {"lb": torch.zeros(N5[3], device="cuda"), "ls": torch.zeros(np.prod(N5[:4]), device="cuda"),
+              "lc": torch.zeros(N5[4] ** 2, device="cuda")}
+    g = cool.step_bwd(tab, p, tf["rho"], tf["B"], tf["H"], tf["ue"], tf["ui"], torch.from_numpy(a).cuda(),
+                      torch.from_numpy(b).cuda(), table_grads=tg)
+    torch.cuda.synchronize()
+    want = oracle.step_bwd(ospec, OT, oracle.Params(n_sub=n_sub, mode=mode), **f, g_ue=a, g_ui=b,
+                           table_grads=table)
+    L = np.abs(a * want["ue"] + b * want["ui"])
+    bad = np.zeros(n, bool)
+    worst = 0.0
+    for k, (name, fld) in enumerate(zip(["g_rho", "g_B", "g_H", "g_ue", "g_ui"], ["rho", "B", "H", "ue", "ui"])):
+        err = np.abs(g[k].cpu().numpy() - want[name]) * np.abs(f[fld]) / np.maximum(L, 1e-30)
+        bad |= err > 2e-4
+        worst = max(worst, np.sort(err)[int(0.995 * n)])
+    return g, want, tg, bad, worst
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_adjoint_matches_oracle(env, oracle, mode):
+    cool, tab, ospec, OT = env
+    f = inputs.uniform(20000 + 5, seed=60, dtype=np.float32)
+    g, want, tg, bad, worst = _compare(cool, tab, oracle, ospec, OT, f, mode)
+    print(f"\nmode {mode}: cells beyond 2e-4: {bad.sum()} of {bad.size}; 99.5th pct {worst:.2e}")
+    assert bad.mean() <= 0.005
+
+
+def test_table_adjoints_match_oracle(env, oracle):
+    cool, tab, ospec, OT = env
+    f = inputs.uniform(4000, seed=61, dtype=np.float32)
+    g, want, tg, bad, worst = _compare(cool, tab, oracle, ospec, OT, f, 0, table=True)
+    for key in ("lb", "ls", "lc"):
+        got = tg[key].cpu().numpy().astype(np.float64)
+        w = np.asarray(want["g_" + key]).reshape(-1)
+        scale = np.abs(w).max()
+        err = np.abs(got - w).max() / scale
+        print(f"\ntable adjoint {key}: max |diff| / max |g| = {err:.2e}")
+        assert err <= 2e-3, key
+
+
+def test_autograd_function(env):
+    cool, tab, _, _ = env
+    f = inputs.uniform(3000, seed=62, dtype=np.float32)
+    t = {k: torch.from_numpy(v).cuda().requires_grad_(True) for k, v in f.items()}
+    p = cool.Params(n_sub=8)
+    ue, ui = cool.cool_step_fn(t["rho"], t["B"], t["H"], t["ue"], t["ui"], tab, p)
+    loss = (ue * 2.0).sum() + (ui * -0.5).sum()
+    loss.backward()
+    g = cool.step_bwd(tab, p, *[t[k].detach() for k in ("rho", "B", "H", "ue", "ui")],
+                      torch.full_like(ue, 2.0), torch.full_like(ui, -0.5))
+    for k, name in enumerate(("rho", "B", "H", "ue", "ui")):
+        assert torch.equal(t[name].grad, g[k]), name
+    # forward values are the plain step's
+    ref = cool.step(tab, p, *[t[k].detach() for k in ("rho", "B", "H", "ue", "ui")])
+    assert torch.equal(ue.detach(), ref[0]) and torch.equal(ui.detach(), ref[1])
+
+
+def test_full_size_sampled_gradients(env, oracle):
+    """128^3 cells (2.1M), full-table-size run on the GPU; 1024 sampled cells
+    (seed 1003) against the oracle adjoint."""
+    cool, tab, ospec, OT = env
+    F = inputs.make("uniform_128c")
+    n = F["rho"].size
+    tf = {k: torch.from_numpy(v).cuda() for k, v in F.items()}
+    a = torch.ones(n, device="cuda")
+    b = torch.full((n,), 0.5, device="cuda")
+    p = cool.Params(n_sub=8)
+    g = cool.step_bwd(tab, p, tf["rho"], tf["B"], tf["H"], tf["ue"], tf["ui"], a, b)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(1003).choice(n, 1024, replace=False))
+    sub = inputs.subsample(F, idx)
+    want = oracle.step_bwd(ospec, OT, oracle.Params(n_sub=8), **sub, g_ue=np.ones(1024), g_ui=np.full(1024, 0.5))
+    L = np.abs(want["ue"] + 0.5 * want["ui"])
+    bad = np.zeros(1024, bool)
+    for k, (name, fld) in enumerate(zip(["g_rho", "g_B", "g_H", "g_ue", "g_ui"], ["rho", "B", "H", "ue", "ui"])):
+        err = np.abs(g[k].cpu().numpy()[idx] - want[name]) * np.abs(sub[fld]) / np.maximum(L, 1e-30)
+        bad |= err > 2e-4
+    assert bad.sum() <= 5
