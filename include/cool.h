@@ -242,6 +242,16 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
                           float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
 
+/* Check entry of the tensor-core GEMM primitive the surrogate is built on
+ * (5th-generation tensor cores, tcgen05.mma kind::f16, FP32 accumulation in
+ * tensor memory): C[M x N] = A[M x K] B[N x K]^T with A, B bf16 row-major
+ * device arrays (16-byte aligned) and C fp32 row-major.  M % 128 == 0,
+ * 16 <= N <= 128 and K <= 128, both multiples of 16.  err (nullable device
+ * word) gets bit 0 set if the tensor core did not signal completion within
+ * the kernel's bounded wait.  Asynchronous on stream. */
+cool_status cool_debug_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, unsigned* err,
+                                 void* stream);
+
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n): idx = the largest j
  * in [0, N-2] with node32[j] <= key (0 below the first node), w = log2(key /

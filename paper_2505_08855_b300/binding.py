@@ -24,6 +24,7 @@ EXPORTS = (
     "cool_build_table", "cool_table_free", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
     "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
+    "cool_debug_gemm_bf16",
 )
 
 
@@ -96,6 +97,7 @@ def lib():
             "cool_build_channels_noalloc": (I, [P, P, P, P, P]),
             "cool_table_packed_bytes": (I, [P, P]),
             "cool_step_bwd": (I, [P, P, LL] + [P] * 15 + [P]),
+            "cool_debug_gemm_bf16": (I, [P, P, P, I, I, I, P, P]),
             "cool_table_export_packed": (I, [P, P, LL]),
         }
         for name, (res, args) in sig.items():
