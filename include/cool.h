@@ -36,6 +36,7 @@
 #define COOL_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -241,6 +242,63 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                           const float* B, const float* H, const float* u_e_in, const float* u_i_in,
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
                           float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
+
+/* ---- learned surrogate of the synchrotron channel (not in the paper) ------
+ * An MLP 4 -> 128 -> 128 -> 1 with SiLU (inputs: the four log2 coordinates
+ * normalised to [-1, 1] over the table box; output: the standardised
+ * log2(eta Q_syn)), BF16 weights and activations on the tensor cores
+ * (tcgen05, FP32 accumulation), trained on the GPU by Adam on MSE in log2
+ * space with samples labelled by the FP64 formulas (half on table nodes,
+ * half uniform in log space).  A bit per 4-D table cell marks where the
+ * network misses the table by more than fallback_tol (relative, checked at
+ * the cell's corners and centre): there the table is used instead. */
+typedef struct cool_surrogate cool_surrogate;   /* opaque; owns device memory */
+
+typedef struct {
+    int channel;               /* 1 = synchrotron (the only one supported) */
+    long long n_samples;       /* training samples (default 2^24), multiple of batch */
+    int batch;                 /* samples per Adam step, multiple of 128 (16384) */
+    int epochs;                /* passes over the samples (4); 0 = initial weights only */
+    double lr, lr_final;       /* Adam learning rate, cosine decay from lr to lr_final */
+    unsigned long long seed;   /* samples and initial weights */
+    double fallback_tol;       /* 1e-3 */
+} cool_fit_spec;
+
+typedef struct {
+    double final_loss;         /* MSE (standardised units) of the last batch */
+    long long steps;           /* Adam steps taken */
+    long long mask_cells;      /* 4-D table cells */
+    long long fallback_cells;  /* cells where the table is used instead of the network */
+    long long param_bytes_bf16;/* bytes of the network as stored for inference */
+    double mean, std;          /* output standardisation (log2 units) */
+} cool_surrogate_stats;
+
+cool_status cool_fit_spec_default(cool_fit_spec* f);
+
+/* Train a surrogate of table t's synchrotron channel (synchronous; device
+ * memory for the samples is allocated and freed inside). */
+cool_status cool_surrogate_fit(const cool_table* t, const cool_fit_spec* f, void* stream, cool_surrogate** out);
+cool_status cool_surrogate_free(cool_surrogate* s);
+cool_status cool_surrogate_info(const cool_surrogate* s, cool_surrogate_stats* out);
+
+/* The 18817 FP32 parameters (W1 [128][16] with input columns 4..15 zero,
+ * b1 [128], W2 [128 out][128 in], b2 [128], w3 [128], b3), host memory. */
+cool_status cool_surrogate_get_params(const cool_surrogate* s, float* host, int n);
+cool_status cool_surrogate_set_params(cool_surrogate* s, const float* host, int n);
+
+/* Gradients of the batch-mean squared error over n samples (device x4
+ * [n][4] normalised inputs, y_std [n] standardised targets, n % 128 == 0)
+ * into host grads [18817]; *loss_host (nullable) the loss.  Check entry of
+ * the training kernel (synchronous). */
+cool_status cool_surrogate_grads(cool_surrogate* s, long long n, const float* x4, const float* y_std,
+                                 float* grads_host, float* loss_host, void* stream);
+
+/* Network output in log2 units at n normalised points (device arrays). */
+cool_status cool_surrogate_eval(const cool_surrogate* s, long long n, const float* x4, float* y, void* stream);
+
+/* The fallback bits (one per 4-D table cell, cell index ((h (nB-1) + b)
+ * (nne-1) + n) (nTe-1) + t), host memory of (cells + 31)/32 words. */
+cool_status cool_surrogate_mask(const cool_surrogate* s, uint32_t* host_bits, long long words);
 
 /* Check entry of the tensor-core GEMM primitive the surrogate is built on
  * (5th-generation tensor cores, tcgen05.mma kind::f16, FP32 accumulation in

@@ -281,3 +281,98 @@ def cool_step_fn(rho, B, H, ue, ui, table, params, table_grads=None):
     if _CoolStepFn is None:
         _CoolStepFn = _make_autograd()
     return _CoolStepFn.apply(rho, B, H, ue, ui, table, params, table_grads)
+
+
+# ---- learned surrogate of the synchrotron channel (not in the paper) ----------
+N_PARAMS = 18817
+
+
+@dataclasses.dataclass
+class FitSpec:
+    channel: int = 1
+    n_samples: int = 1 << 24
+    batch: int = 16384
+    epochs: int = 4
+    lr: float = 2e-3
+    lr_final: float = 2e-5
+    seed: int = 20250513
+    fallback_tol: float = 1e-3
+
+    def c(self):
+        return _b.cool_fit_spec(self.channel, self.n_samples, self.batch, self.epochs, self.lr, self.lr_final,
+                                self.seed, self.fallback_tol)
+
+
+class Surrogate:
+    """An MLP surrogate of a table's synchrotron channel, trained on the GPU
+    (cool_surrogate_fit) by the library's tcgen05 kernels."""
+
+    def __init__(self, table, fit=None, stream=None):
+        self.table = table
+        self.fit_spec = fit if fit is not None else FitSpec()
+        h = C.c_void_p()
+        f = self.fit_spec.c()
+        _b.check(_b.lib().cool_surrogate_fit(table.handle, _b.ref(f), _stream_ptr(stream), _b.ref(h)),
+                 "cool_surrogate_fit")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise _b.CoolError(_b.COOL_ESTATE, "surrogate already freed")
+        return self._h
+
+    def info(self):
+        s = _b.cool_surrogate_stats()
+        _b.check(_b.lib().cool_surrogate_info(self.handle, _b.ref(s)), "cool_surrogate_info")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(N_PARAMS, np.float32)
+        _b.check(_b.lib().cool_surrogate_get_params(self.handle, out.ctypes.data_as(C.c_void_p), N_PARAMS),
+                 "cool_surrogate_get_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, np.float32)
+        _b.check(_b.lib().cool_surrogate_set_params(self.handle, p.ctypes.data_as(C.c_void_p), N_PARAMS),
+                 "cool_surrogate_set_params")
+
+    def grads(self, x4, y_std, stream=None):
+        import numpy as np
+        g = np.zeros(N_PARAMS, np.float32)
+        loss = C.c_float(0.0)
+        _b.check(_b.lib().cool_surrogate_grads(self.handle, x4.shape[0], _ptr(x4.contiguous()),
+                                               _ptr(y_std.contiguous()), g.ctypes.data_as(C.c_void_p),
+                                               _b.ref(loss), _stream_ptr(stream)), "cool_surrogate_grads")
+        return g, loss.value
+
+    def eval(self, x4, stream=None):
+        import torch
+        y = torch.empty(x4.shape[0], dtype=torch.float32, device=x4.device)
+        _b.check(_b.lib().cool_surrogate_eval(self.handle, x4.shape[0], _ptr(x4.contiguous()), _ptr(y),
+                                              _stream_ptr(stream)), "cool_surrogate_eval")
+        return y
+
+    def mask(self):
+        import numpy as np
+        cells = self.info()["mask_cells"]
+        out = np.zeros((cells + 31) // 32, np.uint32)
+        _b.check(_b.lib().cool_surrogate_mask(self.handle, out.ctypes.data_as(C.c_void_p), out.size),
+                 "cool_surrogate_mask")
+        return out
+
+    def free(self):
+        if self._h is not None:
+            _b.check(_b.lib().cool_surrogate_free(self._h), "cool_surrogate_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None and _b._LIB is not None:
+                _b._LIB.cool_surrogate_free(self._h)
+                self._h = None
+        except Exception:
+            pass

@@ -24,7 +24,9 @@ EXPORTS = (
     "cool_build_table", "cool_table_free", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
     "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
-    "cool_debug_gemm_bf16",
+    "cool_debug_gemm_bf16", "cool_fit_spec_default", "cool_surrogate_fit", "cool_surrogate_free",
+    "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
+    "cool_surrogate_eval", "cool_surrogate_mask",
 )
 
 
@@ -45,6 +47,18 @@ class cool_params(C.Structure):
                 ("limiter_frac", C.c_double), ("eq_band", C.c_double),
                 ("coulomb_clamp", C.c_double), ("implicit_iters", C.c_int), ("path", C.c_int),
                 ("fp64_critical", C.c_int)]
+
+
+class cool_fit_spec(C.Structure):
+    _fields_ = [("channel", C.c_int), ("n_samples", C.c_longlong), ("batch", C.c_int), ("epochs", C.c_int),
+                ("lr", C.c_double), ("lr_final", C.c_double), ("seed", C.c_ulonglong),
+                ("fallback_tol", C.c_double)]
+
+
+class cool_surrogate_stats(C.Structure):
+    _fields_ = [("final_loss", C.c_double), ("steps", C.c_longlong), ("mask_cells", C.c_longlong),
+                ("fallback_cells", C.c_longlong), ("param_bytes_bf16", C.c_longlong), ("mean", C.c_double),
+                ("std", C.c_double)]
 
 
 class cool_counters(C.Structure):
@@ -98,6 +112,15 @@ def lib():
             "cool_table_packed_bytes": (I, [P, P]),
             "cool_step_bwd": (I, [P, P, LL] + [P] * 15 + [P]),
             "cool_debug_gemm_bf16": (I, [P, P, P, I, I, I, P, P]),
+            "cool_fit_spec_default": (I, [P]),
+            "cool_surrogate_fit": (I, [P, P, P, P]),
+            "cool_surrogate_free": (I, [P]),
+            "cool_surrogate_info": (I, [P, P]),
+            "cool_surrogate_get_params": (I, [P, P, I]),
+            "cool_surrogate_set_params": (I, [P, P, I]),
+            "cool_surrogate_grads": (I, [P, LL, P, P, P, P, P]),
+            "cool_surrogate_eval": (I, [P, LL, P, P, P]),
+            "cool_surrogate_mask": (I, [P, P, LL]),
             "cool_table_export_packed": (I, [P, P, LL]),
         }
         for name, (res, args) in sig.items():

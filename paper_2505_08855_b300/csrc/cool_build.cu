@@ -284,6 +284,43 @@ __global__ void k_build_small(BuildArgs a, double* lb, double* lc) {
     }
 }
 
+// Counter-based generator: SplitMix64 of (seed, index) -> uniform in [0, 1).
+__device__ __forceinline__ double u01(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Training samples of the synchrotron channel: even samples sit on a random
+// table node, odd ones are uniform in log space over the table box;
+// the label is log2(eta Q_syn) from the formulas (FP64).  x: normalised
+// coordinates 2 (l - l_lo)/(l_hi - l_lo) - 1 per axis (H, B, n_e, T_e).
+__global__ void k_fit_samples(BuildArgs a, double l0_0, double l0_1, double l0_2, double l0_3, double span0,
+                              double span1, double span2, double span3, long long n,
+                              unsigned long long seed, float* x, double* y) {
+    const double l0[4] = {l0_0, l0_1, l0_2, l0_3};
+    const double span[4] = {span0, span1, span2, span3};
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double l[4];
+        for (int d = 0; d < 4; ++d) {
+            const double u = u01(seed + 7919ull * d, (unsigned long long)i);
+            if ((i & 1) == 0) {
+                int j = (int)(u * a.n[d]);
+                j = j > a.n[d] - 1 ? a.n[d] - 1 : j;
+                l[d] = l0[d] + span[d] * j / (a.n[d] - 1);
+            } else {
+                l[d] = l0[d] + span[d] * u;
+            }
+            x[4 * i + d] = (float)(2.0 * (l[d] - l0[d]) / span[d] - 1.0);
+        }
+        SynOut o = eta_qsyn(exp2(l[0]), exp2(l[1]), exp2(l[2]), exp2(l[3]), a.k2_switch_T, a.compton_literal);
+        y[i] = log2(o.eta_qsyn);
+    }
+}
+
 }  // namespace
 
 cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64,
@@ -471,5 +508,39 @@ extern "C" cool_status cool_build_channels_noalloc(const cool_table_spec* spec, 
 }
 
 namespace cool {
+
+cool_status fit_samples_fp64(const cool_table_spec& s, long long n, unsigned long long seed, float* x, double* y,
+                             cudaStream_t st) {
+    BuildArgs a;
+    a.x64 = nullptr;
+    int nn[5] = {s.n_H, s.n_B, s.n_ne, s.n_Te, s.n_Tc};
+    for (int i = 0; i < 5; ++i) { a.off[i] = 0; a.n[i] = nn[i]; }
+    a.k2_switch_T = s.k2_switch_T;
+    a.lnLambda = s.lnLambda;
+    a.theta_i_uses_mp = s.theta_i_uses_mp;
+    a.compton_literal = s.compton_literal;
+    double gx[16], gw[16];
+    gl16_host(gx, gw);
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    double lo[4] = {s.H_min, s.B_min, s.ne_min, s.T_min}, hi[4] = {s.H_max, s.B_max, s.ne_max, s.T_max};
+    double l0[4], sp[4];
+    for (int d = 0; d < 4; ++d) { l0[d] = log2(lo[d]); sp[d] = log2(hi[d]) - l0[d]; }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long chunk = 1LL << 22;
+    for (long long first = 0; first < n; first += chunk) {
+        long long cnt = n - first < chunk ? n - first : chunk;
+        long long blocks = (cnt + 127) / 128;
+        if (blocks > sms * 16LL) blocks = sms * 16LL;
+        k_fit_samples<<<(int)blocks, 128, 0, st>>>(a, l0[0], l0[1], l0[2], l0[3], sp[0], sp[1], sp[2], sp[3], cnt,
+                                                   seed + (unsigned long long)first * 31ull, x + 4 * first, y + first);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return COOL_OK;
+}
 
 }  // namespace cool

@@ -93,6 +93,11 @@ cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64
                                 const int* axis_off64, double* d_lb64, double* d_ls64,
                                 double* d_lc64, cudaStream_t st);
 
+// Surrogate training samples (cool_build.cu): x [n][4] normalised coordinates,
+// y [n] log2(eta Q_syn) from the formulas; even samples sit on table nodes.
+cool_status fit_samples_fp64(const cool_table_spec& s, long long n, unsigned long long seed, float* x, double* y,
+                             cudaStream_t st);
+
 // Step launches (cool_step.cu).
 cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long n,
                             const float* rho, const float* B, const float* H,

@@ -52,6 +52,8 @@ def test_struct_layout_matches_header(tmp_path):
         "cool_table_spec": [f[0] for f in b.cool_table_spec._fields_],
         "cool_params": [f[0] for f in b.cool_params._fields_],
         "cool_counters": [f[0] for f in b.cool_counters._fields_],
+        "cool_fit_spec": [f[0] for f in b.cool_fit_spec._fields_],
+        "cool_surrogate_stats": [f[0] for f in b.cool_surrogate_stats._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fl in fields.items():

@@ -97,3 +97,31 @@ def test_adjoint_table_entries_fd(oracle, tab):
             sub = inputs.subsample(f, np.flatnonzero(ok))
             g_ok = oracle.step_bwd(spec, T, p, **sub, g_ue=a[ok], g_ui=b[ok], table_grads=True)[gkey].reshape(-1)[e]
             assert abs(fd - g_ok) <= 1e-4 * max(abs(g_ok), 1e-30) + 1e-12, (key, e, fd, g_ok)
+
+
+def test_mlp_reference_gradient_fd():
+    """The numpy network's reverse-mode gradient (without the bf16 operand
+    roundings) against central differences of its own loss."""
+    from oracle import mlp
+    rng = np.random.default_rng(9)
+    p = np.zeros(mlp.P_N)
+    W1 = rng.uniform(-1, 1, (128, 16)) * np.sqrt(6 / 4)
+    W1[:, 4:] = 0
+    p[mlp.P_W1:mlp.P_b1] = W1.reshape(-1)
+    p[mlp.P_b1:mlp.P_W2] = rng.normal(0, 0.1, 128)
+    p[mlp.P_W2:mlp.P_b2] = rng.uniform(-1, 1, 128 * 128) * np.sqrt(6 / 128)
+    p[mlp.P_b2:mlp.P_w3] = rng.normal(0, 0.1, 128)
+    p[mlp.P_w3:mlp.P_b3] = rng.normal(0, 0.1, 128)
+    p[mlp.P_b3] = 0.3
+    x = rng.uniform(-1, 1, (64, 4))
+    y = rng.normal(0, 1, 64)
+    g, _ = mlp.grads(p, x, y, rounding=False)
+    idx = np.concatenate([rng.choice(np.flatnonzero(np.arange(mlp.P_b1) % 16 < 4), 6),
+                          rng.integers(mlp.P_b1, mlp.P_N, 30), [mlp.P_b3]])
+    h = 1e-5
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (mlp.grads(pp, x, y, rounding=False)[1] - mlp.grads(pm, x, y, rounding=False)[1]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 + 1e-5 * abs(g[i]), (i, fd, g[i])
