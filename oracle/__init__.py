@@ -129,6 +129,9 @@ def _declare(L):
                                 _P, _P, _P, _P, _P, _i]),
         "orc_step_bwd": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P,
                               _P, _P, _P, _P, _P, _P, _i]),
+        "orc_step_surrogate": (_i, [_P, _P, _P, _P, _P, _d, _d, _P, _P, _d, _P, _i, _P, _ll,
+                                    _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i]),
+        "orc_net_eval": (_i, [_P, _d, _d, _d, _i, _ll, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -389,6 +392,51 @@ def step_bwd(spec, tables, params, rho, B, H, ue, ui, g_ue, g_ui, table_grads=Fa
     if table_grads:
         out.update(g_lb=g_lb, g_ls=g_ls, g_lc=g_lc.reshape(nC, nC))
     return out
+
+
+def net_box(spec):
+    """(l0[4], span[4], xs): the surrogate's input normalisation over the
+    table box (log2 of the H, B, n_e, T_e ranges) and the normalised log2 of
+    the K2 switch temperature."""
+    l0 = np.log2(np.asarray(spec.lo[:4], np.float64))
+    span = np.log2(np.asarray(spec.hi[:4], np.float64)) - l0
+    xs = 2.0 * (np.log2(spec.k2_switch_T) - l0[3]) / span[3] - 1.0
+    return l0, span, float(xs)
+
+
+def net_eval(params, mean, std, xs, x, rounding=True):
+    """The surrogate network (C restatement) at normalised points x [n][4]."""
+    p = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.zeros(x.shape[0])
+    lib().orc_net_eval(_ptr(p), float(mean), float(std), float(xs), int(rounding), x.shape[0], _ptr(x),
+                       _ptr(out))
+    return out
+
+
+def step_surrogate(spec, tables, params, mean, std, mask, prm, rho, B, H, ue, ui, rounding=True,
+                   nthreads=0):
+    """The O2 step with the surrogate network in place of the 4-D channel
+    (table where the uint32 fallback bits `mask` are set; None: nowhere).
+    Returns the same tuple as step(); counters['fallback'] counts cells that
+    read the table in some sub-cycle."""
+    f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui)]
+    n = f[0].size
+    outs = [np.zeros(n) for _ in range(4)]
+    cnt = np.zeros(6, np.int64)
+    s = spec.c()
+    pc = prm.c()
+    l0, span, xs = net_box(spec)
+    pv = np.ascontiguousarray(params, np.float32)
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint32)
+    lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
+    rc = lib().orc_step_surrogate(_ref(s), _ptr(tables["lb"]), _ptr(tables["ls"]), _ptr(lc), _ptr(pv),
+                                  float(mean), float(std), _ptr(l0), _ptr(span), xs, _ptr(m), int(rounding),
+                                  _ref(pc), n, *[_ptr(a) for a in f], *[_ptr(a) for a in outs], _ptr(cnt),
+                                  int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_surrogate failed: {rc}")
+    return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
 
 
 def keys_f32(params, rho, B, H, ue, ui):

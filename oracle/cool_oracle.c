@@ -15,8 +15,7 @@
  *       multilinear interpolation in log2 space, and the sub-cycled energy
  *       update of Sec. 3.2 (explicit with the 30 % limiter, or implicit).
  *
- * Readings of the paper where it is silent, garbled or inconsistent (each is
- * listed again in the design doc):
+ * Readings of the paper where it is silent, garbled or inconsistent:
  *   - sigma in Eq. 11 and in tau_abs (Eq. 12) is Stefan-Boltzmann's constant
  *     (the printed sigma_T is dimensionally impossible there);
  *   - the Compton exponent is -1 - ln P / ln A (the truncated geometric series
@@ -531,12 +530,98 @@ typedef struct {
     int lazy;
     int direct;       /* 1: O1 rates from the formulas instead of the table */
     const double* lsp;  /* optional: per-interval node pairs of the 4-D channel */
+    const struct orc_net* net;  /* optional: the surrogate network replaces the 4-D channel */
     orc_axis ax[5];
 } orc_rates;
+
+/* ---------------------------------------------------------------------- */
+/* Surrogate network (not in the paper): an MLP 4 -> 128 -> 128 -> 1 with  */
+/* SiLU standing in for the 4-D channel l(eta Q_syn).  Inputs: the four    */
+/* log2 coordinates normalised to [-1, 1] over the table box, each as two  */
+/* bf16 parts hi = bf16(x), lo = bf16(x - hi), and the side of the K2      */
+/* switch (+1 above, -1 at or below).  Products in FP64 with the bf16      */
+/* roundings of the tensor-core operands applied where they occur: input   */
+/* parts, W1, W2 and the hidden activations H1.  A fallback bit per 4-D    */
+/* table cell sends the lookup back to the table.                          */
+/* ---------------------------------------------------------------------- */
+typedef struct orc_net {
+    double W1[128][9];    /* operand weights: hi parts, lo parts, switch side */
+    double b1[128], W2[128][128], b2[128], w3[128], b3;
+    double mean, std;     /* output log2 = mean + std * net */
+    double l0[4], span[4], xs;
+    const uint32_t* mask; /* fallback bits, cell ((h (nB-1) + b) (nN-1) + n) (nT-1) + t; nullable */
+    int rounding;
+} orc_net;
+
+/* float64 -> float32 -> bfloat16, round to nearest even (finite values). */
+static double bf16r(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double net_rnd(const orc_net* m, double v) { return m->rounding ? bf16r(v) : v; }
+
+/* p: the library's flat FP32 parameter layout (W1 [128][16] with columns
+ * 0..3 the coordinates and 4 the switch side, b1, W2 [out][in], b2, w3, b3). */
+static void net_init(orc_net* m, const float* p, double mean, double stdv, const double* l0,
+                     const double* span, double xs, const uint32_t* mask, int rounding) {
+    m->rounding = rounding;
+    for (int o = 0; o < 128; ++o) {
+        for (int d = 0; d < 4; ++d) m->W1[o][d] = m->W1[o][4 + d] = net_rnd(m, p[o * 16 + d]);
+        m->W1[o][8] = net_rnd(m, p[o * 16 + 4]);
+        m->b1[o] = p[2048 + o];
+        for (int i = 0; i < 128; ++i) m->W2[o][i] = net_rnd(m, p[2176 + o * 128 + i]);
+        m->b2[o] = p[18560 + o];
+        m->w3[o] = p[18688 + o];
+    }
+    m->b3 = p[18816];
+    m->mean = mean; m->std = stdv;
+    for (int d = 0; d < 4; ++d) { m->l0[d] = l0[d]; m->span[d] = span[d]; }
+    m->xs = xs;
+    m->mask = mask;
+}
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+
+/* Network output in log2 units at normalised inputs x[4] (x in float32, as
+ * the library receives it). */
+static double net_eval(const orc_net* m, const double* x) {
+    double X[9];
+    for (int d = 0; d < 4; ++d) {
+        double xd = m->rounding ? (double)(float)x[d] : x[d];
+        X[d] = net_rnd(m, xd);
+        X[4 + d] = net_rnd(m, xd - X[d]);
+    }
+    X[8] = ((m->rounding ? (double)(float)x[3] : x[3]) > (double)(float)m->xs) ? 1.0 : -1.0;
+    double h1[128];
+    for (int o = 0; o < 128; ++o) {
+        double z = m->b1[o];
+        for (int k = 0; k < 9; ++k) z += X[k] * m->W1[o][k];
+        h1[o] = net_rnd(m, silu(z));
+    }
+    double y = m->b3;
+    for (int o = 0; o < 128; ++o) {
+        double z = m->b2[o];
+        for (int i = 0; i < 128; ++i) z += h1[i] * m->W2[o][i];
+        y += silu(z) * m->w3[o];
+    }
+    return m->mean + m->std * y;
+}
+
+/* Normalised coordinate of log2 value l on axis d, clamped to [-1, 1]. */
+static double net_coord(const orc_net* m, int d, double l) {
+    double x = 2.0 * (l - m->l0[d]) / m->span[d] - 1.0;
+    return x < -1.0 ? -1.0 : (x > 1.0 ? 1.0 : x);
+}
 
 typedef struct {
     double ne, Bg, Hcm, hs, escale, sTe, sTi, ce, ci;
     int j[3]; double w[3]; /* H, B, n_e selections (step-invariant) */
+    int* fallback;         /* set when the surrogate step read the table (nullable) */
 } cell_ctx;
 
 /* Multilinear interpolation of the 4-D channel when the table is given as
@@ -571,7 +656,22 @@ static double cool_q(const orc_rates* R, const cell_ctx* c, double ue, double rh
         if (clamp) *clamp |= cl;
         int j[4] = {c->j[0], c->j[1], c->j[2], jt};
         double w[4] = {c->w[0], c->w[1], c->w[2], wt};
-        double lqs = R->lsp ? interp4_pairs(R->s, R->lsp, j, w) : interp4(R->s, R->ls, R->lazy, j, w);
+        double lqs;
+        const orc_net* m = R->net;
+        int table = 1;
+        if (m) {
+            const int* n = R->s->n;
+            long long cell = (((long long)j[0] * (n[1] - 1) + j[1]) * (n[2] - 1) + j[2]) * (n[3] - 1) + jt;
+            table = m->mask && ((m->mask[cell >> 5] >> (cell & 31)) & 1u);
+            if (table && c->fallback) *c->fallback = 1;
+        }
+        if (!table) {
+            double x[4] = {net_coord(m, 0, log2(c->Hcm)), net_coord(m, 1, log2(c->Bg)),
+                           net_coord(m, 2, log2(c->ne)), net_coord(m, 3, log2(Te))};
+            lqs = net_eval(m, x);
+        } else {
+            lqs = R->lsp ? interp4_pairs(R->s, R->lsp, j, w) : interp4(R->s, R->ls, R->lazy, j, w);
+        }
         double lqb = interp1(R->lb, jt, wt);
         qthin = c->ne * c->ne * exp2(lqb) + exp2(lqs);
     }
@@ -603,6 +703,7 @@ static int cell_setup(const orc_rates* R, const orc_params* p, double rho, doubl
     c->ce = p->gamma_e - 1.0; c->ci = p->gamma_i - 1.0;
     c->sTe = c->ce * O_MP * O_C * O_C / O_KB;
     c->sTi = c->ci * O_MP * O_C * O_C / O_KB;
+    c->fallback = NULL;
     int clamp = 0;
     if (!R->direct) {
         double k[3] = {c->Hcm, c->Bg, c->ne};
@@ -630,7 +731,8 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
     cell_ctx c;
     int clamp = cell_setup(R, p, rho, B, H, &c);
     double sum_cool = 0.0, sum_cc = 0.0;
-    int stiff = 0, eqb = 0, fail = 0;
+    int stiff = 0, eqb = 0, fail = 0, fallback = 0;
+    c.fallback = &fallback;
     for (int k = 0; k < p->n_sub; ++k) {
         /* (i) Coulomb exchange (Eq. 16), clamped so that the step does not
          * cross T_e = T_i. */
@@ -670,20 +772,23 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
     *ue_out = ue; *ui_out = ui;
     if (qcool) *qcool = sum_cool;
     if (qcc) *qcc = sum_cc;
-    *flags = (clamp ? 1u : 0u) | (stiff ? 1u << 2 : 0u) | (eqb ? 1u << 3 : 0u) | (fail ? 1u << 4 : 0u);
+    *flags = (clamp ? 1u : 0u) | (stiff ? 1u << 2 : 0u) | (eqb ? 1u << 3 : 0u) | (fail ? 1u << 4 : 0u) |
+             (fallback ? 1u << 5 : 0u);
 }
 
-/* Step n cells.  counters[0..5] = cells with flag bit k set (bit 5 unused:
- * the oracle has no surrogate fallback).  lazy: the 4-D channel may hold NaN
- * entries, computed on first use (forces one thread).  direct: O1 rates. */
+/* Step n cells.  counters[0..5] = cells with flag bit k set (bit 5: the
+ * surrogate step read the table in some sub-cycle).  lazy: the 4-D channel
+ * may hold NaN entries, computed on first use (forces one thread).
+ * direct: O1 rates.  net: the surrogate network (nullable). */
 static int step_impl(const orc_spec* s, const double* lb, double* ls, const double* lc, int lazy, int direct,
-             const double* lsp, const orc_params* p, long long n,
+             const double* lsp, const orc_net* net, const orc_params* p, long long n,
              const double* rho, const double* B, const double* H, const double* ue, const double* ui,
              double* ue_out, double* ui_out, double* qcool, double* qcc,
              long long* counters, int nthreads) {
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return -1;
     R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = lazy; R->direct = direct; R->lsp = lsp;
+    R->net = net;
     for (int a = 0; a < 5; ++a) {
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
         axis_init(s, a, &R->ax[a]);
@@ -700,7 +805,7 @@ static int step_impl(const orc_spec* s, const double* lb, double* ls, const doub
         step_cell(R, p, rho[i], B[i], H[i], ue[i], ui[i], &a, &b,
                   qcool ? &qcool[i] : NULL, qcc ? &qcc[i] : NULL, &f);
         ue_out[i] = a; ui_out[i] = b;
-        for (int k = 0; k < 5; ++k) cnt[k] += (f >> k) & 1u;
+        for (int k = 0; k < 6; ++k) cnt[k] += (f >> k) & 1u;
     }
     if (counters) for (int k = 0; k < 6; ++k) counters[k] = cnt[k];
     free(R);
@@ -712,8 +817,8 @@ int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, 
              const double* rho, const double* B, const double* H, const double* ue, const double* ui,
              double* ue_out, double* ui_out, double* qcool, double* qcc,
              long long* counters, int nthreads) {
-    return step_impl(s, lb, ls, lc, lazy, direct, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool, qcc,
-                     counters, nthreads);
+    return step_impl(s, lb, ls, lc, lazy, direct, NULL, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool,
+                     qcc, counters, nthreads);
 }
 
 /* The step with the 4-D channel given as per-interval node pairs (the
@@ -723,8 +828,39 @@ int orc_step_pairs(const orc_spec* s, const double* lb, const double* lsp, const
                    const double* rho, const double* B, const double* H, const double* ue, const double* ui,
                    double* ue_out, double* ui_out, double* qcool, double* qcc,
                    long long* counters, int nthreads) {
-    return step_impl(s, lb, NULL, lc, 0, 0, lsp, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool, qcc,
+    return step_impl(s, lb, NULL, lc, 0, 0, lsp, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool, qcc,
                      counters, nthreads);
+}
+
+/* The step with the surrogate network in place of the 4-D channel, except
+ * in table cells whose fallback bit is set (mask nullable: never).  l0,
+ * span: log2 of the table box per axis (H, B, n_e, T_e); xs: normalised
+ * log2 of the K2 switch; rounding: apply the bf16 operand roundings. */
+int orc_step_surrogate(const orc_spec* s, const double* lb, const double* ls, const double* lc,
+                       const float* params, double mean, double stdv, const double* l0, const double* span,
+                       double xs, const uint32_t* mask, int rounding, const orc_params* p, long long n,
+                       const double* rho, const double* B, const double* H, const double* ue, const double* ui,
+                       double* ue_out, double* ui_out, double* qcool, double* qcc,
+                       long long* counters, int nthreads) {
+    orc_net* m = (orc_net*)malloc(sizeof(orc_net));
+    if (!m) return -1;
+    net_init(m, params, mean, stdv, l0, span, xs, mask, rounding);
+    int rc = step_impl(s, lb, (double*)ls, lc, 0, 0, NULL, m, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool,
+                       qcc, counters, nthreads);
+    free(m);
+    return rc;
+}
+
+/* Network output (log2 units) at n normalised points x[n][4]. */
+int orc_net_eval(const float* params, double mean, double stdv, double xs, int rounding, long long n,
+                 const double* x, double* out) {
+    orc_net* m = (orc_net*)malloc(sizeof(orc_net));
+    if (!m) return -1;
+    double l0[4] = {0, 0, 0, 0}, span[4] = {1, 1, 1, 1};
+    net_init(m, params, mean, stdv, l0, span, xs, NULL, rounding);
+    for (long long i = 0; i < n; ++i) out[i] = net_eval(m, x + 4 * i);
+    free(m);
+    return 0;
 }
 
 /* Cooling energy removed in one sub-cycle (code units) at electron energy
@@ -734,6 +870,7 @@ double orc_cool_q_cell(const orc_spec* s, const double* lb, double* ls, const do
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return NAN;
     R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = direct; R->lsp = NULL;
+    R->net = NULL;
     for (int a = 0; a < 5; ++a) axis_init(s, a, &R->ax[a]);
     cell_ctx c;
     cell_setup(R, p, rho, B, H, &c);
@@ -1051,7 +1188,7 @@ int orc_step_bwd(const orc_spec* s, const double* lb, double* ls, const double* 
                  double* ui_out, int nthreads) {
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return -1;
-    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = 0; R->lsp = NULL;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = 0; R->lsp = NULL; R->net = NULL;
     for (int a = 0; a < 5; ++a) {
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
         axis_init(s, a, &R->ax[a]);

@@ -105,8 +105,8 @@ def test_mlp_reference_gradient_fd():
     from oracle import mlp
     rng = np.random.default_rng(9)
     p = np.zeros(mlp.P_N)
-    W1 = rng.uniform(-1, 1, (128, 16)) * np.sqrt(6 / 4)
-    W1[:, 4:] = 0
+    W1 = rng.uniform(-1, 1, (128, 16)) * np.sqrt(6 / 5)
+    W1[:, 5:] = 0
     p[mlp.P_W1:mlp.P_b1] = W1.reshape(-1)
     p[mlp.P_b1:mlp.P_W2] = rng.normal(0, 0.1, 128)
     p[mlp.P_W2:mlp.P_b2] = rng.uniform(-1, 1, 128 * 128) * np.sqrt(6 / 128)
@@ -115,13 +115,32 @@ def test_mlp_reference_gradient_fd():
     p[mlp.P_b3] = 0.3
     x = rng.uniform(-1, 1, (64, 4))
     y = rng.normal(0, 1, 64)
-    g, _ = mlp.grads(p, x, y, rounding=False)
-    idx = np.concatenate([rng.choice(np.flatnonzero(np.arange(mlp.P_b1) % 16 < 4), 6),
+    xs = 0.1   # both sides of the switch occur among the points
+    g, _ = mlp.grads(p, x, y, xs, rounding=False)
+    assert np.all(g[mlp.P_W1:mlp.P_b1].reshape(128, 16)[:, 5:] == 0)
+    idx = np.concatenate([rng.choice(np.flatnonzero(np.arange(mlp.P_b1) % 16 < 5), 8),
+                          np.arange(4, mlp.P_b1, 16)[:3],
                           rng.integers(mlp.P_b1, mlp.P_N, 30), [mlp.P_b3]])
     h = 1e-5
     for i in idx:
         pp, pm = p.copy(), p.copy()
         pp[i] += h
         pm[i] -= h
-        fd = (mlp.grads(pp, x, y, rounding=False)[1] - mlp.grads(pm, x, y, rounding=False)[1]) / (2 * h)
+        fd = (mlp.grads(pp, x, y, xs, rounding=False)[1] - mlp.grads(pm, x, y, xs, rounding=False)[1]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-7 + 1e-5 * abs(g[i]), (i, fd, g[i])
+
+
+def test_mlp_input_parts():
+    """The two bf16 parts of each input carry 16 significant bits (|x - hi -
+    lo| <= 2^-16 |x|, against 2^-8 |x| for hi alone), and the switch side is
+    +1 strictly above xs and -1 at or below it."""
+    from oracle import mlp
+    rng = np.random.default_rng(10)
+    x = rng.uniform(-1, 1, (4000, 4)).astype(np.float32).astype(np.float64)
+    x[0, 3] = np.float32(0.25)
+    X = mlp.features(x, 0.25)
+    err = np.abs(x - X[:, :4] - X[:, 4:8])
+    assert np.all(err <= 2.0 ** -16 * np.abs(x))
+    assert np.max(np.abs(x - X[:, :4]) / np.abs(x)) > 2.0 ** -10
+    assert np.array_equal(X[:, 8], np.where(x[:, 3] > 0.25, 1.0, -1.0))
+    assert X[0, 8] == -1.0
