@@ -120,7 +120,8 @@ typedef struct {
     unsigned long long n_fp64_coulomb;   /* Coulomb exchange inside the equilibrium band in some sub-cycle
                                             (FP64 there when fp64_critical = 1; FP64 fields: always FP64) */
     unsigned long long n_implicit_fail;  /* implicit bracket without sign change: limited explicit step taken */
-    unsigned long long n_fallback;       /* reserved (surrogate fallback) */
+    unsigned long long n_fallback;       /* cool_surrogate_infer: the table read instead of the network in
+                                            some sub-cycle */
 } cool_counters;
 
 typedef struct cool_table cool_table;    /* opaque; owns device memory */
@@ -245,7 +246,9 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
 
 /* ---- learned surrogate of the synchrotron channel (not in the paper) ------
  * An MLP 4 -> 128 -> 128 -> 1 with SiLU (inputs: the four log2 coordinates
- * normalised to [-1, 1] over the table box; output: the standardised
+ * normalised to [-1, 1] over the table box, each as two bf16 parts (value
+ * and rounding residual), plus the side of the K2 switch temperature as
+ * +-1, where the channel jumps; output: the standardised
  * log2(eta Q_syn)), BF16 weights and activations on the tensor cores
  * (tcgen05, FP32 accumulation), trained on the GPU by Adam on MSE in log2
  * space with samples labelled by the FP64 formulas (half on table nodes,
@@ -258,7 +261,7 @@ typedef struct {
     int channel;               /* 1 = synchrotron (the only one supported) */
     long long n_samples;       /* training samples (default 2^24), multiple of batch */
     int batch;                 /* samples per Adam step, multiple of 128 (16384) */
-    int epochs;                /* passes over the samples (4); 0 = initial weights only */
+    int epochs;                /* passes over the samples (16); 0 = initial weights only */
     double lr, lr_final;       /* Adam learning rate, cosine decay from lr to lr_final */
     unsigned long long seed;   /* samples and initial weights */
     double fallback_tol;       /* 1e-3 */
@@ -271,6 +274,7 @@ typedef struct {
     long long fallback_cells;  /* cells where the table is used instead of the network */
     long long param_bytes_bf16;/* bytes of the network as stored for inference */
     double mean, std;          /* output standardisation (log2 units) */
+    double x_switch;           /* normalised log2 T_e of the K2 switch (input column 8 is +1 above it) */
 } cool_surrogate_stats;
 
 cool_status cool_fit_spec_default(cool_fit_spec* f);
@@ -281,8 +285,9 @@ cool_status cool_surrogate_fit(const cool_table* t, const cool_fit_spec* f, void
 cool_status cool_surrogate_free(cool_surrogate* s);
 cool_status cool_surrogate_info(const cool_surrogate* s, cool_surrogate_stats* out);
 
-/* The 18817 FP32 parameters (W1 [128][16] with input columns 4..15 zero,
- * b1 [128], W2 [128 out][128 in], b2 [128], w3 [128], b3), host memory. */
+/* The 18817 FP32 parameters (W1 [128][16]: columns 0..3 the coordinates,
+ * column 4 the switch side, columns 5..15 zero; b1 [128], W2 [128 out][128
+ * in], b2 [128], w3 [128], b3), host memory. */
 cool_status cool_surrogate_get_params(const cool_surrogate* s, float* host, int n);
 cool_status cool_surrogate_set_params(cool_surrogate* s, const float* host, int n);
 
@@ -299,6 +304,27 @@ cool_status cool_surrogate_eval(const cool_surrogate* s, long long n, const floa
 /* The fallback bits (one per 4-D table cell, cell index ((h (nB-1) + b)
  * (nne-1) + n) (nTe-1) + t), host memory of (cells + 31)/32 words. */
 cool_status cool_surrogate_mask(const cool_surrogate* s, uint32_t* host_bits, long long words);
+
+/* Replace the fallback bits (host memory, same layout and size as
+ * cool_surrogate_mask; bits past the last cell are ignored).  A set bit
+ * sends every cell whose sub-cycle lands in that table cell to the table. */
+cool_status cool_surrogate_set_mask(cool_surrogate* s, const uint32_t* host_bits, long long words);
+
+/* The step of cool_step (explicit mode with the limiter, FP32 fields, FP32
+ * table) with the synchrotron channel read from the surrogate instead of
+ * the table: each sub-cycle evaluates the network on tiles of 128 cells
+ * (two tensor-core products) at the cell's (H, B, n_e, T_e), except where
+ * the cell's 4-D table cell carries a fallback bit, which reads the table
+ * as cool_step does.  Brems, Coulomb, the bridge (Eq. 11), the limiter and
+ * the update are those of cool_step.  t must be the table s was fitted to
+ * (same node counts and box, else COOL_EINVAL); implicit mode, fp64_critical
+ * and 16-bit tables give COOL_EUNSUPPORTED.  Arguments, aliasing and
+ * invalid-cell handling as cool_step; counters->n_fallback counts cells that
+ * used the table in some sub-cycle.  Device pointers, asynchronous on stream. */
+cool_status cool_surrogate_infer(const cool_surrogate* s, const cool_table* t, const cool_params* p,
+                                 long long n_cells, const float* rho, const float* B, const float* H,
+                                 const float* u_e_in, const float* u_i_in, float* u_e_out, float* u_i_out,
+                                 float* q_cool_out, float* q_cc_out, cool_counters* counters, void* stream);
 
 /* Check entry of the tensor-core GEMM primitive the surrogate is built on
  * (5th-generation tensor cores, tcgen05.mma kind::f16, FP32 accumulation in

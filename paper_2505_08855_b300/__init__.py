@@ -292,7 +292,7 @@ class FitSpec:
     channel: int = 1
     n_samples: int = 1 << 24
     batch: int = 16384
-    epochs: int = 4
+    epochs: int = 16
     lr: float = 2e-3
     lr_final: float = 2e-5
     seed: int = 20250513
@@ -363,6 +363,36 @@ class Surrogate:
         _b.check(_b.lib().cool_surrogate_mask(self.handle, out.ctypes.data_as(C.c_void_p), out.size),
                  "cool_surrogate_mask")
         return out
+
+    def set_mask(self, bits):
+        """Replace the fallback bits (uint32 words, the layout of mask())."""
+        import numpy as np
+        bits = np.ascontiguousarray(bits, np.uint32)
+        _b.check(_b.lib().cool_surrogate_set_mask(self.handle, bits.ctypes.data_as(C.c_void_p), bits.size),
+                 "cool_surrogate_set_mask")
+
+    def step(self, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None, q_cc=None,
+             counters=None, stream=None, table=None):
+        """cool_surrogate_infer: the explicit step with the synchrotron channel
+        from the network (table fallback where the mask says so).  FP32 CUDA
+        fields; returns (ue_out, ui_out)."""
+        import torch
+        table = self.table if table is None else table
+        fields = (rho, B, H, ue, ui)
+        n = rho.numel()
+        for f in fields:
+            if f.dtype != torch.float32 or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+                raise ValueError("fields must be contiguous float32 CUDA tensors of one size")
+        if ue_out is None:
+            ue_out = torch.empty_like(ue)
+        if ui_out is None:
+            ui_out = torch.empty_like(ui)
+        p = params.c()
+        cptr = C.c_void_p(counters.data_ptr()) if counters is not None else C.c_void_p(0)
+        _b.check(_b.lib().cool_surrogate_infer(self.handle, table.handle, _b.ref(p), n, *[_ptr(f) for f in fields],
+                                               _ptr(ue_out), _ptr(ui_out), _ptr(q_cool), _ptr(q_cc), cptr,
+                                               _stream_ptr(stream)), "cool_surrogate_infer")
+        return ue_out, ui_out
 
     def free(self):
         if self._h is not None:

@@ -26,7 +26,7 @@ EXPORTS = (
     "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
     "cool_debug_gemm_bf16", "cool_fit_spec_default", "cool_surrogate_fit", "cool_surrogate_free",
     "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
-    "cool_surrogate_eval", "cool_surrogate_mask",
+    "cool_surrogate_eval", "cool_surrogate_mask", "cool_surrogate_set_mask", "cool_surrogate_infer",
 )
 
 
@@ -58,7 +58,7 @@ class cool_fit_spec(C.Structure):
 class cool_surrogate_stats(C.Structure):
     _fields_ = [("final_loss", C.c_double), ("steps", C.c_longlong), ("mask_cells", C.c_longlong),
                 ("fallback_cells", C.c_longlong), ("param_bytes_bf16", C.c_longlong), ("mean", C.c_double),
-                ("std", C.c_double)]
+                ("std", C.c_double), ("x_switch", C.c_double)]
 
 
 class cool_counters(C.Structure):
@@ -121,6 +121,8 @@ def lib():
             "cool_surrogate_grads": (I, [P, LL, P, P, P, P, P]),
             "cool_surrogate_eval": (I, [P, LL, P, P, P]),
             "cool_surrogate_mask": (I, [P, P, LL]),
+            "cool_surrogate_set_mask": (I, [P, P, LL]),
+            "cool_surrogate_infer": (I, [P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_table_export_packed": (I, [P, P, LL]),
         }
         for name, (res, args) in sig.items():

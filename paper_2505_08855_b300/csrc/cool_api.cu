@@ -48,6 +48,24 @@ long long syn_count(const cool_table_spec& s) {
     return (long long)s.n_H * s.n_B * s.n_ne * s.n_Te;
 }
 
+cool_status validate_params(const cool_params* p) {
+    if (!p) return COOL_ENULL;
+    if (!(p->rho_scale > 0.0) || !isfinite(p->rho_scale)) return COOL_EINVAL;
+    if (!(p->M_bh_msun > 0.0) || !isfinite(p->M_bh_msun)) return COOL_EINVAL;
+    if (!(p->gamma_e > 1.0) || !(p->gamma_i > 1.0) || !isfinite(p->gamma_e) || !isfinite(p->gamma_i))
+        return COOL_EINVAL;
+    if (!(p->dt >= 0.0) || !isfinite(p->dt)) return COOL_EINVAL;
+    if (p->n_sub < 1 || p->n_sub > 64) return COOL_EINVAL;
+    if (p->mode != COOL_EXPLICIT_LIMITED && p->mode != COOL_IMPLICIT_STIFF) return COOL_EINVAL;
+    if (!(p->limiter_frac > 0.0 && p->limiter_frac <= 1.0)) return COOL_EINVAL;
+    if (!(p->eq_band >= 0.0 && p->eq_band < 1.0)) return COOL_EINVAL;
+    if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
+    if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
+    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
+    if (p->fp64_critical != 0 && p->fp64_critical != 1) return COOL_EINVAL;
+    return COOL_OK;
+}
+
 namespace {
 
 __global__ void k_pack_f32(const double* src, float* dst, long long n) {
@@ -129,23 +147,6 @@ cool_status validate_spec(const cool_table_spec* s) {
     return COOL_OK;
 }
 
-cool_status validate_params(const cool_params* p) {
-    if (!p) return COOL_ENULL;
-    if (!(p->rho_scale > 0.0) || !isfinite(p->rho_scale)) return COOL_EINVAL;
-    if (!(p->M_bh_msun > 0.0) || !isfinite(p->M_bh_msun)) return COOL_EINVAL;
-    if (!(p->gamma_e > 1.0) || !(p->gamma_i > 1.0) || !isfinite(p->gamma_e) || !isfinite(p->gamma_i))
-        return COOL_EINVAL;
-    if (!(p->dt >= 0.0) || !isfinite(p->dt)) return COOL_EINVAL;
-    if (p->n_sub < 1 || p->n_sub > 64) return COOL_EINVAL;
-    if (p->mode != COOL_EXPLICIT_LIMITED && p->mode != COOL_IMPLICIT_STIFF) return COOL_EINVAL;
-    if (!(p->limiter_frac > 0.0 && p->limiter_frac <= 1.0)) return COOL_EINVAL;
-    if (!(p->eq_band >= 0.0 && p->eq_band < 1.0)) return COOL_EINVAL;
-    if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
-    if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
-    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
-    if (p->fp64_critical != 0 && p->fp64_critical != 1) return COOL_EINVAL;
-    return COOL_OK;
-}
 
 // Node arrays of one axis: l_j = log2(min) + j dl, x_j = 2^l_j.
 void axis_nodes(double lo, double hi, int n, double* x64, double* l64) {

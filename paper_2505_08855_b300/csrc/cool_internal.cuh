@@ -111,6 +111,11 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
                                 const float* B, const float* H, const float* ue, const float* ui,
                                 const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
                                 float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st);
+cool_status validate_params(const cool_params* p);
+cool_status launch_step_surrogate(const cool_surrogate* sg, const cool_table* t, const cool_params* p, long long n,
+                                  const float* rho, const float* B, const float* H, const float* ue,
+                                  const float* ui, float* ue_o, float* ui_o, float* qc, float* qx,
+                                  cool_counters* cnt, cudaStream_t st);
 cool_status launch_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
                                 int* idx, float* w, cudaStream_t st);
 

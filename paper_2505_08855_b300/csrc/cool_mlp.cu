@@ -58,63 +58,13 @@ constexpr int kEOffH1 = kEOffX + kT * kIn * 2;
 constexpr int kEOffBar = kEOffH1 + kT * kHid * 2;
 constexpr int kSmemEval = kEOffBar + 16;
 
-__device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + __expf(-z)); }
-
-// 32 values into row r, columns k0..k0+31, of an R x K K-major operand.
-__device__ __forceinline__ void st_row32(unsigned char* base, int r, int k0, int K, const float (&v)[32]) {
-#pragma unroll
-    for (int c = 0; c < 32; c += 8) {
-        __align__(16) bf16 tmp[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) tmp[j] = __float2bfloat16_rn(v[c + j]);
-        *reinterpret_cast<uint4*>(base + mma::kmajor_offset(r, k0 + c, K)) = *reinterpret_cast<const uint4*>(tmp);
-    }
-}
-
-__device__ __forceinline__ void st_bf16(unsigned char* base, int r, int k, int K, float v) {
-    *reinterpret_cast<bf16*>(base + mma::kmajor_offset(r, k, K)) = __float2bfloat16_rn(v);
-}
-
-// Row-major [R][K] bf16 in global memory -> the K-major layout.
-__device__ __forceinline__ void load_kmajor(unsigned char* dst, const bf16* src, int R, int K) {
-    const int kc = K >> 3;
-    for (int i = threadIdx.x; i < R * kc; i += blockDim.x) {
-        const int r = i / kc, c = i % kc;
-        *reinterpret_cast<uint4*>(dst + mma::kmajor_offset(r, c * 8, K)) =
-            *reinterpret_cast<const uint4*>(src + (size_t)r * K + c * 8);
-    }
-}
-
-// D (+)= A B^T over K (multiple of 16); issued by one thread, not committed.
-__device__ __forceinline__ void issue(uint32_t d_tmem, const unsigned char* A, const unsigned char* B, int K, int N) {
-    const uint32_t idesc = mma::idesc_bf16_f32(128, N);
-    const uint32_t sbo = (uint32_t)(K >> 3) * 128;
-    for (int s = 0; s < K / 16; ++s) {
-        const uint64_t ad = mma::sdesc(mma::smem_addr(A) + s * 256, 128, sbo);
-        const uint64_t bd = mma::sdesc(mma::smem_addr(B) + s * 256, 128, sbo);
-        mma::mma_bf16(d_tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
-    }
-}
-
-// Make shared-memory operand writes of all threads visible to the tensor core.
-__device__ __forceinline__ void operands_ready() {
-    mma::fence_async_smem();
-    mma::fence_before_sync();
-    __syncthreads();
-    mma::fence_after_sync();
-}
-
-// Wait for one committed MMA group (phase parity); on timeout report, wait
-// once more (bounded) and continue.
-__device__ __forceinline__ bool mma_done(uint32_t mbar, uint32_t parity, unsigned* err) {
-    bool ok = mma::mbar_wait(mbar, parity, 1 << 20);
-    if (!ok) {
-        if (err) atomicOr(err, 2u);
-        mma::mbar_wait(mbar, parity, 1 << 16);
-    }
-    mma::fence_after_sync();
-    return ok;
-}
+using mma::sigm;
+using mma::st_row32;
+using mma::st_bf16;
+using mma::load_kmajor;
+using mma::issue;
+using mma::operands_ready;
+using mma::mma_done;
 
 // One training tile of 128 samples: forward, MSE against y (standardised
 // targets), backward; the gradients (of the batch mean, inv_batch = 1/B) are
@@ -135,19 +85,19 @@ __global__ void __launch_bounds__(kT, 1) k_mlp_train_tile(MlpDev w, const float*
     load_kmajor(sm + kOffW2T, w.W2Tb, kHid, kHid);
     for (int i = t; i < kRedN; i += kT) red[i] = 0.f;
     {
-        float xv[32];
+        float xv[4];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) xv[k] = k < 4 ? x[4 * row + k] : 0.f;
+        for (int k = 0; k < 4; ++k) xv[k] = x[4 * row + k];
         // X row t (16 columns: two 16-byte chunks) and X^T column t
+        __align__(16) bf16 tmp[16];
+        input_row(xv, w.xs, tmp);
 #pragma unroll
-        for (int c = 0; c < kIn; c += 8) {
-            __align__(16) bf16 tmp[8];
+        for (int c = 0; c < kIn; c += 8)
+            *reinterpret_cast<uint4*>(sm + kOffX + mma::kmajor_offset(t, c, kIn)) =
+                *reinterpret_cast<const uint4*>(tmp + c);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) tmp[j] = __float2bfloat16_rn(xv[c + j]);
-            *reinterpret_cast<uint4*>(sm + kOffX + mma::kmajor_offset(t, c, kIn)) = *reinterpret_cast<const uint4*>(tmp);
-        }
-#pragma unroll
-        for (int k = 0; k < kIn; ++k) st_bf16(sm + kOffXT, k, t, kT, xv[k]);
+        for (int k = 0; k < kIn; ++k)
+            *reinterpret_cast<bf16*>(sm + kOffXT + mma::kmajor_offset(k, t, kT)) = tmp[k];
     }
     const float target = y[row];
     if (t == 0) {
@@ -258,8 +208,10 @@ __global__ void __launch_bounds__(kT, 1) k_mlp_train_tile(MlpDev w, const float*
         }
         float v[32];
         mma::tmem_ld32(tm + lane_off + kColDW1, v);
+        // fold the operand columns back onto W1's master columns
 #pragma unroll
-        for (int k = 0; k < 4; ++k) atomicAdd(&g[kP_W1 + t * kIn + k], v[k]);
+        for (int k = 0; k < 4; ++k) atomicAdd(&g[kP_W1 + t * kIn + k], v[k] + v[4 + k]);
+        atomicAdd(&g[kP_W1 + t * kIn + 4], v[8]);
     }
     mma::fence_before_sync();
     __syncthreads();
@@ -286,10 +238,12 @@ __global__ void k_adam(float* p, float* g, float* m, float* v, float lr, float b
     v[i] = vi;
     g[i] = 0.f;
     float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    if (i < kP_b1 && (i % kIn) >= 4) pi = 0.f;  // padded inputs
+    if (i < kP_b1 && (i % kIn) >= 5) pi = 0.f;  // unused input columns
     p[i] = pi;
     if (i < kP_b1) {
-        W1b[i] = __float2bfloat16_rn(pi);
+        const int r = i / kIn, c = i % kIn;
+        if (c < 4) W1b[r * kIn + 4 + c] = __float2bfloat16_rn(pi);
+        if (c < 5) W1b[r * kIn + w1_op_col(c)] = __float2bfloat16_rn(pi);
     } else if (i >= kP_W2 && i < kP_b2) {
         const int j = i - kP_W2;
         W2b[j] = __float2bfloat16_rn(pi);
@@ -299,7 +253,11 @@ __global__ void k_adam(float* p, float* g, float* m, float* v, float lr, float b
 
 __global__ void k_refresh_bf16(const float* p, bf16* W1b, bf16* W2b, bf16* W2Tb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kP_b1) W1b[i] = __float2bfloat16_rn((i % kIn) < 4 ? p[i] : 0.f);
+    if (i < kP_b1) {
+        const int r = i / kIn, c = i % kIn;
+        const float v = c < 4 ? p[r * kIn + c] : c < 8 ? p[r * kIn + c - 4] : c == 8 ? p[r * kIn + 4] : 0.f;
+        W1b[i] = __float2bfloat16_rn(v);
+    }
     if (i >= kP_W2 && i < kP_b2) {
         const int j = i - kP_W2;
         W2b[j] = __float2bfloat16_rn(p[i]);
@@ -360,8 +318,7 @@ __global__ void __launch_bounds__(kT) k_mlp_eval(MlpDev w, int mode, const float
         }
         {
             __align__(16) bf16 tmp[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) tmp[k] = __float2bfloat16_rn(k < 4 ? xv[k] : 0.f);
+            input_row(xv, w.xs, tmp);
             *reinterpret_cast<uint4*>(sm + kEOffX + mma::kmajor_offset(t, 0, kIn)) = *reinterpret_cast<const uint4*>(tmp);
             *reinterpret_cast<uint4*>(sm + kEOffX + mma::kmajor_offset(t, 8, kIn)) =
                 *reinterpret_cast<const uint4*>(tmp + 8);
@@ -467,6 +424,7 @@ MlpDev mlp_dev(const cool_surrogate* s) {
         w.l0[d] = (float)s->l0[d];
         w.span[d] = (float)s->span[d];
     }
+    w.xs = (float)s->x_switch;
     return w;
 }
 
@@ -554,7 +512,7 @@ cool_status cool_fit_spec_default(cool_fit_spec* f) {
     f->channel = 1;
     f->n_samples = 1LL << 24;
     f->batch = 16384;
-    f->epochs = 4;
+    f->epochs = 16;
     f->lr = 2e-3;
     f->lr_final = 2e-5;
     f->seed = 20250513ull;
@@ -584,6 +542,7 @@ cool_status cool_surrogate_fit(const cool_table* t, const cool_fit_spec* f, void
         s->l0[d] = log2(lo[d]);
         s->span[d] = log2(hi[d]) - s->l0[d];
     }
+    s->x_switch = 2.0 * (log2(t->spec.k2_switch_T) - s->l0[3]) / s->span[3] - 1.0;
     const int cells = 1;
     (void)cells;
     const long long nc = (long long)(t->spec.n_H - 1) * (t->spec.n_B - 1) * (t->spec.n_ne - 1) * (t->spec.n_Te - 1);
@@ -618,11 +577,11 @@ cool_status cool_surrogate_fit(const cool_table* t, const cool_fit_spec* f, void
         return stt;
     };
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? COOL_ENOMEM : set_cuda_error(e));
-    // initial parameters: uniform(-a, a) with a = sqrt(6 / fan_in) (fan_in 4, 128), w3 small
+    // initial parameters: uniform(-a, a) with a = sqrt(6 / fan_in) (fan_in 5, 128), w3 small
     std::vector<float> hp(kP_alloc, 0.f);
     uint64_t rs = f->seed;
     for (int o = 0; o < kHid; ++o)
-        for (int k = 0; k < 4; ++k) hp[kP_W1 + o * kIn + k] = (float)((2.0 * host_uniform(rs) - 1.0) * sqrt(6.0 / 4.0));
+        for (int k = 0; k < 5; ++k) hp[kP_W1 + o * kIn + k] = (float)((2.0 * host_uniform(rs) - 1.0) * sqrt(6.0 / 5.0));
     for (int i = 0; i < kHid * kHid; ++i) hp[kP_W2 + i] = (float)((2.0 * host_uniform(rs) - 1.0) * sqrt(6.0 / 128.0));
     for (int i = 0; i < kHid; ++i) hp[kP_w3 + i] = (float)((2.0 * host_uniform(rs) - 1.0) * sqrt(1.0 / 128.0));
     e = cudaMemcpyAsync(s->d_p, hp.data(), pb, cudaMemcpyHostToDevice, st);
@@ -722,9 +681,10 @@ cool_status cool_surrogate_info(const cool_surrogate* s, cool_surrogate_stats* o
     out->steps = s->steps;
     out->mask_cells = s->mask_bits;
     out->fallback_cells = s->mask_set;
-    out->param_bytes_bf16 = (long long)(kHid * 4 + kHid * kHid) * 2 + (long long)(3 * kHid + 1) * 4;
+    out->param_bytes_bf16 = (long long)(kHid * 5 + kHid * kHid) * 2 + (long long)(3 * kHid + 1) * 4;
     out->mean = s->mean;
     out->std = s->std;
+    out->x_switch = s->x_switch;
     return COOL_OK;
 }
 
@@ -780,6 +740,50 @@ cool_status cool_surrogate_mask(const cool_surrogate* s, uint32_t* host_bits, lo
     if (words != (s->mask_bits + 31) / 32) return COOL_EINVAL;
     cudaError_t e = cudaMemcpy(host_bits, s->d_mask, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+}
+
+cool_status cool_surrogate_set_mask(cool_surrogate* s, const uint32_t* host_bits, long long words) {
+    if (!s || !host_bits) return COOL_ENULL;
+    if (!sur_ok(s)) return COOL_ESTATE;
+    if (words != (s->mask_bits + 31) / 32) return COOL_EINVAL;
+    std::vector<uint32_t> hm(host_bits, host_bits + words);
+    const long long tail = s->mask_bits & 31;
+    if (tail) hm[words - 1] &= (1u << tail) - 1u;   // bits past the last cell stay clear
+    long long set = 0;
+    for (uint32_t w : hm) set += __builtin_popcount(w);
+    cudaError_t e = cudaMemcpy(s->d_mask, hm.data(), sizeof(uint32_t) * words, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    s->mask_set = set;
+    return COOL_OK;
+}
+
+cool_status cool_surrogate_infer(const cool_surrogate* s, const cool_table* t, const cool_params* p, long long n_cells,
+                                 const float* rho, const float* B, const float* H, const float* u_e_in,
+                                 const float* u_i_in, float* u_e_out, float* u_i_out, float* q_cool_out,
+                                 float* q_cc_out, cool_counters* counters, void* stream) {
+    if (!s || !t || !p) return COOL_ENULL;
+    if (!sur_ok(s) || !table_ok(t)) return COOL_ESTATE;
+    cool_status cs = validate_params(p);
+    if (cs != COOL_OK) return cs;
+    if (n_cells < 0) return COOL_EINVAL;
+    const cool_table_spec& a = s->spec;
+    const cool_table_spec& b = t->spec;
+    if (a.n_H != b.n_H || a.n_B != b.n_B || a.n_ne != b.n_ne || a.n_Te != b.n_Te || a.H_min != b.H_min ||
+        a.H_max != b.H_max || a.B_min != b.B_min || a.B_max != b.B_max || a.ne_min != b.ne_min ||
+        a.ne_max != b.ne_max || a.T_min != b.T_min || a.T_max != b.T_max)
+        return COOL_EINVAL;   // fitted to another table box
+    if (b.dtype != COOL_F32 || p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical) return COOL_EUNSUPPORTED;
+    if (n_cells == 0) return COOL_OK;
+    if (!rho || !B || !H || !u_e_in || !u_i_in || !u_e_out || !u_i_out) return COOL_ENULL;
+    const void* ptrs[] = {rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out, q_cc_out};
+    for (const void* q : ptrs)
+        if ((uintptr_t)q % 4 != 0) return COOL_EALIGN;
+    if ((uintptr_t)counters % 8 != 0) return COOL_EALIGN;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device || dev != s->device) return COOL_ESTATE;
+    return launch_step_surrogate(s, t, p, n_cells, rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out,
+                                 q_cc_out, counters, (cudaStream_t)stream);
 }
 
 }  // extern "C"

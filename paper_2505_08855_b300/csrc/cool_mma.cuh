@@ -136,5 +136,70 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Logistic sigmoid 1 / (1 + e^-z) from the hardware exp2 and reciprocal
+// approximations (a few ulp); e^-z = inf for z < -88 gives 0.
+__device__ __forceinline__ float sigm(float z) {
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z * -1.4426950408889634f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.f + e));
+    return r;
+}
+
+// 32 values into row r, columns k0..k0+31, of an R x K K-major operand.
+__device__ __forceinline__ void st_row32(unsigned char* base, int r, int k0, int K, const float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; c += 8) {
+        __align__(16) __nv_bfloat16 tmp[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tmp[j] = __float2bfloat16_rn(v[c + j]);
+        *reinterpret_cast<uint4*>(base + kmajor_offset(r, k0 + c, K)) = *reinterpret_cast<const uint4*>(tmp);
+    }
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char* base, int r, int k, int K, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + kmajor_offset(r, k, K)) = __float2bfloat16_rn(v);
+}
+
+// Row-major [R][K] bf16 in global memory -> the K-major layout.
+__device__ __forceinline__ void load_kmajor(unsigned char* dst, const __nv_bfloat16* src, int R, int K) {
+    const int kc = K >> 3;
+    for (int i = threadIdx.x; i < R * kc; i += blockDim.x) {
+        const int r = i / kc, c = i % kc;
+        *reinterpret_cast<uint4*>(dst + kmajor_offset(r, c * 8, K)) =
+            *reinterpret_cast<const uint4*>(src + (size_t)r * K + c * 8);
+    }
+}
+
+// D (+)= A B^T over K (multiple of 16); issued by one thread, not committed.
+__device__ __forceinline__ void issue(uint32_t d_tmem, const unsigned char* A, const unsigned char* B, int K, int N) {
+    const uint32_t idesc = mma::idesc_bf16_f32(128, N);
+    const uint32_t sbo = (uint32_t)(K >> 3) * 128;
+    for (int s = 0; s < K / 16; ++s) {
+        const uint64_t ad = sdesc(smem_addr(A) + s * 256, 128, sbo);
+        const uint64_t bd = sdesc(smem_addr(B) + s * 256, 128, sbo);
+        mma::mma_bf16(d_tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+    }
+}
+
+// Make shared-memory operand writes of all threads visible to the tensor core.
+__device__ __forceinline__ void operands_ready() {
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+}
+
+// Wait for one committed MMA group (phase parity); on timeout report, wait
+// once more (bounded) and continue.
+__device__ __forceinline__ bool mma_done(uint32_t mbar, uint32_t parity, unsigned* err) {
+    bool ok = mbar_wait(mbar, parity, 1 << 20);
+    if (!ok) {
+        if (err) atomicOr(err, 2u);
+        mbar_wait(mbar, parity, 1 << 16);
+    }
+    fence_after_sync();
+    return ok;
+}
+
 }  // namespace mma
 }  // namespace cool
