@@ -56,11 +56,21 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
+KERNEL_SOURCES = ("cool_step.cu", "cool_step_common.cuh", "cool_internal.cuh")
+
+
+def kernel_source_sha():
+    """sha256 (16 hex digits) over the sources the timed kernel is built from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2505_08855_b300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_per_launch():
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (sha256 of cool_step.cu); else None."""
-    src = os.path.join(ROOT, "paper_2505_08855_b300", "csrc", "cool_step.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    on the current kernel sources (kernel_source_sha); else None."""
+    sha = kernel_source_sha()
     for f in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
         if not f.endswith(".md"):
             continue

@@ -26,389 +26,10 @@
 //     so a sub-cycle that stays in its T_e interval reads no table memory;
 //   - the bridge is evaluated in log2 space so that no intermediate
 //     over/underflows FP32 over the table's 60-decade range.
-#include <cuda_fp16.h>
-#include <math.h>
-
-#include "cool_internal.cuh"
-#include "cool_mlp.cuh"
-#include "cool_mma.cuh"
+#include "cool_step_common.cuh"
 
 namespace cool {
 namespace {
-
-__device__ __forceinline__ float ex2a(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2a(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-
-// Shared-memory view of the small table parts.
-struct Smem {
-    const float* ax;   // concatenated axes (x, rx, lx per axis)
-    const float* lb;
-    const float* lc;
-};
-
-// ---------------------------------------------------------------------------
-// FP64 instantiation: all arithmetic in FP64 on the FP64 table channels
-// (the same algorithm; index selection compares the FP64 key with the FP32
-// nodes, weights from FP64 log2).
-// ---------------------------------------------------------------------------
-struct StepK64 {
-    DevTable tab;
-    double s_n, s_B, s_H, s_Te, s_Ti, ce, ci, hs, escale;
-    double limiter, eq_band, clamp;
-    int n_sub, mode, iters;
-};
-
-__device__ int select64(const DevTable& T, int a, double key, double& w, unsigned& clamp) {
-    const int n = T.n[a];
-    const float* x = T.axes + T.axis_off[a];
-    int j = 0;
-    if (!(key >= (double)x[0])) {
-        clamp = 1u;
-    } else {
-        int lo = 0, hi = n - 2;  // largest j in [0, n-2] with x[j] <= key
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if ((double)x[mid] <= key) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
-        if (key > (double)x[n - 1]) clamp = 1u;
-    }
-    double wl = key > 0.0 ? (log2(key) - (T.l0_64[a] + j * T.dl64[a])) / T.dl64[a] : 0.0;
-    w = fmin(fmax(wl, 0.0), 1.0);
-    return j;
-}
-
-struct Cell64 {
-    int jh, jb, jn;
-    double wh, wb, wn, ne, Hc;
-};
-
-__device__ double cool_q64(const StepK64& k, const Cell64& c, double ue, double rho, unsigned& clamp) {
-    const DevTable& T = k.tab;
-    double Te = k.s_Te * ue / rho;
-    double wt;
-    int jt = select64(T, 3, Te, wt, clamp);
-    const int nB = T.n[1], nN = T.n[2], nT = T.n[3];
-    double ls = 0.0;
-    for (int cidx = 0; cidx < 16; ++cidx) {
-        int bh = cidx & 1, bb = (cidx >> 1) & 1, bn = (cidx >> 2) & 1, bt = (cidx >> 3) & 1;
-        double wgt = (bh ? c.wh : 1.0 - c.wh) * (bb ? c.wb : 1.0 - c.wb) * (bn ? c.wn : 1.0 - c.wn) *
-                     (bt ? wt : 1.0 - wt);
-        long long idx = (((long long)(c.jh + bh) * nB + (c.jb + bb)) * nN + (c.jn + bn)) * nT + jt + bt;
-        ls += wgt * T.ls64[idx];
-    }
-    double lb = (1.0 - wt) * T.lb64[jt] + wt * T.lb64[jt + 1];
-    double qthin = c.ne * c.ne * exp2(lb) + exp2(ls);
-    double bb4 = 4.0 * kSigSB * Te * Te * Te * Te;
-    double tau_sca = 2.0 * c.ne * kSigT * c.Hc;
-    double tau_abs = c.Hc * qthin / bb4;
-    double Q = qthin / (1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca)));
-    return k.hs * Q / k.escale;
-}
-
-// Backward Euler of a stiff cell in FP64 on the FP64 table: bisection in
-// log2 u over [u0 2^-60, u0] (iters halvings).  Returns false when the
-// bracket has no sign change.
-__device__ __noinline__ bool implicit_fp64(const StepK64& k, const Cell64& c, double rho, double u0, double& u_out) {
-    unsigned dummy = 0u;
-    double a = log2(u0) - 60.0, b = log2(u0);
-    if (!(exp2(a) - u0 + cool_q64(k, c, exp2(a), rho, dummy) < 0.0)) return false;
-    for (int it = 0; it < k.iters; ++it) {
-        double m = 0.5 * (a + b);
-        double um = exp2(m);
-        if (um - u0 + cool_q64(k, c, um, rho, dummy) > 0.0) b = m; else a = m;
-    }
-    u_out = exp2(0.5 * (a + b));
-    return true;
-}
-
-struct StepK {
-    DevTable tab;
-    float s_n, s_B, s_H, s_Te, s_Ti;  // FP32 key scales (rounded once from FP64)
-    float ce, ci, inv_cec;            // gamma - 1, 1/(ce + ci)
-    double ce64, ci64, inv_cec64;
-    float s_K;                        // m_p c^2 / k_B  (T_s = (gamma_s - 1) s_K u_s / rho)
-    int fp64_critical;
-    StepK64 k64;                      // FP64 constants for stiff cells when fp64_critical
-    float l_hs_e;                     // log2(h / e_scale)
-    float l_bb;                       // log2(4 sigma_SB h / e_scale)
-    float two_sigT;                   // 2 sigma_T
-    float limiter, eq_band, clamp;
-    int n_sub, mode, iters;
-    int smem_floats;                  // floats of axes + lb + lc in shared memory
-    int axes_floats;
-};
-
-struct Sel {
-    int j;
-    float r;   // log2(key / x_j), unclamped
-};
-
-// Index selection on an axis (x, rx, lx arrays of n floats at `a`): the
-// largest j in [0, n-2] with x[j] <= key, compared exactly in FP32 (j = 0
-// below the first node).  The guess floor((log2 key - l_0)/dl) is within
-// one of that index (lg2.approx is accurate to ~1e-5 absolute, far below
-// one node spacing), so one upward and one downward correction make the
-// selection exact with no data-dependent loop.  The key is clamped when it
-// lies outside [x_0, x_{n-1}].
-__device__ __forceinline__ Sel select_axis(const float* a, int n, float inv_dl, float key,
-                                           unsigned& clamp) {
-    const float* x = a;
-    const float* rx = a + n;
-    const float* lx = a + 2 * n;
-    int j = __float2int_rd((lg2a(key) - lx[0]) * inv_dl);
-    j = min(max(j, 0), n - 2);
-    j += (j < n - 2 && x[j + 1] <= key) ? 1 : 0;
-    j -= (j > 0 && x[j] > key) ? 1 : 0;
-    clamp |= (key < x[0] || key > x[n - 1]) ? 1u : 0u;
-    Sel s;
-    s.j = j;
-    s.r = lg2a(key * rx[j]);
-    return s;
-}
-
-// Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
-struct CellC {
-    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words
-    int oH, oB, oN;     // float offsets to the H+1, B+1, n_e+1 corner rows
-    float wh, wb, wn;
-    float lb_off;       // log2(h n_e^2 / e_scale)
-    float ls_off;       // log2(h / e_scale)
-    float lbb_off;      // log2(4 sigma_SB h / (H_cm e_scale))
-    float tau_sca;      // 2 n_e sigma_T H_cm
-};
-
-// Collapsed synchrotron values of one T_e octet (7 intervals) live in shared
-// memory, node o of thread t at win[o * kThreads + t] (conflict-free).
-struct Cache {
-    int base;           // first node of the held octet (multiple of 7), -8 if none
-    float* win;         // this thread's window column
-};
-
-constexpr int kThreads = 256;
-
-__device__ __forceinline__ float lerpf(float a, float b, float w) { return fmaf(w, b - a, a); }
-
-// Packed formats of the 4-D channel (DevTable::fmt): nodes per 32-byte block
-// W and block stride S = W - 1.
-template <int FMT> struct Fmt;
-template <> struct Fmt<0> { static constexpr int W = 8, S = 7; };    // FP32
-template <> struct Fmt<1> { static constexpr int W = 16, S = 15; };  // BF16
-template <> struct Fmt<2> { static constexpr int W = 16, S = 15; };  // FP16
-template <> struct Fmt<3> { static constexpr int W = 12, S = 11; };  // BF16, block-scaled
-template <> struct Fmt<4> { static constexpr int W = 12, S = 11; };  // FP16, block-scaled
-constexpr int kMaxW = 16;
-
-// 256-bit read-only load of one block (32-byte aligned).
-__device__ __forceinline__ void ld8u(const uint32_t* p, uint32_t (&v)[8]) {
-    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-        : "l"(p));
-}
-
-__device__ __forceinline__ float half_bits(uint32_t h16, bool f16) {
-    return f16 ? __half2float(__ushort_as_half((unsigned short)h16)) : __uint_as_float(h16 << 16);
-}
-
-// Value of node t (0 <= t < W) of a block.
-template <int FMT>
-__device__ __forceinline__ float dec(const uint32_t (&r)[8], int t) {
-    if (FMT == 0) return __uint_as_float(r[t]);
-    if (FMT == 1 || FMT == 2) {
-        const uint32_t w = r[t >> 1];
-        return half_bits((t & 1) ? (w >> 16) : (w & 0xffffu), FMT == 2);
-    }
-    const uint32_t w = r[2 + (t >> 1)];
-    const float res = half_bits((t & 1) ? (w >> 16) : (w & 0xffffu), FMT == 4);
-    return fmaf(__uint_as_float(r[1]), res, __uint_as_float(r[0]));
-}
-
-// Read the 8 corner blocks of block kb (one 32-byte sector each) and collapse
-// the H, B, n_e axes: win[o] = trilinear value at T_e node S kb + o.
-template <int FMT>
-__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
-    constexpr int W = Fmt<FMT>::W;
-    const uint32_t* p = c.row + (long long)kb * 8;
-    if (FMT == 0) {
-        // FP32: all four (h, b) pairs reduced in registers
-        uint32_t a[8], b[8], d[8], e[8];
-        ld8u(p, a);
-        ld8u(p + c.oN, b);
-        float x[8], y[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = lerpf(dec<0>(a, t), dec<0>(b, t), c.wn);
-        ld8u(p + c.oB, b);
-        ld8u(p + c.oB + c.oN, d);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = lerpf(x[t], lerpf(dec<0>(b, t), dec<0>(d, t), c.wn), c.wb);
-        const uint32_t* q = p + c.oH;
-        ld8u(q, b);
-        ld8u(q + c.oN, d);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) y[t] = lerpf(dec<0>(b, t), dec<0>(d, t), c.wn);
-        ld8u(q + c.oB, d);
-        ld8u(q + c.oB + c.oN, e);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            y[t] = lerpf(y[t], lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
-            cc.win[t * kThreads] = lerpf(x[t], y[t], c.wh);
-        }
-    } else {
-        // 16-bit formats (W = 16 or 12 nodes): the partial sums go through
-        // the window in shared memory to bound register use
-        uint32_t r0[8], r1[8];
-        ld8u(p, r0);
-        ld8u(p + c.oN, r1);
-#pragma unroll
-        for (int t = 0; t < W; ++t) cc.win[t * kThreads] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
-        ld8u(p + c.oB, r0);
-        ld8u(p + c.oB + c.oN, r1);
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
-        const uint32_t* q = p + c.oH;
-        float hb[W];
-        ld8u(q, r0);
-        ld8u(q + c.oN, r1);
-#pragma unroll
-        for (int t = 0; t < W; ++t) hb[t] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
-        ld8u(q + c.oB, r0);
-        ld8u(q + c.oB + c.oN, r1);
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-            const float h1 = lerpf(hb[t], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
-            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], h1, c.wh);
-        }
-    }
-    cc.base = Fmt<FMT>::S * kb;
-}
-
-// Energy (code units) that cooling removes in one sub-cycle at T_e, with
-// the bridge of Eq. 11 evaluated in log2 space:
-//   A = log2 q_thin = log2(q_brem + q_syn), B = log2 q_bb with
-//   q_bb = h 4 sigma T^4/(H e_scale), tau_abs = 2^(A - B),
-//   q = q_thin / (1 + tau_abs (sqrt3 + 1.5 (tau_abs + tau_sca))).
-// The common path has no range branches: 2^d underflows to 0 where one
-// channel is negligible and tau_abs to 0 where the cell is thin; only
-// tau_abs > 2^60 (where tau_abs^2 would overflow) takes the asymptotic form.
-template <int FMT>
-__device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, const CellC& c,
-                                             Cache& cc, float Te, unsigned& clamp) {
-    const int nT = k.tab.n[3];
-    const float* axT = S.ax + k.tab.axis_off[3];
-    Sel s = select_axis(axT, nT, k.tab.inv_dl[3], Te, clamp);
-    const int j = s.j;
-    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
-    const int o = j - cc.base;
-    const float w = __saturatef(s.r * k.tab.inv_dl[3]);
-    const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
-    const float Lb = lerpf(S.lb[j], S.lb[j + 1], w) + c.lb_off;
-    const float lT = axT[2 * nT + j] + s.r;
-    const float M = fmaxf(Ls, Lb);
-    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
-    const float Bb = fmaf(4.f, lT, c.lbb_off);
-    const float lt = A - Bb;  // log2 tau_abs
-    float lq;
-    if (lt <= 60.f) {
-        const float tau = ex2a(lt);
-        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
-        lq = A - lg2a(D);
-    } else {
-        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    }
-    return ex2a(fminf(lq, 126.f));
-}
-
-// Backward Euler u' = u0 - q(u') of a stiff cell (q(u0) > limiter u0) in
-// FP32.  Bracket [u0 2^-60, u0]: g(u0) = q(u0) > 0 and g(u0 2^-60) < 0 is
-// checked (false when it fails).  Illinois (modified regula falsi) first on
-// G(x) = log2((2^x + q(2^x))/u0), x = log2 u, which is close to piecewise
-// linear over the 60 octaves, then on g(u) = u + q(u) - u0 in u once the
-// bracket is tight (FP32 x cannot resolve u to better than ~1e-6).  At most
-// implicit_iters evaluations.  Kept out of line: stiff cells are a minority.
-template <int FMT>
-__device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
-                                           float inv_e, float u0, float q0, float& u_out) {
-    const float inv_u0 = 1.f / u0;
-    unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
-    float xb = lg2a(u0);
-    float xa = xb - 60.f;
-    const float ua0 = ex2a(xa);
-    const float qa0 = cool_energy<FMT>(k, S, c, cc, ua0 * inv_e, trial);
-    if (!(ua0 - u0 + qa0 < 0.f)) return false;
-    float Gb = lg2a(fmaf(q0, inv_u0, 1.f));
-    float Ga = lg2a((ua0 + qa0) * inv_u0);
-    int side = 0, it = 0;
-    for (; it < k.iters; ++it) {
-        if (xb - xa < 1e-3f) break;
-        float x = xb - Gb * (xb - xa) / (Gb - Ga);
-        if (!(x > xa && x < xb)) x = 0.5f * (xa + xb);
-        const float u = ex2a(x);
-        const float G = lg2a((u + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
-        if (G > 0.f) {
-            xb = x; Gb = G;
-            if (side == 1) Ga *= 0.5f;
-            side = 1;
-        } else {
-            xa = x; Ga = G;
-            if (side == -1) Gb *= 0.5f;
-            side = -1;
-        }
-    }
-    float a = ex2a(xa), b = ex2a(xb);
-    float ga = a - u0 + cool_energy<FMT>(k, S, c, cc, a * inv_e, trial);
-    float gb = b - u0 + cool_energy<FMT>(k, S, c, cc, b * inv_e, trial);
-    // an end whose residual rounds to the wrong sign is the root to rounding
-    float u = !(ga < 0.f) ? a : (!(gb > 0.f) ? b : 0.5f * (a + b));
-    side = 0;
-    for (; it < k.iters && ga < 0.f && gb > 0.f; ++it) {
-        u = b - gb * (b - a) / (gb - ga);
-        if (!(u > a && u < b)) u = 0.5f * (a + b);
-        if (b - a <= 2.4e-7f * b) break;
-        const float g = u - u0 + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial);
-        if (g > 0.f) {
-            b = u; gb = g;
-            if (side == 1) ga *= 0.5f;
-            side = 1;
-        } else if (g < 0.f) {
-            a = u; ga = g;
-            if (side == -1) gb *= 0.5f;
-            side = -1;
-        } else {
-            break;
-        }
-    }
-    u_out = u;
-    return true;
-}
-
-// The same solve in FP64 on the FP64 table (fp64_critical): the cell's H, B,
-// n_e selections are redone with FP64 keys and implicit_fp64 bisects.
-__device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
-                                                float u0, float& u_out) {
-    Cell64 c64;
-    unsigned dummy = 0u;
-    c64.ne = (double)rho * k.k64.s_n;
-    c64.Hc = (double)H * k.k64.s_H;
-    c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
-    c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
-    c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
-    double u1;
-    if (!implicit_fp64(k.k64, c64, (double)rho, (double)u0, u1)) return false;
-    u_out = (float)u1;
-    return true;
-}
-
 struct Out {
     float ue, ui, qc, qx;
     unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail
@@ -1031,361 +652,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             if (glc_s[i] != 0.f) atomicAdd(&g_lc[i], glc_s[i]);
 }
 
-
-// ---------------------------------------------------------------------------
-// The step with the learned surrogate (cool_surrogate_infer): the network
-// replaces the synchrotron-table read.  A CTA steps a tile of 128 cells (one
-// per thread); each sub-cycle the tile's four log2 coordinates (H, B, n_e,
-// T_e, normalised) form a 128 x 16 bf16 operand and the two hidden layers
-// run as tcgen05.mma (FP32 in TMEM), the 128 -> 1 output on the CUDA cores.
-// Cells whose 4-D table cell carries the fallback bit read the table instead;
-// a sub-cycle where every cell of the tile falls back skips the network.
-// Explicit mode, FP32 fields, FP32 table.
-// ---------------------------------------------------------------------------
-struct SurK {
-    const __nv_bfloat16* W1b;
-    const __nv_bfloat16* W2b;
-    const float* p;
-    float mean, std;
-    float l0[4], sc[4];        // x = (l - l0) sc - 1, sc = 2 / span
-    float xs;                  // normalised log2 of the K2 switch temperature
-    const uint32_t* mask;      // fallback bits (nullable: never fall back)
-};
-
-constexpr int kSurT = 128;
-
-// Table fallback: the two T_e nodes j, j + 1 of the 8 (H, B, n_e) corners
-// (both in block j / 7 of the FP32 layout, one 32-byte sector per corner),
-// collapsed trilinearly into v[0], v[1]; kept while the cell stays in T_e
-// interval j (the common case from one sub-cycle to the next).
-__device__ __forceinline__ void table_pair(const CellC& c, int j, float (&v)[2]) {
-    const float* p = reinterpret_cast<const float*>(c.row) + (j / 7) * 8 + (j % 7);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float* q = p + e;
-        const float a = lerpf(lerpf(__ldg(q), __ldg(q + c.oN), c.wn),
-                              lerpf(__ldg(q + c.oB), __ldg(q + c.oB + c.oN), c.wn), c.wb);
-        const float* r = q + c.oH;
-        const float b = lerpf(lerpf(__ldg(r), __ldg(r + c.oN), c.wn),
-                              lerpf(__ldg(r + c.oB), __ldg(r + c.oB + c.oN), c.wn), c.wb);
-        v[e] = lerpf(a, b, c.wh);
-    }
-}
-
-// Shared memory of the surrogate step: axes and brems channel (the Coulomb
-// table is read through L1), then the network operands.
-__host__ __device__ __forceinline__ int sur_table_floats(const StepK& k) {
-    return (k.axes_floats + k.tab.n[3] + 3) & ~3;
-}
-
-// The bridge of cool_energy, from the two channel values (log2, code units
-// per sub-cycle) and log2 T_e.
-__device__ __forceinline__ float bridge_energy(const CellC& c, float Ls, float Lb, float lT) {
-    const float M = fmaxf(Ls, Lb);
-    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
-    const float Bb = fmaf(4.f, lT, c.lbb_off);
-    const float lt = A - Bb;
-    float lq;
-    if (lt <= 60.f) {
-        const float tau = ex2a(lt);
-        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
-        lq = A - lg2a(D);
-    } else {
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    }
-    return ex2a(fminf(lq, 126.f));
-}
-
-__global__ void __launch_bounds__(kSurT) k_step_surrogate(StepK k, SurK m, long long n, const float* __restrict__ rho_in,
-                                                         const float* __restrict__ B_in, const float* __restrict__ H_in,
-                                                         const float* ue_in, const float* ui_in, float* ue_out,
-                                                         float* ui_out, float* qc_out, float* qx_out,
-                                                         cool_counters* cnt, unsigned* err) {
-    extern __shared__ __align__(1024) float sms[];
-    for (int i = threadIdx.x; i < k.axes_floats; i += blockDim.x) sms[i] = k.tab.axes[i];
-    for (int i = threadIdx.x; i < k.tab.n[3]; i += blockDim.x) sms[k.axes_floats + i] = k.tab.lb[i];
-    Smem S;
-    S.ax = sms;
-    S.lb = sms + k.axes_floats;
-    S.lc = k.tab.lc;
-    unsigned char* W1s = reinterpret_cast<unsigned char*>(sms + sur_table_floats(k));
-    unsigned char* W2s = W1s + 128 * 16 * 2;
-    unsigned char* H1s = W2s + 128 * 128 * 2;
-    // X is consumed by the first product before H1 is written, and written
-    // again only after the second product has consumed H1: they share space
-    unsigned char* Xs = H1s;
-    float* Ps = reinterpret_cast<float*>(H1s + 128 * 128 * 2);        // b1, b2, w3, b3
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(Ps + 3 * 128 + 4);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(Ps + 3 * 128 + 6);
-    const int t = threadIdx.x, warp = t >> 5;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    mma::load_kmajor(W1s, m.W1b, 128, 16);
-    mma::load_kmajor(W2s, m.W2b, 128, 128);
-    Ps[t] = m.p[kP_b1 + t];
-    Ps[128 + t] = m.p[kP_b2 + t];
-    Ps[256 + t] = m.p[kP_w3 + t];
-    if (t == 0) Ps[384] = m.p[kP_b3];
-    if (t == 0) {
-        mma::mbar_init(mma::smem_addr(mbar), 1);
-        mma::fence_mbar_init();
-    }
-    if (warp == 0) mma::tmem_alloc(mma::smem_addr(tslot), 128);
-    mma::operands_ready();
-    const uint32_t tm = *tslot;
-    const uint32_t mb = mma::smem_addr(mbar);
-    uint32_t phase = 0;
-    const DevTable& T = k.tab;
-    const int nB1 = T.n[1] - 1, nN1 = T.n[2] - 1, nT1 = T.n[3] - 1;
-    const long long ntiles = (n + kSurT - 1) / kSurT;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long i = tile * kSurT + t;
-        const bool live = i < n;
-        float rho = 1.f, B = 1e-3f, H = 1.f, ue = 1e-3f, ui = 1e-3f;
-        if (live) {
-            rho = rho_in[i]; B = B_in[i]; H = H_in[i]; ue = ue_in[i]; ui = ui_in[i];
-        }
-        const float ue0 = ue, ui0 = ui;
-        const bool valid = live && isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui) &&
-                           rho > 0.f && ue > 0.f && ui > 0.f && B >= 0.f && H >= 0.f;
-        if (!valid) { rho = 1.f; B = 1e-3f; H = 1.f; ue = 1e-3f; ui = 1e-3f; }
-        unsigned clamp = 0u, band = 0u, fallback = 0u;
-        const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
-        const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
-        CellC c;
-        float xH, xB, xN;
-        int jh, jb, jn;
-        {
-            Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
-            Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
-            Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
-            jh = sh.j; jb = sb.j; jn = sn.j;
-            const int rowf = 8 * T.nblk;
-            c.oN = rowf;
-            c.oB = rowf * T.n[2];
-            c.oH = c.oB * T.n[1];
-            c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
-            c.wh = __saturatef(sh.r * T.inv_dl[0]);
-            c.wb = __saturatef(sb.r * T.inv_dl[1]);
-            c.wn = __saturatef(sn.r * T.inv_dl[2]);
-            const float lH = lg2a(Hc), lB = lg2a(Bg), lN = lg2a(ne);
-            xH = fminf(fmaxf(fmaf(lH - m.l0[0], m.sc[0], -1.f), -1.f), 1.f);
-            xB = fminf(fmaxf(fmaf(lB - m.l0[1], m.sc[1], -1.f), -1.f), 1.f);
-            xN = fminf(fmaxf(fmaf(lN - m.l0[2], m.sc[2], -1.f), -1.f), 1.f);
-            c.ls_off = k.l_hs_e;
-            c.lb_off = fmaf(2.f, lN, k.l_hs_e);
-            c.lbb_off = k.l_bb - lH;
-            c.tau_sca = k.two_sigT * ne * Hc;
-        }
-        const float lcc_off = c.lb_off;
-        const int nC = T.n[4];
-        const float* axC = S.ax + T.axis_off[4];
-        const int nT = T.n[3];
-        const float* axT = S.ax + T.axis_off[3];
-        float sum_q = 0.f, sum_x = 0.f;
-        int pj = -1;             // T_e interval of the held fallback pair
-        float pv[2] = {0.f, 0.f};
-        for (int sub = 0; sub < k.n_sub; ++sub) {
-            // ---- (i) Coulomb exchange (the forward kernel's FP32 form) ----
-            const float Te = ue * inv_e, Ti = ui * inv_i;
-            const Sel se = select_axis(axC, nC, T.inv_dl[4], Te, clamp);
-            const Sel si = select_axis(axC, nC, T.inv_dl[4], Ti, clamp);
-            const float we = __saturatef(se.r * T.inv_dl[4]), wi = __saturatef(si.r * T.inv_dl[4]);
-            const float* row = S.lc + si.j * nC + se.j;
-            const float lC = lerpf(lerpf(__ldg(row), __ldg(row + 1), we),
-                                   lerpf(__ldg(row + nC), __ldg(row + nC + 1), we), wi);
-            const float rate = ex2a(fminf(lC + lcc_off, 126.f));
-            band |= fabsf(Te - Ti) <= k.eq_band * Ti ? 1u : 0u;
-            const float pe = k.ce * ue;
-            const float ee = fmaf(k.ce, ue, -pe);
-            const float D = fmaf(k.ci, ui, -pe) - ee;
-            float X = rate * (kr * D);
-            const float lim = k.clamp * fabsf(D * k.inv_cec);
-            X = fabsf(X) > lim ? copysignf(lim, X) : X;
-            ue += X;
-            ui -= X;
-            sum_x += X;
-            // ---- (ii) cooling: network or table for the synchrotron channel ----
-            const float Te1 = ue * inv_e;
-            const Sel st = select_axis(axT, nT, T.inv_dl[3], Te1, clamp);
-            const float wt = __saturatef(st.r * T.inv_dl[3]);
-            const float lT = axT[2 * nT + st.j] + st.r;
-            bool flagged = false;
-            if (m.mask) {
-                const long long cell = (((long long)jh * nB1 + jb) * nN1 + jn) * nT1 + st.j;
-                flagged = (m.mask[cell >> 5] >> (cell & 31)) & 1u;
-            }
-            float Ls;
-            if (__syncthreads_or(valid && !flagged)) {
-                const float xT = fminf(fmaxf(fmaf(lT - m.l0[3], m.sc[3], -1.f), -1.f), 1.f);
-                {
-                    const float xv[4] = {xH, xB, xN, xT};
-                    __align__(16) __nv_bfloat16 tmp[16];
-                    input_row(xv, m.xs, tmp);
-                    *reinterpret_cast<uint4*>(Xs + mma::kmajor_offset(t, 0, 16)) = *reinterpret_cast<const uint4*>(tmp);
-                    *reinterpret_cast<uint4*>(Xs + mma::kmajor_offset(t, 8, 16)) =
-                        *reinterpret_cast<const uint4*>(tmp + 8);
-                }
-                mma::operands_ready();
-                if (t == 0) {
-                    mma::issue(tm, Xs, W1s, 16, 128);
-                    mma::commit(mb);
-                }
-                mma::mma_done(mb, phase, err);
-                phase ^= 1u;
-#pragma unroll 1
-                for (int c0 = 0; c0 < 128; c0 += 32) {
-                    float z[32];
-                    mma::tmem_ld32(tm + lane_off + c0, z);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float zz = z[j] + Ps[c0 + j];
-                        z[j] = zz * mma::sigm(zz);
-                    }
-                    mma::st_row32(H1s, t, c0, 128, z);
-                }
-                mma::operands_ready();
-                // Z2 overwrites Z1's columns: every thread has read Z1
-                if (t == 0) {
-                    mma::issue(tm, H1s, W2s, 128, 128);
-                    mma::commit(mb);
-                }
-                mma::mma_done(mb, phase, err);
-                phase ^= 1u;
-                float yh = Ps[384];
-#pragma unroll 1
-                for (int c0 = 0; c0 < 128; c0 += 32) {
-                    float z[32];
-                    mma::tmem_ld32(tm + lane_off + c0, z);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float zz = z[j] + Ps[128 + c0 + j];
-                        yh = fmaf(zz * mma::sigm(zz), Ps[256 + c0 + j], yh);
-                    }
-                }
-                Ls = fmaf(m.std, yh, m.mean);
-            } else {
-                Ls = 0.f;
-            }
-            if (flagged) {
-                if (st.j != pj) {
-                    table_pair(c, st.j, pv);
-                    pj = st.j;
-                }
-                Ls = lerpf(pv[0], pv[1], wt);
-                fallback = 1u;
-            }
-            const float Lb = lerpf(S.lb[st.j], S.lb[st.j + 1], wt) + c.lb_off;
-            const float q = bridge_energy(c, Ls + c.ls_off, Lb, lT);
-            const float du = fminf(q, k.limiter * ue);
-            ue -= du;
-            sum_q += du;
-        }
-        if (live) {
-            if (valid) {
-                ue_out[i] = ue;
-                ui_out[i] = ui;
-                if (qc_out) qc_out[i] = sum_q;
-                if (qx_out) qx_out[i] = sum_x;
-            } else {
-                ue_out[i] = ue0;
-                ui_out[i] = ui0;
-                if (qc_out) qc_out[i] = 0.f;
-                if (qx_out) qx_out[i] = 0.f;
-            }
-        }
-        if (cnt) {
-            const unsigned f = !live ? 0u : (!valid ? 2u : (clamp | (band << 3) | (fallback << 5)));
-            const unsigned full = __activemask();
-#pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                if (b == 2 || b == 4) continue;
-                const unsigned msk = __ballot_sync(full, (f >> b) & 1u);
-                if (msk && (threadIdx.x & 31) == (__ffs(full) - 1)) {
-                    unsigned long long* dst = b == 0 ? &cnt->n_clamped : b == 1 ? &cnt->n_nonfinite
-                                            : b == 3 ? &cnt->n_fp64_coulomb : &cnt->n_fallback;
-                    atomicAdd(dst, (unsigned long long)__popc(msk));
-                }
-            }
-        }
-    }
-    mma::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) mma::tmem_dealloc(tm, 128);
-}
-
 }  // namespace
-
-namespace {
-void fill_common(const cool_table* t, const cool_params* p, double& rg, double& hs, double& escale) {
-    rg = (kG * (p->M_bh_msun * kMsun)) / (kC * kC);
-    double tg = rg / kC;
-    hs = p->dt * tg / p->n_sub;
-    escale = p->rho_scale * kC * kC;
-    (void)t;
-}
-
-int sm_count() {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
-
-}  // namespace
-
-void fill_k64(const cool_table* t, const cool_params* p, StepK64& k) {
-    k.tab = t->dev;
-    double rg, hs, escale;
-    fill_common(t, p, rg, hs, escale);
-    k.s_n = p->rho_scale / kMP;
-    k.s_B = sqrt(4.0 * kPi * p->rho_scale) * kC;
-    k.s_H = rg;
-    k.ce = p->gamma_e - 1.0;
-    k.ci = p->gamma_i - 1.0;
-    k.s_Te = k.ce * kMP * kC * kC / kKB;
-    k.s_Ti = k.ci * kMP * kC * kC / kKB;
-    k.hs = hs;
-    k.escale = escale;
-    k.limiter = p->limiter_frac;
-    k.eq_band = p->eq_band;
-    k.clamp = p->coulomb_clamp;
-    k.n_sub = p->n_sub;
-    k.mode = (int)p->mode;
-    k.iters = p->implicit_iters;
-}
-
-void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
-    k.tab = t->dev;
-    double rg, hs, escale;
-    fill_common(t, p, rg, hs, escale);
-    k.s_n = (float)(p->rho_scale / kMP);
-    k.s_B = (float)(sqrt(4.0 * kPi * p->rho_scale) * kC);
-    k.s_H = (float)rg;
-    k.s_Te = (float)((p->gamma_e - 1.0) * kMP * kC * kC / kKB);
-    k.s_Ti = (float)((p->gamma_i - 1.0) * kMP * kC * kC / kKB);
-    k.ce64 = p->gamma_e - 1.0;
-    k.ci64 = p->gamma_i - 1.0;
-    k.inv_cec64 = 1.0 / (k.ce64 + k.ci64);
-    k.ce = (float)k.ce64;
-    k.ci = (float)k.ci64;
-    k.inv_cec = (float)k.inv_cec64;
-    k.s_K = (float)(kMP * kC * kC / kKB);
-    k.fp64_critical = p->fp64_critical;
-    fill_k64(t, p, k.k64);
-    k.l_hs_e = (float)log2(hs / escale);
-    k.l_bb = (float)log2(4.0 * kSigSB * hs / escale);
-    k.two_sigT = (float)(2.0 * kSigT);
-    k.limiter = (float)p->limiter_frac;
-    k.eq_band = (float)p->eq_band;
-    k.clamp = (float)p->coulomb_clamp;
-    k.n_sub = p->n_sub;
-    k.mode = (int)p->mode;
-    k.iters = p->implicit_iters;
-    int na = 0;
-    for (int a = 0; a < 5; ++a) na += 3 * t->dev.n[a];
-    k.axes_floats = na;
-    k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * t->dev.n[4];
-}
 
 cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long n,
                             const float* rho, const float* B, const float* H,
@@ -1484,44 +751,6 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
-}
-
-cool_status launch_step_surrogate(const cool_surrogate* sg, const cool_table* t, const cool_params* p, long long n,
-                                  const float* rho, const float* B, const float* H, const float* ue,
-                                  const float* ui, float* ue_o, float* ui_o, float* qc, float* qx,
-                                  cool_counters* cnt, cudaStream_t st) {
-    if (n == 0) return COOL_OK;
-    if (t->dev.fmt != 0 || p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical) return COOL_EUNSUPPORTED;
-    StepK k;
-    fill_stepk(t, p, k);
-    SurK m;
-    m.W1b = sg->d_W1b;
-    m.W2b = sg->d_W2b;
-    m.p = sg->d_p;
-    m.mean = (float)sg->mean;
-    m.std = (float)sg->std;
-    for (int d = 0; d < 4; ++d) {
-        m.l0[d] = (float)sg->l0[d];
-        m.sc[d] = (float)(2.0 / sg->span[d]);
-    }
-    m.xs = (float)sg->x_switch;
-    m.mask = sg->d_mask;
-    const size_t smem = (size_t)sur_table_floats(k) * sizeof(float) + 128 * 16 * 2 + 128 * 128 * 2 +
-                        128 * 128 * 2 + (3 * 128 + 8) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_step_surrogate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    long long tiles = (n + kSurT - 1) / kSurT;
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_surrogate, kSurT, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    if (per_sm > 4) per_sm = 4;                  // 4 x 128 TMEM columns per SM
-    long long cap = (long long)sm_count() * per_sm;
-    long long blocks = tiles < cap ? tiles : cap;
-    k_step_surrogate<<<(int)blocks, kSurT, smem, st>>>(k, m, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt,
-                                                        sg->d_err);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
 }
 
 cool_status launch_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,

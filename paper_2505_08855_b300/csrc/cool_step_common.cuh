@@ -1,0 +1,462 @@
+// cool_step_common.cuh -- FP32/FP64 building blocks of the cooling step
+// shared by the step kernels (cool_step.cu) and the surrogate step
+// (cool_sur_step.cu): constants of a launch, index selection, the packed
+// 4-D channel gather, the cooling energy with the bridge, the implicit
+// solves, and the host functions that fill the launch constants.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "cool_internal.cuh"
+
+namespace cool {
+namespace {
+
+
+__device__ __forceinline__ float ex2a(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2a(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+
+// Shared-memory view of the small table parts.
+struct Smem {
+    const float* ax;   // concatenated axes (x, rx, lx per axis)
+    const float* lb;
+    const float* lc;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 instantiation: all arithmetic in FP64 on the FP64 table channels
+// (the same algorithm; index selection compares the FP64 key with the FP32
+// nodes, weights from FP64 log2).
+// ---------------------------------------------------------------------------
+struct StepK64 {
+    DevTable tab;
+    double s_n, s_B, s_H, s_Te, s_Ti, ce, ci, hs, escale;
+    double limiter, eq_band, clamp;
+    int n_sub, mode, iters;
+};
+
+__device__ int select64(const DevTable& T, int a, double key, double& w, unsigned& clamp) {
+    const int n = T.n[a];
+    const float* x = T.axes + T.axis_off[a];
+    int j = 0;
+    if (!(key >= (double)x[0])) {
+        clamp = 1u;
+    } else {
+        int lo = 0, hi = n - 2;  // largest j in [0, n-2] with x[j] <= key
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if ((double)x[mid] <= key) lo = mid; else hi = mid - 1;
+        }
+        j = lo;
+        if (key > (double)x[n - 1]) clamp = 1u;
+    }
+    double wl = key > 0.0 ? (log2(key) - (T.l0_64[a] + j * T.dl64[a])) / T.dl64[a] : 0.0;
+    w = fmin(fmax(wl, 0.0), 1.0);
+    return j;
+}
+
+struct Cell64 {
+    int jh, jb, jn;
+    double wh, wb, wn, ne, Hc;
+};
+
+__device__ double cool_q64(const StepK64& k, const Cell64& c, double ue, double rho, unsigned& clamp) {
+    const DevTable& T = k.tab;
+    double Te = k.s_Te * ue / rho;
+    double wt;
+    int jt = select64(T, 3, Te, wt, clamp);
+    const int nB = T.n[1], nN = T.n[2], nT = T.n[3];
+    double ls = 0.0;
+    for (int cidx = 0; cidx < 16; ++cidx) {
+        int bh = cidx & 1, bb = (cidx >> 1) & 1, bn = (cidx >> 2) & 1, bt = (cidx >> 3) & 1;
+        double wgt = (bh ? c.wh : 1.0 - c.wh) * (bb ? c.wb : 1.0 - c.wb) * (bn ? c.wn : 1.0 - c.wn) *
+                     (bt ? wt : 1.0 - wt);
+        long long idx = (((long long)(c.jh + bh) * nB + (c.jb + bb)) * nN + (c.jn + bn)) * nT + jt + bt;
+        ls += wgt * T.ls64[idx];
+    }
+    double lb = (1.0 - wt) * T.lb64[jt] + wt * T.lb64[jt + 1];
+    double qthin = c.ne * c.ne * exp2(lb) + exp2(ls);
+    double bb4 = 4.0 * kSigSB * Te * Te * Te * Te;
+    double tau_sca = 2.0 * c.ne * kSigT * c.Hc;
+    double tau_abs = c.Hc * qthin / bb4;
+    double Q = qthin / (1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca)));
+    return k.hs * Q / k.escale;
+}
+
+// Backward Euler of a stiff cell in FP64 on the FP64 table: bisection in
+// log2 u over [u0 2^-60, u0] (iters halvings).  Returns false when the
+// bracket has no sign change.
+__device__ __noinline__ bool implicit_fp64(const StepK64& k, const Cell64& c, double rho, double u0, double& u_out) {
+    unsigned dummy = 0u;
+    double a = log2(u0) - 60.0, b = log2(u0);
+    if (!(exp2(a) - u0 + cool_q64(k, c, exp2(a), rho, dummy) < 0.0)) return false;
+    for (int it = 0; it < k.iters; ++it) {
+        double m = 0.5 * (a + b);
+        double um = exp2(m);
+        if (um - u0 + cool_q64(k, c, um, rho, dummy) > 0.0) b = m; else a = m;
+    }
+    u_out = exp2(0.5 * (a + b));
+    return true;
+}
+
+struct StepK {
+    DevTable tab;
+    float s_n, s_B, s_H, s_Te, s_Ti;  // FP32 key scales (rounded once from FP64)
+    float ce, ci, inv_cec;            // gamma - 1, 1/(ce + ci)
+    double ce64, ci64, inv_cec64;
+    float s_K;                        // m_p c^2 / k_B  (T_s = (gamma_s - 1) s_K u_s / rho)
+    int fp64_critical;
+    StepK64 k64;                      // FP64 constants for stiff cells when fp64_critical
+    float l_hs_e;                     // log2(h / e_scale)
+    float l_bb;                       // log2(4 sigma_SB h / e_scale)
+    float two_sigT;                   // 2 sigma_T
+    float limiter, eq_band, clamp;
+    int n_sub, mode, iters;
+    int smem_floats;                  // floats of axes + lb + lc in shared memory
+    int axes_floats;
+};
+
+struct Sel {
+    int j;
+    float r;   // log2(key / x_j), unclamped
+};
+
+// Index selection on an axis (x, rx, lx arrays of n floats at `a`): the
+// largest j in [0, n-2] with x[j] <= key, compared exactly in FP32 (j = 0
+// below the first node).  The guess floor((log2 key - l_0)/dl) is within
+// one of that index (lg2.approx is accurate to ~1e-5 absolute, far below
+// one node spacing), so one upward and one downward correction make the
+// selection exact with no data-dependent loop.  The key is clamped when it
+// lies outside [x_0, x_{n-1}].
+__device__ __forceinline__ Sel select_axis(const float* a, int n, float inv_dl, float key,
+                                           unsigned& clamp) {
+    const float* x = a;
+    const float* rx = a + n;
+    const float* lx = a + 2 * n;
+    int j = __float2int_rd((lg2a(key) - lx[0]) * inv_dl);
+    j = min(max(j, 0), n - 2);
+    j += (j < n - 2 && x[j + 1] <= key) ? 1 : 0;
+    j -= (j > 0 && x[j] > key) ? 1 : 0;
+    clamp |= (key < x[0] || key > x[n - 1]) ? 1u : 0u;
+    Sel s;
+    s.j = j;
+    s.r = lg2a(key * rx[j]);
+    return s;
+}
+
+// Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
+struct CellC {
+    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words
+    int oH, oB, oN;     // float offsets to the H+1, B+1, n_e+1 corner rows
+    float wh, wb, wn;
+    float lb_off;       // log2(h n_e^2 / e_scale)
+    float ls_off;       // log2(h / e_scale)
+    float lbb_off;      // log2(4 sigma_SB h / (H_cm e_scale))
+    float tau_sca;      // 2 n_e sigma_T H_cm
+};
+
+// Collapsed synchrotron values of one T_e octet (7 intervals) live in shared
+// memory, node o of thread t at win[o * kThreads + t] (conflict-free).
+struct Cache {
+    int base;           // first node of the held octet (multiple of 7), -8 if none
+    float* win;         // this thread's window column
+};
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float lerpf(float a, float b, float w) { return fmaf(w, b - a, a); }
+
+// Packed formats of the 4-D channel (DevTable::fmt): nodes per 32-byte block
+// W and block stride S = W - 1.
+template <int FMT> struct Fmt;
+template <> struct Fmt<0> { static constexpr int W = 8, S = 7; };    // FP32
+template <> struct Fmt<1> { static constexpr int W = 16, S = 15; };  // BF16
+template <> struct Fmt<2> { static constexpr int W = 16, S = 15; };  // FP16
+template <> struct Fmt<3> { static constexpr int W = 12, S = 11; };  // BF16, block-scaled
+template <> struct Fmt<4> { static constexpr int W = 12, S = 11; };  // FP16, block-scaled
+constexpr int kMaxW = 16;
+
+// 256-bit read-only load of one block (32-byte aligned).
+__device__ __forceinline__ void ld8u(const uint32_t* p, uint32_t (&v)[8]) {
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+        : "l"(p));
+}
+
+__device__ __forceinline__ float half_bits(uint32_t h16, bool f16) {
+    return f16 ? __half2float(__ushort_as_half((unsigned short)h16)) : __uint_as_float(h16 << 16);
+}
+
+// Value of node t (0 <= t < W) of a block.
+template <int FMT>
+__device__ __forceinline__ float dec(const uint32_t (&r)[8], int t) {
+    if (FMT == 0) return __uint_as_float(r[t]);
+    if (FMT == 1 || FMT == 2) {
+        const uint32_t w = r[t >> 1];
+        return half_bits((t & 1) ? (w >> 16) : (w & 0xffffu), FMT == 2);
+    }
+    const uint32_t w = r[2 + (t >> 1)];
+    const float res = half_bits((t & 1) ? (w >> 16) : (w & 0xffffu), FMT == 4);
+    return fmaf(__uint_as_float(r[1]), res, __uint_as_float(r[0]));
+}
+
+// Read the 8 corner blocks of block kb (one 32-byte sector each) and collapse
+// the H, B, n_e axes: win[o] = trilinear value at T_e node S kb + o.
+template <int FMT>
+__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
+    constexpr int W = Fmt<FMT>::W;
+    const uint32_t* p = c.row + (long long)kb * 8;
+    if (FMT == 0) {
+        // FP32: all four (h, b) pairs reduced in registers
+        uint32_t a[8], b[8], d[8], e[8];
+        ld8u(p, a);
+        ld8u(p + c.oN, b);
+        float x[8], y[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = lerpf(dec<0>(a, t), dec<0>(b, t), c.wn);
+        ld8u(p + c.oB, b);
+        ld8u(p + c.oB + c.oN, d);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = lerpf(x[t], lerpf(dec<0>(b, t), dec<0>(d, t), c.wn), c.wb);
+        const uint32_t* q = p + c.oH;
+        ld8u(q, b);
+        ld8u(q + c.oN, d);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) y[t] = lerpf(dec<0>(b, t), dec<0>(d, t), c.wn);
+        ld8u(q + c.oB, d);
+        ld8u(q + c.oB + c.oN, e);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            y[t] = lerpf(y[t], lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
+            cc.win[t * kThreads] = lerpf(x[t], y[t], c.wh);
+        }
+    } else {
+        // 16-bit formats (W = 16 or 12 nodes): the partial sums go through
+        // the window in shared memory to bound register use
+        uint32_t r0[8], r1[8];
+        ld8u(p, r0);
+        ld8u(p + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t) cc.win[t * kThreads] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
+        ld8u(p + c.oB, r0);
+        ld8u(p + c.oB + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t)
+            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
+        const uint32_t* q = p + c.oH;
+        float hb[W];
+        ld8u(q, r0);
+        ld8u(q + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t) hb[t] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
+        ld8u(q + c.oB, r0);
+        ld8u(q + c.oB + c.oN, r1);
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            const float h1 = lerpf(hb[t], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
+            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], h1, c.wh);
+        }
+    }
+    cc.base = Fmt<FMT>::S * kb;
+}
+
+// Energy (code units) that cooling removes in one sub-cycle at T_e, with
+// the bridge of Eq. 11 evaluated in log2 space:
+//   A = log2 q_thin = log2(q_brem + q_syn), B = log2 q_bb with
+//   q_bb = h 4 sigma T^4/(H e_scale), tau_abs = 2^(A - B),
+//   q = q_thin / (1 + tau_abs (sqrt3 + 1.5 (tau_abs + tau_sca))).
+// The common path has no range branches: 2^d underflows to 0 where one
+// channel is negligible and tau_abs to 0 where the cell is thin; only
+// tau_abs > 2^60 (where tau_abs^2 would overflow) takes the asymptotic form.
+template <int FMT>
+__device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, const CellC& c,
+                                             Cache& cc, float Te, unsigned& clamp) {
+    const int nT = k.tab.n[3];
+    const float* axT = S.ax + k.tab.axis_off[3];
+    Sel s = select_axis(axT, nT, k.tab.inv_dl[3], Te, clamp);
+    const int j = s.j;
+    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
+    const int o = j - cc.base;
+    const float w = __saturatef(s.r * k.tab.inv_dl[3]);
+    const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
+    const float Lb = lerpf(S.lb[j], S.lb[j + 1], w) + c.lb_off;
+    const float lT = axT[2 * nT + j] + s.r;
+    const float M = fmaxf(Ls, Lb);
+    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
+    const float Bb = fmaf(4.f, lT, c.lbb_off);
+    const float lt = A - Bb;  // log2 tau_abs
+    float lq;
+    if (lt <= 60.f) {
+        const float tau = ex2a(lt);
+        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
+        lq = A - lg2a(D);
+    } else {
+        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
+        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
+    }
+    return ex2a(fminf(lq, 126.f));
+}
+
+// Backward Euler u' = u0 - q(u') of a stiff cell (q(u0) > limiter u0) in
+// FP32.  Bracket [u0 2^-60, u0]: g(u0) = q(u0) > 0 and g(u0 2^-60) < 0 is
+// checked (false when it fails).  Illinois (modified regula falsi) first on
+// G(x) = log2((2^x + q(2^x))/u0), x = log2 u, which is close to piecewise
+// linear over the 60 octaves, then on g(u) = u + q(u) - u0 in u once the
+// bracket is tight (FP32 x cannot resolve u to better than ~1e-6).  At most
+// implicit_iters evaluations.  Kept out of line: stiff cells are a minority.
+template <int FMT>
+__device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
+                                           float inv_e, float u0, float q0, float& u_out) {
+    const float inv_u0 = 1.f / u0;
+    unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
+    float xb = lg2a(u0);
+    float xa = xb - 60.f;
+    const float ua0 = ex2a(xa);
+    const float qa0 = cool_energy<FMT>(k, S, c, cc, ua0 * inv_e, trial);
+    if (!(ua0 - u0 + qa0 < 0.f)) return false;
+    float Gb = lg2a(fmaf(q0, inv_u0, 1.f));
+    float Ga = lg2a((ua0 + qa0) * inv_u0);
+    int side = 0, it = 0;
+    for (; it < k.iters; ++it) {
+        if (xb - xa < 1e-3f) break;
+        float x = xb - Gb * (xb - xa) / (Gb - Ga);
+        if (!(x > xa && x < xb)) x = 0.5f * (xa + xb);
+        const float u = ex2a(x);
+        const float G = lg2a((u + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
+        if (G > 0.f) {
+            xb = x; Gb = G;
+            if (side == 1) Ga *= 0.5f;
+            side = 1;
+        } else {
+            xa = x; Ga = G;
+            if (side == -1) Gb *= 0.5f;
+            side = -1;
+        }
+    }
+    float a = ex2a(xa), b = ex2a(xb);
+    float ga = a - u0 + cool_energy<FMT>(k, S, c, cc, a * inv_e, trial);
+    float gb = b - u0 + cool_energy<FMT>(k, S, c, cc, b * inv_e, trial);
+    // an end whose residual rounds to the wrong sign is the root to rounding
+    float u = !(ga < 0.f) ? a : (!(gb > 0.f) ? b : 0.5f * (a + b));
+    side = 0;
+    for (; it < k.iters && ga < 0.f && gb > 0.f; ++it) {
+        u = b - gb * (b - a) / (gb - ga);
+        if (!(u > a && u < b)) u = 0.5f * (a + b);
+        if (b - a <= 2.4e-7f * b) break;
+        const float g = u - u0 + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial);
+        if (g > 0.f) {
+            b = u; gb = g;
+            if (side == 1) ga *= 0.5f;
+            side = 1;
+        } else if (g < 0.f) {
+            a = u; ga = g;
+            if (side == -1) gb *= 0.5f;
+            side = -1;
+        } else {
+            break;
+        }
+    }
+    u_out = u;
+    return true;
+}
+
+// The same solve in FP64 on the FP64 table (fp64_critical): the cell's H, B,
+// n_e selections are redone with FP64 keys and implicit_fp64 bisects.
+__device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
+                                                float u0, float& u_out) {
+    Cell64 c64;
+    unsigned dummy = 0u;
+    c64.ne = (double)rho * k.k64.s_n;
+    c64.Hc = (double)H * k.k64.s_H;
+    c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
+    c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
+    c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
+    double u1;
+    if (!implicit_fp64(k.k64, c64, (double)rho, (double)u0, u1)) return false;
+    u_out = (float)u1;
+    return true;
+}
+
+
+void fill_common(const cool_table* t, const cool_params* p, double& rg, double& hs, double& escale) {
+    rg = (kG * (p->M_bh_msun * kMsun)) / (kC * kC);
+    double tg = rg / kC;
+    hs = p->dt * tg / p->n_sub;
+    escale = p->rho_scale * kC * kC;
+    (void)t;
+}
+
+int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+
+void fill_k64(const cool_table* t, const cool_params* p, StepK64& k) {
+    k.tab = t->dev;
+    double rg, hs, escale;
+    fill_common(t, p, rg, hs, escale);
+    k.s_n = p->rho_scale / kMP;
+    k.s_B = sqrt(4.0 * kPi * p->rho_scale) * kC;
+    k.s_H = rg;
+    k.ce = p->gamma_e - 1.0;
+    k.ci = p->gamma_i - 1.0;
+    k.s_Te = k.ce * kMP * kC * kC / kKB;
+    k.s_Ti = k.ci * kMP * kC * kC / kKB;
+    k.hs = hs;
+    k.escale = escale;
+    k.limiter = p->limiter_frac;
+    k.eq_band = p->eq_band;
+    k.clamp = p->coulomb_clamp;
+    k.n_sub = p->n_sub;
+    k.mode = (int)p->mode;
+    k.iters = p->implicit_iters;
+}
+
+void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
+    k.tab = t->dev;
+    double rg, hs, escale;
+    fill_common(t, p, rg, hs, escale);
+    k.s_n = (float)(p->rho_scale / kMP);
+    k.s_B = (float)(sqrt(4.0 * kPi * p->rho_scale) * kC);
+    k.s_H = (float)rg;
+    k.s_Te = (float)((p->gamma_e - 1.0) * kMP * kC * kC / kKB);
+    k.s_Ti = (float)((p->gamma_i - 1.0) * kMP * kC * kC / kKB);
+    k.ce64 = p->gamma_e - 1.0;
+    k.ci64 = p->gamma_i - 1.0;
+    k.inv_cec64 = 1.0 / (k.ce64 + k.ci64);
+    k.ce = (float)k.ce64;
+    k.ci = (float)k.ci64;
+    k.inv_cec = (float)k.inv_cec64;
+    k.s_K = (float)(kMP * kC * kC / kKB);
+    k.fp64_critical = p->fp64_critical;
+    fill_k64(t, p, k.k64);
+    k.l_hs_e = (float)log2(hs / escale);
+    k.l_bb = (float)log2(4.0 * kSigSB * hs / escale);
+    k.two_sigT = (float)(2.0 * kSigT);
+    k.limiter = (float)p->limiter_frac;
+    k.eq_band = (float)p->eq_band;
+    k.clamp = (float)p->coulomb_clamp;
+    k.n_sub = p->n_sub;
+    k.mode = (int)p->mode;
+    k.iters = p->implicit_iters;
+    int na = 0;
+    for (int a = 0; a < 5; ++a) na += 3 * t->dev.n[a];
+    k.axes_floats = na;
+    k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * t->dev.n[4];
+}
+
+}  // namespace
+}  // namespace cool
