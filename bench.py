@@ -199,6 +199,145 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ---- secondary measurements (--suite perf): one JSON line per case ---------------
+
+def _timed(torch, fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=None):
+    line = {"suite": "perf", "case": case, "workload": workload, "cells": n, "ms_per_step": ms,
+            "value": n / (ms * 1e-3), "unit": UNIT, "higher_is_better": True}
+    if bytes_per_cell is not None and peak is not None:
+        a = bytes_per_cell * n / (ms * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                            "bytes_per_cell": bytes_per_cell}
+    if extra:
+        line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_suite_perf(args, torch, cool, inputs, dev):
+    """Step variants on the benchmark workload (formats, modes, FP64), the
+    forward + adjoint on 128^3 uniform cells, and the surrogate step on the
+    512 x 256 x 256 shell."""
+    stream = torch.cuda.current_stream()
+    peak, _ = measured_peak()
+    steps, warm = max(args.steps // 10, 3), 3
+    F = inputs.make(WORKLOAD)
+    n = F["rho"].size
+    tf = {k: torch.from_numpy(v).to(dev) for k, v in F.items()}
+    fl = [tf[k] for k in ("rho", "B", "H", "ue", "ui")]
+    ue_o, ui_o = torch.empty_like(tf["ue"]), torch.empty_like(tf["ui"])
+    tables = {}
+
+    def table(dtype=cool.F32, scaled=0):
+        key = (dtype, scaled)
+        if key not in tables:
+            tables[key] = cool.Table(cool.TableSpec(n=TABLE_N, dtype=dtype, row_scaled=scaled))
+        return tables[key]
+
+    def counters(t, p, fields, outs):
+        c = cool.new_counters(dev)
+        cool.step(t, p, *fields, ue_out=outs[0], ui_out=outs[1], counters=c)
+        torch.cuda.synchronize()
+        return {k: v for k, v in cool.counters_dict(c).items() if v}
+
+    cases = [("explicit, FP32 table", cool.F32, 0, cool.Params(n_sub=N_SUB), steps),
+             ("explicit, fp64_critical", cool.F32, 0, cool.Params(n_sub=N_SUB, fp64_critical=1), steps),
+             ("implicit (Illinois, FP32)", cool.F32, 0, cool.Params(n_sub=N_SUB, mode=cool.IMPLICIT), steps),
+             ("implicit, fp64_critical", cool.F32, 0, cool.Params(n_sub=N_SUB, mode=cool.IMPLICIT,
+                                                                    fp64_critical=1), 3),
+             ("explicit, BF16 table", cool.BF16, 0, cool.Params(n_sub=N_SUB), steps),
+             ("explicit, FP16 table", cool.F16, 0, cool.Params(n_sub=N_SUB), steps),
+             ("explicit, BF16 row-scaled table", cool.BF16, 1, cool.Params(n_sub=N_SUB), steps),
+             ("explicit, FP16 row-scaled table", cool.F16, 1, cool.Params(n_sub=N_SUB), steps),
+             ("explicit, N_sub = 1", cool.F32, 0, cool.Params(n_sub=1), steps)]
+    for name, dt, sc, p, k in cases:
+        t = table(dt, sc)
+        ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=ue_o, ui_out=ui_o), k, warm, stream)
+        _suite_line(name, WORKLOAD, n, ms, {"counters": counters(t, p, fl, (ue_o, ui_o)),
+                                            "table_packed_bytes": t.packed_bytes()},
+                    BYTES_PER_CELL, peak)
+    # unaligned fields: the scalar path
+    off = {k: torch.cat([v[:1], v])[1:] for k, v in tf.items()}
+    ofl = [off[k] for k in ("rho", "B", "H", "ue", "ui")]
+    p = cool.Params(n_sub=N_SUB)
+    ms = _timed(torch, lambda: cool.step(table(), p, *ofl), steps, warm, stream)
+    _suite_line("explicit, fields not 16-byte aligned (scalar path)", WORKLOAD, n, ms, None, BYTES_PER_CELL, peak)
+    del off, ofl
+    # FP64 fields (all-FP64 kernel)
+    f64 = [v.double() for v in fl]
+    o64 = [torch.empty_like(f64[3]), torch.empty_like(f64[4])]
+    ms = _timed(torch, lambda: cool.step(table(), p, *f64, ue_out=o64[0], ui_out=o64[1]), 3, 1, stream)
+    _suite_line("FP64 fields and arithmetic", WORKLOAD, n, ms, None, 56, peak)
+    del f64, o64, tf, fl, ue_o, ui_o
+    torch.cuda.empty_cache()
+
+    # forward + adjoint, 128^3 uniform cells
+    G = inputs.make("uniform_128c")
+    m = G["rho"].size
+    tg = {k: torch.from_numpy(v).to(dev) for k, v in G.items()}
+    gl = [tg[k] for k in ("rho", "B", "H", "ue", "ui")]
+    g_ue = torch.ones_like(tg["ue"])
+    g_ui = torch.full_like(tg["ui"], 0.5)
+    T = table()
+    nH, nB, nN, nT, nC = TABLE_N
+    tgr = {"lb": torch.zeros(nT, device=dev), "ls": torch.zeros(nH * nB * nN * nT, device=dev),
+           "lc": torch.zeros(nC * nC, device=dev)}
+    ms_f = _timed(torch, lambda: cool.step(T, p, *gl), steps * 5, warm, stream)
+    ms_b = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui), steps * 5, warm, stream)
+    ms_bt = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui, tgr), steps * 5, warm, stream)
+    _suite_line("forward, 128^3 uniform", "uniform_128c", m, ms_f, None, BYTES_PER_CELL, peak)
+    _suite_line("adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_b, None, 48, peak)
+    _suite_line("forward + adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_f + ms_b, None, 76, peak)
+    _suite_line("forward + adjoint (inputs and table), 128^3 uniform", "uniform_128c", m, ms_f + ms_bt, None, 76,
+                peak)
+    del tg, gl, g_ue, g_ui, tgr
+    torch.cuda.empty_cache()
+
+    # the surrogate step on the 512 x 256 x 256 shell (training untimed)
+    S = inputs.make("shell_512x256x256")
+    m = S["rho"].size
+    ts = {k: torch.from_numpy(v).to(dev) for k, v in S.items()}
+    sl = [ts[k] for k in ("rho", "B", "H", "ue", "ui")]
+    so = [torch.empty_like(ts["ue"]), torch.empty_like(ts["ui"])]
+    t0 = time.time()
+    sur = cool.Surrogate(T, cool.FitSpec())
+    torch.cuda.synchronize()
+    fit_s = time.time() - t0
+    info = sur.info()
+    ms_t = _timed(torch, lambda: cool.step(T, p, *sl, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
+    _suite_line("table step, 512x256x256 shell", "shell_512x256x256", m, ms_t, None, BYTES_PER_CELL, peak)
+    cells = info["mask_cells"]
+    for name, bits in (("surrogate step, fitted fallback mask (tol 1e-3)", None),
+                       ("surrogate step, network in every cell", np.zeros((cells + 31) // 32, np.uint32))):
+        if bits is not None:
+            sur.set_mask(bits)
+        ms = _timed(torch, lambda: sur.step(p, *sl, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
+        c = cool.new_counters(dev)
+        sur.step(p, *sl, ue_out=so[0], ui_out=so[1], counters=c)
+        torch.cuda.synchronize()
+        cd = cool.counters_dict(c)
+        evals = N_SUB * (m - cd["fallback"])
+        flops = 2.0 * 17024 * evals
+        _suite_line(name, "shell_512x256x256", m, ms,
+                    {"fallback_cells": cd["fallback"], "fit_seconds": fit_s, "fit": info,
+                     "network_tflops": flops / (ms * 1e-3) / 1e12}, BYTES_PER_CELL, peak)
+    sur.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +346,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--suite", default=None, choices=["perf"],
+                    help="secondary measurements, one JSON line per case, instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -229,6 +370,10 @@ def main():
     import paper_2505_08855_b300 as cool
     from paper_2505_08855_b300 import build, inputs
     build.build()
+    if args.suite is not None:
+        if rank != 0:
+            return 0
+        return run_suite_perf(args, torch, cool, inputs, torch.device("cuda", local))
     table = cool.Table(cool.TableSpec(n=TABLE_N))
     F = inputs.make(WORKLOAD, seed=1002 + rank)
     n = F["rho"].size

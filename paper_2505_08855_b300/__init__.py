@@ -121,6 +121,12 @@ class Table:
                                             count), "cool_table_export")
         return out
 
+    def packed_bytes(self):
+        """Bytes of the 4-D channel as packed for the step."""
+        nb = C.c_longlong(0)
+        _b.check(_b.lib().cool_table_packed_bytes(self.handle, _b.ref(nb)), "cool_table_packed_bytes")
+        return nb.value
+
     def export_packed(self):
         """The 4-D channel as packed for the step (uint32 words, 8 per block)."""
         import numpy as np
