@@ -56,11 +56,12 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = ("cool_step.cu", "cool_step_common.cuh", "cool_internal.cuh")
+KERNEL_SOURCES = ("cool_step.cu", "cool_step_common.cuh")
 
 
 def kernel_source_sha():
-    """sha256 (16 hex digits) over the sources the timed kernel is built from."""
+    """sha256 (16 hex digits) over the files that hold the timed kernel's
+    device code (the step kernel and its shared device functions)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2505_08855_b300", "csrc", name), "rb").read())
@@ -262,7 +263,11 @@ def run_suite_perf(args, torch, cool, inputs, dev):
              ("explicit, FP16 table", cool.F16, 0, cool.Params(n_sub=N_SUB), steps),
              ("explicit, BF16 row-scaled table", cool.BF16, 1, cool.Params(n_sub=N_SUB), steps),
              ("explicit, FP16 row-scaled table", cool.F16, 1, cool.Params(n_sub=N_SUB), steps),
-             ("explicit, N_sub = 1", cool.F32, 0, cool.Params(n_sub=1), steps)]
+             ("explicit, N_sub = 1", cool.F32, 0, cool.Params(n_sub=1), steps),
+             ("explicit, texture path: point fetches + FP32 lerp", cool.F32, 0,
+              cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT), steps),
+             ("explicit, texture path: hardware trilinear filtering", cool.F32, 0,
+              cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP), steps)]
     for name, dt, sc, p, k in cases:
         t = table(dt, sc)
         ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=ue_o, ui_out=ui_o), k, warm, stream)

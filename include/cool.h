@@ -59,8 +59,16 @@ typedef enum { COOL_F32 = 0, COOL_BF16 = 1, COOL_F16 = 2, COOL_F64 = 3 } cool_dt
 /* Energy update of Sec. 3.2.1: (i) explicit with the limiter, (ii) implicit. */
 typedef enum { COOL_EXPLICIT_LIMITED = 0, COOL_IMPLICIT_STIFF = 1 } cool_mode;
 
-/* How the 4-D synchrotron channel is read.  L2WINDOW: global memory kept
- * L2-resident by a persisting access-policy window. */
+/* How the 4-D synchrotron channel is read.  L2WINDOW: the packed blocks in
+ * global memory, kept L2-resident (all modes, formats and field types).
+ * TEXTURE_POINT / TEXTURE_HWLERP (the paper's design, Sec. 3.1; comparison
+ * paths, explicit mode with FP32 fields and an FP32 table only): the FP32
+ * channel as a 3-D texture (x = T_e, y = n_e, z = h n_B + b, made on first
+ * use, synchronously), read with 16 point fetches and FP32 interpolation, or
+ * with the hardware's trilinear filtering (weights in fixed point with 8
+ * fractional bits: an error of up to 2^-8 of a node step per filtered axis)
+ * and FP32 interpolation in H.  TMA_SMEM and SURROGATE: COOL_EUNSUPPORTED in
+ * cool_step (the surrogate step is cool_surrogate_infer). */
 typedef enum {
     COOL_PATH_L2WINDOW = 0,
     COOL_PATH_TMA_SMEM = 1,
@@ -103,7 +111,7 @@ typedef struct {
     double eq_band;           /* equilibrium band |T_e - T_i| <= eq_band T_i (0.1), where T_i - T_e cancels */
     double coulomb_clamp;     /* the exchange may move at most this fraction of the way to T_e = T_i (1) */
     int implicit_iters;       /* bisection halvings of the implicit solve, 1 .. 200 (60) */
-    cool_path path;           /* COOL_PATH_L2WINDOW (others: not yet) */
+    cool_path path;           /* COOL_PATH_L2WINDOW (default), TEXTURE_POINT, TEXTURE_HWLERP */
     int fp64_critical;        /* FP32 fields only.  0 (default): the Coulomb difference
                                  (gamma_i-1) u_i - (gamma_e-1) u_e is formed with an error-free FP32
                                  product transformation in every cell, and stiff cells are solved in

@@ -61,8 +61,81 @@ cool_status validate_params(const cool_params* p) {
     if (!(p->eq_band >= 0.0 && p->eq_band < 1.0)) return COOL_EINVAL;
     if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
     if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
-    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
+    if (p->path != COOL_PATH_L2WINDOW && p->path != COOL_PATH_TEXTURE_POINT && p->path != COOL_PATH_TEXTURE_HWLERP)
+        return COOL_EUNSUPPORTED;
+    if (p->path != COOL_PATH_L2WINDOW && (p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical != 0))
+        return COOL_EUNSUPPORTED;   // the texture paths are explicit FP32 only
     if (p->fp64_critical != 0 && p->fp64_critical != 1) return COOL_EINVAL;
+    return COOL_OK;
+}
+
+namespace {
+__global__ void k_f64_to_f32(const double* src, float* dst, long long n) {
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = (float)src[i];
+}
+std::mutex g_tex_mu;
+}  // namespace
+
+// The texture comparison paths' 3-D array (FP32 log2 values of the 4-D
+// channel, x = T_e, y = n_e, z = h n_B + b) and texture objects, made once
+// per table (synchronous).  Limits: the device's 3-D texture extents.
+cool_status table_textures(cool_table* t) {
+    std::lock_guard<std::mutex> g(g_tex_mu);
+    if (t->tex_arr) return COOL_OK;
+    const cool_table_spec& s = t->spec;
+    int wmax = 0, hmax = 0, dmax = 0;
+    cudaDeviceGetAttribute(&wmax, cudaDevAttrMaxTexture3DWidth, t->device);
+    cudaDeviceGetAttribute(&hmax, cudaDevAttrMaxTexture3DHeight, t->device);
+    cudaDeviceGetAttribute(&dmax, cudaDevAttrMaxTexture3DDepth, t->device);
+    const long long depth = (long long)s.n_H * s.n_B;
+    if (s.n_Te > wmax || s.n_ne > hmax || depth > dmax) return COOL_EUNSUPPORTED;
+    const long long cnt = syn_count(s);
+    float* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, sizeof(float) * cnt);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? COOL_ENOMEM : set_cuda_error(e);
+    k_f64_to_f32<<<1184, 256>>>((const double*)t->d_ls64, tmp, cnt);
+    cudaArray_t arr = nullptr;
+    cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+    const cudaExtent ext = make_cudaExtent(s.n_Te, s.n_ne, depth);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMalloc3DArray(&arr, &fd, ext, 0);
+    if (e == cudaSuccess) {
+        cudaMemcpy3DParms cp;
+        memset(&cp, 0, sizeof(cp));
+        cp.srcPtr = make_cudaPitchedPtr(tmp, sizeof(float) * s.n_Te, s.n_Te, s.n_ne);
+        cp.dstArray = arr;
+        cp.extent = ext;
+        cp.kind = cudaMemcpyDeviceToDevice;
+        e = cudaMemcpy3D(&cp);
+    }
+    cudaTextureObject_t to[2] = {0, 0};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        cudaResourceDesc rd;
+        memset(&rd, 0, sizeof(rd));
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td;
+        memset(&td, 0, sizeof(td));
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = k == 0 ? cudaFilterModePoint : cudaFilterModeLinear;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&to[k], &rd, &td, nullptr);
+    }
+    cudaError_t e2 = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        for (int k = 0; k < 2; ++k)
+            if (to[k]) cudaDestroyTextureObject(to[k]);
+        if (arr) cudaFreeArray(arr);
+        return e == cudaErrorMemoryAllocation ? COOL_ENOMEM : set_cuda_error(e);
+    }
+    t->tex_point = (unsigned long long)to[0];
+    t->tex_linear = (unsigned long long)to[1];
+    t->tex_arr = arr;
     return COOL_OK;
 }
 
@@ -159,6 +232,9 @@ void axis_nodes(double lo, double hi, int n, double* x64, double* l64) {
 }
 
 void free_table_memory(cool_table* t) {
+    if (t->tex_point) cudaDestroyTextureObject((cudaTextureObject_t)t->tex_point);
+    if (t->tex_linear) cudaDestroyTextureObject((cudaTextureObject_t)t->tex_linear);
+    if (t->tex_arr) cudaFreeArray(t->tex_arr);
     void* dptrs[] = {t->d_axes, t->d_axes64, t->d_lb, t->d_ls, t->d_lc, t->d_lb64, t->d_ls64, t->d_lc64};
     for (void* p : dptrs)
         if (p) cudaFree(p);
@@ -538,6 +614,14 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
     cudaGetDevice(&dev);
     if (dev != t->device) return COOL_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->path != COOL_PATH_L2WINDOW) {
+        if (field_dtype != COOL_F32 || t->spec.dtype != COOL_F32) return COOL_EUNSUPPORTED;
+        st = table_textures(const_cast<cool_table*>(t));
+        if (st != COOL_OK) return st;
+        return launch_step_tex(t, p, n_cells, (const float*)rho, (const float*)B, (const float*)H,
+                               (const float*)u_e_in, (const float*)u_i_in, (float*)u_e_out, (float*)u_i_out,
+                               (float*)q_cool_out, (float*)q_cc_out, counters, s);
+    }
     if (field_dtype == COOL_F32)
         return launch_step_f32(t, p, n_cells, (const float*)rho, (const float*)B, (const float*)H,
                                (const float*)u_e_in, (const float*)u_i_in, (float*)u_e_out,
@@ -555,6 +639,7 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
     if (!table_ok(t)) return COOL_ESTATE;
     cool_status st = validate_params(p);
     if (st != COOL_OK) return st;
+    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
     if (n_cells < 0) return COOL_EINVAL;
     if (n_cells == 0) return COOL_OK;
     const void* req[] = {rho, B, H, u_e_in, u_i_in, g_u_e_out, g_u_i_out, g_rho, g_B, g_H, g_u_e_in, g_u_i_in};

@@ -77,6 +77,11 @@ struct cool_table {
     double* h_lc64;
     float* h_axes;              // host copy of the FP32 axis arrays
     size_t ls_bytes;
+    // texture comparison paths (created on first use): the FP32 4-D channel
+    // as a 3-D CUDA array (x = T_e, y = n_e, z = h n_B + b) and two texture
+    // objects on it, point sampling and hardware linear filtering
+    cudaArray_t tex_arr;
+    unsigned long long tex_point, tex_linear;
 };
 
 constexpr uint32_t kTableMagic = 0xC0011AB1u;
@@ -112,6 +117,10 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
                                 const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
                                 float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st);
 cool_status validate_params(const cool_params* p);
+cool_status table_textures(cool_table* t);
+cool_status launch_step_tex(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                            const float* B, const float* H, const float* ue, const float* ui, float* ue_o,
+                            float* ui_o, float* qc, float* qx, cool_counters* cnt, cudaStream_t st);
 cool_status launch_step_surrogate(const cool_surrogate* sg, const cool_table* t, const cool_params* p, long long n,
                                   const float* rho, const float* B, const float* H, const float* ue,
                                   const float* ui, float* ue_o, float* ui_o, float* qc, float* qx,

@@ -772,7 +772,8 @@ cool_status cool_surrogate_infer(const cool_surrogate* s, const cool_table* t, c
         a.H_max != b.H_max || a.B_min != b.B_min || a.B_max != b.B_max || a.ne_min != b.ne_min ||
         a.ne_max != b.ne_max || a.T_min != b.T_min || a.T_max != b.T_max)
         return COOL_EINVAL;   // fitted to another table box
-    if (b.dtype != COOL_F32 || p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical) return COOL_EUNSUPPORTED;
+    if (b.dtype != COOL_F32 || p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical || p->path != COOL_PATH_L2WINDOW)
+        return COOL_EUNSUPPORTED;
     if (n_cells == 0) return COOL_OK;
     if (!rho || !B || !H || !u_e_in || !u_i_in || !u_e_out || !u_i_out) return COOL_ENULL;
     const void* ptrs[] = {rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out, q_cc_out};

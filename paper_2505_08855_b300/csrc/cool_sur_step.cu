@@ -5,6 +5,7 @@
 #include "cool_mlp.cuh"
 #include "cool_mma.cuh"
 #include "cool_step_common.cuh"
+#include "cool_bridge.cuh"
 
 namespace cool {
 namespace {
@@ -53,24 +54,6 @@ __device__ __forceinline__ void table_pair(const CellC& c, int j, float (&v)[2])
 // table is read through L1), then the network operands.
 __host__ __device__ __forceinline__ int sur_table_floats(const StepK& k) {
     return (k.axes_floats + k.tab.n[3] + 3) & ~3;
-}
-
-// The bridge of cool_energy, from the two channel values (log2, code units
-// per sub-cycle) and log2 T_e.
-__device__ __forceinline__ float bridge_energy(const CellC& c, float Ls, float Lb, float lT) {
-    const float M = fmaxf(Ls, Lb);
-    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
-    const float Bb = fmaf(4.f, lT, c.lbb_off);
-    const float lt = A - Bb;
-    float lq;
-    if (lt <= 60.f) {
-        const float tau = ex2a(lt);
-        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
-        lq = A - lg2a(D);
-    } else {
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    }
-    return ex2a(fminf(lq, 126.f));
 }
 
 __global__ void __launch_bounds__(kSurT) k_step_surrogate(StepK k, SurK m, long long n, const float* __restrict__ rho_in,
