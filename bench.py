@@ -304,6 +304,14 @@ def run_suite_perf(args, torch, cool, inputs, dev):
     ms_b = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui), steps * 5, warm, stream)
     ms_bt = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui, tgr), steps * 5, warm, stream)
     _suite_line("forward, 128^3 uniform", "uniform_128c", m, ms_f, None, BYTES_PER_CELL, peak)
+    # the paper's analytic-versus-table comparison: every rate from the
+    # formulas (FP64), on the first 2^18 of these cells
+    k = 1 << 18
+    d64 = [t[:k].double().contiguous() for t in gl]
+    ms_d = _timed(torch, lambda: cool.step_direct(cool.TableSpec(n=TABLE_N), p, *d64), 1, 1, stream)
+    _suite_line("direct formulas, no table (FP64), 2^18 of the 128^3 uniform cells", "uniform_128c", k, ms_d,
+                {"table_step_speedup": (m / (ms_f * 1e-3)) / (k / (ms_d * 1e-3))}, 56, peak)
+    del d64
     _suite_line("adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_b, None, 48, peak)
     _suite_line("forward + adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_f + ms_b, None, 76, peak)
     _suite_line("forward + adjoint (inputs and table), 128^3 uniform", "uniform_128c", m, ms_f + ms_bt, None, 76,

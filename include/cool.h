@@ -252,6 +252,23 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
                           float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
 
+/* The step with every rate evaluated from the formulas instead of the
+ * table: the paper's "analytic" comparison (Appendix, direct calculation
+ * against the table).  Per cell and sub-cycle: the bremsstrahlung fits
+ * (Eqs. 1-2), the nu_c root of Eq. 5 and the synchrotron integral of Eq. 6
+ * (1024-point quadrature), the Compton factor (Eqs. 7-9), the bridge
+ * (Eqs. 11-12) and the Coulomb coefficient (Eq. 16); the update is the one
+ * of cool_step (explicit or implicit; fp64_critical and the texture paths
+ * do not apply).  FP64 device arrays only (8-byte aligned).  `physics` gives
+ * k2_switch_T, lnLambda, theta_i_uses_mp and compton_literal; its node
+ * counts and ranges are ignored (no table, no clamping).  counters:
+ * n_clamped counts cells whose nu_c hit the 1e30 Hz cap.  Asynchronous on
+ * stream; FP64-bound on B300 (slow by design: the comparison point). */
+cool_status cool_step_direct(const cool_table_spec* physics, const cool_params* p, long long n_cells,
+                             const double* rho, const double* B, const double* H, const double* u_e_in,
+                             const double* u_i_in, double* u_e_out, double* u_i_out, double* q_cool_out,
+                             double* q_cc_out, cool_counters* counters, void* stream);
+
 /* ---- learned surrogate of the synchrotron channel (not in the paper) ------
  * An MLP 4 -> 128 -> 128 -> 1 with SiLU (inputs: the four log2 coordinates
  * normalised to [-1, 1] over the table box, each as two bf16 parts (value

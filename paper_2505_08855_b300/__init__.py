@@ -211,6 +211,29 @@ def step(table, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None
     return ue_out, ui_out
 
 
+def step_direct(spec, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None, q_cc=None,
+                counters=None, stream=None):
+    """cool_step_direct: the step with every rate from the formulas (FP64
+    CUDA tensors; `spec` supplies the physics flags only)."""
+    import torch
+    fields = (rho, B, H, ue, ui)
+    n = rho.numel()
+    for f in fields:
+        if f.dtype != torch.float64 or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("fields must be contiguous float64 CUDA tensors of one size")
+    if ue_out is None:
+        ue_out = torch.empty_like(ue)
+    if ui_out is None:
+        ui_out = torch.empty_like(ui)
+    cs = spec.c()
+    p = params.c()
+    cptr = C.c_void_p(counters.data_ptr()) if counters is not None else C.c_void_p(0)
+    _b.check(_b.lib().cool_step_direct(_b.ref(cs), _b.ref(p), n, *[_ptr(f) for f in fields], _ptr(ue_out),
+                                       _ptr(ui_out), _ptr(q_cool), _ptr(q_cc), cptr, _stream_ptr(stream)),
+             "cool_step_direct")
+    return ue_out, ui_out
+
+
 def debug_lookup(table, axis, keys, stream=None):
     """(idx int32, w float32) of the interpolation rule for FP32 keys."""
     import torch

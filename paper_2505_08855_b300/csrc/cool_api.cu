@@ -631,6 +631,29 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
                            (double*)u_i_out, (double*)q_cool_out, (double*)q_cc_out, counters, s);
 }
 
+cool_status cool_step_direct(const cool_table_spec* physics, const cool_params* p, long long n_cells,
+                             const double* rho, const double* B, const double* H, const double* u_e_in,
+                             const double* u_i_in, double* u_e_out, double* u_i_out, double* q_cool_out,
+                             double* q_cc_out, cool_counters* counters, void* stream) {
+    if (!physics || !p) return COOL_ENULL;
+    cool_status st = validate_params(p);
+    if (st != COOL_OK) return st;
+    if (p->path != COOL_PATH_L2WINDOW || p->fp64_critical) return COOL_EUNSUPPORTED;
+    if (!(physics->k2_switch_T > 0.0) || !(physics->lnLambda > 0.0) ||
+        (physics->theta_i_uses_mp != 0 && physics->theta_i_uses_mp != 1) ||
+        (physics->compton_literal != 0 && physics->compton_literal != 1))
+        return COOL_EINVAL;
+    if (n_cells < 0) return COOL_EINVAL;
+    if (n_cells == 0) return COOL_OK;
+    if (!rho || !B || !H || !u_e_in || !u_i_in || !u_e_out || !u_i_out) return COOL_ENULL;
+    const void* ptrs[] = {rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out, q_cc_out};
+    for (const void* q : ptrs)
+        if ((uintptr_t)q % 8 != 0) return COOL_EALIGN;
+    if ((uintptr_t)counters % 8 != 0) return COOL_EALIGN;
+    return launch_step_direct(*physics, p, n_cells, rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out,
+                              q_cc_out, counters, (cudaStream_t)stream);
+}
+
 cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
                           const float* B, const float* H, const float* u_e_in, const float* u_i_in,
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
