@@ -274,6 +274,16 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         _suite_line(name, WORKLOAD, n, ms, {"counters": counters(t, p, fl, (ue_o, ui_o)),
                                             "table_packed_bytes": t.packed_bytes()},
                     BYTES_PER_CELL, peak)
+    # the paper's table size (100 nodes per axis): 457 MB packed, far beyond L2
+    big = cool.Table(cool.TableSpec(n=(100,) * 5))
+    for name, path in (("paper-size 100^4 table, L2 block layout", cool.PATH_L2WINDOW),
+                       ("paper-size 100^4 table, texture hardware filtering", cool.PATH_TEXTURE_HWLERP),
+                       ("paper-size 100^4 table, texture point fetches", cool.PATH_TEXTURE_POINT)):
+        p = cool.Params(n_sub=N_SUB, path=path)
+        ms = _timed(torch, lambda: cool.step(big, p, *fl, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
+        _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
+    big.free()
+    del big
     # unaligned fields: the scalar path
     off = {k: torch.cat([v[:1], v])[1:] for k, v in tf.items()}
     ofl = [off[k] for k in ("rho", "B", "H", "ue", "ui")]
@@ -426,21 +436,17 @@ def main():
         ms = float(t.item())
     value = world * n / (ms * 1e-3)
 
-    # end to end through the public API with host buffers: pinned H2D of the
-    # five input fields, the step, D2H of u_e and u_i, every step
+    # end to end through the public API with host buffers (cool_step_host):
+    # every step copies the five input fields from pinned host memory and
+    # u_e, u_i back, in chunks that overlap copies and steps
     host_in = {k: torch.from_numpy(v).pin_memory() for k, v in F.items()}
     host_out = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(2)]
-    dev_in = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in F}
     h2d = sum(v.numel() * v.element_size() for v in host_in.values())
     d2h = sum(v.numel() * v.element_size() for v in host_out)
 
     def e2e_one():
-        for k in F:
-            dev_in[k].copy_(host_in[k], non_blocking=True)
-        a, b = cool.step(table, params, dev_in["rho"], dev_in["B"], dev_in["H"], dev_in["ue"], dev_in["ui"],
-                         ue_out=ue_o, ui_out=ui_o)
-        host_out[0].copy_(a, non_blocking=True)
-        host_out[1].copy_(b, non_blocking=True)
+        cool.step_host(table, params, host_in["rho"], host_in["B"], host_in["H"], host_in["ue"], host_in["ui"],
+                       host_out[0], host_out[1])
 
     for _ in range(2):
         e2e_one()

@@ -252,6 +252,21 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
                           float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
 
+/* cool_step on HOST arrays (FP32; the L2WINDOW path): the cells are
+ * streamed through the device in chunks of chunk_cells (0: n/8, at least
+ * 65536; rounded to a multiple of 128), each chunk's five input copies,
+ * its step and its two output copies on one of two internal streams, so that
+ * host-to-device copies, steps and device-to-host copies of consecutive
+ * chunks overlap.  The host arrays should be page-locked (cudaHostAlloc or
+ * cudaHostRegister) for the copies to run asynchronously; they must stay
+ * valid until `stream` reaches the end of the call's work.  Device staging
+ * (14 chunk_cells floats) is allocated and freed stream-ordered on `stream`.
+ * Outputs q_cool/q_cc are not produced.  counters: device pointer or NULL. */
+cool_status cool_step_host(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
+                           const float* B, const float* H, const float* u_e_in, const float* u_i_in,
+                           float* u_e_out, float* u_i_out, long long chunk_cells, cool_counters* counters,
+                           void* stream);
+
 /* The step with every rate evaluated from the formulas instead of the
  * table: the paper's "analytic" comparison (Appendix, direct calculation
  * against the table).  Per cell and sub-cycle: the bremsstrahlung fits

@@ -211,6 +211,23 @@ def step(table, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None
     return ue_out, ui_out
 
 
+def step_host(table, params, rho, B, H, ue, ui, ue_out, ui_out, chunk_cells=0, counters=None, stream=None):
+    """cool_step_host: the step on host (CPU, preferably pinned) float32
+    tensors, streamed through the device in overlapping chunks; asynchronous
+    on `stream` (synchronise before reading ue_out / ui_out)."""
+    import torch
+    fields = (rho, B, H, ue, ui, ue_out, ui_out)
+    n = rho.numel()
+    for f in fields:
+        if f.dtype != torch.float32 or f.numel() != n or f.is_cuda or not f.is_contiguous():
+            raise ValueError("fields must be contiguous float32 host tensors of one size")
+    p = params.c()
+    cptr = C.c_void_p(counters.data_ptr()) if counters is not None else C.c_void_p(0)
+    _b.check(_b.lib().cool_step_host(table.handle, _b.ref(p), n, *[_ptr(f) for f in fields], int(chunk_cells), cptr,
+                                     _stream_ptr(stream)), "cool_step_host")
+    return ue_out, ui_out
+
+
 def step_direct(spec, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None, q_cc=None,
                 counters=None, stream=None):
     """cool_step_direct: the step with every rate from the formulas (FP64

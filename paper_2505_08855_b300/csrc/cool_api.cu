@@ -631,6 +631,101 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
                            (double*)u_i_out, (double*)q_cool_out, (double*)q_cc_out, counters, s);
 }
 
+}  // extern "C"
+
+namespace cool {
+namespace {
+// Two copy/compute streams per device for the host-buffer step (created once).
+constexpr int kMaxDevices = 64;
+cudaStream_t g_pipe[kMaxDevices][2];
+std::mutex g_pipe_mu;
+
+cool_status pipe_streams(int dev, cudaStream_t (&out)[2]) {
+    if (dev < 0 || dev >= kMaxDevices) return COOL_EUNSUPPORTED;
+    std::lock_guard<std::mutex> g(g_pipe_mu);
+    for (int k = 0; k < 2; ++k) {
+        if (!g_pipe[dev][k]) {
+            cudaError_t e = cudaStreamCreateWithFlags(&g_pipe[dev][k], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return set_cuda_error(e);
+        }
+        out[k] = g_pipe[dev][k];
+    }
+    return COOL_OK;
+}
+}  // namespace
+}  // namespace cool
+
+extern "C" {
+
+cool_status cool_step_host(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
+                           const float* B, const float* H, const float* u_e_in, const float* u_i_in,
+                           float* u_e_out, float* u_i_out, long long chunk_cells, cool_counters* counters,
+                           void* stream) {
+    if (!t || !p) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    cool_status st = validate_params(p);
+    if (st != COOL_OK) return st;
+    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
+    if (n_cells < 0 || chunk_cells < 0) return COOL_EINVAL;
+    if (n_cells == 0) return COOL_OK;
+    if (!rho || !B || !H || !u_e_in || !u_i_in || !u_e_out || !u_i_out) return COOL_ENULL;
+    if ((uintptr_t)counters % 8 != 0) return COOL_EALIGN;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return COOL_ESTATE;
+    cudaStream_t ps[2];
+    st = pipe_streams(dev, ps);
+    if (st != COOL_OK) return st;
+    // chunks: a multiple of 128 cells (every staged array stays 16-byte aligned)
+    long long chunk = chunk_cells > 0 ? chunk_cells : (n_cells + 7) / 8;
+    if (chunk < (1 << 16)) chunk = 1 << 16;
+    chunk = (chunk + 127) / 128 * 128;
+    if (chunk > n_cells) chunk = (n_cells + 127) / 128 * 128;
+    const long long nchunks = (n_cells + chunk - 1) / chunk;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // staging: two sets (one per stream) of 7 arrays of `chunk` floats
+    float* buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, sizeof(float) * 14 * (size_t)chunk, cs);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? COOL_ENOMEM : set_cuda_error(e);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], cs);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ps[k], ev[0], 0);
+    const float* in[5] = {rho, B, H, u_e_in, u_i_in};
+    float* out[2] = {u_e_out, u_i_out};
+    for (long long c = 0; c < nchunks && e == cudaSuccess && st == COOL_OK; ++c) {
+        const int k = (int)(c & 1);
+        float* d = buf + (size_t)k * 7 * chunk;
+        const long long first = c * chunk;
+        const long long m = n_cells - first < chunk ? n_cells - first : chunk;
+        for (int a = 0; a < 5 && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(d + (size_t)a * chunk, in[a] + first, sizeof(float) * m, cudaMemcpyHostToDevice,
+                                ps[k]);
+        if (e != cudaSuccess) break;
+        st = launch_step_f32(t, p, m, d, d + chunk, d + 2 * chunk, d + 3 * chunk, d + 4 * chunk, d + 5 * chunk,
+                             d + 6 * chunk, nullptr, nullptr, counters, ps[k]);
+        for (int a = 0; a < 2 && e == cudaSuccess && st == COOL_OK; ++a)
+            e = cudaMemcpyAsync(out[a] + first, d + (size_t)(5 + a) * chunk, sizeof(float) * m,
+                                cudaMemcpyDeviceToHost, ps[k]);
+    }
+    // the caller's stream continues after both pipeline streams, then frees
+    cudaError_t e2 = cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        if (ev[1 + k]) {
+            cudaError_t a = cudaEventRecord(ev[1 + k], ps[k]);
+            if (a == cudaSuccess) a = cudaStreamWaitEvent(cs, ev[1 + k], 0);
+            if (a != cudaSuccess) e2 = a;
+        }
+    }
+    cudaFreeAsync(buf, cs);
+    for (int k = 0; k < 3; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (st != COOL_OK) return st;
+    if (e2 != cudaSuccess) return set_cuda_error(e2);
+    return COOL_OK;
+}
+
 cool_status cool_step_direct(const cool_table_spec* physics, const cool_params* p, long long n_cells,
                              const double* rho, const double* B, const double* H, const double* u_e_in,
                              const double* u_i_in, double* u_e_out, double* u_i_out, double* q_cool_out,

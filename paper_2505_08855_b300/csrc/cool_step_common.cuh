@@ -137,20 +137,23 @@ struct Sel {
 // one of that index (lg2.approx is accurate to ~1e-5 absolute, far below
 // one node spacing), so one upward and one downward correction make the
 // selection exact with no data-dependent loop.  The key is clamped when it
-// lies outside [x_0, x_{n-1}].
+// lies outside [x_0, x_{n-1}]; the two compared nodes tell: below x_0 the
+// guess is 0 and x_0 > key, above x_{n-1} the guess is n-2 and x_{n-1} < key.
 __device__ __forceinline__ Sel select_axis(const float* a, int n, float inv_dl, float key,
                                            unsigned& clamp) {
     const float* x = a;
     const float* rx = a + n;
     const float* lx = a + 2 * n;
-    int j = __float2int_rd((lg2a(key) - lx[0]) * inv_dl);
-    j = min(max(j, 0), n - 2);
-    j += (j < n - 2 && x[j + 1] <= key) ? 1 : 0;
-    j -= (j > 0 && x[j] > key) ? 1 : 0;
-    clamp |= (key < x[0] || key > x[n - 1]) ? 1u : 0u;
+    int j0 = __float2int_rd((lg2a(key) - lx[0]) * inv_dl);
+    j0 = min(max(j0, 0), n - 2);
+    const float xa = x[j0 + 1];
+    const int j1 = j0 + ((j0 < n - 2 && xa <= key) ? 1 : 0);
+    const float xb = x[j1];
+    const bool above = xb > key;
+    clamp |= ((j1 == 0 && above) || (j0 == n - 2 && xa < key)) ? 1u : 0u;
     Sel s;
-    s.j = j;
-    s.r = lg2a(key * rx[j]);
+    s.j = j1 - ((j1 > 0 && above) ? 1 : 0);
+    s.r = lg2a(key * rx[s.j]);
     return s;
 }
 
