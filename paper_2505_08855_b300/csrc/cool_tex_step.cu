@@ -10,9 +10,9 @@
 //     the table step up to rounding;
 //   COOL_PATH_TEXTURE_HWLERP: the texture unit interpolates T_e, n_e and B
 //     (trilinear filtering, 2 fetches per sub-cycle), H is interpolated in
-//     FP32.  The hardware forms its weights in 9-bit fixed point (8
-//     fractional bits), so each weight is off by up to 2^-9: an error of up
-//     to 2^-9 of a node-to-node step of the channel per axis.
+//     FP32.  The hardware forms its weights in fixed point with 8
+//     fractional bits, so each weight is off by up to 2^-8: an error of up
+//     to 2^-8 of a node-to-node step of the channel per filtered axis.
 // Everything else (keys, index selection, Coulomb exchange, bremsstrahlung,
 // bridge, limiter) is the explicit FP32 step.
 #include "cool_bridge.cuh"
@@ -156,6 +156,9 @@ cool_status launch_step_tex(const cool_table* t, const cool_params* p, long long
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTexThreads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
+#ifdef COOL_TEX_PER_SM
+    if (per_sm > COOL_TEX_PER_SM) per_sm = COOL_TEX_PER_SM;
+#endif
     long long blocks = (n + kTexThreads - 1) / kTexThreads;
     long long cap = (long long)sm_count() * per_sm;
     if (blocks > cap) blocks = cap;
