@@ -132,6 +132,8 @@ def _declare(L):
         "orc_step_surrogate": (_i, [_P, _P, _P, _P, _P, _d, _d, _P, _P, _d, _P, _i, _P, _ll,
                                     _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i]),
         "orc_net_eval": (_i, [_P, _d, _d, _d, _i, _ll, _P, _P]),
+        "orc_quartic_root": (_d, [_d, _d, _d]),
+        "orc_radiation_te": (None, [_P, _d, _d, _ll, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -437,6 +439,26 @@ def step_surrogate(spec, tables, params, mean, std, mask, prm, rho, B, H, ue, ui
     if rc != 0:
         raise RuntimeError(f"orc_step_surrogate failed: {rc}")
     return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
+
+
+A_RAD = 7.5646e-15   # radiation constant as printed with the total-pressure equation (Sec. 5.2)
+
+
+def quartic_root(a, b, c):
+    """Positive root of a x^4 + b x - c = 0 (closed form, a, b, c > 0)."""
+    return lib().orc_quartic_root(float(a), float(b), float(c))
+
+
+def radiation_te(params, rho, H, ue, tau_crit=4.6, a_rad=A_RAD):
+    """(T_e [K], thick flag) of the radiation-pressure correction per cell."""
+    f = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in (rho, H, ue)]
+    n = f[0].size
+    te = np.zeros(n)
+    thick = np.zeros(n, np.int32)
+    p = params.c()
+    lib().orc_radiation_te(_ref(p), float(tau_crit), float(a_rad), n, *[_ptr(x) for x in f], _ptr(te),
+                           _ptr(thick))
+    return te, thick.astype(bool)
 
 
 def keys_f32(params, rho, B, H, ue, ui):

@@ -1210,3 +1210,57 @@ int orc_step_bwd(const orc_spec* s, const double* lb, double* ls, const double* 
     free(R);
     return 0;
 }
+
+/* ===================================================================== */
+/* Radiation-pressure correction of T_e (Sec. 5.2, total-pressure Eq.): in */
+/* optically thick cells the simulation's thermal pressure is read as gas  */
+/* plus radiation, P = a T_e^4 + n k (T_e + T_i), and T_e is recomputed.   */
+/* With P = n k (T_e,sim + T_i) (hydrogen, n = n_e = n_i) the ion terms    */
+/* cancel: a T^4 + n k T = n k T_e,sim.                                    */
+/* ===================================================================== */
+
+/* The positive root of a x^4 + b x - c = 0 (a, b, c > 0; unique, since the
+ * left side increases on x > 0), in closed form (Ferrari): with P = b/a and
+ * q = c/a, x^4 + P x - q = 0; adding 2 m x^2 + m^2 to both sides makes
+ * (x^2 + m)^2 = 2m x^2 - P x + m^2 + q a perfect square when m solves the
+ * resolvent cubic 8 m^3 + 8 q m - P^2 = 0 (one positive root: the
+ * trigonometric/hyperbolic Cardano form for a cubic with one real root).
+ * Then x^2 + sqrt(2m) x + m - P/(2 sqrt(2m)) = 0 gives
+ *   x = (A - B)/2,  A = sqrt(2P/sqrt(2m) - 2m),  B = sqrt(2m),
+ * evaluated as 8 q m / (sqrt(2m) (P + sqrt(8 m^3)) (A + B)), which follows
+ * from P^2 - 8 m^3 = 8 q m and has no cancellation. */
+double orc_quartic_root(double a, double b, double c) {
+    if (!(a > 0.0) || !(b > 0.0) || !(c > 0.0)) return NAN;
+    double P = b / a, q = c / a;
+    /* resolvent m^3 + q m - P^2/8 = 0: t^3 + pp t + qq = 0, pp > 0 */
+    double pp = q, qq = -P * P / 8.0;
+    double m = -2.0 * sqrt(pp / 3.0) * sinh(asinh(1.5 * qq / pp * sqrt(3.0 / pp)) / 3.0);
+    double s2m = sqrt(2.0 * m);
+    double A = sqrt((2.0 * P - sqrt(8.0 * m * m * m)) / s2m);
+    return 8.0 * q * m / (s2m * (P + sqrt(8.0 * m * m * m)) * (A + s2m));
+}
+
+/* Per cell: tau_sca = n_e sigma_T H_cm (the local optical depth of Sec.
+ * 5.2); where tau_sca > tau_crit the corrected T_e, else T_e,sim.  thick
+ * (nullable) marks the corrected cells.  Invalid cells (non-finite or
+ * non-positive rho, u_e; negative H) give NaN. */
+void orc_radiation_te(const orc_params* p, double tau_crit, double a_rad, long long n, const double* rho,
+                      const double* H, const double* ue, double* te_out, int* thick) {
+    double rg = (O_G * (p->M_bh_msun * O_MSUN)) / (O_C * O_C);
+    for (long long i = 0; i < n; ++i) {
+        int th = 0;
+        double t = NAN;
+        if (isfinite(rho[i]) && isfinite(H[i]) && isfinite(ue[i]) && rho[i] > 0.0 && ue[i] > 0.0 && H[i] >= 0.0) {
+            double ne = rho[i] * p->rho_scale / O_MP;
+            double Te = (p->gamma_e - 1.0) * O_MP * O_C * O_C / O_KB * ue[i] / rho[i];
+            double tau = ne * O_SIGT * H[i] * rg;
+            t = Te;
+            if (tau > tau_crit) {
+                th = 1;
+                t = orc_quartic_root(a_rad, ne * O_KB, ne * O_KB * Te);
+            }
+        }
+        te_out[i] = t;
+        if (thick) thick[i] = th;
+    }
+}
