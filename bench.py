@@ -284,6 +284,15 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
     big.free()
     del big
+    # radiation-pressure correction of T_e: an elementwise pass (12 B read,
+    # 4 B T_e + 1 B flag written per cell), 285 MB per pass > L2
+    thick = torch.empty(n, dtype=torch.uint8, device=dev)
+    p = cool.Params(n_sub=N_SUB)
+    ms = _timed(torch, lambda: cool.radiation_te(p, tf["rho"], tf["H"], tf["ue"], te_out=ue_o, thick_out=thick),
+                steps * 5, warm, stream)
+    _suite_line("radiation-pressure T_e correction (Sec. 5.2 quartic), elementwise", WORKLOAD, n, ms,
+                {"thick_cells": int(thick.sum().item())}, 17, peak)
+    del thick
     # unaligned fields: the scalar path
     off = {k: torch.cat([v[:1], v])[1:] for k, v in tf.items()}
     ofl = [off[k] for k in ("rho", "B", "H", "ue", "ui")]

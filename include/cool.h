@@ -284,6 +284,22 @@ cool_status cool_step_direct(const cool_table_spec* physics, const cool_params* 
                              const double* u_i_in, double* u_e_out, double* u_i_out, double* q_cool_out,
                              double* q_cc_out, cool_counters* counters, void* stream);
 
+/* Radiation-pressure correction of the electron temperature (Sec. 5.2, the
+ * total-pressure equation): where the local scattering depth tau_sca =
+ * n_e sigma_T H exceeds tau_crit (4.6: fewer than 1 % of photons escape
+ * unscattered), the thermal pressure is read as gas plus radiation,
+ * P = a_rad T_e^4 + n k (T_e + T_i), and T_e recomputed; with P = n k (T_e +
+ * T_i) from the fields this is a_rad T^4 + n k T = n k T_e,sim (u_i drops
+ * out).  te_out[i] = the corrected T_e [K] in thick cells, T_e,sim
+ * elsewhere, NaN for invalid cells (non-finite or non-positive rho, u_e,
+ * negative H).  thick_out (nullable) = 1 where corrected.  FP32 device
+ * arrays (4-byte aligned; 16-byte aligned with thick_out 4-byte aligned
+ * takes the vector path).  a_rad: the paper prints 7.5646e-15 erg cm^-3
+ * K^-4.  Uses rho_scale, M_bh_msun and gamma_e of p.  Asynchronous. */
+cool_status cool_radiation_te(const cool_params* p, double tau_crit, double a_rad, long long n_cells,
+                              const float* rho, const float* H, const float* u_e, float* te_out,
+                              unsigned char* thick_out, void* stream);
+
 /* ---- learned surrogate of the synchrotron channel (not in the paper) ------
  * An MLP 4 -> 128 -> 128 -> 1 with SiLU (inputs: the four log2 coordinates
  * normalised to [-1, 1] over the table box, each as two bf16 parts (value

@@ -228,6 +228,25 @@ def step_host(table, params, rho, B, H, ue, ui, ue_out, ui_out, chunk_cells=0, c
     return ue_out, ui_out
 
 
+A_RAD_PAPER = 7.5646e-15   # erg cm^-3 K^-4, as printed with the total-pressure equation
+
+
+def radiation_te(params, rho, H, ue, tau_crit=4.6, a_rad=A_RAD_PAPER, te_out=None, thick_out=None, stream=None):
+    """cool_radiation_te: the radiation-pressure corrected T_e [K] (float32
+    CUDA tensors); returns (te_out, thick_out or None)."""
+    import torch
+    n = rho.numel()
+    for f in (rho, H, ue):
+        if f.dtype != torch.float32 or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("fields must be contiguous float32 CUDA tensors of one size")
+    if te_out is None:
+        te_out = torch.empty_like(rho)
+    p = params.c()
+    _b.check(_b.lib().cool_radiation_te(_b.ref(p), float(tau_crit), float(a_rad), n, _ptr(rho), _ptr(H), _ptr(ue),
+                                        _ptr(te_out), _ptr(thick_out), _stream_ptr(stream)), "cool_radiation_te")
+    return te_out, thick_out
+
+
 def step_direct(spec, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None, q_cc=None,
                 counters=None, stream=None):
     """cool_step_direct: the step with every rate from the formulas (FP64

@@ -27,7 +27,7 @@ EXPORTS = (
     "cool_debug_gemm_bf16", "cool_fit_spec_default", "cool_surrogate_fit", "cool_surrogate_free",
     "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
     "cool_surrogate_eval", "cool_surrogate_mask", "cool_surrogate_set_mask", "cool_surrogate_infer",
-    "cool_step_direct", "cool_step_host",
+    "cool_step_direct", "cool_step_host", "cool_radiation_te",
 )
 
 
@@ -125,6 +125,7 @@ def lib():
             "cool_surrogate_set_mask": (I, [P, P, LL]),
             "cool_step_direct": (I, [P, P, LL, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_step_host": (I, [P, P, LL, P, P, P, P, P, P, P, LL, P, P]),
+            "cool_radiation_te": (I, [P, D, D, LL, P, P, P, P, P, P]),
             "cool_surrogate_infer": (I, [P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_table_export_packed": (I, [P, P, LL]),
         }
