@@ -42,6 +42,10 @@ class _Params(C.Structure):
                 ("coulomb_clamp", C.c_double), ("implicit_iters", C.c_int)]
 
 
+class _Disk(C.Structure):
+    _fields_ = [("spin", C.c_double), ("h_floor", C.c_double), ("h_from_state", C.c_int)]
+
+
 # Axis order: 0 H_th [cm], 1 |B| [G], 2 n_e [cm^-3], 3 T_e [K] (cooling),
 # 4 T [K] (Coulomb, both T_i and T_e).  Ranges of Sec. 2.6 / 2.8.
 PAPER_LO = (1e3, 1.0, 1e2, 1e2, 1e2)
@@ -133,6 +137,9 @@ def _declare(L):
                                     _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i]),
         "orc_net_eval": (_i, [_P, _d, _d, _d, _i, _ll, _P, _P]),
         "orc_quartic_root": (_d, [_d, _d, _d]),
+        "orc_h_thermal": (_d, [_P, _d, _d, _d, _d, _d]),
+        "orc_step_disk": (_i, [_P, _P, _P, _P, _i, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                               _i]),
         "orc_radiation_te": (None, [_P, _d, _d, _ll, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
@@ -312,7 +319,7 @@ def round_tables(tables, dtype=np.float32):
 
 # ---- step ------------------------------------------------------------------
 
-COUNTER_NAMES = ("clamped", "invalid", "stiff", "eq_band", "implicit_fail", "fallback")
+COUNTER_NAMES = ("clamped", "invalid", "stiff", "eq_band", "implicit_fail", "fallback", "floor")
 
 
 def step(spec, tables, params, rho, B, H, ue, ui, lazy=False, direct=False, nthreads=0):
@@ -324,7 +331,7 @@ def step(spec, tables, params, rho, B, H, ue, ui, lazy=False, direct=False, nthr
     ui_o = np.zeros(n)
     qc = np.zeros(n)
     qx = np.zeros(n)
-    cnt = np.zeros(6, np.int64)
+    cnt = np.zeros(7, np.int64)
     s = spec.c()
     p = params.c()
     lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
@@ -354,7 +361,7 @@ def step_pairs(spec, lb, lsp, lc, params, rho, B, H, ue, ui, nthreads=0):
     f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui)]
     n = f[0].size
     outs = [np.zeros(n) for _ in range(4)]
-    cnt = np.zeros(6, np.int64)
+    cnt = np.zeros(7, np.int64)
     s = spec.c()
     p = params.c()
     lsp = np.ascontiguousarray(lsp, dtype=np.float64)
@@ -425,7 +432,7 @@ def step_surrogate(spec, tables, params, mean, std, mask, prm, rho, B, H, ue, ui
     f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui)]
     n = f[0].size
     outs = [np.zeros(n) for _ in range(4)]
-    cnt = np.zeros(6, np.int64)
+    cnt = np.zeros(7, np.int64)
     s = spec.c()
     pc = prm.c()
     l0, span, xs = net_box(spec)
@@ -438,6 +445,34 @@ def step_surrogate(spec, tables, params, mean, std, mask, prm, rho, B, H, ue, ui
                                   int(nthreads))
     if rc != 0:
         raise RuntimeError(f"orc_step_surrogate failed: {rc}")
+    return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
+
+
+def h_thermal(params, rho, ue, ui, r, spin=0.0):
+    """H_th = c_s / Omega_K [r_g] of one cell (Sec. 2.7)."""
+    p = params.c()
+    return lib().orc_h_thermal(_ref(p), float(rho), float(ue), float(ui), float(r), float(spin))
+
+
+def step_disk(spec, tables, params, rho, B, H, ue, ui, r, spin=0.0, h_floor=0.0, h_from_state=False,
+              direct=False, nthreads=0):
+    """The O2 (or O1) step with the disk geometry of each cell: H_th from the
+    state when h_from_state (H may be None), the temperature floor when
+    h_floor > 0.  Returns the same tuple as step(); counters['floor']."""
+    f = [None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+         for a in (rho, B, H, ue, ui, r)]
+    n = f[0].size
+    outs = [np.zeros(n) for _ in range(4)]
+    cnt = np.zeros(7, np.int64)
+    s = spec.c()
+    p = params.c()
+    d = _Disk(float(spin), float(h_floor), int(bool(h_from_state)))
+    lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
+    rc = lib().orc_step_disk(_ref(s), _ptr(tables["lb"]), _ptr(tables["ls"]), _ptr(lc), int(direct), _ref(p),
+                             _ref(d), n, *[_ptr(a) for a in f[:5]], _ptr(f[5]), *[_ptr(a) for a in outs],
+                             _ptr(cnt), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_disk failed: {rc}")
     return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
 
 

@@ -85,6 +85,16 @@ typedef struct {
     int implicit_iters;
 } orc_params;
 
+/* Disk geometry of a cell (Sec. 2.7 scale height, Sec. 3.2.3 temperature
+ * floor): r in r_g per cell, the black-hole spin a.  h_from_state: the
+ * thermal scale height H_th = c_s / Omega_K from the cell's own state
+ * replaces the H field; h_floor > 0: no cooling in a sub-cycle whose gas
+ * temperature P/rho is below T_floor = (pi/2) (h_floor Omega_K r)^2. */
+typedef struct {
+    double spin, h_floor;
+    int h_from_state;
+} orc_disk;
+
 /* ---------------------------------------------------------------------- */
 /* Exponentially scaled modified Bessel functions of the second kind,     */
 /* Kt_nu(z) = e^z K_nu(z), nu = 0, 1, 2, z > 0.                           */
@@ -716,12 +726,30 @@ static int cell_setup(const orc_rates* R, const orc_params* p, double rho, doubl
  * non-positive; passed through unchanged), 2 stiff (implicit solve entered),
  * 3 Coulomb inside the equilibrium band |T_e/T_i - 1| <= eq_band,
  * 4 implicit solve without a sign change (limited explicit step taken). */
-static void step_cell(const orc_rates* R, const orc_params* p, double rho, double B, double H,
-                      double ue, double ui, double* ue_out, double* ui_out,
+/* Omega_K = 1/(r^(3/2) + a) (code units, Sec. 2.7). */
+static double omega_k(double r, double a) { return 1.0 / (r * sqrt(r) + a); }
+
+/* H_th = c_s / Omega_K with c_s^2 = gamma P / (rho h), rho h = rho + u + P
+ * (c = 1), P = (gamma_e - 1) u_e + (gamma_i - 1) u_i, u = u_e + u_i, and the
+ * mixture's adiabatic index gamma = 1 + P/u (Sec. 2.7). */
+double orc_h_thermal(const orc_params* p, double rho, double ue, double ui, double r, double a) {
+    double P = (p->gamma_e - 1.0) * ue + (p->gamma_i - 1.0) * ui;
+    double u = ue + ui;
+    double gam = 1.0 + P / u;
+    double cs = sqrt(gam * P / (rho + u + P));
+    return cs / omega_k(r, a);
+}
+
+static void step_cell(const orc_rates* R, const orc_params* p, const orc_disk* dk, double r, double rho,
+                      double B, double H, double ue, double ui, double* ue_out, double* ui_out,
                       double* qcool, double* qcc, unsigned* flags) {
     *flags = 0;
+    if (dk && dk->h_from_state && isfinite(r) && r > 0.0 && isfinite(rho) && rho > 0.0 && isfinite(ue) &&
+        ue > 0.0 && isfinite(ui) && ui > 0.0)
+        H = orc_h_thermal(p, rho, ue, ui, r, dk->spin);
     if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
-        !(rho > 0.0) || !(ue > 0.0) || !(ui > 0.0) || B < 0.0 || H < 0.0) {
+        !(rho > 0.0) || !(ue > 0.0) || !(ui > 0.0) || B < 0.0 || H < 0.0 ||
+        (dk && !(isfinite(r) && r > 0.0))) {
         *ue_out = ue; *ui_out = ui;
         if (qcool) *qcool = 0.0;
         if (qcc) *qcc = 0.0;
@@ -731,8 +759,13 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
     cell_ctx c;
     int clamp = cell_setup(R, p, rho, B, H, &c);
     double sum_cool = 0.0, sum_cc = 0.0;
-    int stiff = 0, eqb = 0, fail = 0, fallback = 0;
+    int stiff = 0, eqb = 0, fail = 0, fallback = 0, floored = 0;
     c.fallback = &fallback;
+    double t_floor = -1.0;
+    if (dk && dk->h_floor > 0.0) {
+        double v = dk->h_floor * omega_k(r, dk->spin) * r;
+        t_floor = 0.5 * O_PI * v * v;
+    }
     for (int k = 0; k < p->n_sub; ++k) {
         /* (i) Coulomb exchange (Eq. 16), clamped so that the step does not
          * cross T_e = T_i. */
@@ -744,6 +777,11 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
         double lim = p->coulomb_clamp * fabs(Xeq);
         if (fabs(X) > lim) X = (X >= 0.0 ? lim : -lim);
         ue += X; ui -= X; sum_cc += X;
+        /* temperature floor: no cooling below T_floor (gas temperature P/rho) */
+        if (((p->gamma_e - 1.0) * ue + (p->gamma_i - 1.0) * ui) / rho < t_floor) {
+            floored = 1;
+            continue;
+        }
         /* (ii) cooling with the bridge (Eqs. 10-12) */
         double q = cool_q(R, &c, ue, rho, &clamp);
         double du;
@@ -773,7 +811,7 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
     if (qcool) *qcool = sum_cool;
     if (qcc) *qcc = sum_cc;
     *flags = (clamp ? 1u : 0u) | (stiff ? 1u << 2 : 0u) | (eqb ? 1u << 3 : 0u) | (fail ? 1u << 4 : 0u) |
-             (fallback ? 1u << 5 : 0u);
+             (fallback ? 1u << 5 : 0u) | (floored ? 1u << 6 : 0u);
 }
 
 /* Step n cells.  counters[0..5] = cells with flag bit k set (bit 5: the
@@ -781,8 +819,8 @@ static void step_cell(const orc_rates* R, const orc_params* p, double rho, doubl
  * may hold NaN entries, computed on first use (forces one thread).
  * direct: O1 rates.  net: the surrogate network (nullable). */
 static int step_impl(const orc_spec* s, const double* lb, double* ls, const double* lc, int lazy, int direct,
-             const double* lsp, const orc_net* net, const orc_params* p, long long n,
-             const double* rho, const double* B, const double* H, const double* ue, const double* ui,
+             const double* lsp, const orc_net* net, const orc_disk* dk, const double* rr, const orc_params* p,
+             long long n, const double* rho, const double* B, const double* H, const double* ue, const double* ui,
              double* ue_out, double* ui_out, double* qcool, double* qcc,
              long long* counters, int nthreads) {
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
@@ -793,21 +831,21 @@ static int step_impl(const orc_spec* s, const double* lb, double* ls, const doub
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
         axis_init(s, a, &R->ax[a]);
     }
-    long long cnt[6] = {0, 0, 0, 0, 0, 0};
+    long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
     if (lazy || direct) nthreads = 1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1024) reduction(+:cnt[:6]) if (nthreads != 1)
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+:cnt[:7]) if (nthreads != 1)
 #endif
     for (long long i = 0; i < n; ++i) {
         unsigned f;
         double a, b;
-        step_cell(R, p, rho[i], B[i], H[i], ue[i], ui[i], &a, &b,
+        step_cell(R, p, dk, rr ? rr[i] : 0.0, rho[i], B[i], H ? H[i] : 0.0, ue[i], ui[i], &a, &b,
                   qcool ? &qcool[i] : NULL, qcc ? &qcc[i] : NULL, &f);
         ue_out[i] = a; ui_out[i] = b;
-        for (int k = 0; k < 6; ++k) cnt[k] += (f >> k) & 1u;
+        for (int k = 0; k < 7; ++k) cnt[k] += (f >> k) & 1u;
     }
-    if (counters) for (int k = 0; k < 6; ++k) counters[k] = cnt[k];
+    if (counters) for (int k = 0; k < 7; ++k) counters[k] = cnt[k];
     free(R);
     return 0;
 }
@@ -817,8 +855,8 @@ int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, 
              const double* rho, const double* B, const double* H, const double* ue, const double* ui,
              double* ue_out, double* ui_out, double* qcool, double* qcc,
              long long* counters, int nthreads) {
-    return step_impl(s, lb, ls, lc, lazy, direct, NULL, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool,
-                     qcc, counters, nthreads);
+    return step_impl(s, lb, ls, lc, lazy, direct, NULL, NULL, NULL, NULL, p, n, rho, B, H, ue, ui, ue_out,
+                     ui_out, qcool, qcc, counters, nthreads);
 }
 
 /* The step with the 4-D channel given as per-interval node pairs (the
@@ -828,8 +866,8 @@ int orc_step_pairs(const orc_spec* s, const double* lb, const double* lsp, const
                    const double* rho, const double* B, const double* H, const double* ue, const double* ui,
                    double* ue_out, double* ui_out, double* qcool, double* qcc,
                    long long* counters, int nthreads) {
-    return step_impl(s, lb, NULL, lc, 0, 0, lsp, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool, qcc,
-                     counters, nthreads);
+    return step_impl(s, lb, NULL, lc, 0, 0, lsp, NULL, NULL, NULL, p, n, rho, B, H, ue, ui, ue_out, ui_out,
+                     qcool, qcc, counters, nthreads);
 }
 
 /* The step with the surrogate network in place of the 4-D channel, except
@@ -845,10 +883,22 @@ int orc_step_surrogate(const orc_spec* s, const double* lb, const double* ls, co
     orc_net* m = (orc_net*)malloc(sizeof(orc_net));
     if (!m) return -1;
     net_init(m, params, mean, stdv, l0, span, xs, mask, rounding);
-    int rc = step_impl(s, lb, (double*)ls, lc, 0, 0, NULL, m, p, n, rho, B, H, ue, ui, ue_out, ui_out, qcool,
-                       qcc, counters, nthreads);
+    int rc = step_impl(s, lb, (double*)ls, lc, 0, 0, NULL, m, NULL, NULL, p, n, rho, B, H, ue, ui, ue_out,
+                       ui_out, qcool, qcc, counters, nthreads);
     free(m);
     return rc;
+}
+
+/* The step with the disk geometry of each cell (r per cell, spin, optional
+ * H_th from the state and the temperature floor); H may be NULL when
+ * h_from_state.  counters[6] = cells floored in some sub-cycle. */
+int orc_step_disk(const orc_spec* s, const double* lb, double* ls, const double* lc, int direct,
+                  const orc_params* p, const orc_disk* dk, long long n, const double* rho, const double* B,
+                  const double* H, const double* ue, const double* ui, const double* r, double* ue_out,
+                  double* ui_out, double* qcool, double* qcc, long long* counters, int nthreads) {
+    if (!H && !dk->h_from_state) return -4;
+    return step_impl(s, lb, ls, lc, 0, direct, NULL, NULL, dk, r, p, n, rho, B, H, ue, ui, ue_out, ui_out,
+                     qcool, qcc, counters, nthreads);
 }
 
 /* Network output (log2 units) at n normalised points x[n][4]. */

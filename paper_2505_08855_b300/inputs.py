@@ -12,6 +12,7 @@ Fields, all code units, structure of arrays:
     H    thermal scale height, in r_g
     ue   electron internal energy density
     ui   ion internal energy density
+    r    radius in r_g (only with ``with_r=True``: the disk-geometry step)
 
 Recipes (seed fixed per workload):
   * ``uniform``  -- rho ~ logU[1e-4, 1]; u_i/rho, u_e/rho ~ logU[1e-6, 1e-1]
@@ -43,7 +44,13 @@ def _b_from_beta(ue, ui, beta, gamma=GAMMA):
     return np.sqrt(2.0 * (gamma - 1.0) * (ui + ue) / beta)
 
 
-def uniform(n, seed=1001, dtype=np.float64):
+def _out(d, r, with_r, dtype):
+    if with_r:
+        d = dict(d, r=r)
+    return {k: np.ascontiguousarray(v.astype(dtype)) for k, v in d.items()}
+
+
+def uniform(n, seed=1001, dtype=np.float64, with_r=False):
     rng = np.random.default_rng(seed)
     rho = _logu(rng, 1e-4, 1.0, n)
     ui = rho * _logu(rng, 1e-6, 1e-1, n)
@@ -52,8 +59,7 @@ def uniform(n, seed=1001, dtype=np.float64):
     B = _b_from_beta(ue, ui, beta)
     r = _logu(rng, 2.0, 1000.0, n)
     H = rng.uniform(0.05, 0.5, n) * r
-    return {k: np.ascontiguousarray(v.astype(dtype)) for k, v in
-            dict(rho=rho, B=B, H=H, ue=ue, ui=ui).items()}
+    return _out(dict(rho=rho, B=B, H=H, ue=ue, ui=ui), r, with_r, dtype)
 
 
 def _mask(shape, rng):
@@ -75,11 +81,11 @@ def _mask(shape, rng):
     return out.reshape(-1)
 
 
-def two_region(shape=(256, 256, 256), seed=1002, dtype=np.float32):
+def two_region(shape=(256, 256, 256), seed=1002, dtype=np.float32, with_r=False):
     n = int(np.prod(shape))
     rng = np.random.default_rng(seed)
     hot = _mask(shape, rng)
-    base = uniform(n, seed=seed + 7, dtype=np.float64)
+    base = uniform(n, seed=seed + 7, dtype=np.float64, with_r=True)
     rho = base["rho"]
     nh = int(hot.sum())
     nc = n - nh
@@ -100,10 +106,10 @@ def two_region(shape=(256, 256, 256), seed=1002, dtype=np.float32):
     beta = _logu(rng, 0.1, 100.0, n)
     B = _b_from_beta(ue, ui, beta)
     out = dict(rho=rho, B=B, H=base["H"], ue=ue, ui=ui)
-    return {k: np.ascontiguousarray(v.astype(dtype)) for k, v in out.items()}
+    return _out(out, base["r"], with_r, dtype)
 
 
-def shell(shape=(448, 192, 192), seed=1004, dtype=np.float32):
+def shell(shape=(448, 192, 192), seed=1004, dtype=np.float32, with_r=False):
     nr, nth, nph = shape
     n = nr * nth * nph
     rng = np.random.default_rng(seed)
@@ -121,7 +127,7 @@ def shell(shape=(448, 192, 192), seed=1004, dtype=np.float32):
     beta = _logu(rng, 0.1, 100.0, n)
     B = _b_from_beta(ue, ui, beta)
     out = dict(rho=rho, B=B, H=H, ue=ue, ui=ui)
-    return {k: np.ascontiguousarray(v.astype(dtype)) for k, v in out.items()}
+    return _out(out, r, with_r, dtype)
 
 
 # The workloads by name: (recipe, keyword arguments).
