@@ -284,6 +284,21 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
     big.free()
     del big
+    # the disk geometry fused into the step (H_th from the state, floor)
+    r_dev = torch.from_numpy(inputs.make(WORKLOAD, with_r=True)["r"]).to(dev)
+    for name, disk in (("disk geometry: H_th from the state (H not read)", cool.Disk(h_from_state=1)),
+                       ("disk geometry: H_th from the state + temperature floor 0.1",
+                        cool.Disk(h_from_state=1, h_floor=0.1))):
+        p = cool.Params(n_sub=N_SUB)
+        ms = _timed(torch, lambda: cool.step_disk(table(), p, disk, tf["rho"], tf["B"], None, tf["ue"], tf["ui"],
+                                                  r_dev, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
+        c = cool.new_counters(dev)
+        cool.step_disk(table(), p, disk, tf["rho"], tf["B"], None, tf["ue"], tf["ui"], r_dev, ue_out=ue_o,
+                       ui_out=ui_o, counters=c)
+        torch.cuda.synchronize()
+        _suite_line(name, WORKLOAD, n, ms, {"counters": {k: v for k, v in cool.counters_dict(c).items() if v}},
+                    BYTES_PER_CELL, peak)
+    del r_dev
     # radiation-pressure correction of T_e: an elementwise pass (12 B read,
     # 4 B T_e + 1 B flag written per cell), 285 MB per pass > L2
     thick = torch.empty(n, dtype=torch.uint8, device=dev)

@@ -130,7 +130,22 @@ typedef struct {
     unsigned long long n_implicit_fail;  /* implicit bracket without sign change: limited explicit step taken */
     unsigned long long n_fallback;       /* cool_surrogate_infer: the table read instead of the network in
                                             some sub-cycle */
+    unsigned long long n_floor;          /* cool_step_disk: cooling skipped under the temperature floor in
+                                            some sub-cycle */
 } cool_counters;
+
+/* Disk geometry for cool_step_disk (Sec. 2.7 scale height, Sec. 3.2.3
+ * temperature floor).  Omega_K = 1/(r^1.5 + spin) (code units, r in r_g).
+ * h_from_state = 1: H_th = c_s / Omega_K with c_s^2 = gamma P/(rho + u + P),
+ * P = (gamma_e - 1) u_e + (gamma_i - 1) u_i, u = u_e + u_i, gamma = 1 + P/u,
+ * from the step's input state, replaces the H field.  h_floor > 0: a
+ * sub-cycle whose gas temperature P/rho lies below T_floor = (pi/2)
+ * (h_floor Omega_K r)^2 does not cool (the exchange still acts). */
+typedef struct {
+    double spin;               /* black-hole spin a (paper: 0.9375) */
+    double h_floor;            /* (H/R)_floor (paper: 0.1); 0 = no floor */
+    int h_from_state;          /* 0: H from the field; 1: H_th from the state */
+} cool_disk;
 
 typedef struct cool_table cool_table;    /* opaque; owns device memory */
 
@@ -251,6 +266,19 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                           const float* B, const float* H, const float* u_e_in, const float* u_i_in,
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
                           float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
+
+/* cool_step with the disk geometry of each cell: r (radius in r_g per
+ * cell, FP32 device array, > 0) and `disk` (spin, optional H_th from the
+ * state, optional temperature floor).  H may be NULL when
+ * disk->h_from_state.  FP32 fields and an FP32 table (L2WINDOW path);
+ * explicit or implicit, fp64_critical allowed; otherwise as cool_step.
+ * counters->n_floor counts cells whose cooling the floor skipped in some
+ * sub-cycle.  A cell with a non-finite or non-positive r is invalid
+ * (passed through, counted). */
+cool_status cool_step_disk(const cool_table* t, const cool_params* p, const cool_disk* disk, long long n_cells,
+                           const float* rho, const float* B, const float* H, const float* u_e_in,
+                           const float* u_i_in, const float* r, float* u_e_out, float* u_i_out,
+                           float* q_cool_out, float* q_cc_out, cool_counters* counters, void* stream);
 
 /* cool_step on HOST arrays (FP32; the L2WINDOW path): the cells are
  * streamed through the device in chunks of chunk_cells (0: n/8, at least

@@ -174,12 +174,12 @@ def _ptr(t):
 
 
 def new_counters(device=None):
-    """A zeroed device counter block (int64 x 6) for step(..., counters=)."""
+    """A zeroed device counter block (int64 x 7) for step(..., counters=)."""
     import torch
-    return torch.zeros(6, dtype=torch.int64, device=device or "cuda")
+    return torch.zeros(7, dtype=torch.int64, device=device or "cuda")
 
 
-COUNTER_NAMES = ("clamped", "nonfinite", "stiff", "fp64_coulomb", "implicit_fail", "fallback")
+COUNTER_NAMES = ("clamped", "nonfinite", "stiff", "fp64_coulomb", "implicit_fail", "fallback", "floor")
 
 
 def counters_dict(c):
@@ -208,6 +208,41 @@ def step(table, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_cool=None
                             _ptr(ue_out), _ptr(ui_out), _ptr(q_cool), _ptr(q_cc), cptr,
                             _stream_ptr(stream))
     _b.check(st, "cool_step")
+    return ue_out, ui_out
+
+
+@dataclasses.dataclass
+class Disk:
+    """Disk geometry for step_disk (cool_disk)."""
+    spin: float = 0.9375
+    h_floor: float = 0.0
+    h_from_state: int = 0
+
+    def c(self):
+        return _b.cool_disk(self.spin, self.h_floor, self.h_from_state)
+
+
+def step_disk(table, params, disk, rho, B, H, ue, ui, r, ue_out=None, ui_out=None, q_cool=None, q_cc=None,
+              counters=None, stream=None):
+    """cool_step_disk: the step with each cell's radius r (H may be None when
+    disk.h_from_state).  float32 CUDA tensors; returns (ue_out, ui_out)."""
+    import torch
+    n = rho.numel()
+    for f in (rho, B, H, ue, ui, r):
+        if f is None:
+            continue
+        if f.dtype != torch.float32 or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("fields must be contiguous float32 CUDA tensors of one size")
+    if ue_out is None:
+        ue_out = torch.empty_like(ue)
+    if ui_out is None:
+        ui_out = torch.empty_like(ui)
+    p = params.c()
+    d = disk.c()
+    cptr = C.c_void_p(counters.data_ptr()) if counters is not None else C.c_void_p(0)
+    _b.check(_b.lib().cool_step_disk(table.handle, _b.ref(p), _b.ref(d), n, _ptr(rho), _ptr(B), _ptr(H), _ptr(ue),
+                                     _ptr(ui), _ptr(r), _ptr(ue_out), _ptr(ui_out), _ptr(q_cool), _ptr(q_cc), cptr,
+                                     _stream_ptr(stream)), "cool_step_disk")
     return ue_out, ui_out
 
 

@@ -27,7 +27,7 @@ EXPORTS = (
     "cool_debug_gemm_bf16", "cool_fit_spec_default", "cool_surrogate_fit", "cool_surrogate_free",
     "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
     "cool_surrogate_eval", "cool_surrogate_mask", "cool_surrogate_set_mask", "cool_surrogate_infer",
-    "cool_step_direct", "cool_step_host", "cool_radiation_te",
+    "cool_step_direct", "cool_step_host", "cool_radiation_te", "cool_step_disk",
 )
 
 
@@ -64,7 +64,11 @@ class cool_surrogate_stats(C.Structure):
 
 class cool_counters(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("n_clamped", "n_nonfinite", "n_stiff",
-                                              "n_fp64_coulomb", "n_implicit_fail", "n_fallback")]
+                                              "n_fp64_coulomb", "n_implicit_fail", "n_fallback", "n_floor")]
+
+
+class cool_disk(C.Structure):
+    _fields_ = [("spin", C.c_double), ("h_floor", C.c_double), ("h_from_state", C.c_int)]
 
 
 class CoolError(RuntimeError):
@@ -126,6 +130,7 @@ def lib():
             "cool_step_direct": (I, [P, P, LL, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_step_host": (I, [P, P, LL, P, P, P, P, P, P, P, LL, P, P]),
             "cool_radiation_te": (I, [P, D, D, LL, P, P, P, P, P, P]),
+            "cool_step_disk": (I, [P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_surrogate_infer": (I, [P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_table_export_packed": (I, [P, P, LL]),
         }

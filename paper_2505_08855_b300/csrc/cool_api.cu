@@ -726,6 +726,34 @@ cool_status cool_step_host(const cool_table* t, const cool_params* p, long long 
     return COOL_OK;
 }
 
+cool_status cool_step_disk(const cool_table* t, const cool_params* p, const cool_disk* disk, long long n_cells,
+                           const float* rho, const float* B, const float* H, const float* u_e_in,
+                           const float* u_i_in, const float* r, float* u_e_out, float* u_i_out,
+                           float* q_cool_out, float* q_cc_out, cool_counters* counters, void* stream) {
+    if (!t || !p || !disk) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    cool_status st = validate_params(p);
+    if (st != COOL_OK) return st;
+    if (p->path != COOL_PATH_L2WINDOW || t->spec.dtype != COOL_F32) return COOL_EUNSUPPORTED;
+    if (!isfinite(disk->spin) || !(disk->h_floor >= 0.0) || !isfinite(disk->h_floor) ||
+        (disk->h_from_state != 0 && disk->h_from_state != 1))
+        return COOL_EINVAL;
+    if (n_cells < 0) return COOL_EINVAL;
+    if (n_cells == 0) return COOL_OK;
+    if (!rho || !B || !u_e_in || !u_i_in || !r || !u_e_out || !u_i_out) return COOL_ENULL;
+    if (!H && !disk->h_from_state) return COOL_ENULL;
+    const float* Hs = H ? H : r;   // with h_from_state the H values are not used
+    const void* ptrs[] = {rho, B, Hs, u_e_in, u_i_in, r, u_e_out, u_i_out, q_cool_out, q_cc_out};
+    for (const void* q : ptrs)
+        if ((uintptr_t)q % 4 != 0) return COOL_EALIGN;
+    if ((uintptr_t)counters % 8 != 0) return COOL_EALIGN;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return COOL_ESTATE;
+    return launch_step_f32(t, p, n_cells, rho, B, Hs, u_e_in, u_i_in, u_e_out, u_i_out, q_cool_out, q_cc_out,
+                           counters, (cudaStream_t)stream, disk, r);
+}
+
 cool_status cool_step_direct(const cool_table_spec* physics, const cool_params* p, long long n_cells,
                              const double* rho, const double* B, const double* H, const double* u_e_in,
                              const double* u_i_in, double* u_e_out, double* u_i_out, double* q_cool_out,

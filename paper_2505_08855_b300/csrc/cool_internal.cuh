@@ -107,7 +107,8 @@ cool_status fit_samples_fp64(const cool_table_spec& s, long long n, unsigned lon
 cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long n,
                             const float* rho, const float* B, const float* H,
                             const float* ue, const float* ui, float* ue_o, float* ui_o,
-                            float* qc, float* qx, cool_counters* cnt, cudaStream_t st);
+                            float* qc, float* qx, cool_counters* cnt, cudaStream_t st,
+                            const cool_disk* disk = nullptr, const float* r = nullptr);
 cool_status launch_step_f64(const cool_table* t, const cool_params* p, long long n,
                             const double* rho, const double* B, const double* H,
                             const double* ue, const double* ui, double* ue_o, double* ui_o,

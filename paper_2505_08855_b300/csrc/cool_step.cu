@@ -32,21 +32,39 @@ namespace cool {
 namespace {
 struct Out {
     float ue, ui, qc, qx;
-    unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail
+    unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail, 6 floored
 };
 
-// VAR: bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in
-// (the explicit FP32 kernel carries no solver code and no FP64 code).
+// VAR: bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in,
+// bit 2 = disk geometry (radius r per cell: H_th from the state and the
+// temperature floor; Sec. 2.7, Sec. 3.2.3).  The explicit FP32 kernel carries
+// no solver code, no FP64 code and no geometry.
 template <int FMT, int VAR>
 __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* win, float rho, float B,
-                                         float H, float ue, float ui) {
+                                         float H, float ue, float ui, float r) {
     Out o;
+    float t_floor = -1.f;   // gas temperature P/rho below which a sub-cycle does not cool
+    if (VAR & 4) {
+        if (k.h_from_state && isfinite(r) && r > 0.f && rho > 0.f && ue > 0.f && ui > 0.f) {
+            // H_th = c_s / Omega_K, c_s^2 = gamma P / (rho + u + P), gamma = 1 + P/u,
+            // Omega_K = 1 / (r^1.5 + a)
+            const float P = fmaf(k.ce, ue, k.ci * ui);
+            const float u = ue + ui;
+            const float cs2 = (1.f + P / u) * P / (rho + u + P);
+            H = sqrtf(cs2) * fmaf(r, sqrtf(r), k.spin);
+        }
+        if (k.h_floor > 0.f) {
+            const float v = k.h_floor * r / fmaf(r, sqrtf(r), k.spin);
+            t_floor = 1.5707963f * v * v;
+        }
+    }
     if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
-        !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
+        !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f ||
+        ((VAR & 4) && !(isfinite(r) && r > 0.f))) {
         o.ue = ue; o.ui = ui; o.qc = 0.f; o.qx = 0.f; o.flags = 2u;
         return o;
     }
-    unsigned clamp = 0u, stiff = 0u, band = 0u, fail = 0u;
+    unsigned clamp = 0u, stiff = 0u, band = 0u, fail = 0u, floored = 0u;
     const DevTable& T = k.tab;
     const float ne = rho * k.s_n;
     const float Bg = B * k.s_B;
@@ -118,6 +136,11 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
             ui -= X;
         }
         sum_x += X;
+        // ---- temperature floor: no cooling below T_floor -----------------------
+        if ((VAR & 4) && fmaf(k.ce, ue, k.ci * ui) < t_floor * rho) {
+            floored = 1u;
+            continue;
+        }
         // ---- (ii) radiative cooling ----------------------------------------
         const float q = cool_energy<FMT>(k, S, c, cc, ue * inv_e, clamp);
         float du = fminf(q, k.limiter * ue);
@@ -133,7 +156,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         sum_q += du;
     }
     o.ue = ue; o.ui = ui; o.qc = sum_q; o.qx = sum_x;
-    o.flags = clamp | (stiff << 2) | (band << 3) | (fail << 4);
+    o.flags = clamp | (stiff << 2) | (band << 3) | (fail << 4) | (floored << 6);
     return o;
 }
 
@@ -151,7 +174,8 @@ __device__ __forceinline__ void count_flags(unsigned f, cool_counters* cnt) {
     // warp-aggregated counter updates
     const unsigned full = __activemask();
 #pragma unroll
-    for (int b = 0; b < 5; ++b) {
+    for (int b = 0; b < 7; ++b) {
+        if (b == 5) continue;   // surrogate fallback: not set by this kernel
         unsigned m = __ballot_sync(full, (f >> b) & 1u);
         if (m && (threadIdx.x & 31) == (__ffs(full) - 1)) {
             unsigned long long* dst = nullptr;
@@ -160,7 +184,8 @@ __device__ __forceinline__ void count_flags(unsigned f, cool_counters* cnt) {
             case 1: dst = &cnt->n_nonfinite; break;
             case 2: dst = &cnt->n_stiff; break;
             case 3: dst = &cnt->n_fp64_coulomb; break;
-            default: dst = &cnt->n_implicit_fail; break;
+            case 4: dst = &cnt->n_implicit_fail; break;
+            default: dst = &cnt->n_floor; break;
             }
             atomicAdd(dst, (unsigned long long)__popc(m));
         }
@@ -190,7 +215,8 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
                                                          const float* __restrict__ Bf, const float* __restrict__ Hf,
                                                          const float* ue_in, const float* ui_in, float* ue_out,
                                                          float* ui_out, float* qc_out, float* qx_out,
-                                                         cool_counters* cnt) {
+                                                         cool_counters* cnt, const float* __restrict__ rr) {
+    constexpr int NF = (VAR & 4) ? 6 : 5;   // staged input fields
     extern __shared__ float sm[];
     load_smem(k, sm);
     Smem S;
@@ -202,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     const int warp = threadIdx.x >> 5;
     long long scalar_start = 0;
     if (VEC) {
-        float* tile = sm + smem_table_floats(k) + kMaxW * kThreads + warp * 5 * kWarpCells;
+        float* tile = sm + smem_table_floats(k) + kMaxW * kThreads + warp * NF * kWarpCells;
         float4* t4 = reinterpret_cast<float4*>(tile);
         const long long ntiles = n / kWarpCells;
         for (long long tw = (long long)blockIdx.x * kWarps + warp; tw < ntiles; tw += (long long)gridDim.x * kWarps) {
@@ -212,12 +238,14 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
             t4[2 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(Hf) + q);
             t4[3 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ue_in) + q);
             t4[4 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ui_in) + q);
+            if (VAR & 4) t4[5 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rr) + q);
             __syncwarp();
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
                 Out o = step_cell<FMT, VAR>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
-                                            tile[3 * kWarpCells + j], tile[4 * kWarpCells + j]);
+                                            tile[3 * kWarpCells + j], tile[4 * kWarpCells + j],
+                                            (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
                 // inputs of cell j are consumed: outputs reuse its slots
                 tile[3 * kWarpCells + j] = o.ue;
                 tile[4 * kWarpCells + j] = o.ui;
@@ -236,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT, VAR>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i]);
+        Out o = step_cell<FMT, VAR>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], (VAR & 4) ? rr[i] : 0.f);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
@@ -657,26 +685,36 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long n,
                             const float* rho, const float* B, const float* H,
                             const float* ue, const float* ui, float* ue_o, float* ui_o,
-                            float* qc, float* qx, cool_counters* cnt, cudaStream_t st) {
+                            float* qc, float* qx, cool_counters* cnt, cudaStream_t st,
+                            const cool_disk* disk, const float* r) {
     StepK k;
     fill_stepk(t, p, k);
+    k.spin = disk ? (float)disk->spin : 0.f;
+    k.h_floor = disk ? (float)disk->h_floor : 0.f;
+    k.h_from_state = disk ? disk->h_from_state : 0;
     if (n == 0) return COOL_OK;
     bool vec = ((uintptr_t)rho | (uintptr_t)B | (uintptr_t)H | (uintptr_t)ue | (uintptr_t)ui |
-                (uintptr_t)ue_o | (uintptr_t)ui_o | (uintptr_t)qc | (uintptr_t)qx) % 16 == 0;
+                (uintptr_t)ue_o | (uintptr_t)ui_o | (uintptr_t)qc | (uintptr_t)qx | (uintptr_t)r) % 16 == 0;
     size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads) * sizeof(float);
-    if (vec) smem += (size_t)kWarps * 5 * kWarpCells * sizeof(float);
+    if (vec) smem += (size_t)kWarps * (disk ? 6 : 5) * kWarpCells * sizeof(float);
     using KFn = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
-                         float*, float*, float*, float*, cool_counters*);
+                         float*, float*, float*, float*, cool_counters*, const float*);
 #define COOL_KV(V, F) k_step_f32<V, F, 0>, k_step_f32<V, F, 1>, k_step_f32<V, F, 2>, k_step_f32<V, F, 3>
     static const KFn table_v[5][4] = {{COOL_KV(true, 0)}, {COOL_KV(true, 1)}, {COOL_KV(true, 2)},
                                       {COOL_KV(true, 3)}, {COOL_KV(true, 4)}};
     static const KFn table_s[5][4] = {{COOL_KV(false, 0)}, {COOL_KV(false, 1)}, {COOL_KV(false, 2)},
                                       {COOL_KV(false, 3)}, {COOL_KV(false, 4)}};
 #undef COOL_KV
+    // disk geometry: FP32 table only
+    static const KFn disk_v[4] = {k_step_f32<true, 0, 4>, k_step_f32<true, 0, 5>, k_step_f32<true, 0, 6>,
+                                  k_step_f32<true, 0, 7>};
+    static const KFn disk_s[4] = {k_step_f32<false, 0, 4>, k_step_f32<false, 0, 5>, k_step_f32<false, 0, 6>,
+                                  k_step_f32<false, 0, 7>};
     const int fmt = t->dev.fmt;
     if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
+    if (disk && (fmt != 0 || !r)) return COOL_EUNSUPPORTED;
     const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0);
-    KFn fn = vec ? table_v[fmt][var] : table_s[fmt][var];
+    KFn fn = disk ? (vec ? disk_v[var] : disk_s[var]) : (vec ? table_v[fmt][var] : table_s[fmt][var]);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;
@@ -687,7 +725,7 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
     long long blocks = work < cap ? work : cap;
     if (blocks < 1) blocks = 1;
-    fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt);
+    fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt, r);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;

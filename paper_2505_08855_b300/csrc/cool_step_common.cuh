@@ -124,6 +124,8 @@ struct StepK {
     int n_sub, mode, iters;
     int smem_floats;                  // floats of axes + lb + lc in shared memory
     int axes_floats;
+    float spin, h_floor;              // disk geometry (the disk step): a, (H/R)_floor
+    int h_from_state;                 // H_th = c_s / Omega_K replaces the H field
 };
 
 struct Sel {

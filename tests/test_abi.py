@@ -54,6 +54,7 @@ def test_struct_layout_matches_header(tmp_path):
         "cool_counters": [f[0] for f in b.cool_counters._fields_],
         "cool_fit_spec": [f[0] for f in b.cool_fit_spec._fields_],
         "cool_surrogate_stats": [f[0] for f in b.cool_surrogate_stats._fields_],
+        "cool_disk": [f[0] for f in b.cool_disk._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fl in fields.items():
