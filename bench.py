@@ -228,18 +228,20 @@ def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=Non
     print(json.dumps(line), flush=True)
 
 
+SECTIONS = ("cfg2", "paper_size", "disk", "radiation", "scalar", "fp64", "adjoint", "direct", "surrogate")
+
+
 def run_suite_perf(args, torch, cool, inputs, dev):
-    """Step variants on the benchmark workload (formats, modes, FP64), the
-    forward + adjoint on 128^3 uniform cells, and the surrogate step on the
+    """Secondary measurements, one JSON line per case, by section (--section,
+    default all): step variants on the benchmark workload (formats, modes,
+    texture paths), the paper-size table, the disk geometry, the radiation
+    correction, unaligned and FP64 fields, the forward + adjoint and the
+    direct-formula step on 128^3 uniform cells, and the surrogate step on the
     512 x 256 x 256 shell."""
+    want = set(SECTIONS) if args.section == "all" else set(args.section.split(","))
     stream = torch.cuda.current_stream()
     peak, _ = measured_peak()
     steps, warm = max(args.steps // 10, 3), 3
-    F = inputs.make(WORKLOAD)
-    n = F["rho"].size
-    tf = {k: torch.from_numpy(v).to(dev) for k, v in F.items()}
-    fl = [tf[k] for k in ("rho", "B", "H", "ue", "ui")]
-    ue_o, ui_o = torch.empty_like(tf["ue"]), torch.empty_like(tf["ui"])
     tables = {}
 
     def table(dtype=cool.F32, scaled=0):
@@ -254,134 +256,163 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         torch.cuda.synchronize()
         return {k: v for k, v in cool.counters_dict(c).items() if v}
 
-    cases = [("explicit, FP32 table", cool.F32, 0, cool.Params(n_sub=N_SUB), steps),
-             ("explicit, fp64_critical", cool.F32, 0, cool.Params(n_sub=N_SUB, fp64_critical=1), steps),
-             ("implicit (Illinois, FP32)", cool.F32, 0, cool.Params(n_sub=N_SUB, mode=cool.IMPLICIT), steps),
-             ("implicit, fp64_critical", cool.F32, 0, cool.Params(n_sub=N_SUB, mode=cool.IMPLICIT,
-                                                                    fp64_critical=1), 3),
-             ("explicit, BF16 table", cool.BF16, 0, cool.Params(n_sub=N_SUB), steps),
-             ("explicit, FP16 table", cool.F16, 0, cool.Params(n_sub=N_SUB), steps),
-             ("explicit, BF16 row-scaled table", cool.BF16, 1, cool.Params(n_sub=N_SUB), steps),
-             ("explicit, FP16 row-scaled table", cool.F16, 1, cool.Params(n_sub=N_SUB), steps),
-             ("explicit, N_sub = 1", cool.F32, 0, cool.Params(n_sub=1), steps),
-             ("explicit, texture path: point fetches + FP32 lerp", cool.F32, 0,
-              cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT), steps),
-             ("explicit, texture path: hardware trilinear filtering", cool.F32, 0,
-              cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP), steps)]
-    for name, dt, sc, p, k in cases:
-        t = table(dt, sc)
-        ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=ue_o, ui_out=ui_o), k, warm, stream)
-        _suite_line(name, WORKLOAD, n, ms, {"counters": counters(t, p, fl, (ue_o, ui_o)),
-                                            "table_packed_bytes": t.packed_bytes()},
-                    BYTES_PER_CELL, peak)
-    # the paper's table size (100 nodes per axis): 457 MB packed, far beyond L2
-    big = cool.Table(cool.TableSpec(n=(100,) * 5))
-    for name, path in (("paper-size 100^4 table, L2 block layout", cool.PATH_L2WINDOW),
-                       ("paper-size 100^4 table, texture hardware filtering", cool.PATH_TEXTURE_HWLERP),
-                       ("paper-size 100^4 table, texture point fetches", cool.PATH_TEXTURE_POINT)):
-        p = cool.Params(n_sub=N_SUB, path=path)
-        ms = _timed(torch, lambda: cool.step(big, p, *fl, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
-        _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
-    big.free()
-    del big
-    # the disk geometry fused into the step (H_th from the state, floor)
-    r_dev = torch.from_numpy(inputs.make(WORKLOAD, with_r=True)["r"]).to(dev)
-    for name, disk in (("disk geometry: H_th from the state (H not read)", cool.Disk(h_from_state=1)),
-                       ("disk geometry: H_th from the state + temperature floor 0.1",
-                        cool.Disk(h_from_state=1, h_floor=0.1))):
+    if want & {"cfg2", "paper_size", "disk", "radiation", "scalar", "fp64"}:
+        F = inputs.make(WORKLOAD)
+        n = F["rho"].size
+        tf = {k: torch.from_numpy(v).to(dev) for k, v in F.items()}
+        fl = [tf[k] for k in ("rho", "B", "H", "ue", "ui")]
+        ue_o, ui_o = torch.empty_like(tf["ue"]), torch.empty_like(tf["ui"])
+        del F
+    if "cfg2" in want:
+        cases = [("explicit, FP32 table", cool.F32, 0, cool.Params(n_sub=N_SUB), steps),
+                 ("explicit, fp64_critical", cool.F32, 0, cool.Params(n_sub=N_SUB, fp64_critical=1), steps),
+                 ("implicit (Illinois, FP32)", cool.F32, 0, cool.Params(n_sub=N_SUB, mode=cool.IMPLICIT), steps),
+                 ("implicit, fp64_critical", cool.F32, 0, cool.Params(n_sub=N_SUB, mode=cool.IMPLICIT,
+                                                                        fp64_critical=1), 3),
+                 ("explicit, BF16 table", cool.BF16, 0, cool.Params(n_sub=N_SUB), steps),
+                 ("explicit, FP16 table", cool.F16, 0, cool.Params(n_sub=N_SUB), steps),
+                 ("explicit, BF16 row-scaled table", cool.BF16, 1, cool.Params(n_sub=N_SUB), steps),
+                 ("explicit, FP16 row-scaled table", cool.F16, 1, cool.Params(n_sub=N_SUB), steps),
+                 ("explicit, N_sub = 1", cool.F32, 0, cool.Params(n_sub=1), steps),
+                 ("explicit, texture path: point fetches + FP32 lerp", cool.F32, 0,
+                  cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT), steps),
+                 ("explicit, texture path: hardware trilinear filtering", cool.F32, 0,
+                  cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP), steps)]
+        for name, dt, sc, p, k in cases:
+            t = table(dt, sc)
+            ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=ue_o, ui_out=ui_o), k, warm, stream)
+            _suite_line(name, WORKLOAD, n, ms, {"counters": counters(t, p, fl, (ue_o, ui_o)),
+                                                "table_packed_bytes": t.packed_bytes()},
+                        BYTES_PER_CELL, peak)
+    if "paper_size" in want:
+        # the paper's table size (100 nodes per axis): 457 MB packed, far beyond L2
+        big = cool.Table(cool.TableSpec(n=(100,) * 5))
+        for name, path in (("paper-size 100^4 table, L2 block layout", cool.PATH_L2WINDOW),
+                           ("paper-size 100^4 table, texture hardware filtering", cool.PATH_TEXTURE_HWLERP),
+                           ("paper-size 100^4 table, texture point fetches", cool.PATH_TEXTURE_POINT)):
+            p = cool.Params(n_sub=N_SUB, path=path)
+            ms = _timed(torch, lambda: cool.step(big, p, *fl, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
+            _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
+        big.free()
+        del big
+    if "disk" in want:
+        # the disk geometry fused into the step (H_th from the state, floor)
+        r_dev = torch.from_numpy(inputs.make(WORKLOAD, with_r=True)["r"]).to(dev)
+        for name, disk in (("disk geometry: H_th from the state (H not read)", cool.Disk(h_from_state=1)),
+                           ("disk geometry: H_th from the state + temperature floor 0.1",
+                            cool.Disk(h_from_state=1, h_floor=0.1))):
+            p = cool.Params(n_sub=N_SUB)
+            ms = _timed(torch, lambda: cool.step_disk(table(), p, disk, tf["rho"], tf["B"], None, tf["ue"],
+                                                      tf["ui"], r_dev, ue_out=ue_o, ui_out=ui_o), steps, warm,
+                        stream)
+            c = cool.new_counters(dev)
+            cool.step_disk(table(), p, disk, tf["rho"], tf["B"], None, tf["ue"], tf["ui"], r_dev, ue_out=ue_o,
+                           ui_out=ui_o, counters=c)
+            torch.cuda.synchronize()
+            _suite_line(name, WORKLOAD, n, ms, {"counters": {k: v for k, v in cool.counters_dict(c).items() if v}},
+                        BYTES_PER_CELL, peak)
+        del r_dev
+    if "radiation" in want:
+        # radiation-pressure correction of T_e: an elementwise pass (12 B
+        # read, 4 B T_e + 1 B flag written per cell), 285 MB per pass > L2
+        thick = torch.empty(n, dtype=torch.uint8, device=dev)
         p = cool.Params(n_sub=N_SUB)
-        ms = _timed(torch, lambda: cool.step_disk(table(), p, disk, tf["rho"], tf["B"], None, tf["ue"], tf["ui"],
-                                                  r_dev, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
-        c = cool.new_counters(dev)
-        cool.step_disk(table(), p, disk, tf["rho"], tf["B"], None, tf["ue"], tf["ui"], r_dev, ue_out=ue_o,
-                       ui_out=ui_o, counters=c)
-        torch.cuda.synchronize()
-        _suite_line(name, WORKLOAD, n, ms, {"counters": {k: v for k, v in cool.counters_dict(c).items() if v}},
-                    BYTES_PER_CELL, peak)
-    del r_dev
-    # radiation-pressure correction of T_e: an elementwise pass (12 B read,
-    # 4 B T_e + 1 B flag written per cell), 285 MB per pass > L2
-    thick = torch.empty(n, dtype=torch.uint8, device=dev)
-    p = cool.Params(n_sub=N_SUB)
-    ms = _timed(torch, lambda: cool.radiation_te(p, tf["rho"], tf["H"], tf["ue"], te_out=ue_o, thick_out=thick),
-                steps * 5, warm, stream)
-    _suite_line("radiation-pressure T_e correction (Sec. 5.2 quartic), elementwise", WORKLOAD, n, ms,
-                {"thick_cells": int(thick.sum().item())}, 17, peak)
-    del thick
-    # unaligned fields: the scalar path
-    off = {k: torch.cat([v[:1], v])[1:] for k, v in tf.items()}
-    ofl = [off[k] for k in ("rho", "B", "H", "ue", "ui")]
-    p = cool.Params(n_sub=N_SUB)
-    ms = _timed(torch, lambda: cool.step(table(), p, *ofl), steps, warm, stream)
-    _suite_line("explicit, fields not 16-byte aligned (scalar path)", WORKLOAD, n, ms, None, BYTES_PER_CELL, peak)
-    del off, ofl
-    # FP64 fields (all-FP64 kernel)
-    f64 = [v.double() for v in fl]
-    o64 = [torch.empty_like(f64[3]), torch.empty_like(f64[4])]
-    ms = _timed(torch, lambda: cool.step(table(), p, *f64, ue_out=o64[0], ui_out=o64[1]), 3, 1, stream)
-    _suite_line("FP64 fields and arithmetic", WORKLOAD, n, ms, None, 56, peak)
-    del f64, o64, tf, fl, ue_o, ui_o
-    torch.cuda.empty_cache()
+        ms = _timed(torch, lambda: cool.radiation_te(p, tf["rho"], tf["H"], tf["ue"], te_out=ue_o, thick_out=thick),
+                    steps * 5, warm, stream)
+        _suite_line("radiation-pressure T_e correction (Sec. 5.2 quartic), elementwise", WORKLOAD, n, ms,
+                    {"thick_cells": int(thick.sum().item())}, 17, peak)
+        del thick
+    if "scalar" in want:
+        # unaligned fields: the scalar path
+        off = {k: torch.cat([v[:1], v])[1:] for k, v in tf.items()}
+        ofl = [off[k] for k in ("rho", "B", "H", "ue", "ui")]
+        p = cool.Params(n_sub=N_SUB)
+        ms = _timed(torch, lambda: cool.step(table(), p, *ofl), steps, warm, stream)
+        _suite_line("explicit, fields not 16-byte aligned (scalar path)", WORKLOAD, n, ms, None, BYTES_PER_CELL,
+                    peak)
+        del off, ofl
+    if "fp64" in want:
+        # FP64 fields (all-FP64 kernel)
+        p = cool.Params(n_sub=N_SUB)
+        f64 = [v.double() for v in fl]
+        o64 = [torch.empty_like(f64[3]), torch.empty_like(f64[4])]
+        ms = _timed(torch, lambda: cool.step(table(), p, *f64, ue_out=o64[0], ui_out=o64[1]), 3, 1, stream)
+        _suite_line("FP64 fields and arithmetic", WORKLOAD, n, ms, None, 56, peak)
+        del f64, o64
+    if want & {"cfg2", "paper_size", "disk", "radiation", "scalar", "fp64"}:
+        del tf, fl, ue_o, ui_o
+        torch.cuda.empty_cache()
 
-    # forward + adjoint, 128^3 uniform cells
-    G = inputs.make("uniform_128c")
-    m = G["rho"].size
-    tg = {k: torch.from_numpy(v).to(dev) for k, v in G.items()}
-    gl = [tg[k] for k in ("rho", "B", "H", "ue", "ui")]
-    g_ue = torch.ones_like(tg["ue"])
-    g_ui = torch.full_like(tg["ui"], 0.5)
-    T = table()
-    nH, nB, nN, nT, nC = TABLE_N
-    tgr = {"lb": torch.zeros(nT, device=dev), "ls": torch.zeros(nH * nB * nN * nT, device=dev),
-           "lc": torch.zeros(nC * nC, device=dev)}
-    ms_f = _timed(torch, lambda: cool.step(T, p, *gl), steps * 5, warm, stream)
-    ms_b = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui), steps * 5, warm, stream)
-    ms_bt = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui, tgr), steps * 5, warm, stream)
-    _suite_line("forward, 128^3 uniform", "uniform_128c", m, ms_f, None, BYTES_PER_CELL, peak)
-    # the paper's analytic-versus-table comparison: every rate from the
-    # formulas (FP64), on the first 2^18 of these cells
-    k = 1 << 18
-    d64 = [t[:k].double().contiguous() for t in gl]
-    ms_d = _timed(torch, lambda: cool.step_direct(cool.TableSpec(n=TABLE_N), p, *d64), 1, 1, stream)
-    _suite_line("direct formulas, no table (FP64), 2^18 of the 128^3 uniform cells", "uniform_128c", k, ms_d,
-                {"table_step_speedup": (m / (ms_f * 1e-3)) / (k / (ms_d * 1e-3))}, 56, peak)
-    del d64
-    _suite_line("adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_b, None, 48, peak)
-    _suite_line("forward + adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_f + ms_b, None, 76, peak)
-    _suite_line("forward + adjoint (inputs and table), 128^3 uniform", "uniform_128c", m, ms_f + ms_bt, None, 76,
-                peak)
-    del tg, gl, g_ue, g_ui, tgr
-    torch.cuda.empty_cache()
+    if want & {"adjoint", "direct"}:
+        # forward + adjoint, 128^3 uniform cells
+        G = inputs.make("uniform_128c")
+        m = G["rho"].size
+        tg = {k: torch.from_numpy(v).to(dev) for k, v in G.items()}
+        gl = [tg[k] for k in ("rho", "B", "H", "ue", "ui")]
+        T = table()
+        p = cool.Params(n_sub=N_SUB)
+        ms_f = _timed(torch, lambda: cool.step(T, p, *gl), steps * 5, warm, stream)
+        _suite_line("forward, 128^3 uniform", "uniform_128c", m, ms_f, None, BYTES_PER_CELL, peak)
+    if "adjoint" in want:
+        g_ue = torch.ones_like(tg["ue"])
+        g_ui = torch.full_like(tg["ui"], 0.5)
+        nH, nB, nN, nT, nC = TABLE_N
+        tgr = {"lb": torch.zeros(nT, device=dev), "ls": torch.zeros(nH * nB * nN * nT, device=dev),
+               "lc": torch.zeros(nC * nC, device=dev)}
+        ms_b = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui), steps * 5, warm, stream)
+        ms_bt = _timed(torch, lambda: cool.step_bwd(T, p, *gl, g_ue, g_ui, tgr), steps * 5, warm, stream)
+        _suite_line("adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_b, None, 48, peak)
+        _suite_line("forward + adjoint (inputs only), 128^3 uniform", "uniform_128c", m, ms_f + ms_b, None, 76,
+                    peak)
+        _suite_line("forward + adjoint (inputs and table), 128^3 uniform", "uniform_128c", m, ms_f + ms_bt, None,
+                    76, peak)
+        del g_ue, g_ui, tgr
+    if "direct" in want:
+        # the paper's analytic-versus-table comparison: every rate from the
+        # formulas (FP64), on the first 2^18 of these cells
+        k = 1 << 18
+        d64 = [t[:k].double().contiguous() for t in gl]
+        ms_d = _timed(torch, lambda: cool.step_direct(cool.TableSpec(n=TABLE_N), p, *d64), 1, 1, stream)
+        _suite_line("direct formulas, no table (FP64), 2^18 of the 128^3 uniform cells", "uniform_128c", k, ms_d,
+                    {"table_step_speedup": (m / (ms_f * 1e-3)) / (k / (ms_d * 1e-3))}, 56, peak)
+        del d64
+    if want & {"adjoint", "direct"}:
+        del tg, gl
+        torch.cuda.empty_cache()
 
-    # the surrogate step on the 512 x 256 x 256 shell (training untimed)
-    S = inputs.make("shell_512x256x256")
-    m = S["rho"].size
-    ts = {k: torch.from_numpy(v).to(dev) for k, v in S.items()}
-    sl = [ts[k] for k in ("rho", "B", "H", "ue", "ui")]
-    so = [torch.empty_like(ts["ue"]), torch.empty_like(ts["ui"])]
-    t0 = time.time()
-    sur = cool.Surrogate(T, cool.FitSpec())
-    torch.cuda.synchronize()
-    fit_s = time.time() - t0
-    info = sur.info()
-    ms_t = _timed(torch, lambda: cool.step(T, p, *sl, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
-    _suite_line("table step, 512x256x256 shell", "shell_512x256x256", m, ms_t, None, BYTES_PER_CELL, peak)
-    cells = info["mask_cells"]
-    for name, bits in (("surrogate step, fitted fallback mask (tol 1e-3)", None),
-                       ("surrogate step, network in every cell", np.zeros((cells + 31) // 32, np.uint32))):
-        if bits is not None:
-            sur.set_mask(bits)
-        ms = _timed(torch, lambda: sur.step(p, *sl, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
-        c = cool.new_counters(dev)
-        sur.step(p, *sl, ue_out=so[0], ui_out=so[1], counters=c)
+    if "surrogate" in want:
+        # the surrogate step on the 512 x 256 x 256 shell (training untimed)
+        S = inputs.make("shell_512x256x256")
+        m = S["rho"].size
+        ts = {k: torch.from_numpy(v).to(dev) for k, v in S.items()}
+        del S
+        sl = [ts[k] for k in ("rho", "B", "H", "ue", "ui")]
+        so = [torch.empty_like(ts["ue"]), torch.empty_like(ts["ui"])]
+        T = table()
+        p = cool.Params(n_sub=N_SUB)
+        t0 = time.time()
+        sur = cool.Surrogate(T, cool.FitSpec(epochs=args.fit_epochs))
         torch.cuda.synchronize()
-        cd = cool.counters_dict(c)
-        evals = N_SUB * (m - cd["fallback"])
-        flops = 2.0 * 17024 * evals
-        _suite_line(name, "shell_512x256x256", m, ms,
-                    {"fallback_cells": cd["fallback"], "fit_seconds": fit_s, "fit": info,
-                     "network_tflops": flops / (ms * 1e-3) / 1e12}, BYTES_PER_CELL, peak)
-    sur.free()
+        fit_s = time.time() - t0
+        info = sur.info()
+        ms_t = _timed(torch, lambda: cool.step(T, p, *sl, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
+        _suite_line("table step, 512x256x256 shell", "shell_512x256x256", m, ms_t, None, BYTES_PER_CELL, peak)
+        cells = info["mask_cells"]
+        for name, bits in (("surrogate step, fitted fallback mask (tol 1e-3)", None),
+                           ("surrogate step, network in every cell", np.zeros((cells + 31) // 32, np.uint32))):
+            if bits is not None:
+                sur.set_mask(bits)
+            ms = _timed(torch, lambda: sur.step(p, *sl, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
+            c = cool.new_counters(dev)
+            sur.step(p, *sl, ue_out=so[0], ui_out=so[1], counters=c)
+            torch.cuda.synchronize()
+            cd = cool.counters_dict(c)
+            evals = N_SUB * (m - cd["fallback"])
+            flops = 2.0 * 17024 * evals
+            _suite_line(name, "shell_512x256x256", m, ms,
+                        {"fallback_cells": cd["fallback"], "fit_seconds": fit_s, "fit": info,
+                         "network_tflops": flops / (ms * 1e-3) / 1e12}, BYTES_PER_CELL, peak)
+        sur.free()
     return 0
 
 
@@ -395,6 +426,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--suite", default=None, choices=["perf"],
                     help="secondary measurements, one JSON line per case, instead of the benchmark line")
+    ap.add_argument("--section", default="all",
+                    help="with --suite perf: comma-separated subset of " + ",".join(SECTIONS))
+    ap.add_argument("--fit-epochs", type=int, default=16,
+                    help="with --suite perf: training epochs of the surrogate (0: untrained network)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

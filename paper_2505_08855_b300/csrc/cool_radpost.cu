@@ -32,18 +32,33 @@ struct RadK {
     float sqrt_k_a;   // sqrt(k_B / a)
 };
 
-__device__ __forceinline__ float rad_te(const RadK& k, float rho, float H, float ue, unsigned char& thick) {
-    thick = 0;
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The thin/thick split of one cell.  Returns T_e,sim (or NaN for an invalid
+// cell) and sets *thick when the quartic must be solved; then s and beta
+// are its scale and parameter (see the header comment).
+__device__ __forceinline__ float rad_split(const RadK& k, float rho, float H, float ue, bool& thick, float& s,
+                                           float& beta) {
+    thick = false;
     if (!(isfinite(rho) && isfinite(H) && isfinite(ue)) || !(rho > 0.f) || !(ue > 0.f) || H < 0.f)
         return __int_as_float(0x7fc00000);   // NaN: invalid cell
     const float te = __fdividef(k.s_Te * ue, rho);
     const float tau = k.s_tau * rho * H;
     if (!(tau > k.tau_crit)) return te;
-    thick = 1;
+    thick = true;
     // s = (n k T_e / a)^(1/4) as nested square roots (no FP32 overflow for
     // n <= 1e30 cm^-3, T_e <= 1e30 K), beta = s / T_e
-    const float s = sqrtf(sqrtf(k.s_n * rho) * sqrtf(te) * k.sqrt_k_a);
-    const float beta = __fdividef(s, te);
+    s = sqrt_approx(sqrt_approx(k.s_n * rho) * sqrt_approx(te) * k.sqrt_k_a);
+    beta = __fdividef(s, te);
+    return te;
+}
+
+// The corrected temperature s y of a thick cell (T_e,sim given).
+__device__ __forceinline__ float rad_solve(float te, float s, float beta) {
     if (beta > 0x1p40f) return te;                // radiation negligible: T = T_e (1 - O(beta^-4))
     if (beta < 0x1p-40f) return s;                // gas pressure negligible: T = s (1 - O(beta))
     float y = fminf(1.f, __fdividef(1.f, beta));
@@ -55,34 +70,89 @@ __device__ __forceinline__ float rad_te(const RadK& k, float rho, float H, float
     return s * y;
 }
 
-__global__ void __launch_bounds__(256) k_radiation_te(RadK k, long long n, const float* __restrict__ rho,
-                                                      const float* __restrict__ H, const float* __restrict__ ue,
-                                                      float* __restrict__ te_out, unsigned char* thick_out,
-                                                      bool vec) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long start = 0;
-    if (vec) {
-        const long long n4 = n / 4;
-        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
-            const float4 r = __ldcs(reinterpret_cast<const float4*>(rho) + q);
-            const float4 h = __ldcs(reinterpret_cast<const float4*>(H) + q);
-            const float4 u = __ldcs(reinterpret_cast<const float4*>(ue) + q);
-            unsigned char t0, t1, t2, t3;
-            float4 o;
-            o.x = rad_te(k, r.x, h.x, u.x, t0);
-            o.y = rad_te(k, r.y, h.y, u.y, t1);
-            o.z = rad_te(k, r.z, h.z, u.z, t2);
-            o.w = rad_te(k, r.w, h.w, u.w, t3);
-            __stcs(reinterpret_cast<float4*>(te_out) + q, o);
-            if (thick_out)
-                reinterpret_cast<uchar4*>(thick_out)[q] = make_uchar4(t0, t1, t2, t3);
+constexpr int kRadThreads = 256;
+constexpr int kRadWarps = kRadThreads / 32;
+constexpr int kWarpRad = 128;   // cells per warp and round (one float4 per lane)
+
+// Each warp takes rounds of 128 consecutive cells.  Thin cells are finished
+// at once; the thick ones (about one in ten on the benchmark cells,
+// scattered) go to the warp's queue in shared memory and are solved by
+// consecutive lanes, so the Newton iterations run on full lanes instead of
+// on the one or two lanes per float4 slot that need them.  Outputs are
+// staged in shared memory and leave as 128-bit stores.  Warps synchronise
+// only with themselves.
+__global__ void __launch_bounds__(kRadThreads) k_radiation_te(RadK k, long long n, const float* __restrict__ rho,
+                                                              const float* __restrict__ H,
+                                                              const float* __restrict__ ue,
+                                                              float* __restrict__ te_out, unsigned char* thick_out,
+                                                              bool vec) {
+    __shared__ float s_te[kRadWarps][kWarpRad];
+    __shared__ float s_s[kRadWarps][kWarpRad];
+    __shared__ float s_b[kRadWarps][kWarpRad];
+    __shared__ unsigned char s_q[kRadWarps][kWarpRad];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    float* te_w = s_te[w];
+    float* s_w = s_s[w];
+    float* b_w = s_b[w];
+    unsigned char* q_w = s_q[w];
+    const long long rounds = (n + kWarpRad - 1) / kWarpRad;
+    for (long long rd = (long long)blockIdx.x * kRadWarps + w; rd < rounds; rd += (long long)gridDim.x * kRadWarps) {
+        const long long c0 = rd * kWarpRad + 4 * lane;
+        float rv[4], hv[4], uv[4];
+        if (vec && c0 + 3 < n) {
+            const float4 r = __ldcs(reinterpret_cast<const float4*>(rho + c0));
+            const float4 h = __ldcs(reinterpret_cast<const float4*>(H + c0));
+            const float4 u = __ldcs(reinterpret_cast<const float4*>(ue + c0));
+            rv[0] = r.x; rv[1] = r.y; rv[2] = r.z; rv[3] = r.w;
+            hv[0] = h.x; hv[1] = h.y; hv[2] = h.z; hv[3] = h.w;
+            uv[0] = u.x; uv[1] = u.y; uv[2] = u.z; uv[3] = u.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool in = c0 + e < n;
+                rv[e] = in ? rho[c0 + e] : 1.f;
+                hv[e] = in ? H[c0 + e] : 0.f;
+                uv[e] = in ? ue[c0 + e] : 1.f;
+            }
         }
-        start = n4 * 4;
-    }
-    for (long long i = start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        unsigned char t;
-        te_out[i] = rad_te(k, rho[i], H[i], ue[i], t);
-        if (thick_out) thick_out[i] = t;
+        unsigned char th[4];
+        int nq = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            bool tk;
+            float sc = 0.f, be = 0.f;
+            const int slot = 4 * lane + e;
+            te_w[slot] = rad_split(k, rv[e], hv[e], uv[e], tk, sc, be);
+            th[e] = tk ? 1 : 0;
+            const unsigned m = __ballot_sync(0xffffffffu, tk);
+            if (tk) {
+                const int pos = nq + __popc(m & lt);
+                s_w[slot] = sc;
+                b_w[slot] = be;
+                q_w[pos] = (unsigned char)slot;
+            }
+            nq += __popc(m);
+        }
+        __syncwarp();
+        for (int q = lane; q < nq; q += 32) {
+            const int slot = q_w[q];
+            te_w[slot] = rad_solve(te_w[slot], s_w[slot], b_w[slot]);
+        }
+        __syncwarp();
+        if (vec && c0 + 3 < n) {
+            __stcs(reinterpret_cast<float4*>(te_out + c0),
+                   make_float4(te_w[4 * lane], te_w[4 * lane + 1], te_w[4 * lane + 2], te_w[4 * lane + 3]));
+            if (thick_out) *reinterpret_cast<uchar4*>(thick_out + c0) = make_uchar4(th[0], th[1], th[2], th[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c0 + e < n) {
+                    te_out[c0 + e] = te_w[4 * lane + e];
+                    if (thick_out) thick_out[c0 + e] = th[e];
+                }
+        }
+        __syncwarp();
     }
 }
 
@@ -114,10 +184,11 @@ extern "C" cool_status cool_radiation_te(const cool_params* p, double tau_crit, 
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long work = vec ? (n_cells / 4 + 255) / 256 : (n_cells + 255) / 256;
-    long long blocks = work < sms * 8LL ? work : sms * 8LL;
+    const long long rounds = (n_cells + kRadThreads * 4 - 1) / (kRadThreads * 4);
+    long long blocks = rounds < sms * 8LL ? rounds : sms * 8LL;
     if (blocks < 1) blocks = 1;
-    k_radiation_te<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(k, n_cells, rho, H, u_e, te_out, thick_out, vec);
+    k_radiation_te<<<(int)blocks, kRadThreads, 0, (cudaStream_t)stream>>>(k, n_cells, rho, H, u_e, te_out,
+                                                                           thick_out, vec);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
 }

@@ -301,11 +301,20 @@ cool_status launch_step_surrogate(const cool_surrogate* sg, const cool_table* t,
     cudaError_t e = cudaFuncSetAttribute(k_step_surrogate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     long long tiles = (n + kSurT - 1) / kSurT;
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_surrogate, kSurT, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    if (per_sm > 4) per_sm = 4;                  // 4 x 128 TMEM columns per SM
+    // resident blocks per SM from the kernel's shared memory and registers
+    // (the TMEM allows 4 blocks of 128 columns)
+    int dev = 0, smem_sm = 0, smem_rsv = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa;
+    int regs = 128;
+    if (cudaFuncGetAttributes(&fa, k_step_surrogate) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+    int per_sm = smem_sm / (int)(smem + smem_rsv);
+    const int by_regs = 65536 / (regs * kSurT);
+    if (by_regs < per_sm) per_sm = by_regs;
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) per_sm = 1;
     long long cap = (long long)sm_count() * per_sm;
     long long blocks = tiles < cap ? tiles : cap;
     k_step_surrogate<<<(int)blocks, kSurT, smem, st>>>(k, m, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt,
