@@ -381,8 +381,43 @@ struct CellD {                   // per-cell derivative constants
     float cH, cB, cN;            // d w_{h,b,n} / d ln(H, B, rho) (0 where clamped)
 };
 
+// The 4-D channel collapsed over (H, B, n_e) at the two T_e nodes of
+// interval j, with its derivatives along H, B and n_e: kept while the
+// cell's reverse sweep stays in that interval (the common case), so the 16
+// corner values are read once per visited interval instead of once per
+// sub-cycle.
+struct GCache {
+    int j;                       // interval held, -1 if none
+    float Sv[2], dSh[2], dSb[2], dSn[2];
+};
+
+__device__ __forceinline__ void grad_corners(const CellC& c, int j, GCache& gc) {
+    const float* p = reinterpret_cast<const float*>(c.row) + (j / 7) * 8 + (j % 7);
+    const float* q1 = p + c.oH;
+    const float* base[8] = {p, p + c.oN, p + c.oB, p + c.oB + c.oN, q1, q1 + c.oN, q1 + c.oB, q1 + c.oB + c.oN};
+    float v[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        v[i][0] = __ldg(base[i]);
+        v[i][1] = __ldg(base[i] + 1);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        // corner order: (h, b, n) = 000, 001, 010, 011, 100, 101, 110, 111
+        const float q00 = lerpf(v[0][t], v[1][t], c.wn), q01 = lerpf(v[2][t], v[3][t], c.wn);
+        const float q10 = lerpf(v[4][t], v[5][t], c.wn), q11 = lerpf(v[6][t], v[7][t], c.wn);
+        const float P0 = lerpf(q00, q01, c.wb), P1 = lerpf(q10, q11, c.wb);
+        gc.Sv[t] = lerpf(P0, P1, c.wh);
+        gc.dSh[t] = P1 - P0;
+        gc.dSb[t] = lerpf(q01 - q00, q11 - q10, c.wh);
+        const float n00 = v[1][t] - v[0][t], n01 = v[3][t] - v[2][t], n10 = v[5][t] - v[4][t], n11 = v[7][t] - v[6][t];
+        gc.dSn[t] = lerpf(lerpf(n00, n01, c.wb), lerpf(n10, n11, c.wb), c.wh);
+    }
+    gc.j = j;
+}
+
 __device__ __forceinline__ QGrad cool_grad(const StepK& k, const Smem& S, const CellC& c, const CellD& cd,
-                                           float u, float inv_e) {
+                                           GCache& gc, float u, float inv_e) {
     QGrad g;
     const DevTable& T = k.tab;
     const int nT = T.n[3];
@@ -395,28 +430,11 @@ __device__ __forceinline__ QGrad cool_grad(const StepK& k, const Smem& S, const 
     const float wt = __saturatef(wraw);
     const float cT = (wraw > 0.f && wraw < 1.f) ? T.inv_dl[3] / kLn2 : 0.f;   // dwt / d ln Te
     // corner values at nodes j, j+1 (octet layout: block j/7, offset j%7)
-    const float* p = reinterpret_cast<const float*>(c.row) + (j / 7) * 8 + (j % 7);
-    const float* q1 = p + c.oH;
-    float v[8][2];
-    const float* base[8] = {p, p + c.oN, p + c.oB, p + c.oB + c.oN, q1, q1 + c.oN, q1 + c.oB, q1 + c.oB + c.oN};
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        v[i][0] = __ldg(base[i]);
-        v[i][1] = __ldg(base[i] + 1);
-    }
-    float Sv[2], dSh[2], dSb[2], dSn[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        // corner order: (h, b, n) = 000, 001, 010, 011, 100, 101, 110, 111
-        const float q00 = lerpf(v[0][t], v[1][t], c.wn), q01 = lerpf(v[2][t], v[3][t], c.wn);
-        const float q10 = lerpf(v[4][t], v[5][t], c.wn), q11 = lerpf(v[6][t], v[7][t], c.wn);
-        const float P0 = lerpf(q00, q01, c.wb), P1 = lerpf(q10, q11, c.wb);
-        Sv[t] = lerpf(P0, P1, c.wh);
-        dSh[t] = P1 - P0;
-        dSb[t] = lerpf(q01 - q00, q11 - q10, c.wh);
-        const float n00 = v[1][t] - v[0][t], n01 = v[3][t] - v[2][t], n10 = v[5][t] - v[4][t], n11 = v[7][t] - v[6][t];
-        dSn[t] = lerpf(lerpf(n00, n01, c.wb), lerpf(n10, n11, c.wb), c.wh);
-    }
+    if (gc.j != j) grad_corners(c, j, gc);
+    const float* Sv = gc.Sv;
+    const float* dSh = gc.dSh;
+    const float* dSb = gc.dSb;
+    const float* dSn = gc.dSn;
     const float b0 = S.lb[j], b1 = S.lb[j + 1];
     const float Ls = lerpf(Sv[0], Sv[1], wt) + c.ls_off;
     const float Lb = lerpf(b0, b1, wt) + c.lb_off;
@@ -523,6 +541,11 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
     return x;
 }
 
+// SMS: the per-sub-cycle state lives in shared memory (n_sub <= kSmemSub,
+// column layout, conflict-free) instead of thread-local arrays.
+constexpr int kSmemSub = 8;
+
+template <bool SMS>
 __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
     const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
@@ -541,8 +564,17 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     const int nT = T.n[3], nC = T.n[4];
     for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
     __syncthreads();
-    float st_ue[kMaxSub], st_ui[kMaxSub], st_u1[kMaxSub], st_us[kMaxSub];
-    unsigned char st_br[kMaxSub];   // 0 free, 1 limited, 2 implicit
+    // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
+    // implicit root, and the branch taken (0 free, 1 limited, 2 implicit)
+    float* sst = glc_s + ((nC * nC + 3) & ~3);
+    unsigned char* sbr = reinterpret_cast<unsigned char*>(sst + 4 * kSmemSub * kThreads);
+    float l_ue[SMS ? 1 : kMaxSub], l_ui[SMS ? 1 : kMaxSub], l_u1[SMS ? 1 : kMaxSub], l_us[SMS ? 1 : kMaxSub];
+    unsigned char l_br[SMS ? 1 : kMaxSub];
+#define ST_UE(sub) (*(SMS ? &sst[(4 * (sub) + 0) * kThreads + threadIdx.x] : &l_ue[(sub)]))
+#define ST_UI(sub) (*(SMS ? &sst[(4 * (sub) + 1) * kThreads + threadIdx.x] : &l_ui[(sub)]))
+#define ST_U1(sub) (*(SMS ? &sst[(4 * (sub) + 2) * kThreads + threadIdx.x] : &l_u1[(sub)]))
+#define ST_US(sub) (*(SMS ? &sst[(4 * (sub) + 3) * kThreads + threadIdx.x] : &l_us[(sub)]))
+#define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float rho = rho_in[i], B = B_in[i], H = H_in[i];
@@ -585,12 +617,12 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
         cc.win = win;
         // ---- forward, recorded (the forward kernel's arithmetic) ----
         for (int sub = 0; sub < k.n_sub; ++sub) {
-            st_ue[sub] = ue;
-            st_ui[sub] = ui;
+            ST_UE(sub) = ue;
+            ST_UI(sub) = ui;
             const XGrad xg = coulomb_grad(k, S, ue, ui, rho, inv_e, inv_i, kr, lcc_off);
             ue += xg.X;
             ui -= xg.X;
-            st_u1[sub] = ue;
+            ST_U1(sub) = ue;
             const float q = cool_energy<0>(k, S, c, cc, ue * inv_e, clamp);
             float du = fminf(q, k.limiter * ue);
             unsigned char br = q < k.limiter * ue ? 0 : 1;
@@ -599,22 +631,24 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 if (implicit_fp32<0>(k, S, c, cc, inv_e, ue, q, u1)) {
                     du = ue - u1;
                     br = 2;
-                    st_us[sub] = u1;
+                    ST_US(sub) = u1;
                 }
             }
-            st_br[sub] = br;
+            ST_BR(sub) = br;
             ue -= du;
         }
         // ---- reverse sweep ----
         float ge = ge_out, gi = gi_out, grho = 0.f, gB = 0.f, gH = 0.f;
+        GCache gc;
+        gc.j = -1;
         for (int sub = k.n_sub - 1; sub >= 0; --sub) {
             float ge1;
-            const unsigned char br = st_br[sub];
+            const unsigned char br = ST_BR(sub);
             if (br == 1) {
                 ge1 = (1.f - k.limiter) * ge;
             } else {
-                const float u = br == 2 ? st_us[sub] : st_u1[sub];
-                const QGrad g = cool_grad(k, S, c, cd, u, inv_e);
+                const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
+                const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
                 const float qu = g.q * g.du / u;
                 float sc;
                 if (br == 2) {
@@ -652,7 +686,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                     atomicAdd(&glb_s[g.jt + 1], sc * g.Gb * g.wt);
                 }
             }
-            const XGrad xg = coulomb_grad(k, S, st_ue[sub], st_ui[sub], rho, inv_e, inv_i, kr, lcc_off);
+            const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), rho, inv_e, inv_i, kr, lcc_off);
             const float gX = ge1 - gi;
             ge = ge1 + gX * xg.due;
             gi = gi + gX * xg.dui;
@@ -671,6 +705,11 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
         g_ue[i] = ge;
         g_ui[i] = gi;
     }
+#undef ST_UE
+#undef ST_UI
+#undef ST_U1
+#undef ST_US
+#undef ST_BR
     __syncthreads();
     if (g_lb)
         for (int i = threadIdx.x; i < nT; i += blockDim.x)
@@ -773,19 +812,22 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     if (t->dev.fmt != 0 || p->fp64_critical || p->n_sub > kMaxSub) return COOL_EUNSUPPORTED;
     StepK k;
     fill_stepk(t, p, k);
-    size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads + t->dev.n[3] + t->dev.n[4] * t->dev.n[4]) *
-                  sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_step_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool sms = p->n_sub <= kSmemSub;
+    size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads + t->dev.n[3] +
+                           ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
+    if (sms) smem += (size_t)kSmemSub * kThreads * (4 * sizeof(float) + 1);
+    auto fn = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_bwd_f32, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     if (per_sm < 1) per_sm = 1;
     long long work = (n + kThreads - 1) / kThreads;
     long long cap = (long long)sm_count() * per_sm;
     long long blocks = work < cap ? work : cap;
-    k_step_bwd_f32<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue,
-                                                        g_ui, g_lb, g_ls, g_lc);
+    fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui, g_lb,
+                                            g_ls, g_lc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;

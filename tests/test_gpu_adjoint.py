@@ -56,12 +56,14 @@ def _compare(cool, tab, oracle, ospec, OT, f, mode, n_sub=8, table=False):
     return g, want, tg, bad, worst
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_adjoint_matches_oracle(env, oracle, mode):
+@pytest.mark.parametrize("mode,n_sub", [(0, 8), (1, 8), (0, 12), (1, 3)])
+def test_adjoint_matches_oracle(env, oracle, mode, n_sub):
+    """n_sub <= 8 keeps the per-sub-cycle state in shared memory, more in
+    thread-local arrays: both layouts are covered."""
     cool, tab, ospec, OT = env
     f = inputs.uniform(20000 + 5, seed=60, dtype=np.float32)
-    g, want, tg, bad, worst = _compare(cool, tab, oracle, ospec, OT, f, mode)
-    print(f"\nmode {mode}: cells beyond 2e-4: {bad.sum()} of {bad.size}; 99.5th pct {worst:.2e}")
+    g, want, tg, bad, worst = _compare(cool, tab, oracle, ospec, OT, f, mode, n_sub=n_sub)
+    print(f"\nmode {mode} n_sub {n_sub}: cells beyond 2e-4: {bad.sum()} of {bad.size}; 99.5th pct {worst:.2e}")
     assert bad.mean() <= 0.005
 
 
