@@ -135,6 +135,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def job_rate(dist, world, ms_local, cells_per_rank, device):
+    """Whole-job rate of a weak-scaled step: the slowest rank's time (max
+    over ranks, one all-reduce of a scalar) and all ranks' cells over it.
+    Returns (ms, cell-updates/s)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * cells_per_rank / (ms * 1e-3)
+
+
+def cell_shard(n, rank, world):
+    """(first, count) of rank's contiguous block when n cells are split over
+    world ranks (sizes differ by at most one cell)."""
+    base, extra = divmod(n, world)
+    first = rank * base + min(rank, extra)
+    return first, base + (1 if rank < extra else 0)
+
+
 def cpu_oracle_rate(n_cells_sample, nthreads, seed_off=0, repeats=1):
     """The FP64 oracle's step on a sample of the workload, host cores.  The
     oracle builds its 64^4 table first (untimed, like the GPU table)."""
@@ -489,11 +510,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3)
+    ms, value = job_rate(dist, world, ms, n, dev)
 
     # end to end through the public API with host buffers (cool_step_host):
     # every step copies the five input fields from pinned host memory and
@@ -516,11 +533,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * n / (ms_e2e * 1e-3)
+    ms_e2e, e2e_value = job_rate(dist, world, ms_e2e, n, dev)
 
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_CELL * n / (ms * 1e-3) / 1e9
