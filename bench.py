@@ -298,6 +298,8 @@ def run_suite_perf(args, torch, cool, inputs, dev):
                  ("explicit, BF16 row-scaled table", cool.BF16, 1, cool.Params(n_sub=N_SUB), steps),
                  ("explicit, FP16 row-scaled table", cool.F16, 1, cool.Params(n_sub=N_SUB), steps),
                  ("explicit, N_sub = 1", cool.F32, 0, cool.Params(n_sub=1), steps),
+                 ("explicit, TMA-staged fields (bulk copies, double-buffered)", cool.F32, 0,
+                  cool.Params(n_sub=N_SUB, path=cool.PATH_TMA_SMEM), steps),
                  ("explicit, texture path: point fetches + FP32 lerp", cool.F32, 0,
                   cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT), steps),
                  ("explicit, texture path: hardware trilinear filtering", cool.F32, 0,

@@ -67,7 +67,10 @@ typedef enum { COOL_EXPLICIT_LIMITED = 0, COOL_IMPLICIT_STIFF = 1 } cool_mode;
  * use, synchronously), read with 16 point fetches and FP32 interpolation, or
  * with the hardware's trilinear filtering (weights in fixed point with 8
  * fractional bits: an error of up to 2^-8 of a node step per filtered axis)
- * and FP32 interpolation in H.  TMA_SMEM and SURROGATE: COOL_EUNSUPPORTED in
+ * and FP32 interpolation in H.  TMA_SMEM: the L2WINDOW step with its field
+ * staging done by bulk asynchronous copies into shared memory,
+ * double-buffered per warp (FP32 fields, all arrays 16-byte aligned, else
+ * COOL_EALIGN; same results as L2WINDOW).  SURROGATE: COOL_EUNSUPPORTED in
  * cool_step (the surrogate step is cool_surrogate_infer). */
 typedef enum {
     COOL_PATH_L2WINDOW = 0,
@@ -111,7 +114,7 @@ typedef struct {
     double eq_band;           /* equilibrium band |T_e - T_i| <= eq_band T_i (0.1), where T_i - T_e cancels */
     double coulomb_clamp;     /* the exchange may move at most this fraction of the way to T_e = T_i (1) */
     int implicit_iters;       /* bisection halvings of the implicit solve, 1 .. 200 (60) */
-    cool_path path;           /* COOL_PATH_L2WINDOW (default), TEXTURE_POINT, TEXTURE_HWLERP */
+    cool_path path;           /* COOL_PATH_L2WINDOW (default), TMA_SMEM, TEXTURE_POINT, TEXTURE_HWLERP */
     int fp64_critical;        /* FP32 fields only.  0 (default): the Coulomb difference
                                  (gamma_i-1) u_i - (gamma_e-1) u_e is formed with an error-free FP32
                                  product transformation in every cell, and stiff cells are solved in

@@ -17,8 +17,8 @@ from . import binding as _b
 
 F32, BF16, F16, F64 = _b.COOL_F32, _b.COOL_BF16, _b.COOL_F16, _b.COOL_F64
 EXPLICIT, IMPLICIT = _b.COOL_EXPLICIT_LIMITED, _b.COOL_IMPLICIT_STIFF
-PATH_L2WINDOW, PATH_TEXTURE_POINT, PATH_TEXTURE_HWLERP = (_b.COOL_PATH_L2WINDOW, _b.COOL_PATH_TEXTURE_POINT,
-                                                         _b.COOL_PATH_TEXTURE_HWLERP)
+PATH_L2WINDOW, PATH_TMA_SMEM, PATH_TEXTURE_POINT, PATH_TEXTURE_HWLERP = (
+    _b.COOL_PATH_L2WINDOW, _b.COOL_PATH_TMA_SMEM, _b.COOL_PATH_TEXTURE_POINT, _b.COOL_PATH_TEXTURE_HWLERP)
 CoolError = _b.CoolError
 
 # Axis order of the table: 0 H [cm], 1 |B| [G], 2 n_e [cm^-3], 3 T_e [K],

@@ -61,9 +61,11 @@ cool_status validate_params(const cool_params* p) {
     if (!(p->eq_band >= 0.0 && p->eq_band < 1.0)) return COOL_EINVAL;
     if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
     if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
-    if (p->path != COOL_PATH_L2WINDOW && p->path != COOL_PATH_TEXTURE_POINT && p->path != COOL_PATH_TEXTURE_HWLERP)
+    if (p->path != COOL_PATH_L2WINDOW && p->path != COOL_PATH_TMA_SMEM && p->path != COOL_PATH_TEXTURE_POINT &&
+        p->path != COOL_PATH_TEXTURE_HWLERP)
         return COOL_EUNSUPPORTED;
-    if (p->path != COOL_PATH_L2WINDOW && (p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical != 0))
+    if ((p->path == COOL_PATH_TEXTURE_POINT || p->path == COOL_PATH_TEXTURE_HWLERP) &&
+        (p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical != 0))
         return COOL_EUNSUPPORTED;   // the texture paths are explicit FP32 only
     if (p->fp64_critical != 0 && p->fp64_critical != 1) return COOL_EINVAL;
     return COOL_OK;
@@ -614,7 +616,8 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
     cudaGetDevice(&dev);
     if (dev != t->device) return COOL_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->path != COOL_PATH_L2WINDOW) {
+    if (p->path == COOL_PATH_TMA_SMEM && field_dtype != COOL_F32) return COOL_EUNSUPPORTED;
+    if (p->path == COOL_PATH_TEXTURE_POINT || p->path == COOL_PATH_TEXTURE_HWLERP) {
         if (field_dtype != COOL_F32 || t->spec.dtype != COOL_F32) return COOL_EUNSUPPORTED;
         st = table_textures(const_cast<cool_table*>(t));
         if (st != COOL_OK) return st;

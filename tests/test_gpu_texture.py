@@ -114,6 +114,3 @@ def test_texture_paths_refuse_what_they_do_not_cover(env):
         with pytest.raises(cool.CoolError) as e:
             cool.step_bwd(tab, cool.Params(path=path), *tf, g, g)
         assert e.value.status == _b.COOL_EUNSUPPORTED
-    with pytest.raises(cool.CoolError) as e:
-        cool.step(tab, cool.Params(path=_b.COOL_PATH_TMA_SMEM), *tf)
-    assert e.value.status == _b.COOL_EUNSUPPORTED
