@@ -56,7 +56,7 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = ("cool_step.cu", "cool_step_common.cuh")
+KERNEL_SOURCES = ("cool_step.cu", "cool_step_cell.cuh", "cool_step_common.cuh")
 
 
 def kernel_source_sha():

@@ -616,7 +616,12 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
     cudaGetDevice(&dev);
     if (dev != t->device) return COOL_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->path == COOL_PATH_TMA_SMEM && field_dtype != COOL_F32) return COOL_EUNSUPPORTED;
+    if (p->path == COOL_PATH_TMA_SMEM) {
+        if (field_dtype != COOL_F32) return COOL_EUNSUPPORTED;
+        return launch_step_tma(t, p, n_cells, (const float*)rho, (const float*)B, (const float*)H,
+                               (const float*)u_e_in, (const float*)u_i_in, (float*)u_e_out, (float*)u_i_out,
+                               (float*)q_cool_out, (float*)q_cc_out, counters, s);
+    }
     if (p->path == COOL_PATH_TEXTURE_POINT || p->path == COOL_PATH_TEXTURE_HWLERP) {
         if (field_dtype != COOL_F32 || t->spec.dtype != COOL_F32) return COOL_EUNSUPPORTED;
         st = table_textures(const_cast<cool_table*>(t));

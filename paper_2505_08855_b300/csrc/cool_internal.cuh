@@ -119,6 +119,9 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
                                 float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st);
 cool_status validate_params(const cool_params* p);
 cool_status table_textures(cool_table* t);
+cool_status launch_step_tma(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                            const float* B, const float* H, const float* ue, const float* ui, float* ue_o,
+                            float* ui_o, float* qc, float* qx, cool_counters* cnt, cudaStream_t st);
 cool_status launch_step_direct(const cool_table_spec& phys, const cool_params* p, long long n, const double* rho,
                                const double* B, const double* H, const double* ue, const double* ui, double* ue_o,
                                double* ui_o, double* qc, double* qx, cool_counters* cnt, cudaStream_t st);

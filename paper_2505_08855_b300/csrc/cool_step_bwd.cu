@@ -1,0 +1,404 @@
+// cool_step_bwd.cu -- the adjoint of the FP32 step (cool_step_bwd).
+#include "cool_step_cell.cuh"
+
+namespace cool {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Adjoint (cool_step_bwd).  Per cell: the forward sub-cycles are recomputed
+// with the forward kernel's own functions (same trajectory, same branches),
+// keeping each sub-cycle's state; then a reverse sweep applies, per
+// sub-cycle, the hand-derived partial derivatives of the cooling energy q
+// and of the Coulomb transfer X (below), the limiter's branch, and for an
+// implicit sub-cycle the implicit-function theorem at the root
+// (du*/du1 = 1/(1 + dq/du), du*/dtheta = -dq/dtheta / (1 + dq/du)).
+// Table adjoints go to the natural layouts: synchrotron [nH nB nN nT] with
+// global atomics, brems and Coulomb through shared-memory partial sums.
+// ---------------------------------------------------------------------------
+constexpr int kMaxSub = 64;
+constexpr float kLn2 = 0.69314718056f;
+
+// Cooling energy q(u) and d ln q / d ln x for x = u, rho, B, H, plus
+// dq/dLs and dq/dLb for the table scatter (FP32 octet layout).
+struct QGrad {
+    float q, du, drho, dB, dH;   // d ln q / d ln x
+    float Gs, Gb;                // dq/dLs, dq/dLb
+    int jt;
+    float wt;
+    float S0, S1;
+};
+
+struct CellD {                   // per-cell derivative constants
+    float cH, cB, cN;            // d w_{h,b,n} / d ln(H, B, rho) (0 where clamped)
+};
+
+// The 4-D channel collapsed over (H, B, n_e) at the two T_e nodes of
+// interval j, with its derivatives along H, B and n_e: kept while the
+// cell's reverse sweep stays in that interval (the common case), so the 16
+// corner values are read once per visited interval instead of once per
+// sub-cycle.
+struct GCache {
+    int j;                       // interval held, -1 if none
+    float Sv[2], dSh[2], dSb[2], dSn[2];
+};
+
+__device__ __forceinline__ void grad_corners(const CellC& c, int j, GCache& gc) {
+    const float* p = reinterpret_cast<const float*>(c.row) + (j / 7) * 8 + (j % 7);
+    const float* q1 = p + c.oH;
+    const float* base[8] = {p, p + c.oN, p + c.oB, p + c.oB + c.oN, q1, q1 + c.oN, q1 + c.oB, q1 + c.oB + c.oN};
+    float v[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        v[i][0] = __ldg(base[i]);
+        v[i][1] = __ldg(base[i] + 1);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        // corner order: (h, b, n) = 000, 001, 010, 011, 100, 101, 110, 111
+        const float q00 = lerpf(v[0][t], v[1][t], c.wn), q01 = lerpf(v[2][t], v[3][t], c.wn);
+        const float q10 = lerpf(v[4][t], v[5][t], c.wn), q11 = lerpf(v[6][t], v[7][t], c.wn);
+        const float P0 = lerpf(q00, q01, c.wb), P1 = lerpf(q10, q11, c.wb);
+        gc.Sv[t] = lerpf(P0, P1, c.wh);
+        gc.dSh[t] = P1 - P0;
+        gc.dSb[t] = lerpf(q01 - q00, q11 - q10, c.wh);
+        const float n00 = v[1][t] - v[0][t], n01 = v[3][t] - v[2][t], n10 = v[5][t] - v[4][t], n11 = v[7][t] - v[6][t];
+        gc.dSn[t] = lerpf(lerpf(n00, n01, c.wb), lerpf(n10, n11, c.wb), c.wh);
+    }
+    gc.j = j;
+}
+
+__device__ __forceinline__ QGrad cool_grad(const StepK& k, const Smem& S, const CellC& c, const CellD& cd,
+                                           GCache& gc, float u, float inv_e) {
+    QGrad g;
+    const DevTable& T = k.tab;
+    const int nT = T.n[3];
+    const float* axT = S.ax + T.axis_off[3];
+    unsigned dummy = 0u;
+    const float Te = u * inv_e;
+    const Sel s = select_axis(axT, nT, T.inv_dl[3], Te, dummy);
+    const int j = s.j;
+    const float wraw = s.r * T.inv_dl[3];
+    const float wt = __saturatef(wraw);
+    const float cT = (wraw > 0.f && wraw < 1.f) ? T.inv_dl[3] / kLn2 : 0.f;   // dwt / d ln Te
+    // corner values at nodes j, j+1 (octet layout: block j/7, offset j%7)
+    if (gc.j != j) grad_corners(c, j, gc);
+    const float* Sv = gc.Sv;
+    const float* dSh = gc.dSh;
+    const float* dSb = gc.dSb;
+    const float* dSn = gc.dSn;
+    const float b0 = S.lb[j], b1 = S.lb[j + 1];
+    const float Ls = lerpf(Sv[0], Sv[1], wt) + c.ls_off;
+    const float Lb = lerpf(b0, b1, wt) + c.lb_off;
+    const float lT = axT[2 * nT + j] + s.r;
+    const float M = fmaxf(Ls, Lb);
+    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
+    const float sig_s = ex2a(Ls - A);
+    const float Bb = fmaf(4.f, lT, c.lbb_off);
+    const float lt = A - Bb;
+    float lq, kap, ctau;
+    if (lt <= 60.f) {
+        const float tau = ex2a(lt);
+        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
+        lq = A - lg2a(D);
+        kap = tau * (1.7320508f + 3.f * tau + 1.5f * c.tau_sca) / D;
+        ctau = 1.5f * tau / (D * kLn2);
+    } else {
+        const float tau = ex2a(fminf(lt, 126.f));
+        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
+        const float fr = 1.f / (1.f + c.tau_sca * ex2a(-lt));   // tau / (tau + tau_sca)
+        kap = 1.f + fr;
+        ctau = fr / (tau * kLn2);
+    }
+    g.q = ex2a(fminf(lq, 126.f));
+    const float live = lq < 126.f ? 1.f : 0.f;
+    // derivatives of Ls, Lb, Bb, tau_sca with respect to ln u, ln rho, ln B, ln H
+    const float dLs_u = (Sv[1] - Sv[0]) * cT;
+    const float dLs_rho = -dLs_u + lerpf(dSn[0], dSn[1], wt) * cd.cN;
+    const float dLs_B = lerpf(dSb[0], dSb[1], wt) * cd.cB;
+    const float dLs_H = lerpf(dSh[0], dSh[1], wt) * cd.cH;
+    const float dLb_u = (b1 - b0) * cT;
+    const float dLb_rho = -dLb_u + 2.f / kLn2;
+    const float dA_u = sig_s * dLs_u + (1.f - sig_s) * dLb_u;
+    const float dA_rho = sig_s * dLs_rho + (1.f - sig_s) * dLb_rho;
+    const float dA_B = sig_s * dLs_B;
+    const float dA_H = sig_s * dLs_H;
+    const float w1 = (1.f - kap) * kLn2 * live, w2 = kap * kLn2 * live, w3 = ctau * kLn2 * live;
+    g.du = w1 * dA_u + w2 * (4.f / kLn2);
+    g.drho = w1 * dA_rho + w2 * (-4.f / kLn2) - w3 * c.tau_sca;
+    g.dB = w1 * dA_B;
+    g.dH = w1 * dA_H + w2 * (-1.f / kLn2) - w3 * c.tau_sca;
+    g.Gs = g.q * w1 * sig_s;
+    g.Gb = g.q * w1 * (1.f - sig_s);
+    g.jt = j;
+    g.wt = wt;
+    g.S0 = Sv[0];
+    g.S1 = Sv[1];
+    return g;
+}
+
+// Coulomb transfer X(u_e, u_i) of one sub-cycle (the forward's FP32 form)
+// and its partial derivatives.
+struct XGrad {
+    float X, due, dui, drho;
+    bool clamped;
+    int ji, je;
+    float wi, we;
+};
+
+__device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, float ue, float ui, float rho,
+                                              float inv_e, float inv_i, float kr, float lcc_off) {
+    XGrad x;
+    const DevTable& T = k.tab;
+    const int nC = T.n[4];
+    const float* axC = S.ax + T.axis_off[4];
+    unsigned dummy = 0u;
+    const Sel se = select_axis(axC, nC, T.inv_dl[4], ue * inv_e, dummy);
+    const Sel si = select_axis(axC, nC, T.inv_dl[4], ui * inv_i, dummy);
+    const float re = se.r * T.inv_dl[4], ri = si.r * T.inv_dl[4];
+    const float we = __saturatef(re), wi = __saturatef(ri);
+    const float ce_w = (re > 0.f && re < 1.f) ? T.inv_dl[4] / kLn2 : 0.f;
+    const float ci_w = (ri > 0.f && ri < 1.f) ? T.inv_dl[4] / kLn2 : 0.f;
+    const float* row = S.lc + si.j * nC + se.j;
+    const float c00 = row[0], c01 = row[1], c10 = row[nC], c11 = row[nC + 1];
+    const float lC = lerpf(lerpf(c00, c01, we), lerpf(c10, c11, we), wi);
+    const float rate = ex2a(fminf(lC + lcc_off, 126.f));
+    const float pe = k.ce * ue;
+    const float ee = fmaf(k.ce, ue, -pe);
+    const float D = fmaf(k.ci, ui, -pe) - ee;
+    float X = rate * (kr * D);
+    const float lim = k.clamp * fabsf(D * k.inv_cec);
+    x.clamped = fabsf(X) > lim;
+    if (x.clamped) {
+        const float sg = (X >= 0.f ? 1.f : -1.f) * (D >= 0.f ? 1.f : -1.f);
+        X = copysignf(lim, X);
+        x.due = -sg * k.clamp * k.inv_cec * k.ce;
+        x.dui = sg * k.clamp * k.inv_cec * k.ci;
+        x.drho = 0.f;
+    } else {
+        const float dlC_we = lerpf(c01 - c00, c11 - c10, wi);
+        const float dlC_wi = lerpf(c10 - c00, c11 - c01, we);
+        const float live = (lC + lcc_off) < 126.f ? 1.f : 0.f;
+        x.due = X * kLn2 * dlC_we * ce_w * live / ue - rate * kr * k.ce;
+        x.dui = X * kLn2 * dlC_wi * ci_w * live / ui + rate * kr * k.ci;
+        // d ln X / d ln rho = ln2 dlC/d ln rho + 2 (n_e^2) - 1 (s_K/rho); a saturated
+        // rate keeps only the -1
+        x.drho = live > 0.f ? X * (1.f - kLn2 * (dlC_we * ce_w + dlC_wi * ci_w)) / rho : -X / rho;
+    }
+    x.X = X;
+    x.ji = si.j;
+    x.je = se.j;
+    x.wi = wi;
+    x.we = we;
+    return x;
+}
+
+// SMS: the per-sub-cycle state lives in shared memory (n_sub <= kSmemSub,
+// column layout, conflict-free) instead of thread-local arrays.
+constexpr int kSmemSub = 8;
+
+template <bool SMS>
+__global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
+    StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
+    const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
+    const float* __restrict__ gue_out, const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
+    float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc) {
+    extern __shared__ float sm[];
+    load_smem(k, sm);
+    Smem S;
+    S.ax = sm;
+    S.lb = sm + k.axes_floats;
+    S.lc = sm + k.axes_floats + k.tab.n[3];
+    float* win = sm + smem_table_floats(k) + threadIdx.x;
+    float* glb_s = sm + smem_table_floats(k) + kMaxW * kThreads;   // partial brems adjoints
+    float* glc_s = glb_s + k.tab.n[3];                             // partial Coulomb adjoints
+    const DevTable& T = k.tab;
+    const int nT = T.n[3], nC = T.n[4];
+    for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
+    __syncthreads();
+    // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
+    // implicit root, and the branch taken (0 free, 1 limited, 2 implicit)
+    float* sst = glc_s + ((nC * nC + 3) & ~3);
+    unsigned char* sbr = reinterpret_cast<unsigned char*>(sst + 4 * kSmemSub * kThreads);
+    float l_ue[SMS ? 1 : kMaxSub], l_ui[SMS ? 1 : kMaxSub], l_u1[SMS ? 1 : kMaxSub], l_us[SMS ? 1 : kMaxSub];
+    unsigned char l_br[SMS ? 1 : kMaxSub];
+#define ST_UE(sub) (*(SMS ? &sst[(4 * (sub) + 0) * kThreads + threadIdx.x] : &l_ue[(sub)]))
+#define ST_UI(sub) (*(SMS ? &sst[(4 * (sub) + 1) * kThreads + threadIdx.x] : &l_ui[(sub)]))
+#define ST_U1(sub) (*(SMS ? &sst[(4 * (sub) + 2) * kThreads + threadIdx.x] : &l_u1[(sub)]))
+#define ST_US(sub) (*(SMS ? &sst[(4 * (sub) + 3) * kThreads + threadIdx.x] : &l_us[(sub)]))
+#define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float rho = rho_in[i], B = B_in[i], H = H_in[i];
+        float ue = ue_in[i], ui = ui_in[i];
+        const float ge_out = gue_out[i], gi_out = gui_out[i];
+        if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
+            !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
+            g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
+            continue;
+        }
+        unsigned clamp = 0u;
+        const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
+        const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
+        CellC c;
+        CellD cd;
+        {
+            Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
+            Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
+            Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
+            const int rowf = 8 * T.nblk;
+            c.oN = rowf;
+            c.oB = rowf * T.n[2];
+            c.oH = c.oB * T.n[1];
+            c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
+            const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
+            c.wh = __saturatef(rh);
+            c.wb = __saturatef(rb);
+            c.wn = __saturatef(rn);
+            cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] / kLn2 : 0.f;
+            cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] / kLn2 : 0.f;
+            cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] / kLn2 : 0.f;
+            c.ls_off = k.l_hs_e;
+            c.lb_off = fmaf(2.f, lg2a(ne), k.l_hs_e);
+            c.lbb_off = k.l_bb - lg2a(Hc);
+            c.tau_sca = k.two_sigT * ne * Hc;
+        }
+        const float lcc_off = c.lb_off;
+        Cache cc;
+        cc.base = -8;
+        cc.win = win;
+        // ---- forward, recorded (the forward kernel's arithmetic) ----
+        for (int sub = 0; sub < k.n_sub; ++sub) {
+            ST_UE(sub) = ue;
+            ST_UI(sub) = ui;
+            const XGrad xg = coulomb_grad(k, S, ue, ui, rho, inv_e, inv_i, kr, lcc_off);
+            ue += xg.X;
+            ui -= xg.X;
+            ST_U1(sub) = ue;
+            const float q = cool_energy<0>(k, S, c, cc, ue * inv_e, clamp);
+            float du = fminf(q, k.limiter * ue);
+            unsigned char br = q < k.limiter * ue ? 0 : 1;
+            if (k.mode == 1 && q > k.limiter * ue) {
+                float u1;
+                if (implicit_fp32<0>(k, S, c, cc, inv_e, ue, q, u1)) {
+                    du = ue - u1;
+                    br = 2;
+                    ST_US(sub) = u1;
+                }
+            }
+            ST_BR(sub) = br;
+            ue -= du;
+        }
+        // ---- reverse sweep ----
+        float ge = ge_out, gi = gi_out, grho = 0.f, gB = 0.f, gH = 0.f;
+        GCache gc;
+        gc.j = -1;
+        for (int sub = k.n_sub - 1; sub >= 0; --sub) {
+            float ge1;
+            const unsigned char br = ST_BR(sub);
+            if (br == 1) {
+                ge1 = (1.f - k.limiter) * ge;
+            } else {
+                const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
+                const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
+                const float qu = g.q * g.du / u;
+                float sc;
+                if (br == 2) {
+                    const float den = 1.f + qu;
+                    ge1 = ge / den;
+                    sc = -ge / den;
+                } else {
+                    ge1 = ge * (1.f - qu);
+                    sc = -ge;
+                }
+                grho += sc * g.q * g.drho / rho;
+                if (g.dB != 0.f) gB += sc * g.q * g.dB / B;
+                if (g.dH != 0.f) gH += sc * g.q * g.dH / H;
+                if (g_ls) {
+                    const float gs = sc * g.Gs;
+                    const float wts[2] = {1.f - g.wt, g.wt};
+                    const long long rowT = nT;
+                    // natural-layout row of corner (jh, jb, jn): rebuilt from the packed row offset
+                    const long long r0 = (long long)(c.row - T.lsb) / (8 * T.nblk);
+                    const long long rows[8] = {r0, r0 + 1, r0 + T.n[2], r0 + T.n[2] + 1,
+                                               r0 + (long long)T.n[1] * T.n[2], r0 + (long long)T.n[1] * T.n[2] + 1,
+                                               r0 + (long long)T.n[1] * T.n[2] + T.n[2],
+                                               r0 + (long long)T.n[1] * T.n[2] + T.n[2] + 1};
+                    const float wh[2] = {1.f - c.wh, c.wh}, wb[2] = {1.f - c.wb, c.wb}, wn[2] = {1.f - c.wn, c.wn};
+#pragma unroll
+                    for (int cidx = 0; cidx < 8; ++cidx) {
+                        const float wc = wh[cidx >> 2] * wb[(cidx >> 1) & 1] * wn[cidx & 1];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+                            atomicAdd(&g_ls[rows[cidx] * rowT + g.jt + t], gs * wc * wts[t]);
+                    }
+                }
+                if (g_lb) {
+                    atomicAdd(&glb_s[g.jt], sc * g.Gb * (1.f - g.wt));
+                    atomicAdd(&glb_s[g.jt + 1], sc * g.Gb * g.wt);
+                }
+            }
+            const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), rho, inv_e, inv_i, kr, lcc_off);
+            const float gX = ge1 - gi;
+            ge = ge1 + gX * xg.due;
+            gi = gi + gX * xg.dui;
+            grho += gX * xg.drho;
+            if (g_lc && !xg.clamped) {
+                const float cl = gX * xg.X * kLn2;
+                atomicAdd(&glc_s[xg.ji * nC + xg.je], cl * (1.f - xg.wi) * (1.f - xg.we));
+                atomicAdd(&glc_s[xg.ji * nC + xg.je + 1], cl * (1.f - xg.wi) * xg.we);
+                atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je], cl * xg.wi * (1.f - xg.we));
+                atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je + 1], cl * xg.wi * xg.we);
+            }
+        }
+        g_rho[i] = grho;
+        g_B[i] = gB;
+        g_H[i] = gH;
+        g_ue[i] = ge;
+        g_ui[i] = gi;
+    }
+#undef ST_UE
+#undef ST_UI
+#undef ST_U1
+#undef ST_US
+#undef ST_BR
+    __syncthreads();
+    if (g_lb)
+        for (int i = threadIdx.x; i < nT; i += blockDim.x)
+            if (glb_s[i] != 0.f) atomicAdd(&g_lb[i], glb_s[i]);
+    if (g_lc)
+        for (int i = threadIdx.x; i < nC * nC; i += blockDim.x)
+            if (glc_s[i] != 0.f) atomicAdd(&g_lc[i], glc_s[i]);
+}
+
+}  // namespace
+
+cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                                const float* B, const float* H, const float* ue, const float* ui,
+                                const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
+                                float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st) {
+    if (n == 0) return COOL_OK;
+    if (t->dev.fmt != 0 || p->fp64_critical || p->n_sub > kMaxSub) return COOL_EUNSUPPORTED;
+    StepK k;
+    fill_stepk(t, p, k);
+    const bool sms = p->n_sub <= kSmemSub;
+    size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads + t->dev.n[3] +
+                           ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
+    if (sms) smem += (size_t)kSmemSub * kThreads * (4 * sizeof(float) + 1);
+    auto fn = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (per_sm < 1) per_sm = 1;
+    long long work = (n + kThreads - 1) / kThreads;
+    long long cap = (long long)sm_count() * per_sm;
+    long long blocks = work < cap ? work : cap;
+    fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui, g_lb,
+                                            g_ls, g_lc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return COOL_OK;
+}
+
+}  // namespace cool

@@ -1,0 +1,148 @@
+// cool_step_tma.cu -- the step with its field staging done by the TMA engine
+// (COOL_PATH_TMA_SMEM).
+#include "cool_step_cell.cuh"
+#include "cool_tma.cuh"
+
+namespace cool {
+namespace {
+
+// COOL_PATH_TMA_SMEM: the vector kernel with its field staging done by the
+// TMA engine.  Each warp owns two staging buffers (5 fields x 128 cells) and
+// two mbarriers; while the warp steps tile i from one buffer, lane 0 has the
+// bulk copies of tile i + 1 (five 512-byte copies) landing in the other, so
+// the fields of the next tile need no load instructions and no wait at the
+// start of the tile.  Outputs overwrite the inputs of their cell in the
+// buffer and leave by 128-bit streaming stores, as in k_step_f32.  The
+// window holds only the W nodes of the table format's block.  Waits are
+// bounded: a copy that does not complete sets *err bit 0 (the tile's
+// outputs are then not written).
+__device__ unsigned g_tma_err;
+
+template <int FMT, int VAR>
+__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long long n, const float* __restrict__ rho,
+                                                         const float* __restrict__ Bf, const float* __restrict__ Hf,
+                                                         const float* ue_in, const float* ui_in, float* ue_out,
+                                                         float* ui_out, float* qc_out, float* qx_out,
+                                                         cool_counters* cnt) {
+    constexpr int W = Fmt<FMT>::W;
+    constexpr int TILE = 5 * kWarpCells;     // floats per buffer
+    extern __shared__ __align__(16) float smt[];
+    load_smem(k, smt);
+    Smem S;
+    S.ax = smt;
+    S.lb = smt + k.axes_floats;
+    S.lc = smt + k.axes_floats + k.tab.n[3];
+    float* win = smt + smem_table_floats(k) + threadIdx.x;   // W x kThreads window
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float* bufs = smt + smem_table_floats(k) + W * kThreads + warp * 2 * TILE;
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smt + smem_table_floats(k) + W * kThreads + kWarps * 2 * TILE) +
+                   warp * 2;
+    const uint32_t mbar[2] = {mma::smem_addr(mb), mma::smem_addr(mb + 1)};
+    if (lane == 0) {
+        mma::mbar_init(mbar[0], 1);
+        mma::mbar_init(mbar[1], 1);
+        mma::fence_mbar_init();
+    }
+    __syncwarp();
+    const float* src[5] = {rho, Bf, Hf, ue_in, ui_in};
+    const long long ntiles = n / kWarpCells;
+    const long long step = (long long)gridDim.x * kWarps;
+    auto issue = [&](long long tw, int b) {   // lane 0
+        tma::arrive_expect_tx(mbar[b], 5 * kWarpCells * sizeof(float));
+#pragma unroll
+        for (int f = 0; f < 5; ++f)
+            tma::bulk_g2s(mma::smem_addr(bufs + b * TILE + f * kWarpCells), src[f] + tw * kWarpCells,
+                          kWarpCells * sizeof(float), mbar[b]);
+    };
+    long long tw = (long long)blockIdx.x * kWarps + warp;
+    if (lane == 0 && tw < ntiles) issue(tw, 0);
+    uint32_t phase[2] = {0u, 0u};
+    int b = 0;
+    for (; tw < ntiles; tw += step) {
+        const long long nx = tw + step;
+        if (lane == 0 && nx < ntiles) {
+            mma::fence_async_smem();   // the other buffer's generic reads and writes are done (warp-synchronised)
+            issue(nx, b ^ 1);
+        }
+        const bool ok = mma::mbar_wait(mbar[b], phase[b], 1 << 22);
+        phase[b] ^= 1u;
+        if (!ok) {
+            if (lane == 0) atomicOr(&g_tma_err, 1u);
+            mma::mbar_wait(mbar[b], phase[b] ^ 1u, 1 << 16);
+        }
+        float* tile = bufs + b * TILE;
+        float4* t4 = reinterpret_cast<float4*>(tile);
+        const long long q = tw * 32 + lane;
+        if (ok) {
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                const int j = c * 32 + lane;
+                Out o = step_cell<FMT, VAR>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
+                                            tile[3 * kWarpCells + j], tile[4 * kWarpCells + j], 0.f);
+                tile[3 * kWarpCells + j] = o.ue;
+                tile[4 * kWarpCells + j] = o.ui;
+                tile[0 * kWarpCells + j] = o.qc;
+                tile[1 * kWarpCells + j] = o.qx;
+                if (cnt) count_flags(o.flags, cnt);
+            }
+            __syncwarp();
+            __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
+            __stcs(reinterpret_cast<float4*>(ui_out) + q, t4[4 * 32 + lane]);
+            if (qc_out) __stcs(reinterpret_cast<float4*>(qc_out) + q, t4[0 * 32 + lane]);
+            if (qx_out) __stcs(reinterpret_cast<float4*>(qx_out) + q, t4[1 * 32 + lane]);
+        }
+        __syncwarp();
+        b ^= 1;
+    }
+    const long long scalar_start = ntiles * kWarpCells;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Out o = step_cell<FMT, VAR>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        ue_out[i] = o.ue;
+        ui_out[i] = o.ui;
+        if (qc_out) qc_out[i] = o.qc;
+        if (qx_out) qx_out[i] = o.qx;
+        if (cnt) count_flags(o.flags, cnt);
+    }
+}
+
+}  // namespace
+
+cool_status launch_step_tma(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                            const float* B, const float* H, const float* ue, const float* ui, float* ue_o,
+                            float* ui_o, float* qc, float* qx, cool_counters* cnt, cudaStream_t st) {
+    StepK k;
+    fill_stepk(t, p, k);
+    if (n == 0) return COOL_OK;
+    const bool vec = ((uintptr_t)rho | (uintptr_t)B | (uintptr_t)H | (uintptr_t)ue | (uintptr_t)ui |
+                      (uintptr_t)ue_o | (uintptr_t)ui_o | (uintptr_t)qc | (uintptr_t)qx) % 16 == 0;
+    if (!vec) return COOL_EALIGN;   // bulk copies need 16-byte aligned fields
+    const int fmt = t->dev.fmt;
+    if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
+    const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0);
+    using KFnT = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
+                          float*, float*, float*, float*, cool_counters*);
+#define COOL_KT(F) k_step_tma<F, 0>, k_step_tma<F, 1>, k_step_tma<F, 2>, k_step_tma<F, 3>
+    static const KFnT table_t[5][4] = {{COOL_KT(0)}, {COOL_KT(1)}, {COOL_KT(2)}, {COOL_KT(3)}, {COOL_KT(4)}};
+#undef COOL_KT
+    static const int width[5] = {Fmt<0>::W, Fmt<1>::W, Fmt<2>::W, Fmt<3>::W, Fmt<4>::W};
+    KFnT fn = table_t[fmt][var];
+    const size_t sm_t = (size_t)(smem_table_floats(k) + width[fmt] * kThreads + kWarps * 2 * 5 * kWarpCells) *
+                            sizeof(float) + kWarps * 2 * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_t);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, sm_t);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (per < 1) per = 1;
+    long long wk = (n + kWarps * kWarpCells - 1) / (kWarps * kWarpCells);
+    long long cp = (long long)sm_count() * per;
+    long long bl = wk < cp ? wk : cp;
+    if (bl < 1) bl = 1;
+    fn<<<(int)bl, kThreads, sm_t, st>>>(k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+}
+
+}  // namespace cool
