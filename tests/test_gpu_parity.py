@@ -221,8 +221,9 @@ def test_bad_arguments(cool, cfg1):
         cool.step(tab, cool.Params(n_sub=0), t, t, t, t, t)
     with pytest.raises(cool.CoolError):
         cool.step(tab, cool.Params(limiter_frac=0.0), t, t, t, t, t)
-    with pytest.raises(cool.CoolError):
-        cool.step(tab, cool.Params(path=1), t, t, t, t, t)
+    for path in (4, 99):   # the surrogate path is cool_surrogate_infer's; 99 is no path
+        with pytest.raises(cool.CoolError):
+            cool.step(tab, cool.Params(path=path), t, t, t, t, t)
 
 
 def test_save_load_roundtrip(cool, cfg1, tmp_path):
