@@ -26,6 +26,8 @@
 //     so a sub-cycle that stays in its T_e interval reads no table memory;
 //   - the bridge is evaluated in log2 space so that no intermediate
 //     over/underflows FP32 over the table's 60-decade range.
+#include <string.h>
+
 #include "cool_step_cell.cuh"
 
 namespace cool {
@@ -226,7 +228,33 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
     long long blocks = work < cap ? work : cap;
     if (blocks < 1) blocks = 1;
-    fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt, r);
+    // the packed 4-D channel as a persisting L2 access-policy window of this
+    // launch (the stream's own attributes are left alone)
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    int max_win = 0, max_persist = 0;
+    cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device);
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, t->device);
+    if (max_win > 0 && max_persist > 0 && t->ls_bytes > 0) {
+        const size_t win = t->ls_bytes < (size_t)max_win ? t->ls_bytes : (size_t)max_win;
+        size_t limit = 0;
+        cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize);
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = (void*)t->dev.lsb;
+        attr[0].val.accessPolicyWindow.num_bytes = win;
+        attr[0].val.accessPolicyWindow.hitRatio = limit >= win ? 1.f : (float)limit / (float)win;
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    e = cudaLaunchKernelEx(&cfg, fn, k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt, r);
+    if (e != cudaSuccess) return set_cuda_error(e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
