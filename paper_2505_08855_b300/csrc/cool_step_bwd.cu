@@ -158,8 +158,9 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
     const float we = __saturatef(re), wi = __saturatef(ri);
     const float ce_w = (re > 0.f && re < 1.f) ? T.inv_dl[4] / kLn2 : 0.f;
     const float ci_w = (ri > 0.f && ri < 1.f) ? T.inv_dl[4] / kLn2 : 0.f;
-    const float* row = S.lc + si.j * nC + se.j;
-    const float c00 = row[0], c01 = row[1], c10 = row[nC], c11 = row[nC + 1];
+    const int ls = k.lc_stride;
+    const float* row = S.lc + si.j * ls + se.j;
+    const float c00 = row[0], c01 = row[1], c10 = row[ls], c11 = row[ls + 1];
     const float lC = lerpf(lerpf(c00, c01, we), lerpf(c10, c11, we), wi);
     const float rate = ex2a(fminf(lC + lcc_off, 126.f));
     const float pe = k.ce * ue;

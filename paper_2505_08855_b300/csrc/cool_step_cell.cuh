@@ -81,12 +81,13 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         // ---- (i) Coulomb exchange --------------------------------------------
         const float Te = ue * inv_e;
         const float Ti = ui * inv_i;
-        const Sel se = select_axis(axC, nC, T.inv_dl[4], Te, clamp);
-        const Sel si = select_axis(axC, nC, T.inv_dl[4], Ti, clamp);
-        const float we = __saturatef(se.r * T.inv_dl[4]);
-        const float wi = __saturatef(si.r * T.inv_dl[4]);
-        const float* row = S.lc + si.j * nC + se.j;
-        const float lC = lerpf(lerpf(row[0], row[1], we), lerpf(row[nC], row[nC + 1], we), wi);
+        const SelW se = select_sub<1>(k, axC + nC, nC, T.inv_dl[4], Te, clamp);
+        const SelW si = select_sub<1>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp);
+        const float we = se.w;
+        const float wi = si.w;
+        const int ls = k.lc_stride;
+        const float* row = S.lc + si.j * ls + se.j;
+        const float lC = lerpf(lerpf(row[0], row[1], we), lerpf(row[ls], row[ls + 1], we), wi);
         const float rate = ex2a(fminf(lC + lcc_off, 126.f));
         // D = (gamma_i - 1) u_i - (gamma_e - 1) u_e; T_i - T_e = (s_K/rho) D and
         // the equilibrium point is X_eq = D / (ce + ci).  D cancels as T_e -> T_i:
@@ -144,8 +145,11 @@ __device__ __forceinline__ void load_smem(const StepK& k, float* sm) {
     for (int i = threadIdx.x; i < na; i += blockDim.x) sm[i] = k.tab.axes[i];
     const int nT = k.tab.n[3];
     for (int i = threadIdx.x; i < nT; i += blockDim.x) sm[na + i] = k.tab.lb[i];
-    const int nC2 = k.tab.n[4] * k.tab.n[4];
-    for (int i = threadIdx.x; i < nC2; i += blockDim.x) sm[na + nT + i] = k.tab.lc[i];
+    const int nC = k.tab.n[4];
+    for (int i = threadIdx.x; i < nC * nC; i += blockDim.x) {
+        const int r = i / nC;
+        sm[na + nT + r * k.lc_stride + (i - r * nC)] = k.tab.lc[i];
+    }
     __syncthreads();
 }
 

@@ -123,9 +123,15 @@ struct StepK {
     float limiter, eq_band, clamp;
     int n_sub, mode, iters;
     int smem_floats;                  // floats of axes + lb + lc in shared memory
+    int lc_stride;                    // row stride of the Coulomb channel in shared memory: odd, so
+                                      // rows of one column fall in different banks
     int axes_floats;
     float spin, h_floor;              // disk geometry (the disk step): a, (H/R)_floor
     int h_from_state;                 // H_th = c_s / Omega_K replaces the H field
+    // select_sub constants of the two axes whose keys change every sub-cycle
+    // ([0] the synchrotron T_e axis, [1] the Coulomb temperature axis):
+    // -log2(x_0)/dl - 1/2, n - 2, and the end nodes x_0, x_{n-1}
+    float g_c0[2], g_hi[2], g_x0[2], g_xn[2];
 };
 
 struct Sel {
@@ -156,6 +162,44 @@ __device__ __forceinline__ Sel select_axis(const float* a, int n, float inv_dl, 
     Sel s;
     s.j = j1 - ((j1 > 0 && above) ? 1 : 0);
     s.r = lg2a(key * rx[s.j]);
+    return s;
+}
+
+struct SelW {
+    int j;
+    float r;   // log2(key / x_j)
+    float w;   // interpolation weight r / dl, saturated to [0, 1]
+};
+
+// Index selection for the keys that change every sub-cycle (T_e on the
+// synchrotron axis, A = 0; T_e and T_i on the Coulomb axis, A = 1), with no
+// node loads besides 1/x_j.  The guess floor((log2 key - l_0)/dl) is taken
+// as round-to-nearest of the value shifted by -1/2 (the FP32 addition of
+// 1.5 * 2^23 rounds to an integer); lg2.approx puts it within one of the
+// true index, and wrong only for keys within ~1e-5 node spacings of a node.
+// Then r = log2(key / x_j) comes from the ratio, accurate to ~1e-7, and a
+// wrong guess shows as a weight outside [0, 1]: one step to the
+// neighbouring interval fixes it (a branch that lanes almost never take).
+// Either side of a node interpolates to the same value up to the accuracy
+// of r, so no exact node compares are needed for the values; the clamp flag
+// compares the key with the end nodes exactly in FP32, as select_axis does.
+template <int A>
+__device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int n, float inv_dl, float key,
+                                           unsigned& clamp) {
+    float t = fmaf(lg2a(key), inv_dl, k.g_c0[A]);
+    t = fminf(fmaxf(t, 0.f), k.g_hi[A]);
+    SelW s;
+    s.j = __float_as_int(__fadd_rn(t, 12582912.f)) - 0x4B400000;
+    s.r = lg2a(key * rx[s.j]);
+    float w = s.r * inv_dl;
+    const bool out = key < k.g_x0[A] || key > k.g_xn[A];
+    clamp |= out ? 1u : 0u;
+    if (!out && fabsf(w - 0.5f) > 0.5f) {
+        s.j = min(max(s.j + (w < 0.5f ? -1 : 1), 0), n - 2);
+        s.r = lg2a(key * rx[s.j]);
+        w = s.r * inv_dl;
+    }
+    s.w = __saturatef(w);
     return s;
 }
 
@@ -288,11 +332,11 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
                                              Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
     const float* axT = S.ax + k.tab.axis_off[3];
-    Sel s = select_axis(axT, nT, k.tab.inv_dl[3], Te, clamp);
+    const SelW s = select_sub<0>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp);
     const int j = s.j;
     if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
     const int o = j - cc.base;
-    const float w = __saturatef(s.r * k.tab.inv_dl[3]);
+    const float w = s.w;
     const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
     const float Lb = lerpf(S.lb[j], S.lb[j + 1], w) + c.lb_off;
     const float lT = axT[2 * nT + j] + s.r;
@@ -460,7 +504,16 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
     int na = 0;
     for (int a = 0; a < 5; ++a) na += 3 * t->dev.n[a];
     k.axes_floats = na;
-    k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * t->dev.n[4];
+    for (int g = 0; g < 2; ++g) {
+        const int a = 3 + g, n = t->dev.n[a];
+        const float* x = t->h_axes + t->dev.axis_off[a];
+        k.g_c0[g] = (float)(-(double)x[2 * n] * (double)t->dev.inv_dl[a] - 0.5);
+        k.g_hi[g] = (float)(n - 2);
+        k.g_x0[g] = x[0];
+        k.g_xn[g] = x[n - 1];
+    }
+    k.lc_stride = t->dev.n[4] | 1;
+    k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * k.lc_stride;
 }
 
 }  // namespace
