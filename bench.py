@@ -240,6 +240,34 @@ def _timed(torch, fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def _timed_graph(torch, fn, steps, warmup, calls=10):
+    """CUDA-event time per call of `fn` captured `calls` times in a CUDA
+    graph and replayed: for kernels shorter than the Python call that
+    launches them, where back-to-back calls would time the host."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(calls):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    del g
+    return e0.elapsed_time(e1) / (steps * calls)
+
+
 def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=None):
     line = {"suite": "perf", "case": case, "workload": workload, "cells": n, "ms_per_step": ms,
             "value": n / (ms * 1e-3), "unit": UNIT, "higher_is_better": True}
@@ -252,7 +280,8 @@ def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=Non
     print(json.dumps(line), flush=True)
 
 
-SECTIONS = ("cfg2", "paper_size", "disk", "radiation", "scalar", "fp64", "adjoint", "direct", "surrogate")
+SECTIONS = ("cfg2", "paper_size", "staging_bound", "l2_persist", "disk", "radiation", "scalar", "fp64", "adjoint",
+            "direct", "surrogate")
 
 
 def run_suite_perf(args, torch, cool, inputs, dev):
@@ -280,7 +309,7 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         torch.cuda.synchronize()
         return {k: v for k, v in cool.counters_dict(c).items() if v}
 
-    if want & {"cfg2", "paper_size", "disk", "radiation", "scalar", "fp64"}:
+    if want & {"cfg2", "paper_size", "staging_bound", "l2_persist", "disk", "radiation", "scalar", "fp64"}:
         F = inputs.make(WORKLOAD)
         n = F["rho"].size
         tf = {k: torch.from_numpy(v).to(dev) for k, v in F.items()}
@@ -321,6 +350,56 @@ def run_suite_perf(args, torch, cool, inputs, dev):
             _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
         big.free()
         del big
+    if "staging_bound" in want:
+        # what staging the 4-D channel on chip could gain at most: the same
+        # step with a 4-D channel of 2x2x2 (H, B, n_e) corners x 64 T_e nodes
+        # (10 KB, L1-resident: every gather hits L1) against the 64^4 table
+        # (75.5 MB, L2-resident), at 1 and 8 sub-cycles
+        for nn, label in (((64, 64, 64, 64, 64), "64^4 table (L2-resident)"),
+                          ((2, 2, 2, 64, 64), "2x2x2x64 4-D channel (L1-resident)")):
+            tt = cool.Table(cool.TableSpec(n=nn))
+            for ns in (1, N_SUB):
+                p = cool.Params(n_sub=ns)
+                ms = _timed(torch, lambda: cool.step(tt, p, *fl, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
+                _suite_line(f"staging bound: {label}, N_sub = {ns}", WORKLOAD, n, ms,
+                            {"table_packed_bytes": tt.packed_bytes()}, BYTES_PER_CELL, peak)
+            tt.free()
+            del tt
+    if "l2_persist" in want:
+        # the opt-in persisting-L2 reservation of the packed channel
+        # (cool_table_l2_persist): the step with and without it, and the
+        # radiation correction (a streaming kernel) run after it in the same
+        # context
+        thick = torch.empty(n, dtype=torch.uint8, device=dev)
+        p = cool.Params(n_sub=N_SUB)
+        t = table()
+        for on in (False, True):
+            t.l2_persist(on)
+            ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
+            _suite_line(f"L2 reservation {'on' if on else 'off'}: step, 64^4 table (75.5 MB)", WORKLOAD, n, ms,
+                        None, BYTES_PER_CELL, peak)
+            ms = _timed_graph(torch, lambda: cool.radiation_te(p, tf["rho"], tf["H"], tf["ue"], te_out=ue_o,
+                                                               thick_out=thick), steps, warm)
+            _suite_line(f"L2 reservation {'on' if on else 'off'}: radiation correction after it", WORKLOAD, n, ms,
+                        {"timing": "CUDA graph of 10 calls, replayed"}, 17, peak)
+        t.l2_persist(False)
+        del thick
+        # a table larger than L2: 128 x 128 x 64 x 64 FP32 (302 MB packed) on
+        # the 448 x 192 x 192 shell
+        S = inputs.make("shell_448x192x192")
+        sf = [torch.from_numpy(S[k]).to(dev) for k in ("rho", "B", "H", "ue", "ui")]
+        ns = sf[0].numel()
+        del S
+        so = (torch.empty_like(sf[3]), torch.empty_like(sf[4]))
+        big = cool.Table(cool.TableSpec(n=(128, 128, 64, 64, 64)))
+        for on in (False, True):
+            big.l2_persist(on)
+            ms = _timed(torch, lambda: cool.step(big, p, *sf, ue_out=so[0], ui_out=so[1]), steps, warm, stream)
+            _suite_line(f"L2 reservation {'on' if on else 'off'}: step, 128x128x64x64 table (302 MB)",
+                        "shell_448x192x192", ns, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL,
+                        peak)
+        big.free()
+        del big, sf, so
     if "disk" in want:
         # the disk geometry fused into the step (H_th from the state, floor)
         r_dev = torch.from_numpy(inputs.make(WORKLOAD, with_r=True)["r"]).to(dev)
@@ -343,10 +422,11 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         # read, 4 B T_e + 1 B flag written per cell), 285 MB per pass > L2
         thick = torch.empty(n, dtype=torch.uint8, device=dev)
         p = cool.Params(n_sub=N_SUB)
-        ms = _timed(torch, lambda: cool.radiation_te(p, tf["rho"], tf["H"], tf["ue"], te_out=ue_o, thick_out=thick),
-                    steps * 5, warm, stream)
+        ms = _timed_graph(torch, lambda: cool.radiation_te(p, tf["rho"], tf["H"], tf["ue"], te_out=ue_o,
+                                                           thick_out=thick), steps, warm)
         _suite_line("radiation-pressure T_e correction (Sec. 5.2 quartic), elementwise", WORKLOAD, n, ms,
-                    {"thick_cells": int(thick.sum().item())}, 17, peak)
+                    {"thick_cells": int(thick.sum().item()), "timing": "CUDA graph of 10 calls, replayed"}, 17,
+                    peak)
         del thick
     if "scalar" in want:
         # unaligned fields: the scalar path
@@ -365,7 +445,7 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         ms = _timed(torch, lambda: cool.step(table(), p, *f64, ue_out=o64[0], ui_out=o64[1]), 3, 1, stream)
         _suite_line("FP64 fields and arithmetic", WORKLOAD, n, ms, None, 56, peak)
         del f64, o64
-    if want & {"cfg2", "paper_size", "disk", "radiation", "scalar", "fp64"}:
+    if want & {"cfg2", "paper_size", "staging_bound", "l2_persist", "disk", "radiation", "scalar", "fp64"}:
         del tf, fl, ue_o, ui_o
         torch.cuda.empty_cache()
 

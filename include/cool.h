@@ -60,7 +60,9 @@ typedef enum { COOL_F32 = 0, COOL_BF16 = 1, COOL_F16 = 2, COOL_F64 = 3 } cool_dt
 typedef enum { COOL_EXPLICIT_LIMITED = 0, COOL_IMPLICIT_STIFF = 1 } cool_mode;
 
 /* How the 4-D synchrotron channel is read.  L2WINDOW: the packed blocks in
- * global memory, kept L2-resident (all modes, formats and field types).
+ * global memory, L2-resident through their reuse; with
+ * cool_table_l2_persist on, each step launch also carries an access-policy
+ * window marking them persisting (all modes, formats and field types).
  * TEXTURE_POINT / TEXTURE_HWLERP (the paper's design, Sec. 3.1; comparison
  * paths, explicit mode with FP32 fields and an FP32 table only): the FP32
  * channel as a 3-D texture (x = T_e, y = n_e, z = h n_B + b, made on first
@@ -175,6 +177,26 @@ cool_status cool_build_table(const cool_table_spec* spec, void* stream, cool_tab
 
 /* Release a table (NULL is a no-op). */
 cool_status cool_table_free(cool_table* t);
+
+/* Reserve persisting L2 for the table's packed 4-D channel (on = 1) or give
+ * it back (on = 0, the state of a new table).  On: the context's
+ * persisting-L2 limit (cudaLimitPersistingL2CacheSize, one value per CUDA
+ * context) is raised to min(packed bytes, the device maximum) if it is
+ * lower, and every L2WINDOW step launch with this table attaches an
+ * access-policy window over the packed channel (hit property persisting,
+ * miss property streaming, hit ratio = limit / window, capped at 1).  Off:
+ * persisting lines are reset to normal and the limit this call raised is
+ * put back.  The carve-out is context-wide: L2 set aside for persisting
+ * lines is not available to other kernels' ordinary accesses.  Measured on
+ * B300 (8 sub-cycles, 16.8 M cells): the step does not gain, with a table
+ * that fits L2 beside the streamed fields (75.5 MB: 1.170 ms off, 1.186 ms
+ * on) or not (302 MB: 1.180 / 1.178 ms) -- the table's own reuse keeps it
+ * in L2 -- while a streaming kernel run after it in the same context slows
+ * down 1.7x (62 -> 105 us); hence off by default.  Freeing the table turns
+ * it off.  Errors:
+ * COOL_ENULL, COOL_ESTATE (not a live table), COOL_EINVAL (on not 0 or 1),
+ * COOL_ECUDA. */
+cool_status cool_table_l2_persist(cool_table* t, int on);
 
 /* The spec a table was built with. */
 cool_status cool_table_get_spec(const cool_table* t, cool_table_spec* spec);
@@ -424,9 +446,14 @@ cool_status cool_debug_gemm_bf16(const void* A, const void* B, float* C, int M, 
                                  void* stream);
 
 /* Index/weight selection of the table interpolation on one axis, for FP32
- * keys in the axis' physical unit (device arrays of n): idx = the largest j
- * in [0, N-2] with node32[j] <= key (0 below the first node), w = log2(key /
- * x_j) / dl clamped to [0, 1].  The same rule the step uses. */
+ * keys in the axis' physical unit (device arrays of n).  axis 0..4 (H, B,
+ * n_e, T_e, Coulomb T): idx = the largest j in [0, N-2] with node32[j] <=
+ * key (0 below the first node), w = log2(key / x_j) / dl clamped to [0, 1]:
+ * the rule of the step's per-cell keys (H, B, n_e).  axis 5, 6: the rule of
+ * the keys that change every sub-cycle (T_e on axis 3, T_e and T_i on axis
+ * 4): the same j and w except for keys within ~1e-5 node spacings of a
+ * node, where j may be the neighbouring interval with w = 1 (or 0), so that
+ * j + w, the interpolation position, agrees.  Asynchronous on stream. */
 cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
                               int* idx, float* w, void* stream);
 

@@ -146,6 +146,11 @@ class Table:
                                            out.size), "cool_table_nodes")
         return out
 
+    def l2_persist(self, on=True):
+        """cool_table_l2_persist: reserve persisting L2 for the packed 4-D
+        channel (context-wide; off by default) or give it back."""
+        _b.check(_b.lib().cool_table_l2_persist(self.handle, 1 if on else 0), "cool_table_l2_persist")
+
     def free(self):
         if self._h is not None:
             _b.check(_b.lib().cool_table_free(self._h), "cool_table_free")

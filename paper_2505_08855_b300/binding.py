@@ -21,7 +21,7 @@ COOL_PATH_L2WINDOW, COOL_PATH_TMA_SMEM, COOL_PATH_TEXTURE_POINT, COOL_PATH_TEXTU
 # Every entry point declared in include/cool.h (checked by the CPU tests).
 EXPORTS = (
     "cool_strerror", "cool_last_cuda_error", "cool_table_spec_default", "cool_params_default",
-    "cool_build_table", "cool_table_free", "cool_table_get_spec", "cool_table_export",
+    "cool_build_table", "cool_table_free", "cool_table_l2_persist", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
     "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
     "cool_debug_gemm_bf16", "cool_fit_spec_default", "cool_surrogate_fit", "cool_surrogate_free",
@@ -106,6 +106,7 @@ def lib():
             "cool_params_default": (I, [P]),
             "cool_build_table": (I, [P, P, P]),
             "cool_table_free": (I, [P]),
+            "cool_table_l2_persist": (I, [P, I]),
             "cool_table_get_spec": (I, [P, P]),
             "cool_table_export": (I, [P, I, P, LL]),
             "cool_table_nodes": (I, [P, I, P, I]),

@@ -359,17 +359,18 @@ cool_status table_finish(cool_table* t, cudaStream_t st, bool copy_host) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_cuda_error(e);
-    // Keep the 4-D channel L2-resident: reserve persisting L2 for it (a
-    // per-context limit; the access-policy window is set per launch).
-    int dev = t->device;
-    int maxp = 0;
-    cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev);
-    size_t want = t->ls_bytes < (size_t)maxp ? t->ls_bytes : (size_t)maxp;
-    size_t cur = 0;
-    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
-    if (want > cur) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
-    cudaGetLastError();  // the limit is an optimisation: ignore failure
     return COOL_OK;
+}
+
+// Turn the table's persisting-L2 reservation off: persisting lines back to
+// normal, and the context limit back to what it was if this table raised it.
+static cool_status l2_persist_off(cool_table* t) {
+    cudaError_t e = cudaSuccess;
+    if (t->l2_persist) e = cudaCtxResetPersistingL2Cache();
+    if (e == cudaSuccess && t->l2_raised) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, t->l2_prev_limit);
+    t->l2_persist = 0;
+    t->l2_raised = 0;
+    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
 }
 
 uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
@@ -468,9 +469,32 @@ cool_status cool_build_table(const cool_table_spec* spec, void* stream, cool_tab
     return COOL_OK;
 }
 
+cool_status cool_table_l2_persist(cool_table* t, int on) {
+    if (!t) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    if (on != 0 && on != 1) return COOL_EINVAL;
+    if (!on) return l2_persist_off(t);
+    if (t->l2_persist) return COOL_OK;
+    int maxp = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, t->device);
+    size_t cur = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    const size_t want = t->ls_bytes < (size_t)maxp ? t->ls_bytes : (size_t)maxp;
+    if (want > cur) {
+        e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        t->l2_raised = 1;
+        t->l2_prev_limit = cur;
+    }
+    t->l2_persist = 1;
+    return COOL_OK;
+}
+
 cool_status cool_table_free(cool_table* t) {
     if (!t) return COOL_OK;
     if (!unregister_table(t)) return COOL_ESTATE;
+    l2_persist_off(t);   // best effort: the table goes regardless
     t->magic = 0;
     free_table_memory(t);
     delete t;
@@ -815,7 +839,7 @@ cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const 
                               float* w, void* stream) {
     if (!t) return COOL_ENULL;
     if (!table_ok(t)) return COOL_ESTATE;
-    if (axis < 0 || axis > 4 || n < 0) return COOL_EINVAL;
+    if (axis < 0 || axis > 6 || n < 0) return COOL_EINVAL;
     if (n == 0) return COOL_OK;
     if (!keys || !idx || !w) return COOL_ENULL;
     return launch_debug_lookup(t, axis, n, keys, idx, w, (cudaStream_t)stream);

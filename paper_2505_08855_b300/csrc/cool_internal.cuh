@@ -77,6 +77,9 @@ struct cool_table {
     double* h_lc64;
     float* h_axes;              // host copy of the FP32 axis arrays
     size_t ls_bytes;
+    int l2_persist;             // cool_table_l2_persist on: step launches carry the L2 window
+    int l2_raised;              // this table raised the context's persisting-L2 limit ...
+    size_t l2_prev_limit;       // ... from this value
     // texture comparison paths (created on first use): the FP32 4-D channel
     // as a 3-D CUDA array (x = T_e, y = n_e, z = h n_B + b) and two texture
     // objects on it, point sampling and hardware linear filtering

@@ -172,13 +172,25 @@ __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const doub
     }
 }
 
-__global__ void k_debug_lookup(DevTable T, int axis, long long n, const float* keys, int* idx, float* w) {
+// axis 0..4: select_axis (the per-cell keys); 5, 6: select_sub on axes 3
+// and 4 (the keys of every sub-cycle)
+__global__ void k_debug_lookup(StepK k, int axis, long long n, const float* keys, int* idx, float* w) {
+    const DevTable& T = k.tab;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         unsigned clamp = 0u;
-        Sel s = select_axis(T.axes + T.axis_off[axis], T.n[axis], T.inv_dl[axis], keys[i], clamp);
-        idx[i] = s.j;
-        w[i] = __saturatef(s.r * T.inv_dl[axis]);
+        if (axis < 5) {
+            Sel s = select_axis(T.axes + T.axis_off[axis], T.n[axis], T.inv_dl[axis], keys[i], clamp);
+            idx[i] = s.j;
+            w[i] = __saturatef(s.r * T.inv_dl[axis]);
+        } else {
+            const int a = axis - 2;
+            const float* ax = T.axes + T.axis_off[a];
+            const SelW s = axis == 5 ? select_sub<0>(k, ax + T.n[a], T.n[a], T.inv_dl[a], keys[i], clamp)
+                                     : select_sub<1>(k, ax + T.n[a], T.n[a], T.inv_dl[a], keys[i], clamp);
+            idx[i] = s.j;
+            w[i] = s.w;
+        }
     }
 }
 
@@ -228,8 +240,9 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
     long long blocks = work < cap ? work : cap;
     if (blocks < 1) blocks = 1;
-    // the packed 4-D channel as a persisting L2 access-policy window of this
-    // launch (the stream's own attributes are left alone)
+    // with cool_table_l2_persist on: the packed 4-D channel as a persisting
+    // L2 access-policy window of this launch (the stream's own attributes are
+    // left alone)
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)blocks);
@@ -237,13 +250,12 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
-    int max_win = 0, max_persist = 0;
-    cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device);
-    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, t->device);
-    if (max_win > 0 && max_persist > 0 && t->ls_bytes > 0) {
+    int max_win = 0;
+    size_t limit = 0;
+    if (t->l2_persist && t->ls_bytes > 0 &&
+        cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device) == cudaSuccess &&
+        max_win > 0 && cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize) == cudaSuccess && limit > 0) {
         const size_t win = t->ls_bytes < (size_t)max_win ? t->ls_bytes : (size_t)max_win;
-        size_t limit = 0;
-        cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize);
         attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
         attr[0].val.accessPolicyWindow.base_ptr = (void*)t->dev.lsb;
         attr[0].val.accessPolicyWindow.num_bytes = win;
@@ -297,7 +309,11 @@ cool_status launch_debug_lookup(const cool_table* t, int axis, long long n, cons
     if (n == 0) return COOL_OK;
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_debug_lookup<<<(int)blocks, 256, 0, st>>>(t->dev, axis, n, keys, idx, w);
+    cool_params p;
+    cool_params_default(&p);
+    StepK k;
+    fill_stepk(t, &p, k);
+    k_debug_lookup<<<(int)blocks, 256, 0, st>>>(k, axis, n, keys, idx, w);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
