@@ -53,12 +53,13 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     S.ax = sm;
     S.lb = sm + k.axes_floats;
     S.lc = sm + k.axes_floats + k.tab.n[3];
-    float* win = sm + smem_table_floats(k) + threadIdx.x;   // kMaxW x kThreads window
+    constexpr int WR = Fmt<FMT>::W;                          // window rows of this format
+    float* win = sm + smem_table_floats(k) + threadIdx.x;   // WR x kThreads window
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     long long scalar_start = 0;
     if (VEC) {
-        float* tile = sm + smem_table_floats(k) + kMaxW * kThreads + warp * NF * kWarpCells;
+        float* tile = sm + smem_table_floats(k) + WR * kThreads + warp * NF * kWarpCells;
         float4* t4 = reinterpret_cast<float4*>(tile);
         const long long ntiles = n / kWarpCells;
         for (long long tw = (long long)blockIdx.x * kWarps + warp; tw < ntiles; tw += (long long)gridDim.x * kWarps) {
@@ -210,7 +211,11 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     if (n == 0) return COOL_OK;
     bool vec = ((uintptr_t)rho | (uintptr_t)B | (uintptr_t)H | (uintptr_t)ue | (uintptr_t)ui |
                 (uintptr_t)ue_o | (uintptr_t)ui_o | (uintptr_t)qc | (uintptr_t)qx | (uintptr_t)r) % 16 == 0;
-    size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads) * sizeof(float);
+    const int fmt = t->dev.fmt;
+    if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
+    // shared memory: the table parts, the window (one row per node of a
+    // block of this format) and the warps' field tiles
+    size_t smem = (size_t)(smem_table_floats(k) + fmt_nodes(fmt) * kThreads) * sizeof(float);
     if (vec) smem += (size_t)kWarps * (disk ? 6 : 5) * kWarpCells * sizeof(float);
     using KFn = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
                          float*, float*, float*, float*, cool_counters*, const float*);
@@ -225,8 +230,6 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                                   k_step_f32<true, 0, 7>};
     static const KFn disk_s[4] = {k_step_f32<false, 0, 4>, k_step_f32<false, 0, 5>, k_step_f32<false, 0, 6>,
                                   k_step_f32<false, 0, 7>};
-    const int fmt = t->dev.fmt;
-    if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
     if (disk && (fmt != 0 || !r)) return COOL_EUNSUPPORTED;
     const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0);
     KFn fn = disk ? (vec ? disk_v[var] : disk_s[var]) : (vec ? table_v[fmt][var] : table_s[fmt][var]);

@@ -234,6 +234,8 @@ template <> struct Fmt<2> { static constexpr int W = 16, S = 15; };  // FP16
 template <> struct Fmt<3> { static constexpr int W = 12, S = 11; };  // BF16, block-scaled
 template <> struct Fmt<4> { static constexpr int W = 12, S = 11; };  // FP16, block-scaled
 constexpr int kMaxW = 16;
+// nodes per block of a format, on the host (the window rows a kernel needs)
+constexpr int fmt_nodes(int fmt) { return fmt == 0 ? Fmt<0>::W : (fmt <= 2 ? Fmt<1>::W : Fmt<3>::W); }
 
 // 256-bit read-only load of one block (32-byte aligned).
 __device__ __forceinline__ void ld8u(const uint32_t* p, uint32_t (&v)[8]) {
