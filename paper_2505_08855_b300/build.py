@@ -2,10 +2,12 @@
 
     python -m paper_2505_08855_b300.build [--force]
 
-nvcc compiles every csrc/*.cu for sm_103a only and links one shared
-library next to this file.  No JIT, no torch extension machinery: the
-library has a plain C ABI and the Python binding loads it with ctypes.
+nvcc compiles every csrc/*.cu for sm_103a only (one process per source, in
+parallel, objects under _build/) and links one shared library next to this
+file.  No JIT, no torch extension machinery: the library has a plain C ABI
+and the Python binding loads it with ctypes.
 """
+import concurrent.futures
 import glob
 import os
 import subprocess
@@ -14,6 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcool.so")
+OBJ = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 NVCC_FLAGS = [
@@ -36,18 +39,34 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _compile(src):
+    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+    nvcc = os.environ.get("NVCC", "nvcc")
+    r = subprocess.run([nvcc, *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj], capture_output=True, text=True)
+    return obj, r
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *NVCC_FLAGS, "-shared", "-cudart", "shared", "-I", INCLUDE,
-           "-o", LIB + ".tmp", *sources()]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
+    os.makedirs(OBJ, exist_ok=True)
+    srcs = sources()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 1)) as ex:
+        results = list(ex.map(_compile, srcs))
+    failed = [r for _, r in results if r.returncode != 0]
+    if failed:
+        for r in failed:
+            sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("nvcc failed building libcool.so")
     if verbose:
-        sys.stderr.write(r.stderr)
+        for _, r in results:
+            sys.stderr.write(r.stderr)
+    nvcc = os.environ.get("NVCC", "nvcc")
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "shared",
+                        "-o", LIB + ".tmp", *[o for o, _ in results]], capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed linking libcool.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -33,6 +33,10 @@
 namespace cool {
 namespace {
 
+// VAR: the step_cell variant bits (0 implicit, 1 fp64_critical, 2 disk
+// geometry) and bit 3, counters requested: without it no counter flag is
+// formed (the flag arithmetic of step_cell is dead code) and nothing is
+// counted.
 // VEC: all arrays 16-byte aligned.  Each warp walks its own tiles of 128
 // cells: the five input fields arrive by 128-bit streaming loads into the
 // warp's staging area, each lane steps cells lane, lane+32, lane+64, lane+96
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                Out o = step_cell<FMT, VAR>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
+                Out o = step_cell<FMT, VAR & 7>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
                                             tile[3 * kWarpCells + j], tile[4 * kWarpCells + j],
                                             (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
                 // inputs of cell j are consumed: outputs reuse its slots
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
                 tile[4 * kWarpCells + j] = o.ui;
                 tile[0 * kWarpCells + j] = o.qc;
                 tile[1 * kWarpCells + j] = o.qx;
-                if (cnt) count_flags(o.flags, cnt);
+                if (VAR & 8) count_flags(o.flags, cnt);
             }
             __syncwarp();
             __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
@@ -95,12 +99,12 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT, VAR>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], (VAR & 4) ? rr[i] : 0.f);
+        Out o = step_cell<FMT, VAR & 7>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], (VAR & 4) ? rr[i] : 0.f);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
         if (qx_out) qx_out[i] = o.qx;
-        if (cnt) count_flags(o.flags, cnt);
+        if (VAR & 8) count_flags(o.flags, cnt);
     }
 }
 
@@ -219,19 +223,23 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     if (vec) smem += (size_t)kWarps * (disk ? 6 : 5) * kWarpCells * sizeof(float);
     using KFn = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
                          float*, float*, float*, float*, cool_counters*, const float*);
-#define COOL_KV(V, F) k_step_f32<V, F, 0>, k_step_f32<V, F, 1>, k_step_f32<V, F, 2>, k_step_f32<V, F, 3>
-    static const KFn table_v[5][4] = {{COOL_KV(true, 0)}, {COOL_KV(true, 1)}, {COOL_KV(true, 2)},
+    // the tables are indexed by implicit | fp64_critical << 1 | counters << 2
+    // (template bits 0, 1 and 3)
+#define COOL_KV(V, F) k_step_f32<V, F, 0>, k_step_f32<V, F, 1>, k_step_f32<V, F, 2>, k_step_f32<V, F, 3>, \
+                      k_step_f32<V, F, 8>, k_step_f32<V, F, 9>, k_step_f32<V, F, 10>, k_step_f32<V, F, 11>
+    static const KFn table_v[5][8] = {{COOL_KV(true, 0)}, {COOL_KV(true, 1)}, {COOL_KV(true, 2)},
                                       {COOL_KV(true, 3)}, {COOL_KV(true, 4)}};
-    static const KFn table_s[5][4] = {{COOL_KV(false, 0)}, {COOL_KV(false, 1)}, {COOL_KV(false, 2)},
+    static const KFn table_s[5][8] = {{COOL_KV(false, 0)}, {COOL_KV(false, 1)}, {COOL_KV(false, 2)},
                                       {COOL_KV(false, 3)}, {COOL_KV(false, 4)}};
 #undef COOL_KV
-    // disk geometry: FP32 table only
-    static const KFn disk_v[4] = {k_step_f32<true, 0, 4>, k_step_f32<true, 0, 5>, k_step_f32<true, 0, 6>,
-                                  k_step_f32<true, 0, 7>};
-    static const KFn disk_s[4] = {k_step_f32<false, 0, 4>, k_step_f32<false, 0, 5>, k_step_f32<false, 0, 6>,
-                                  k_step_f32<false, 0, 7>};
+    // disk geometry (template bit 2): FP32 table only
+#define COOL_KD(V) k_step_f32<V, 0, 4>, k_step_f32<V, 0, 5>, k_step_f32<V, 0, 6>, k_step_f32<V, 0, 7>, \
+                   k_step_f32<V, 0, 12>, k_step_f32<V, 0, 13>, k_step_f32<V, 0, 14>, k_step_f32<V, 0, 15>
+    static const KFn disk_v[8] = {COOL_KD(true)};
+    static const KFn disk_s[8] = {COOL_KD(false)};
+#undef COOL_KD
     if (disk && (fmt != 0 || !r)) return COOL_EUNSUPPORTED;
-    const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0);
+    const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0) | (cnt ? 4 : 0);
     KFn fn = disk ? (vec ? disk_v[var] : disk_s[var]) : (vec ? table_v[fmt][var] : table_s[fmt][var]);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);

@@ -78,13 +78,13 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long 
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                Out o = step_cell<FMT, VAR>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
+                Out o = step_cell<FMT, VAR & 7>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
                                             tile[3 * kWarpCells + j], tile[4 * kWarpCells + j], 0.f);
                 tile[3 * kWarpCells + j] = o.ue;
                 tile[4 * kWarpCells + j] = o.ui;
                 tile[0 * kWarpCells + j] = o.qc;
                 tile[1 * kWarpCells + j] = o.qx;
-                if (cnt) count_flags(o.flags, cnt);
+                if (VAR & 8) count_flags(o.flags, cnt);
             }
             __syncwarp();
             __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
@@ -98,12 +98,12 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long 
     const long long scalar_start = ntiles * kWarpCells;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT, VAR>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        Out o = step_cell<FMT, VAR & 7>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
         if (qx_out) qx_out[i] = o.qx;
-        if (cnt) count_flags(o.flags, cnt);
+        if (VAR & 8) count_flags(o.flags, cnt);
     }
 }
 
@@ -120,11 +120,13 @@ cool_status launch_step_tma(const cool_table* t, const cool_params* p, long long
     if (!vec) return COOL_EALIGN;   // bulk copies need 16-byte aligned fields
     const int fmt = t->dev.fmt;
     if (fmt < 0 || fmt > 4) return COOL_EUNSUPPORTED;
-    const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0);
+    // indexed by implicit | fp64_critical << 1 | counters << 2 (template bits 0, 1, 3)
+    const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0) | (cnt ? 4 : 0);
     using KFnT = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
                           float*, float*, float*, float*, cool_counters*);
-#define COOL_KT(F) k_step_tma<F, 0>, k_step_tma<F, 1>, k_step_tma<F, 2>, k_step_tma<F, 3>
-    static const KFnT table_t[5][4] = {{COOL_KT(0)}, {COOL_KT(1)}, {COOL_KT(2)}, {COOL_KT(3)}, {COOL_KT(4)}};
+#define COOL_KT(F) k_step_tma<F, 0>, k_step_tma<F, 1>, k_step_tma<F, 2>, k_step_tma<F, 3>, \
+                   k_step_tma<F, 8>, k_step_tma<F, 9>, k_step_tma<F, 10>, k_step_tma<F, 11>
+    static const KFnT table_t[5][8] = {{COOL_KT(0)}, {COOL_KT(1)}, {COOL_KT(2)}, {COOL_KT(3)}, {COOL_KT(4)}};
 #undef COOL_KT
     static const int width[5] = {Fmt<0>::W, Fmt<1>::W, Fmt<2>::W, Fmt<3>::W, Fmt<4>::W};
     KFnT fn = table_t[fmt][var];
