@@ -447,13 +447,12 @@ cool_status cool_debug_gemm_bf16(const void* A, const void* B, float* C, int M, 
 
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n).  axis 0..4 (H, B,
- * n_e, T_e, Coulomb T): idx = the largest j in [0, N-2] with node32[j] <=
- * key (0 below the first node), w = log2(key / x_j) / dl clamped to [0, 1]:
- * the rule of the step's per-cell keys (H, B, n_e).  axis 5, 6: the rule of
- * the keys that change every sub-cycle (T_e on axis 3, T_e and T_i on axis
- * 4): the same j and w except for keys within ~1e-5 node spacings of a
- * node, where j may be the neighbouring interval with w = 1 (or 0), so that
- * j + w, the interpolation position, agrees.  Asynchronous on stream. */
+ * n_e, T_e, Coulomb T), the exact rule: idx = the largest j in [0, N-2]
+ * with node32[j] <= key (0 below the first node), w = log2(key / x_j) / dl
+ * clamped to [0, 1].  axis 5..9: the rule the step uses on axes 0..4: the
+ * same j and w except for keys within ~1e-7 of a node, where j may be the
+ * neighbouring interval with w = 1 (or 0), so that j + w, the
+ * interpolation position, agrees.  Asynchronous on stream. */
 cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
                               int* idx, float* w, void* stream);
 

@@ -839,7 +839,7 @@ cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const 
                               float* w, void* stream) {
     if (!t) return COOL_ENULL;
     if (!table_ok(t)) return COOL_ESTATE;
-    if (axis < 0 || axis > 6 || n < 0) return COOL_EINVAL;
+    if (axis < 0 || axis > 9 || n < 0) return COOL_EINVAL;
     if (n == 0) return COOL_OK;
     if (!keys || !idx || !w) return COOL_ENULL;
     return launch_debug_lookup(t, axis, n, keys, idx, w, (cudaStream_t)stream);

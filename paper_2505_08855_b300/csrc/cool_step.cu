@@ -177,8 +177,8 @@ __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const doub
     }
 }
 
-// axis 0..4: select_axis (the per-cell keys); 5, 6: select_sub on axes 3
-// and 4 (the keys of every sub-cycle)
+// axis 0..4: select_axis (the exact rule, the oracle's); 5..9: select_sub
+// on axes 0..4 (the step's rule)
 __global__ void k_debug_lookup(StepK k, int axis, long long n, const float* keys, int* idx, float* w) {
     const DevTable& T = k.tab;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -189,10 +189,16 @@ __global__ void k_debug_lookup(StepK k, int axis, long long n, const float* keys
             idx[i] = s.j;
             w[i] = __saturatef(s.r * T.inv_dl[axis]);
         } else {
-            const int a = axis - 2;
-            const float* ax = T.axes + T.axis_off[a];
-            const SelW s = axis == 5 ? select_sub<0>(k, ax + T.n[a], T.n[a], T.inv_dl[a], keys[i], clamp)
-                                     : select_sub<1>(k, ax + T.n[a], T.n[a], T.inv_dl[a], keys[i], clamp);
+            const int a = axis - 5;
+            const float* rx = T.axes + T.axis_off[a] + T.n[a];
+            SelW s;
+            switch (a) {
+            case 0: s = select_sub<0>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
+            case 1: s = select_sub<1>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
+            case 2: s = select_sub<2>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
+            case 3: s = select_sub<3>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
+            default: s = select_sub<4>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
+            }
             idx[i] = s.j;
             w[i] = s.w;
         }

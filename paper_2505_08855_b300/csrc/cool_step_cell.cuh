@@ -53,17 +53,17 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
     const float kr = k.s_K / rho;
     CellC c;
     {
-        Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
-        Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
-        Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
+        const SelW sh = select_sub<0>(k, S.ax + T.axis_off[0] + T.n[0], T.n[0], T.inv_dl[0], Hc, clamp);
+        const SelW sb = select_sub<1>(k, S.ax + T.axis_off[1] + T.n[1], T.n[1], T.inv_dl[1], Bg, clamp);
+        const SelW sn = select_sub<2>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne, clamp);
         const int rowf = 8 * T.nblk;                       // floats per n_e row
         c.oN = rowf;
         c.oB = rowf * T.n[2];
         c.oH = c.oB * T.n[1];
         c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
-        c.wh = __saturatef(sh.r * T.inv_dl[0]);
-        c.wb = __saturatef(sb.r * T.inv_dl[1]);
-        c.wn = __saturatef(sn.r * T.inv_dl[2]);
+        c.wh = sh.w;
+        c.wb = sb.w;
+        c.wn = sn.w;
         const float lne = lg2a(ne);
         c.ls_off = k.l_hs_e;
         c.lb_off = fmaf(2.f, lne, k.l_hs_e);
@@ -81,8 +81,8 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         // ---- (i) Coulomb exchange --------------------------------------------
         const float Te = ue * inv_e;
         const float Ti = ui * inv_i;
-        const SelW se = select_sub<1>(k, axC + nC, nC, T.inv_dl[4], Te, clamp);
-        const SelW si = select_sub<1>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp);
+        const SelW se = select_sub<4>(k, axC + nC, nC, T.inv_dl[4], Te, clamp);
+        const SelW si = select_sub<4>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp);
         const float we = se.w;
         const float wi = si.w;
         const int ls = k.lc_stride;

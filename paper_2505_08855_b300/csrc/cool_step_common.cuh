@@ -128,10 +128,9 @@ struct StepK {
     int axes_floats;
     float spin, h_floor;              // disk geometry (the disk step): a, (H/R)_floor
     int h_from_state;                 // H_th = c_s / Omega_K replaces the H field
-    // select_sub constants of the two axes whose keys change every sub-cycle
-    // ([0] the synchrotron T_e axis, [1] the Coulomb temperature axis):
+    // select_sub constants per axis (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T):
     // -log2(x_0)/dl - 1/2, n - 2, and the end nodes x_0, x_{n-1}
-    float g_c0[2], g_hi[2], g_x0[2], g_xn[2];
+    float g_c0[5], g_hi[5], g_x0[5], g_xn[5];
 };
 
 struct Sel {
@@ -171,9 +170,8 @@ struct SelW {
     float w;   // interpolation weight r / dl, saturated to [0, 1]
 };
 
-// Index selection for the keys that change every sub-cycle (T_e on the
-// synchrotron axis, A = 0; T_e and T_i on the Coulomb axis, A = 1), with no
-// node loads besides 1/x_j.  The guess floor((log2 key - l_0)/dl) is taken
+// Index selection on axis A (0..4) as the step does it, with no node loads
+// besides 1/x_j.  The guess floor((log2 key - l_0)/dl) is taken
 // as round-to-nearest of the value shifted by -1/2 (the FP32 addition of
 // 1.5 * 2^23 rounds to an integer); lg2.approx puts it within one of the
 // true index, and wrong only for keys within ~1e-5 node spacings of a node.
@@ -334,7 +332,7 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
                                              Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
     const float* axT = S.ax + k.tab.axis_off[3];
-    const SelW s = select_sub<0>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp);
+    const SelW s = select_sub<3>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp);
     const int j = s.j;
     if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
     const int o = j - cc.base;
@@ -506,13 +504,13 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
     int na = 0;
     for (int a = 0; a < 5; ++a) na += 3 * t->dev.n[a];
     k.axes_floats = na;
-    for (int g = 0; g < 2; ++g) {
-        const int a = 3 + g, n = t->dev.n[a];
+    for (int a = 0; a < 5; ++a) {
+        const int n = t->dev.n[a];
         const float* x = t->h_axes + t->dev.axis_off[a];
-        k.g_c0[g] = (float)(-(double)x[2 * n] * (double)t->dev.inv_dl[a] - 0.5);
-        k.g_hi[g] = (float)(n - 2);
-        k.g_x0[g] = x[0];
-        k.g_xn[g] = x[n - 1];
+        k.g_c0[a] = (float)(-(double)x[2 * n] * (double)t->dev.inv_dl[a] - 0.5);
+        k.g_hi[a] = (float)(n - 2);
+        k.g_x0[a] = x[0];
+        k.g_xn[a] = x[n - 1];
     }
     k.lc_stride = t->dev.n[4] | 1;
     k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * k.lc_stride;
