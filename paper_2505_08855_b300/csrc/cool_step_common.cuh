@@ -266,32 +266,33 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
     constexpr int W = Fmt<FMT>::W;
     const uint32_t* p = c.row + (long long)kb * 8;
     if (FMT == 0) {
-        // FP32: all four (h, b) pairs reduced in registers
+        // FP32: the four corners of one H plane in flight together (two L2
+        // round trips per gather); the first plane's bilinear value waits in
+        // the window while the second plane loads
         uint32_t a[8], b[8], d[8], e[8];
         ld8u(p, a);
         ld8u(p + c.oN, b);
-        float x[8], y[8];
+        ld8u(p + c.oB, d);
+        ld8u(p + c.oB + c.oN, e);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = lerpf(dec<0>(a, t), dec<0>(b, t), c.wn);
-        ld8u(p + c.oB, b);
-        ld8u(p + c.oB + c.oN, d);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = lerpf(x[t], lerpf(dec<0>(b, t), dec<0>(d, t), c.wn), c.wb);
+        for (int t = 0; t < 8; ++t)
+            cc.win[t * kThreads] = lerpf(lerpf(dec<0>(a, t), dec<0>(b, t), c.wn),
+                                         lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
         const uint32_t* q = p + c.oH;
-        ld8u(q, b);
-        ld8u(q + c.oN, d);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) y[t] = lerpf(dec<0>(b, t), dec<0>(d, t), c.wn);
+        ld8u(q, a);
+        ld8u(q + c.oN, b);
         ld8u(q + c.oB, d);
         ld8u(q + c.oB + c.oN, e);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-            y[t] = lerpf(y[t], lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
-            cc.win[t * kThreads] = lerpf(x[t], y[t], c.wh);
+            const float y = lerpf(lerpf(dec<0>(a, t), dec<0>(b, t), c.wn), lerpf(dec<0>(d, t), dec<0>(e, t), c.wn),
+                                  c.wb);
+            cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], y, c.wh);
         }
     } else {
         // 16-bit formats (W = 16 or 12 nodes): the partial sums go through
-        // the window in shared memory to bound register use
+        // the window in shared memory to bound register use (four corners
+        // in flight, as for FP32, measured slower for BF16)
         uint32_t r0[8], r1[8];
         ld8u(p, r0);
         ld8u(p + c.oN, r1);
