@@ -7,9 +7,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <new>
 #include <unordered_set>
+#include <utility>
 
 #include "cool_internal.cuh"
 
@@ -36,6 +38,31 @@ static void register_table(const cool_table* t) {
 static bool unregister_table(const cool_table* t) {
     std::lock_guard<std::mutex> g(g_tables_mu);
     return live_tables().erase(t) == 1;
+}
+
+unsigned long long* sched_counter(cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<std::pair<int, cudaStream_t>, unsigned long long*> counters;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    auto it = counters.find({dev, st});
+    if (it != counters.end()) return it->second;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;   // no allocation inside a capture
+    }
+    unsigned long long* p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    counters[{dev, st}] = p;
+    return p;
 }
 
 bool table_ok(const cool_table* t) {

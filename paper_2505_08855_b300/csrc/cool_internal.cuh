@@ -92,6 +92,12 @@ constexpr uint32_t kTableMagic = 0xC0011AB1u;
 namespace cool {
 
 // Host helpers shared by the .cu files of the library.
+// The step's tile counter for the current device and stream `st`: created
+// on first use (8 bytes of device memory kept for the life of the process),
+// one per (device, stream) so that steps on different streams never share
+// one; nullptr if it cannot be created (first use inside stream capture, or
+// an allocation failure), and the step then takes its static tile order.
+unsigned long long* sched_counter(cudaStream_t st);
 cool_status set_cuda_error(cudaError_t e);
 bool table_ok(const cool_table* t);
 long long syn_count(const cool_table_spec& s);

@@ -37,8 +37,11 @@ namespace {
 // geometry) and bit 3, counters requested: without it no counter flag is
 // formed (the flag arithmetic of step_cell is dead code) and nothing is
 // counted.
-// VEC: all arrays 16-byte aligned.  Each warp walks its own tiles of 128
-// cells: the five input fields arrive by 128-bit streaming loads into the
+// VEC: all arrays 16-byte aligned.  Each warp walks tiles of 128 cells: its
+// first tile by its index in the grid, the next ones from a device counter
+// (k.sched) as it finishes, so the warps that draw cheap tiles take more of
+// them (static round-robin order when k.sched is null).  Per tile the five
+// input fields arrive by 128-bit streaming loads into the
 // warp's staging area, each lane steps cells lane, lane+32, lane+64, lane+96
 // (one cell's state in registers at a time), the outputs overwrite the
 // staging area and leave by 128-bit streaming stores.  Warps synchronise
@@ -66,7 +69,9 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
         float* tile = sm + smem_table_floats(k) + WR * kThreads + warp * NF * kWarpCells;
         float4* t4 = reinterpret_cast<float4*>(tile);
         const long long ntiles = n / kWarpCells;
-        for (long long tw = (long long)blockIdx.x * kWarps + warp; tw < ntiles; tw += (long long)gridDim.x * kWarps) {
+        const long long first = (long long)gridDim.x * kWarps;   // tiles taken statically
+        long long tw = (long long)blockIdx.x * kWarps + warp;
+        while (tw < ntiles) {
             const long long q = tw * 32 + lane;  // float4 index of this lane
             t4[0 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rho) + q);
             t4[1 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(Bf) + q);
@@ -94,6 +99,13 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
             if (qc_out) __stcs(reinterpret_cast<float4*>(qc_out) + q, t4[0 * 32 + lane]);
             if (qx_out) __stcs(reinterpret_cast<float4*>(qx_out) + q, t4[1 * 32 + lane]);
             __syncwarp();
+            if (k.sched) {
+                unsigned long long nt = 0;
+                if (lane == 0) nt = atomicAdd(k.sched, 1ull);
+                tw = first + (long long)__shfl_sync(0xffffffffu, nt, 0);
+            } else {
+                tw += first;
+            }
         }
         scalar_start = ntiles * kWarpCells;
     }
@@ -257,6 +269,14 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
     long long blocks = work < cap ? work : cap;
     if (blocks < 1) blocks = 1;
+    if (vec && n / kWarpCells > blocks * kWarps) {
+        // more tiles than warps: the dynamic tile order (a no-op otherwise)
+        k.sched = sched_counter(st);
+        if (k.sched) {
+            e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return set_cuda_error(e);
+        }
+    }
     // with cool_table_l2_persist on: the packed 4-D channel as a persisting
     // L2 access-policy window of this launch (the stream's own attributes are
     // left alone)

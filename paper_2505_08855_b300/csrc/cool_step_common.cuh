@@ -131,6 +131,9 @@ struct StepK {
     // select_sub constants per axis (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T):
     // -log2(x_0)/dl - 1/2, n - 2, and the end nodes x_0, x_{n-1}
     float g_c0[5], g_hi[5], g_x0[5], g_xn[5];
+    // tile counter of the vector step's dynamic tile order (zeroed on the
+    // launch stream before the launch); nullptr: the static order
+    unsigned long long* sched;
 };
 
 struct Sel {
@@ -515,6 +518,7 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
     }
     k.lc_stride = t->dev.n[4] | 1;
     k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * k.lc_stride;
+    k.sched = nullptr;
 }
 
 }  // namespace
