@@ -306,7 +306,7 @@ cool_status cool_step_disk(const cool_table* t, const cool_params* p, const cool
                            float* q_cool_out, float* q_cc_out, cool_counters* counters, void* stream);
 
 /* cool_step on HOST arrays (FP32; the L2WINDOW path): the cells are
- * streamed through the device in chunks of chunk_cells (0: n/8, at least
+ * streamed through the device in chunks of chunk_cells (0: n/12, at least
  * 65536; rounded to a multiple of 128), each chunk's five input copies,
  * its step and its two output copies on one of two internal streams, so that
  * host-to-device copies, steps and device-to-host copies of consecutive
