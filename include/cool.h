@@ -445,6 +445,16 @@ cool_status cool_surrogate_infer(const cool_surrogate* s, const cool_table* t, c
 cool_status cool_debug_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, unsigned* err,
                                  void* stream);
 
+/* Check entry of the kernels' bounded waits: one thread polls an mbarrier
+ * that nothing completes, `polls` times (1 <= polls <= 2^20; each poll is
+ * itself time-bounded by the hardware), then sets bit 0 of *err (a device
+ * word) and returns -- the failure path that the TMA-staged step and the
+ * tensor-core kernels take, reporting through their error words, when a
+ * bulk copy or a tcgen05.mma never signals completion; the context stays
+ * usable.  Errors: COOL_ENULL (err NULL), COOL_EINVAL (polls out of range).
+ * Asynchronous on stream. */
+cool_status cool_debug_wait_timeout(int polls, unsigned* err, void* stream);
+
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n).  axis 0..4 (H, B,
  * n_e, T_e, Coulomb T), the exact rule: idx = the largest j in [0, N-2]

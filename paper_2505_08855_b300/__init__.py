@@ -310,6 +310,18 @@ def step_direct(spec, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, q_coo
     return ue_out, ui_out
 
 
+def debug_wait_timeout(polls, stream=None):
+    """cool_debug_wait_timeout: run a bounded wait on a barrier that never
+    completes; returns the error word it reported (1 when the wait ran out).
+    Synchronous."""
+    import torch
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _b.check(_b.lib().cool_debug_wait_timeout(int(polls), _ptr(err), _stream_ptr(stream)),
+             "cool_debug_wait_timeout")
+    torch.cuda.synchronize()
+    return int(err.item())
+
+
 def debug_lookup(table, axis, keys, stream=None):
     """(idx int32, w float32) of the interpolation rule for FP32 keys."""
     import torch

@@ -80,8 +80,31 @@ k_gemm_bf16_tc(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
     if (warp == 0) mma::tmem_dealloc(tmem, kGemmTmemCols);
 }
 
+// The failure path of the bounded waits: one thread polls the first phase of
+// an mbarrier that nothing arrives on, `polls` times, then reports and
+// invalidates the barrier.  No copy or product is in flight, so nothing else
+// needs to be waited for or freed.
+__global__ void k_wait_timeout(int polls, unsigned* err) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x != 0) return;
+    const uint32_t a = mma::smem_addr(&mbar);
+    mma::mbar_init(a, 1);
+    mma::fence_mbar_init();
+    if (!mma::mbar_wait(a, 0, polls)) atomicOr(err, 1u);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" : : "r"(a) : "memory");
+}
+
 }  // namespace
 }  // namespace cool
+
+extern "C" cool_status cool_debug_wait_timeout(int polls, unsigned* err, void* stream) {
+    using namespace cool;
+    if (!err) return COOL_ENULL;
+    if (polls < 1 || polls > (1 << 20)) return COOL_EINVAL;
+    k_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(polls, err);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+}
 
 extern "C" cool_status cool_debug_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K,
                                             unsigned* err, void* stream) {
