@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     S.ax = sm;
     S.lb = sm + k.axes_floats;
     S.lc = sm + k.axes_floats + k.tab.n[3];
-    float* win = sm + smem_table_floats(k) + threadIdx.x;
-    float* glb_s = sm + smem_table_floats(k) + kMaxW * kThreads;   // partial brems adjoints
+    float* win = sm + smem_table_floats(k) + threadIdx.x;           // 8-row window (FP32 table)
+    float* glb_s = sm + smem_table_floats(k) + Fmt<0>::W * kThreads;  // partial brems adjoints
     float* glc_s = glb_s + k.tab.n[3];                             // partial Coulomb adjoints
     const DevTable& T = k.tab;
     const int nT = T.n[3], nC = T.n[4];
@@ -227,135 +227,152 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 #define ST_U1(sub) (*(SMS ? &sst[(4 * (sub) + 2) * kThreads + threadIdx.x] : &l_u1[(sub)]))
 #define ST_US(sub) (*(SMS ? &sst[(4 * (sub) + 3) * kThreads + threadIdx.x] : &l_us[(sub)]))
 #define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float rho = rho_in[i], B = B_in[i], H = H_in[i];
-        float ue = ue_in[i], ui = ui_in[i];
-        const float ge_out = gue_out[i], gi_out = gui_out[i];
-        if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
-            !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
-            g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
-            continue;
-        }
-        unsigned clamp = 0u;
-        const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
-        const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
-        CellC c;
-        CellD cd;
-        {
-            Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
-            Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
-            Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
-            const int rowf = 8 * T.nblk;
-            c.oN = rowf;
-            c.oB = rowf * T.n[2];
-            c.oH = c.oB * T.n[1];
-            c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
-            const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
-            c.wh = __saturatef(rh);
-            c.wb = __saturatef(rb);
-            c.wn = __saturatef(rn);
-            cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] / kLn2 : 0.f;
-            cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] / kLn2 : 0.f;
-            cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] / kLn2 : 0.f;
-            c.ls_off = k.l_hs_e;
-            c.lb_off = fmaf(2.f, lg2a(ne), k.l_hs_e);
-            c.lbb_off = k.l_bb - lg2a(Hc);
-            c.tau_sca = k.two_sigT * ne * Hc;
-        }
-        const float lcc_off = c.lb_off;
-        Cache cc;
-        cc.base = -8;
-        cc.win = win;
-        // ---- forward, recorded (the forward kernel's arithmetic) ----
-        for (int sub = 0; sub < k.n_sub; ++sub) {
-            ST_UE(sub) = ue;
-            ST_UI(sub) = ui;
-            const XGrad xg = coulomb_grad(k, S, ue, ui, rho, inv_e, inv_i, kr, lcc_off);
-            ue += xg.X;
-            ui -= xg.X;
-            ST_U1(sub) = ue;
-            const float q = cool_energy<0>(k, S, c, cc, ue * inv_e, clamp);
-            float du = fminf(q, k.limiter * ue);
-            unsigned char br = q < k.limiter * ue ? 0 : 1;
-            if (k.mode == 1 && q > k.limiter * ue) {
-                float u1;
-                if (implicit_fp32<0>(k, S, c, cc, inv_e, ue, q, u1)) {
-                    du = ue - u1;
-                    br = 2;
-                    ST_US(sub) = u1;
-                }
+    // cells in chunks of 32 (one per lane): each warp's first chunk by its
+    // index in the grid, the next ones from the tile counter (k.sched) as
+    // it finishes, or round-robin without one
+    const int lane = threadIdx.x & 31;
+    const long long nchunks = (n + 31) / 32;
+    const long long first = (long long)gridDim.x * kWarps;
+    long long chunk = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    while (chunk < nchunks) {
+        const long long i = chunk * 32 + lane;
+        if (i < n) {
+            const float rho = rho_in[i], B = B_in[i], H = H_in[i];
+            float ue = ue_in[i], ui = ui_in[i];
+            const float ge_out = gue_out[i], gi_out = gui_out[i];
+            if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
+                !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
+                g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
+                goto next_chunk;
             }
-            ST_BR(sub) = br;
-            ue -= du;
-        }
-        // ---- reverse sweep ----
-        float ge = ge_out, gi = gi_out, grho = 0.f, gB = 0.f, gH = 0.f;
-        GCache gc;
-        gc.j = -1;
-        for (int sub = k.n_sub - 1; sub >= 0; --sub) {
-            float ge1;
-            const unsigned char br = ST_BR(sub);
-            if (br == 1) {
-                ge1 = (1.f - k.limiter) * ge;
-            } else {
-                const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
-                const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
-                const float qu = g.q * g.du / u;
-                float sc;
-                if (br == 2) {
-                    const float den = 1.f + qu;
-                    ge1 = ge / den;
-                    sc = -ge / den;
-                } else {
-                    ge1 = ge * (1.f - qu);
-                    sc = -ge;
-                }
-                grho += sc * g.q * g.drho / rho;
-                if (g.dB != 0.f) gB += sc * g.q * g.dB / B;
-                if (g.dH != 0.f) gH += sc * g.q * g.dH / H;
-                if (g_ls) {
-                    const float gs = sc * g.Gs;
-                    const float wts[2] = {1.f - g.wt, g.wt};
-                    const long long rowT = nT;
-                    // natural-layout row of corner (jh, jb, jn): rebuilt from the packed row offset
-                    const long long r0 = (long long)(c.row - T.lsb) / (8 * T.nblk);
-                    const long long rows[8] = {r0, r0 + 1, r0 + T.n[2], r0 + T.n[2] + 1,
-                                               r0 + (long long)T.n[1] * T.n[2], r0 + (long long)T.n[1] * T.n[2] + 1,
-                                               r0 + (long long)T.n[1] * T.n[2] + T.n[2],
-                                               r0 + (long long)T.n[1] * T.n[2] + T.n[2] + 1};
-                    const float wh[2] = {1.f - c.wh, c.wh}, wb[2] = {1.f - c.wb, c.wb}, wn[2] = {1.f - c.wn, c.wn};
-#pragma unroll
-                    for (int cidx = 0; cidx < 8; ++cidx) {
-                        const float wc = wh[cidx >> 2] * wb[(cidx >> 1) & 1] * wn[cidx & 1];
-#pragma unroll
-                        for (int t = 0; t < 2; ++t)
-                            atomicAdd(&g_ls[rows[cidx] * rowT + g.jt + t], gs * wc * wts[t]);
+            unsigned clamp = 0u;
+            const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
+            const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
+            CellC c;
+            CellD cd;
+            {
+                Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
+                Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
+                Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
+                const int rowf = 8 * T.nblk;
+                c.oN = rowf;
+                c.oB = rowf * T.n[2];
+                c.oH = c.oB * T.n[1];
+                c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
+                const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
+                c.wh = __saturatef(rh);
+                c.wb = __saturatef(rb);
+                c.wn = __saturatef(rn);
+                cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] / kLn2 : 0.f;
+                cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] / kLn2 : 0.f;
+                cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] / kLn2 : 0.f;
+                c.ls_off = k.l_hs_e;
+                c.lb_off = fmaf(2.f, lg2a(ne), k.l_hs_e);
+                c.lbb_off = k.l_bb - lg2a(Hc);
+                c.tau_sca = k.two_sigT * ne * Hc;
+            }
+            const float lcc_off = c.lb_off;
+            Cache cc;
+            cc.base = -8;
+            cc.win = win;
+            // ---- forward, recorded (the forward kernel's arithmetic) ----
+            for (int sub = 0; sub < k.n_sub; ++sub) {
+                ST_UE(sub) = ue;
+                ST_UI(sub) = ui;
+                const XGrad xg = coulomb_grad(k, S, ue, ui, rho, inv_e, inv_i, kr, lcc_off);
+                ue += xg.X;
+                ui -= xg.X;
+                ST_U1(sub) = ue;
+                const float q = cool_energy<0>(k, S, c, cc, ue * inv_e, clamp);
+                float du = fminf(q, k.limiter * ue);
+                unsigned char br = q < k.limiter * ue ? 0 : 1;
+                if (k.mode == 1 && q > k.limiter * ue) {
+                    float u1;
+                    if (implicit_fp32<0>(k, S, c, cc, inv_e, ue, q, u1)) {
+                        du = ue - u1;
+                        br = 2;
+                        ST_US(sub) = u1;
                     }
                 }
-                if (g_lb) {
-                    atomicAdd(&glb_s[g.jt], sc * g.Gb * (1.f - g.wt));
-                    atomicAdd(&glb_s[g.jt + 1], sc * g.Gb * g.wt);
+                ST_BR(sub) = br;
+                ue -= du;
+            }
+            // ---- reverse sweep ----
+            float ge = ge_out, gi = gi_out, grho = 0.f, gB = 0.f, gH = 0.f;
+            GCache gc;
+            gc.j = -1;
+            for (int sub = k.n_sub - 1; sub >= 0; --sub) {
+                float ge1;
+                const unsigned char br = ST_BR(sub);
+                if (br == 1) {
+                    ge1 = (1.f - k.limiter) * ge;
+                } else {
+                    const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
+                    const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
+                    const float qu = g.q * g.du / u;
+                    float sc;
+                    if (br == 2) {
+                        const float den = 1.f + qu;
+                        ge1 = ge / den;
+                        sc = -ge / den;
+                    } else {
+                        ge1 = ge * (1.f - qu);
+                        sc = -ge;
+                    }
+                    grho += sc * g.q * g.drho / rho;
+                    if (g.dB != 0.f) gB += sc * g.q * g.dB / B;
+                    if (g.dH != 0.f) gH += sc * g.q * g.dH / H;
+                    if (g_ls) {
+                        const float gs = sc * g.Gs;
+                        const float wts[2] = {1.f - g.wt, g.wt};
+                        const long long rowT = nT;
+                        // natural-layout row of corner (jh, jb, jn): rebuilt from the packed row offset
+                        const long long r0 = (long long)(c.row - T.lsb) / (8 * T.nblk);
+                        const long long rows[8] = {r0, r0 + 1, r0 + T.n[2], r0 + T.n[2] + 1,
+                                                   r0 + (long long)T.n[1] * T.n[2], r0 + (long long)T.n[1] * T.n[2] + 1,
+                                                   r0 + (long long)T.n[1] * T.n[2] + T.n[2],
+                                                   r0 + (long long)T.n[1] * T.n[2] + T.n[2] + 1};
+                        const float wh[2] = {1.f - c.wh, c.wh}, wb[2] = {1.f - c.wb, c.wb}, wn[2] = {1.f - c.wn, c.wn};
+    #pragma unroll
+                        for (int cidx = 0; cidx < 8; ++cidx) {
+                            const float wc = wh[cidx >> 2] * wb[(cidx >> 1) & 1] * wn[cidx & 1];
+    #pragma unroll
+                            for (int t = 0; t < 2; ++t)
+                                atomicAdd(&g_ls[rows[cidx] * rowT + g.jt + t], gs * wc * wts[t]);
+                        }
+                    }
+                    if (g_lb) {
+                        atomicAdd(&glb_s[g.jt], sc * g.Gb * (1.f - g.wt));
+                        atomicAdd(&glb_s[g.jt + 1], sc * g.Gb * g.wt);
+                    }
+                }
+                const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), rho, inv_e, inv_i, kr, lcc_off);
+                const float gX = ge1 - gi;
+                ge = ge1 + gX * xg.due;
+                gi = gi + gX * xg.dui;
+                grho += gX * xg.drho;
+                if (g_lc && !xg.clamped) {
+                    const float cl = gX * xg.X * kLn2;
+                    atomicAdd(&glc_s[xg.ji * nC + xg.je], cl * (1.f - xg.wi) * (1.f - xg.we));
+                    atomicAdd(&glc_s[xg.ji * nC + xg.je + 1], cl * (1.f - xg.wi) * xg.we);
+                    atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je], cl * xg.wi * (1.f - xg.we));
+                    atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je + 1], cl * xg.wi * xg.we);
                 }
             }
-            const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), rho, inv_e, inv_i, kr, lcc_off);
-            const float gX = ge1 - gi;
-            ge = ge1 + gX * xg.due;
-            gi = gi + gX * xg.dui;
-            grho += gX * xg.drho;
-            if (g_lc && !xg.clamped) {
-                const float cl = gX * xg.X * kLn2;
-                atomicAdd(&glc_s[xg.ji * nC + xg.je], cl * (1.f - xg.wi) * (1.f - xg.we));
-                atomicAdd(&glc_s[xg.ji * nC + xg.je + 1], cl * (1.f - xg.wi) * xg.we);
-                atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je], cl * xg.wi * (1.f - xg.we));
-                atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je + 1], cl * xg.wi * xg.we);
-            }
+            g_rho[i] = grho;
+            g_B[i] = gB;
+            g_H[i] = gH;
+            g_ue[i] = ge;
+            g_ui[i] = gi;
         }
-        g_rho[i] = grho;
-        g_B[i] = gB;
-        g_H[i] = gH;
-        g_ue[i] = ge;
-        g_ui[i] = gi;
+    next_chunk:
+        if (k.sched) {
+            unsigned long long nt = 0;
+            if (lane == 0) nt = atomicAdd(k.sched, 1ull);
+            chunk = first + (long long)__shfl_sync(0xffffffffu, nt, 0);
+        } else {
+            chunk += first;
+        }
     }
 #undef ST_UE
 #undef ST_UI
@@ -382,7 +399,7 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     StepK k;
     fill_stepk(t, p, k);
     const bool sms = p->n_sub <= kSmemSub;
-    size_t smem = (size_t)(smem_table_floats(k) + kMaxW * kThreads + t->dev.n[3] +
+    size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads + t->dev.n[3] +
                            ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
     if (sms) smem += (size_t)kSmemSub * kThreads * (4 * sizeof(float) + 1);
     auto fn = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
@@ -395,6 +412,14 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     long long work = (n + kThreads - 1) / kThreads;
     long long cap = (long long)sm_count() * per_sm;
     long long blocks = work < cap ? work : cap;
+    if ((n + 31) / 32 > blocks * kWarps) {
+        // more chunks than warps: the dynamic order
+        k.sched = sched_counter(st);
+        if (k.sched) {
+            e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return set_cuda_error(e);
+        }
+    }
     fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui, g_lb,
                                             g_ls, g_lc);
     e = cudaGetLastError();
