@@ -8,8 +8,10 @@ namespace {
 
 // COOL_PATH_TMA_SMEM: the vector kernel with its field staging done by the
 // TMA engine.  Each warp owns two staging buffers (5 fields x 128 cells) and
-// two mbarriers; while the warp steps tile i from one buffer, lane 0 has the
-// bulk copies of tile i + 1 (five 512-byte copies) landing in the other, so
+// two mbarriers; while the warp steps one tile from one buffer, lane 0 has
+// the bulk copies of its next tile (five 512-byte copies; the tile taken
+// from the tile counter when there is one, as in k_step_f32) landing in
+// the other, so
 // the fields of the next tile need no load instructions and no wait at the
 // start of the tile.  Outputs overwrite the inputs of their cell in the
 // buffer and leave by 128-bit streaming stores, as in k_step_f32.  The
@@ -59,8 +61,15 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long 
     if (lane == 0 && tw < ntiles) issue(tw, 0);
     uint32_t phase[2] = {0u, 0u};
     int b = 0;
-    for (; tw < ntiles; tw += step) {
-        const long long nx = tw + step;
+    while (tw < ntiles) {
+        // the next tile: from the tile counter (dynamic order, taken one
+        // tile ahead so that its copies overlap this tile) or round-robin
+        long long nx = tw + step;
+        if (k.sched) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(k.sched, 1ull);
+            nx = step + (long long)__shfl_sync(0xffffffffu, t, 0);
+        }
         if (lane == 0 && nx < ntiles) {
             mma::fence_async_smem();   // the other buffer's generic reads and writes are done (warp-synchronised)
             issue(nx, b ^ 1);
@@ -94,6 +103,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long 
         }
         __syncwarp();
         b ^= 1;
+        tw = nx;
     }
     const long long scalar_start = ntiles * kWarpCells;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -142,6 +152,14 @@ cool_status launch_step_tma(const cool_table* t, const cool_params* p, long long
     long long cp = (long long)sm_count() * per;
     long long bl = wk < cp ? wk : cp;
     if (bl < 1) bl = 1;
+    if (n / kWarpCells > bl * kWarps) {
+        // more tiles than warps: the dynamic order of the default step
+        k.sched = sched_counter(st);
+        if (k.sched) {
+            e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return set_cuda_error(e);
+        }
+    }
     fn<<<(int)bl, kThreads, sm_t, st>>>(k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt);
     e = cudaGetLastError();
     return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
