@@ -459,10 +459,9 @@ cool_status cool_debug_wait_timeout(int polls, unsigned* err, void* stream);
  * keys in the axis' physical unit (device arrays of n).  axis 0..4 (H, B,
  * n_e, T_e, Coulomb T), the exact rule: idx = the largest j in [0, N-2]
  * with node32[j] <= key (0 below the first node), w = log2(key / x_j) / dl
- * clamped to [0, 1].  axis 5..9: the rule the step uses on axes 0..4: the
- * same j and w except for keys within ~1e-7 of a node, where j may be the
- * neighbouring interval with w = 1 (or 0), so that j + w, the
- * interpolation position, agrees.  Asynchronous on stream. */
+ * clamped to [0, 1].  axis 5..9: the same selection as the step computes
+ * it on axes 0..4 (a guess from log2, confirmed by the weight, exact node
+ * compares near a node): the same idx and w.  Asynchronous on stream. */
 cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys,
                               int* idx, float* w, void* stream);
 

@@ -48,7 +48,8 @@ namespace {
 // only with themselves (__syncwarp), so a slow cell delays one warp, not the
 // block.  The remainder (and unaligned arrays) take a scalar loop.
 template <bool VEC, int FMT, int VAR>
-__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long long n, const float* __restrict__ rho,
+__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_constant__ StepK k, long long n,
+                                                                  const float* __restrict__ rho,
                                                          const float* __restrict__ Bf, const float* __restrict__ Hf,
                                                          const float* ue_in, const float* ui_in, float* ue_out,
                                                          float* ui_out, float* qc_out, float* qx_out,
@@ -80,18 +81,42 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
             t4[4 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ui_in) + q);
             if (VAR & 4) t4[5 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rr) + q);
             __syncwarp();
+            unsigned redo = 0u;   // cells with a key near a node, redone below
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                Out o = step_cell<FMT, VAR & 7>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
-                                            tile[3 * kWarpCells + j], tile[4 * kWarpCells + j],
-                                            (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
-                // inputs of cell j are consumed: outputs reuse its slots
-                tile[3 * kWarpCells + j] = o.ue;
-                tile[4 * kWarpCells + j] = o.ui;
-                tile[0 * kWarpCells + j] = o.qc;
-                tile[1 * kWarpCells + j] = o.qx;
-                if (VAR & 8) count_flags(o.flags, cnt);
+                const Out o = step_cell<FMT, VAR & 7, false>(k, S, win, tile[j], tile[kWarpCells + j],
+                                                             tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
+                                                             tile[4 * kWarpCells + j],
+                                                             (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
+                if (o.near) {
+                    redo |= 1u << c;   // its inputs stay in the tile
+                } else {
+                    // inputs of cell j are consumed: outputs reuse its slots
+                    tile[3 * kWarpCells + j] = o.ue;
+                    tile[4 * kWarpCells + j] = o.ui;
+                    tile[0 * kWarpCells + j] = o.qc;
+                    tile[1 * kWarpCells + j] = o.qx;
+                    if (VAR & 8) count_flags(o.flags, cnt);
+                }
+            }
+            if (__any_sync(0xffffffffu, redo != 0u)) {
+                // a few cells in a million: every index by node compares,
+                // kept out of the loop above so that it leaves its code alone
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    if (!((redo >> c) & 1u)) continue;
+                    const int j = c * 32 + lane;
+                    const Out o = step_cell<FMT, VAR & 7, true>(k, S, win, tile[j], tile[kWarpCells + j],
+                                                                tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
+                                                                tile[4 * kWarpCells + j],
+                                                                (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
+                    tile[3 * kWarpCells + j] = o.ue;
+                    tile[4 * kWarpCells + j] = o.ui;
+                    tile[0 * kWarpCells + j] = o.qc;
+                    tile[1 * kWarpCells + j] = o.qx;
+                    if (VAR & 8) count_flags(o.flags, cnt);
+                }
             }
             __syncwarp();
             __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
@@ -111,7 +136,9 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(StepK k, long 
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT, VAR & 7>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], (VAR & 4) ? rr[i] : 0.f);
+        const float ri = (VAR & 4) ? rr[i] : 0.f;
+        Out o = step_cell<FMT, VAR & 7, false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+        if (o.near) o = step_cell<FMT, VAR & 7, true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
@@ -189,8 +216,8 @@ __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const doub
     }
 }
 
-// axis 0..4: select_axis (the exact rule, the oracle's); 5..9: select_sub
-// on axes 0..4 (the step's rule)
+// axis 0..4: select_axis (node compares, the oracle's rule); 5..9:
+// select_sub on axes 0..4 (the same rule as the step computes it)
 __global__ void k_debug_lookup(StepK k, int axis, long long n, const float* keys, int* idx, float* w) {
     const DevTable& T = k.tab;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -204,13 +231,17 @@ __global__ void k_debug_lookup(StepK k, int axis, long long n, const float* keys
             const int a = axis - 5;
             const float* rx = T.axes + T.axis_off[a] + T.n[a];
             SelW s;
+            unsigned near = 0u;
             switch (a) {
-            case 0: s = select_sub<0>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
-            case 1: s = select_sub<1>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
-            case 2: s = select_sub<2>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
-            case 3: s = select_sub<3>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
-            default: s = select_sub<4>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp); break;
+            case 0: s = select_sub<0, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
+            case 1: s = select_sub<1, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
+            case 2: s = select_sub<2, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
+            case 3: s = select_sub<3, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
+            default: s = select_sub<4, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
             }
+            // near a node: node compares, as the step redoes such a cell (the
+            // EXACT form does not use the axis' constants, so A = 0 serves)
+            if (near) s = select_sub<0, true>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near);
             idx[i] = s.j;
             w[i] = s.w;
         }

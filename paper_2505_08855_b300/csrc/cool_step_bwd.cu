@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             Cache cc;
             cc.base = -8;
             cc.win = win;
+            cc.near = 0u;
             // ---- forward, recorded (the forward kernel's arithmetic) ----
             for (int sub = 0; sub < k.n_sub; ++sub) {
                 ST_UE(sub) = ue;
@@ -283,12 +284,12 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 ue += xg.X;
                 ui -= xg.X;
                 ST_U1(sub) = ue;
-                const float q = cool_energy<0>(k, S, c, cc, ue * inv_e, clamp);
+                const float q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
                 float du = fminf(q, k.limiter * ue);
                 unsigned char br = q < k.limiter * ue ? 0 : 1;
                 if (k.mode == 1 && q > k.limiter * ue) {
                     float u1;
-                    if (implicit_fp32<0>(k, S, c, cc, inv_e, ue, q, u1)) {
+                    if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
                         du = ue - u1;
                         br = 2;
                         ST_US(sub) = u1;

@@ -12,16 +12,20 @@ namespace {
 struct Out {
     float ue, ui, qc, qx;
     unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail, 6 floored
+    unsigned near;   // a key fell near a node: redo the cell with EXACT (select_sub)
 };
 
 // VAR: bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in,
 // bit 2 = disk geometry (radius r per cell: H_th from the state and the
 // temperature floor; Sec. 2.7, Sec. 3.2.3).  The explicit FP32 kernel carries
-// no solver code, no FP64 code and no geometry.
-template <int FMT, int VAR>
+// no solver code, no FP64 code and no geometry.  EXACT: every index by node
+// compares (select_axis); otherwise o.near asks for that when some key fell
+// near a node (see select_sub).
+template <int FMT, int VAR, bool EXACT>
 __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* win, float rho, float B,
                                          float H, float ue, float ui, float r) {
     Out o;
+    o.near = 0u;
     float t_floor = -1.f;   // gas temperature P/rho below which a sub-cycle does not cool
     if (VAR & 4) {
         if (k.h_from_state && isfinite(r) && r > 0.f && rho > 0.f && ue > 0.f && ui > 0.f) {
@@ -45,6 +49,10 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
     }
     unsigned clamp = 0u, stiff = 0u, band = 0u, fail = 0u, floored = 0u;
     const DevTable& T = k.tab;
+    Cache cc;
+    cc.base = -8;
+    cc.win = win;
+    cc.near = 0u;
     const float ne = rho * k.s_n;
     const float Bg = B * k.s_B;
     const float Hc = H * k.s_H;
@@ -53,9 +61,12 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
     const float kr = k.s_K / rho;
     CellC c;
     {
-        const SelW sh = select_sub<0>(k, S.ax + T.axis_off[0] + T.n[0], T.n[0], T.inv_dl[0], Hc, clamp);
-        const SelW sb = select_sub<1>(k, S.ax + T.axis_off[1] + T.n[1], T.n[1], T.inv_dl[1], Bg, clamp);
-        const SelW sn = select_sub<2>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne, clamp);
+        const SelW sh = select_sub<0, EXACT>(k, S.ax + T.axis_off[0] + T.n[0], T.n[0], T.inv_dl[0], Hc, clamp,
+                                             cc.near);
+        const SelW sb = select_sub<1, EXACT>(k, S.ax + T.axis_off[1] + T.n[1], T.n[1], T.inv_dl[1], Bg, clamp,
+                                             cc.near);
+        const SelW sn = select_sub<2, EXACT>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne, clamp,
+                                             cc.near);
         const int rowf = 8 * T.nblk;                       // floats per n_e row
         c.oN = rowf;
         c.oB = rowf * T.n[2];
@@ -73,16 +84,13 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
     const float lcc_off = c.lb_off;  // log2(h n_e^2 / e_scale)
     const int nC = T.n[4];
     const float* axC = S.ax + T.axis_off[4];
-    Cache cc;
-    cc.base = -8;
-    cc.win = win;
     float sum_q = 0.f, sum_x = 0.f;
     for (int sub = 0; sub < k.n_sub; ++sub) {
         // ---- (i) Coulomb exchange --------------------------------------------
         const float Te = ue * inv_e;
         const float Ti = ui * inv_i;
-        const SelW se = select_sub<4>(k, axC + nC, nC, T.inv_dl[4], Te, clamp);
-        const SelW si = select_sub<4>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp);
+        const SelW se = select_sub<4, EXACT>(k, axC + nC, nC, T.inv_dl[4], Te, clamp, cc.near);
+        const SelW si = select_sub<4, EXACT>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp, cc.near);
         const float we = se.w;
         const float wi = si.w;
         const int ls = k.lc_stride;
@@ -122,13 +130,13 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
             continue;
         }
         // ---- (ii) radiative cooling ----------------------------------------
-        const float q = cool_energy<FMT>(k, S, c, cc, ue * inv_e, clamp);
+        const float q = cool_energy<FMT, EXACT>(k, S, c, cc, ue * inv_e, clamp);
         float du = fminf(q, k.limiter * ue);
         if ((VAR & 1) && q > k.limiter * ue) {
             stiff = 1u;
             float u1;
             const bool ok = (VAR & 2) ? implicit_fp64_cell(k, T, rho, B, H, ue, u1)
-                                      : implicit_fp32<FMT>(k, S, c, cc, inv_e, ue, q, u1);
+                                      : implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u1);
             if (ok) du = ue - u1;
             else fail = 1u;
         }
@@ -137,6 +145,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
     }
     o.ue = ue; o.ui = ui; o.qc = sum_q; o.qx = sum_x;
     o.flags = clamp | (stiff << 2) | (band << 3) | (fail << 4) | (floored << 6);
+    o.near = EXACT ? 0u : cc.near;
     return o;
 }
 

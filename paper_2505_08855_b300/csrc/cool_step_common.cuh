@@ -129,8 +129,9 @@ struct StepK {
     float spin, h_floor;              // disk geometry (the disk step): a, (H/R)_floor
     int h_from_state;                 // H_th = c_s / Omega_K replaces the H field
     // select_sub constants per axis (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T):
-    // -log2(x_0)/dl - 1/2, n - 2, and the end nodes x_0, x_{n-1}
-    float g_c0[5], g_hi[5], g_x0[5], g_xn[5];
+    // -log2(x_0)/dl - 1/2, n - 2, the end nodes x_0, x_{n-1}, and the
+    // weight band 1/2 - 1e-6/dl outside which a key is treated as on a node
+    float g_c0[5], g_hi[5], g_x0[5], g_xn[5], g_wb[5];
     // tile counter of the vector step's dynamic tile order (zeroed on the
     // launch stream before the launch); nullptr: the static order
     unsigned long long* sched;
@@ -173,20 +174,30 @@ struct SelW {
     float w;   // interpolation weight r / dl, saturated to [0, 1]
 };
 
-// Index selection on axis A (0..4) as the step does it, with no node loads
-// besides 1/x_j.  The guess floor((log2 key - l_0)/dl) is taken
-// as round-to-nearest of the value shifted by -1/2 (the FP32 addition of
-// 1.5 * 2^23 rounds to an integer); lg2.approx puts it within one of the
-// true index, and wrong only for keys within ~1e-5 node spacings of a node.
-// Then r = log2(key / x_j) comes from the ratio, accurate to ~1e-7, and a
-// wrong guess shows as a weight outside [0, 1]: one step to the
-// neighbouring interval fixes it (a branch that lanes almost never take).
-// Either side of a node interpolates to the same value up to the accuracy
-// of r, so no exact node compares are needed for the values; the clamp flag
-// compares the key with the end nodes exactly in FP32, as select_axis does.
-template <int A>
+// Index selection on axis A (0..4) as the step does it.  EXACT: select_axis
+// (the largest j with x_j <= key in exact FP32 compares).  Otherwise the
+// same j and w without node loads besides 1/x_j, or the flag `near`: the
+// guess floor((log2 key - l_0)/dl) is taken as round-to-nearest of the value
+// shifted by -1/2 (the FP32 addition of 1.5 * 2^23 rounds to an integer);
+// lg2.approx puts it within one of the true index, and wrong only for keys
+// within ~1e-5 node spacings of a node.  Then r = log2(key / x_j) comes from
+// the ratio, accurate to ~2e-7 in log2: a weight inside the band
+// (1e-6/dl, 1 - 1e-6/dl) proves x_j < key < x_{j+1}, so j is the index.
+// Outside it (a key within ~1e-6 of a node, or a wrong guess: a few keys in
+// a million) `near` is set and the caller redoes the cell with EXACT; the
+// values returned meanwhile are those of the guessed interval.  The clamp
+// flag compares the key with the end nodes exactly, as select_axis does.
+template <int A, bool EXACT>
 __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int n, float inv_dl, float key,
-                                           unsigned& clamp) {
+                                           unsigned& clamp, unsigned& near) {
+    if (EXACT) {
+        const Sel e = select_axis(rx - n, n, inv_dl, key, clamp);
+        SelW s;
+        s.j = e.j;
+        s.r = e.r;
+        s.w = __saturatef(e.r * inv_dl);
+        return s;
+    }
     float t = fmaf(lg2a(key), inv_dl, k.g_c0[A]);
     t = fminf(fmaxf(t, 0.f), k.g_hi[A]);
     SelW s;
@@ -195,11 +206,7 @@ __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int 
     float w = s.r * inv_dl;
     const bool out = key < k.g_x0[A] || key > k.g_xn[A];
     clamp |= out ? 1u : 0u;
-    if (!out && fabsf(w - 0.5f) > 0.5f) {
-        s.j = min(max(s.j + (w < 0.5f ? -1 : 1), 0), n - 2);
-        s.r = lg2a(key * rx[s.j]);
-        w = s.r * inv_dl;
-    }
+    near |= (!out && fabsf(w - 0.5f) > k.g_wb[A]) ? 1u : 0u;
     s.w = __saturatef(w);
     return s;
 }
@@ -220,6 +227,7 @@ struct CellC {
 struct Cache {
     int base;           // first node of the held octet (multiple of 7), -8 if none
     float* win;         // this thread's window column
+    unsigned near;      // a key of this cell fell near a node (select_sub)
 };
 
 constexpr int kThreads = 256;
@@ -234,7 +242,6 @@ template <> struct Fmt<1> { static constexpr int W = 16, S = 15; };  // BF16
 template <> struct Fmt<2> { static constexpr int W = 16, S = 15; };  // FP16
 template <> struct Fmt<3> { static constexpr int W = 12, S = 11; };  // BF16, block-scaled
 template <> struct Fmt<4> { static constexpr int W = 12, S = 11; };  // FP16, block-scaled
-constexpr int kMaxW = 16;
 // nodes per block of a format, on the host (the window rows a kernel needs)
 constexpr int fmt_nodes(int fmt) { return fmt == 0 ? Fmt<0>::W : (fmt <= 2 ? Fmt<1>::W : Fmt<3>::W); }
 
@@ -331,12 +338,12 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
 // The common path has no range branches: 2^d underflows to 0 where one
 // channel is negligible and tau_abs to 0 where the cell is thin; only
 // tau_abs > 2^60 (where tau_abs^2 would overflow) takes the asymptotic form.
-template <int FMT>
+template <int FMT, bool EXACT>
 __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, const CellC& c,
                                              Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
     const float* axT = S.ax + k.tab.axis_off[3];
-    const SelW s = select_sub<3>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp);
+    const SelW s = select_sub<3, EXACT>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
     const int j = s.j;
     if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
     const int o = j - cc.base;
@@ -367,7 +374,7 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
 // linear over the 60 octaves, then on g(u) = u + q(u) - u0 in u once the
 // bracket is tight (FP32 x cannot resolve u to better than ~1e-6).  At most
 // implicit_iters evaluations.  Kept out of line: stiff cells are a minority.
-template <int FMT>
+template <int FMT, bool EXACT>
 __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
                                            float inv_e, float u0, float q0, float& u_out) {
     const float inv_u0 = 1.f / u0;
@@ -375,7 +382,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
     float xb = lg2a(u0);
     float xa = xb - 60.f;
     const float ua0 = ex2a(xa);
-    const float qa0 = cool_energy<FMT>(k, S, c, cc, ua0 * inv_e, trial);
+    const float qa0 = cool_energy<FMT, EXACT>(k, S, c, cc, ua0 * inv_e, trial);
     if (!(ua0 - u0 + qa0 < 0.f)) return false;
     float Gb = lg2a(fmaf(q0, inv_u0, 1.f));
     float Ga = lg2a((ua0 + qa0) * inv_u0);
@@ -385,7 +392,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
         float x = xb - Gb * (xb - xa) / (Gb - Ga);
         if (!(x > xa && x < xb)) x = 0.5f * (xa + xb);
         const float u = ex2a(x);
-        const float G = lg2a((u + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
+        const float G = lg2a((u + cool_energy<FMT, EXACT>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
         if (G > 0.f) {
             xb = x; Gb = G;
             if (side == 1) Ga *= 0.5f;
@@ -397,8 +404,8 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
         }
     }
     float a = ex2a(xa), b = ex2a(xb);
-    float ga = a - u0 + cool_energy<FMT>(k, S, c, cc, a * inv_e, trial);
-    float gb = b - u0 + cool_energy<FMT>(k, S, c, cc, b * inv_e, trial);
+    float ga = a - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, a * inv_e, trial);
+    float gb = b - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, b * inv_e, trial);
     // an end whose residual rounds to the wrong sign is the root to rounding
     float u = !(ga < 0.f) ? a : (!(gb > 0.f) ? b : 0.5f * (a + b));
     side = 0;
@@ -406,7 +413,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
         u = b - gb * (b - a) / (gb - ga);
         if (!(u > a && u < b)) u = 0.5f * (a + b);
         if (b - a <= 2.4e-7f * b) break;
-        const float g = u - u0 + cool_energy<FMT>(k, S, c, cc, u * inv_e, trial);
+        const float g = u - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, u * inv_e, trial);
         if (g > 0.f) {
             b = u; gb = g;
             if (side == 1) ga *= 0.5f;
@@ -515,6 +522,7 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
         k.g_hi[a] = (float)(n - 2);
         k.g_x0[a] = x[0];
         k.g_xn[a] = x[n - 1];
+        k.g_wb[a] = (float)(0.5 - 1e-6 * (double)t->dev.inv_dl[a]);
     }
     k.lc_stride = t->dev.n[4] | 1;
     k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * k.lc_stride;

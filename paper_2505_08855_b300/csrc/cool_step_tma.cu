@@ -21,7 +21,8 @@ namespace {
 __device__ unsigned g_tma_err;
 
 template <int FMT, int VAR>
-__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long long n, const float* __restrict__ rho,
+__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_constant__ StepK k, long long n,
+                                                                  const float* __restrict__ rho,
                                                          const float* __restrict__ Bf, const float* __restrict__ Hf,
                                                          const float* ue_in, const float* ui_in, float* ue_out,
                                                          float* ui_out, float* qc_out, float* qx_out,
@@ -84,16 +85,37 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long 
         float4* t4 = reinterpret_cast<float4*>(tile);
         const long long q = tw * 32 + lane;
         if (ok) {
+            unsigned redo = 0u;   // cells with a key near a node, redone below (as k_step_f32)
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                Out o = step_cell<FMT, VAR & 7>(k, S, win, tile[j], tile[kWarpCells + j], tile[2 * kWarpCells + j],
-                                            tile[3 * kWarpCells + j], tile[4 * kWarpCells + j], 0.f);
-                tile[3 * kWarpCells + j] = o.ue;
-                tile[4 * kWarpCells + j] = o.ui;
-                tile[0 * kWarpCells + j] = o.qc;
-                tile[1 * kWarpCells + j] = o.qx;
-                if (VAR & 8) count_flags(o.flags, cnt);
+                const Out o = step_cell<FMT, VAR & 7, false>(k, S, win, tile[j], tile[kWarpCells + j],
+                                                             tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
+                                                             tile[4 * kWarpCells + j], 0.f);
+                if (o.near) {
+                    redo |= 1u << c;
+                } else {
+                    tile[3 * kWarpCells + j] = o.ue;
+                    tile[4 * kWarpCells + j] = o.ui;
+                    tile[0 * kWarpCells + j] = o.qc;
+                    tile[1 * kWarpCells + j] = o.qx;
+                    if (VAR & 8) count_flags(o.flags, cnt);
+                }
+            }
+            if (__any_sync(0xffffffffu, redo != 0u)) {
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    if (!((redo >> c) & 1u)) continue;
+                    const int j = c * 32 + lane;
+                    const Out o = step_cell<FMT, VAR & 7, true>(k, S, win, tile[j], tile[kWarpCells + j],
+                                                                tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
+                                                                tile[4 * kWarpCells + j], 0.f);
+                    tile[3 * kWarpCells + j] = o.ue;
+                    tile[4 * kWarpCells + j] = o.ui;
+                    tile[0 * kWarpCells + j] = o.qc;
+                    tile[1 * kWarpCells + j] = o.qx;
+                    if (VAR & 8) count_flags(o.flags, cnt);
+                }
             }
             __syncwarp();
             __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
@@ -108,7 +130,8 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(StepK k, long 
     const long long scalar_start = ntiles * kWarpCells;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT, VAR & 7>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        Out o = step_cell<FMT, VAR & 7, false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        if (o.near) o = step_cell<FMT, VAR & 7, true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
