@@ -13,17 +13,24 @@
 //        through by tau_abs), energy q = h Q / e_scale removed from u_e:
 //        explicitly as min(q, limiter u_e) (Sec. 3.2.1 (i)), or in mode
 //        IMPLICIT for stiff cells (q > limiter u_e) by backward Euler
-//        u' = u_e - q(u'), bisection in log2 u (Sec. 3.2.1 (ii)).
+//        u' = u_e - q(u') (Sec. 3.2.1 (ii)): Illinois iterations in FP32, or
+//        bisection in log2 u in FP64 with fp64_critical.
 //
 // FP32 path design (B300):
 //   - fields are SoA; 16-byte aligned arrays are read and written with
-//     128-bit accesses, four cells per thread;
+//     128-bit accesses, staged per warp in tiles of 128 cells, which warps
+//     take in a dynamic order from a per-stream counter;
 //   - node arrays, the 1-D bremsstrahlung and the 2-D Coulomb channels live
-//     in shared memory (loaded once per persistent block);
-//   - the 4-D synchrotron channel stays in global memory (L2-resident): the
-//     step-invariant H, B, n_e axes are collapsed once per visited T_e
-//     interval (8 corners x 2 adjacent T_e values, T_e fastest in memory),
-//     so a sub-cycle that stays in its T_e interval reads no table memory;
+//     in shared memory (loaded once per persistent block; Coulomb rows at an
+//     odd stride against bank conflicts);
+//   - the 4-D synchrotron channel stays in global memory, L2-resident by its
+//     reuse: the step-invariant H, B, n_e axes are collapsed once per visited
+//     T_e block (8 corners x one 32-byte block of nodes, T_e fastest in
+//     memory, two L2 round trips), so a sub-cycle that stays in its block
+//     reads no table memory;
+//   - index selection without node loads (a log2 guess confirmed by its
+//     weight); the few cells with a key near a node are redone after their
+//     tile with node compares, so every index equals the node-compare rule;
 //   - the bridge is evaluated in log2 space so that no intermediate
 //     over/underflows FP32 over the table's 60-decade range.
 #include <string.h>
