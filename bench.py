@@ -61,10 +61,16 @@ KERNEL_SOURCES = ("cool_step.cu", "cool_step_cell.cuh", "cool_step_common.cuh")
 
 def kernel_source_sha():
     """sha256 (16 hex digits) over the files that hold the timed kernel's
-    device code (the step kernel and its shared device functions)."""
+    device code (the step kernel and its shared device functions), with
+    comments and trailing blanks removed: a change of wording does not
+    change the kernel."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2505_08855_b300", "csrc", name), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2505_08855_b300", "csrc", name)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = "\n".join(line.rstrip() for line in src.split("\n") if line.strip())
+        h.update(src.encode())
     return h.hexdigest()[:16]
 
 
