@@ -338,7 +338,9 @@ def run_suite_perf(args, torch, cool, inputs, dev):
                  ("explicit, texture path: point fetches + FP32 lerp", cool.F32, 0,
                   cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT), steps),
                  ("explicit, texture path: hardware trilinear filtering", cool.F32, 0,
-                  cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP), steps)]
+                  cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP), steps),
+                 ("explicit, the paper's layout: one 4-D table of Q_total (bridge folded in)", cool.F32, 0,
+                  cool.Params(n_sub=N_SUB, path=cool.PATH_QTOTAL), steps)]
         for name, dt, sc, p, k in cases:
             t = table(dt, sc)
             ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=ue_o, ui_out=ui_o), k, warm, stream)
@@ -349,6 +351,7 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         # the paper's table size (100 nodes per axis): 457 MB packed, far beyond L2
         big = cool.Table(cool.TableSpec(n=(100,) * 5))
         for name, path in (("paper-size 100^4 table, L2 block layout", cool.PATH_L2WINDOW),
+                           ("paper-size 100^4 table, the paper's layout (one Q_total table)", cool.PATH_QTOTAL),
                            ("paper-size 100^4 table, texture hardware filtering", cool.PATH_TEXTURE_HWLERP),
                            ("paper-size 100^4 table, texture point fetches", cool.PATH_TEXTURE_POINT)):
             p = cool.Params(n_sub=N_SUB, path=path)

@@ -72,14 +72,21 @@ typedef enum { COOL_EXPLICIT_LIMITED = 0, COOL_IMPLICIT_STIFF = 1 } cool_mode;
  * and FP32 interpolation in H.  TMA_SMEM: the L2WINDOW step with its field
  * staging done by bulk asynchronous copies into shared memory,
  * double-buffered per warp (FP32 fields, all arrays 16-byte aligned, else
- * COOL_EALIGN; same results as L2WINDOW).  SURROGATE: COOL_EUNSUPPORTED in
- * cool_step (the surrogate step is cool_surrogate_infer). */
+ * COOL_EALIGN; same results as L2WINDOW).  QTOTAL (the paper's table layout,
+ * Sec. 3.1; comparison path, explicit mode with FP32 fields and an FP32
+ * table only): one 4-D table of log2 Q_total, the bridge of Eqs. 11-12
+ * applied at each node to the table's brems and synchrotron values (made on
+ * first use, synchronously; cool_table_export channel 3), interpolated in
+ * place of the brems and synchrotron channels and the run-time bridge.
+ * SURROGATE: COOL_EUNSUPPORTED in cool_step (the surrogate step is
+ * cool_surrogate_infer). */
 typedef enum {
     COOL_PATH_L2WINDOW = 0,
     COOL_PATH_TMA_SMEM = 1,
     COOL_PATH_TEXTURE_POINT = 2,
     COOL_PATH_TEXTURE_HWLERP = 3,
-    COOL_PATH_SURROGATE = 4
+    COOL_PATH_SURROGATE = 4,
+    COOL_PATH_QTOTAL = 5
 } cool_path;
 
 /* Table specification.  Axis nodes are log-spaced with inclusive endpoints
@@ -116,7 +123,7 @@ typedef struct {
     double eq_band;           /* equilibrium band |T_e - T_i| <= eq_band T_i (0.1), where T_i - T_e cancels */
     double coulomb_clamp;     /* the exchange may move at most this fraction of the way to T_e = T_i (1) */
     int implicit_iters;       /* bisection halvings of the implicit solve, 1 .. 200 (60) */
-    cool_path path;           /* COOL_PATH_L2WINDOW (default), TMA_SMEM, TEXTURE_POINT, TEXTURE_HWLERP */
+    cool_path path;           /* COOL_PATH_L2WINDOW (default), TMA_SMEM, TEXTURE_POINT, TEXTURE_HWLERP, QTOTAL */
     int fp64_critical;        /* FP32 fields only.  0 (default): the Coulomb difference
                                  (gamma_i-1) u_i - (gamma_e-1) u_e is formed with an error-free FP32
                                  product transformation in every cell, and stiff cells are solved in
@@ -203,7 +210,9 @@ cool_status cool_table_get_spec(const cool_table* t, cool_table_spec* spec);
 
 /* Copy the FP64 log2 values of one channel to host memory.
  * channel 0: brems [n_Te]; 1: synchrotron [n_H*n_B*n_ne*n_Te]; 2: Coulomb
- * [n_Tc*n_Tc].  host_out must hold that many doubles.  Synchronous. */
+ * [n_Tc*n_Tc]; 3: the paper's layout, log2 Q_total [n_H*n_B*n_ne*n_Te]
+ * (FP32 tables; made on first use).  host_out must hold that many
+ * doubles.  Synchronous. */
 cool_status cool_table_export(const cool_table* t, int channel, double* host_out, long long count);
 
 /* FP32 node coordinates of one axis (0 H, 1 B, 2 n_e, 3 T_e, 4 Coulomb T)

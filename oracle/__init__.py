@@ -131,6 +131,8 @@ def _declare(L):
         "orc_cool_q_cell": (_d, [_P, _P, _P, _P, _i, _P, _d, _d, _d, _d]),
         "orc_step_pairs": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P,
                                 _P, _P, _P, _P, _P, _i]),
+        "orc_build_qtotal": (None, [_P, _P, _P, _P]),
+        "orc_step_qtotal": (_i, [_P, _P, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i]),
         "orc_step_bwd": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P,
                               _P, _P, _P, _P, _P, _P, _i]),
         "orc_step_surrogate": (_i, [_P, _P, _P, _P, _P, _d, _d, _P, _P, _d, _P, _i, _P, _ll,
@@ -371,6 +373,37 @@ def step_pairs(spec, lb, lsp, lc, params, rho, B, H, ue, ui, nthreads=0):
                               *[_ptr(a) for a in outs], _ptr(cnt), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"orc_step_pairs failed: {rc}")
+    return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
+
+
+def build_qtotal(spec, tables):
+    """The paper's table layout (Sec. 3.1): log2 Q_total on the 4-D grid,
+    the bridge of Eqs. 11-12 applied at each node to the table's brems and
+    synchrotron values (flat, the layout of tables['ls'])."""
+    s = spec.c()
+    ls = tables["ls"]
+    assert ls.flags.c_contiguous and ls.dtype == np.float64 and not np.isnan(ls).any()
+    ltot = np.zeros_like(ls)
+    lib().orc_build_qtotal(_ref(s), _ptr(tables["lb"]), _ptr(ls), _ptr(ltot))
+    return ltot
+
+
+def step_qtotal(spec, tables, ltot, params, rho, B, H, ue, ui, nthreads=0):
+    """The O2 step on the paper's layout: the cooling rate interpolated from
+    ltot (build_qtotal) instead of brems + synchrotron + run-time bridge;
+    the Coulomb exchange as step().  Returns the same tuple as step()."""
+    f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui)]
+    n = f[0].size
+    outs = [np.zeros(n) for _ in range(4)]
+    cnt = np.zeros(7, np.int64)
+    s = spec.c()
+    p = params.c()
+    lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
+    ltot = np.ascontiguousarray(ltot, dtype=np.float64)
+    rc = lib().orc_step_qtotal(_ref(s), _ptr(lc), _ptr(ltot), _ref(p), n, *[_ptr(a) for a in f],
+                               *[_ptr(a) for a in outs], _ptr(cnt), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_qtotal failed: {rc}")
     return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
 
 

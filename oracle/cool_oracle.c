@@ -412,6 +412,24 @@ void orc_build_syn(const orc_spec* s, double* ls, int nthreads) {
     }
 }
 
+/* The paper's table layout (Sec. 3.1): one 4-D table of the total rate,
+ * ltot[((h*nB+b)*nN+n)*nT+t] = log2 Q_total(H_h, B_b, n_n, T_t) with
+ * Q_total the bridge (Eqs. 11-12) of n_e^2 Q_brem/n_e^2 + eta Q_syn, from
+ * the table's own brems and synchrotron channels at the node. */
+void orc_build_qtotal(const orc_spec* s, const double* lb, const double* ls, double* ltot) {
+    const long long total = (long long)s->n[0] * s->n[1] * s->n[2] * s->n[3];
+    for (long long i = 0; i < total; ++i) {
+        long long r = i;
+        int t = (int)(r % s->n[3]); r /= s->n[3];
+        int n = (int)(r % s->n[2]); r /= s->n[2];
+        r /= s->n[1];
+        int h = (int)r;
+        double H = exp2(axis_l(s, 0, h)), ne = exp2(axis_l(s, 2, n)), T = exp2(axis_l(s, 3, t));
+        double qthin = ne * ne * exp2(lb[t]) + exp2(ls[i]);
+        ltot[i] = log2(orc_bridge(qthin, T, H, ne));
+    }
+}
+
 /* Selected synchrotron nodes only: idx[k] are flat indices into the 4-D
  * table; out[k] receives the node value. */
 void orc_build_syn_at(const orc_spec* s, long long m, const long long* idx, double* out, int nthreads) {
@@ -541,6 +559,7 @@ typedef struct {
     int direct;       /* 1: O1 rates from the formulas instead of the table */
     const double* lsp;  /* optional: per-interval node pairs of the 4-D channel */
     const struct orc_net* net;  /* optional: the surrogate network replaces the 4-D channel */
+    double* ltot;       /* optional: the paper's layout, log2 Q_total on the 4-D grid */
     orc_axis ax[5];
 } orc_rates;
 
@@ -657,6 +676,15 @@ static double interp4_pairs(const orc_spec* s, const double* lsp, const int* j, 
  * density ue, through T_e = s_Te ue/rho.  *clamp is or-ed with key clamping. */
 static double cool_q(const orc_rates* R, const cell_ctx* c, double ue, double rho, int* clamp) {
     double Te = c->sTe * ue / rho;
+    if (R->ltot) {
+        /* the paper's layout: the total rate (bridge included) interpolated */
+        int jt; double wt;
+        int cl = select_ax(&R->ax[3], Te, &jt, &wt);
+        if (clamp) *clamp |= cl;
+        int j[4] = {c->j[0], c->j[1], c->j[2], jt};
+        double w[4] = {c->w[0], c->w[1], c->w[2], wt};
+        return c->hs * exp2(interp4(R->s, R->ltot, 0, j, w)) / c->escale;
+    }
     double qthin;
     if (R->direct) {
         qthin = c->ne * c->ne * orc_brems(Te) + orc_eta_qsyn(c->Hcm, c->Bg, c->ne, Te, R->s, NULL);
@@ -827,6 +855,7 @@ static int step_impl(const orc_spec* s, const double* lb, double* ls, const doub
     if (!R) return -1;
     R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = lazy; R->direct = direct; R->lsp = lsp;
     R->net = net;
+    R->ltot = NULL;
     for (int a = 0; a < 5; ++a) {
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
         axis_init(s, a, &R->ax[a]);
@@ -857,6 +886,39 @@ int orc_step(const orc_spec* s, const double* lb, double* ls, const double* lc, 
              long long* counters, int nthreads) {
     return step_impl(s, lb, ls, lc, lazy, direct, NULL, NULL, NULL, NULL, p, n, rho, B, H, ue, ui, ue_out,
                      ui_out, qcool, qcc, counters, nthreads);
+}
+
+/* The step on the paper's table layout: ltot (orc_build_qtotal) in place of
+ * the brems and synchrotron channels and the run-time bridge. */
+int orc_step_qtotal(const orc_spec* s, const double* lc, double* ltot, const orc_params* p, long long n,
+                    const double* rho, const double* B, const double* H, const double* ue, const double* ui,
+                    double* ue_out, double* ui_out, double* qcool, double* qcc,
+                    long long* counters, int nthreads) {
+    orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
+    if (!R) return -1;
+    R->s = s; R->lb = NULL; R->ls = NULL; R->lc = lc; R->lazy = 0; R->direct = 0; R->lsp = NULL;
+    R->net = NULL;
+    R->ltot = ltot;
+    for (int a = 0; a < 5; ++a) {
+        if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
+        axis_init(s, a, &R->ax[a]);
+    }
+    long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+:cnt[:7]) if (nthreads != 1)
+#endif
+    for (long long i = 0; i < n; ++i) {
+        unsigned f;
+        double a, b;
+        step_cell(R, p, NULL, 0.0, rho[i], B[i], H[i], ue[i], ui[i], &a, &b, qcool ? &qcool[i] : NULL,
+                  qcc ? &qcc[i] : NULL, &f);
+        ue_out[i] = a; ui_out[i] = b;
+        for (int k = 0; k < 7; ++k) cnt[k] += (f >> k) & 1u;
+    }
+    if (counters) for (int k = 0; k < 7; ++k) counters[k] = cnt[k];
+    free(R);
+    return 0;
 }
 
 /* The step with the 4-D channel given as per-interval node pairs (the
@@ -921,6 +983,7 @@ double orc_cool_q_cell(const orc_spec* s, const double* lb, double* ls, const do
     if (!R) return NAN;
     R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = direct; R->lsp = NULL;
     R->net = NULL;
+    R->ltot = NULL;
     for (int a = 0; a < 5; ++a) axis_init(s, a, &R->ax[a]);
     cell_ctx c;
     cell_setup(R, p, rho, B, H, &c);
@@ -1239,6 +1302,7 @@ int orc_step_bwd(const orc_spec* s, const double* lb, double* ls, const double* 
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return -1;
     R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = 0; R->lsp = NULL; R->net = NULL;
+    R->ltot = NULL;
     for (int a = 0; a < 5; ++a) {
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }
         axis_init(s, a, &R->ax[a]);

@@ -17,8 +17,9 @@ from . import binding as _b
 
 F32, BF16, F16, F64 = _b.COOL_F32, _b.COOL_BF16, _b.COOL_F16, _b.COOL_F64
 EXPLICIT, IMPLICIT = _b.COOL_EXPLICIT_LIMITED, _b.COOL_IMPLICIT_STIFF
-PATH_L2WINDOW, PATH_TMA_SMEM, PATH_TEXTURE_POINT, PATH_TEXTURE_HWLERP = (
-    _b.COOL_PATH_L2WINDOW, _b.COOL_PATH_TMA_SMEM, _b.COOL_PATH_TEXTURE_POINT, _b.COOL_PATH_TEXTURE_HWLERP)
+PATH_L2WINDOW, PATH_TMA_SMEM, PATH_TEXTURE_POINT, PATH_TEXTURE_HWLERP, PATH_QTOTAL = (
+    _b.COOL_PATH_L2WINDOW, _b.COOL_PATH_TMA_SMEM, _b.COOL_PATH_TEXTURE_POINT, _b.COOL_PATH_TEXTURE_HWLERP,
+    _b.COOL_PATH_QTOTAL)
 CoolError = _b.CoolError
 
 # Axis order of the table: 0 H [cm], 1 |B| [G], 2 n_e [cm^-3], 3 T_e [K],
@@ -114,10 +115,11 @@ class Table:
         _b.check(_b.lib().cool_table_save(self.handle, path.encode()), "cool_table_save")
 
     def export(self, channel):
-        """FP64 log2 values of channel 0 (brems), 1 (synchrotron) or 2 (Coulomb) as numpy."""
+        """FP64 log2 values of channel 0 (brems), 1 (synchrotron), 2 (Coulomb)
+        or 3 (the paper's layout, log2 Q_total; made on first use) as numpy."""
         import numpy as np
         n = self.spec.n
-        count = {0: n[3], 1: n[0] * n[1] * n[2] * n[3], 2: n[4] * n[4]}[channel]
+        count = {0: n[3], 1: n[0] * n[1] * n[2] * n[3], 2: n[4] * n[4], 3: n[0] * n[1] * n[2] * n[3]}[channel]
         out = np.zeros(count, np.float64)
         _b.check(_b.lib().cool_table_export(self.handle, channel, out.ctypes.data_as(C.c_void_p),
                                             count), "cool_table_export")

@@ -16,7 +16,7 @@ COOL_OK, COOL_EINVAL, COOL_ENULL, COOL_EALIGN, COOL_ECUDA, COOL_ENOMEM, COOL_EST
 COOL_F32, COOL_BF16, COOL_F16, COOL_F64 = range(4)
 COOL_EXPLICIT_LIMITED, COOL_IMPLICIT_STIFF = 0, 1
 COOL_PATH_L2WINDOW, COOL_PATH_TMA_SMEM, COOL_PATH_TEXTURE_POINT, COOL_PATH_TEXTURE_HWLERP, \
-    COOL_PATH_SURROGATE = range(5)
+    COOL_PATH_SURROGATE, COOL_PATH_QTOTAL = range(6)
 
 # Every entry point declared in include/cool.h (checked by the CPU tests).
 EXPORTS = (

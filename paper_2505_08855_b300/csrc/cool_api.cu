@@ -89,11 +89,12 @@ cool_status validate_params(const cool_params* p) {
     if (!(p->coulomb_clamp > 0.0 && p->coulomb_clamp <= 1.0)) return COOL_EINVAL;
     if (p->implicit_iters < 1 || p->implicit_iters > 200) return COOL_EINVAL;
     if (p->path != COOL_PATH_L2WINDOW && p->path != COOL_PATH_TMA_SMEM && p->path != COOL_PATH_TEXTURE_POINT &&
-        p->path != COOL_PATH_TEXTURE_HWLERP)
+        p->path != COOL_PATH_TEXTURE_HWLERP && p->path != COOL_PATH_QTOTAL)
         return COOL_EUNSUPPORTED;
-    if ((p->path == COOL_PATH_TEXTURE_POINT || p->path == COOL_PATH_TEXTURE_HWLERP) &&
+    if ((p->path == COOL_PATH_TEXTURE_POINT || p->path == COOL_PATH_TEXTURE_HWLERP ||
+         p->path == COOL_PATH_QTOTAL) &&
         (p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical != 0))
-        return COOL_EUNSUPPORTED;   // the texture paths are explicit FP32 only
+        return COOL_EUNSUPPORTED;   // the texture and paper's-layout paths are explicit FP32 only
     if (p->fp64_critical != 0 && p->fp64_critical != 1) return COOL_EINVAL;
     return COOL_OK;
 }
@@ -168,6 +169,7 @@ cool_status table_textures(cool_table* t) {
     return COOL_OK;
 }
 
+
 namespace {
 
 __global__ void k_pack_f32(const double* src, float* dst, long long n) {
@@ -226,6 +228,7 @@ __global__ void k_pack_blocks(const double* src, uint32_t* dst, long long rows, 
     }
 }
 
+
 cool_status validate_spec(const cool_table_spec* s) {
     if (!s) return COOL_ENULL;
     int n[5] = {s->n_H, s->n_B, s->n_ne, s->n_Te, s->n_Tc};
@@ -264,7 +267,8 @@ void free_table_memory(cool_table* t) {
     if (t->tex_point) cudaDestroyTextureObject((cudaTextureObject_t)t->tex_point);
     if (t->tex_linear) cudaDestroyTextureObject((cudaTextureObject_t)t->tex_linear);
     if (t->tex_arr) cudaFreeArray(t->tex_arr);
-    void* dptrs[] = {t->d_axes, t->d_axes64, t->d_lb, t->d_ls, t->d_lc, t->d_lb64, t->d_ls64, t->d_lc64};
+    void* dptrs[] = {t->d_axes, t->d_axes64, t->d_lb, t->d_ls, t->d_lc, t->d_lb64, t->d_ls64, t->d_lc64,
+                     t->d_lt64, t->d_lst};
     for (void* p : dptrs)
         if (p) cudaFree(p);
     free(t->h_lb64);
@@ -412,6 +416,51 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
 const char kFileMagic[8] = {'C', 'O', 'O', 'L', 'T', 'A', 'B', '1'};
 
 }  // namespace
+
+// The paper's layout channel (COOL_PATH_QTOTAL) of an FP32 table, made once
+// (synchronous): log2 Q_total in FP64 on the device from the table's FP64
+// brems and synchrotron channels, then packed into FP32 blocks like the
+// synchrotron channel.
+cool_status table_qtotal(cool_table* t) {
+    std::lock_guard<std::mutex> g(g_tex_mu);
+    if (t->d_lst) return COOL_OK;
+    if (t->dev.fmt != 0) return COOL_EUNSUPPORTED;
+    const cool_table_spec& s = t->spec;
+    const long long cnt = syn_count(s);
+    double* lt = nullptr;
+    void* packed = nullptr;
+    cudaError_t e = cudaMalloc(&lt, sizeof(double) * cnt);
+    if (e == cudaSuccess) e = cudaMalloc(&packed, t->ls_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(lt);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? COOL_ENOMEM : set_cuda_error(e);
+    }
+    int off64[5], o = 0;
+    for (int a = 0; a < 5; ++a) { off64[a] = o; o += 2 * t->dev.n[a]; }
+    cool_status st = build_qtotal_fp64(s, (const double*)t->d_axes64, off64, (const double*)t->d_lb64,
+                                       (const double*)t->d_ls64, lt, 0);
+    if (st == COOL_OK) {
+        const long long rows = cnt / s.n_Te;
+        const long long total = rows * t->dev.nblk;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 8192) blocks = 8192;
+        k_pack_blocks<<<(int)blocks, 256>>>(lt, (uint32_t*)packed, rows, s.n_Te, t->dev.nblk, 0);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = set_cuda_error(e);
+    }
+    if (st != COOL_OK) {
+        cudaFree(lt);
+        cudaFree(packed);
+        return st;
+    }
+    t->d_lt64 = lt;
+    t->d_lst = packed;
+    t->dev.lst = (const uint32_t*)packed;
+    return COOL_OK;
+}
+
 }  // namespace cool
 
 using namespace cool;
@@ -544,6 +593,15 @@ cool_status cool_table_export(const cool_table* t, int channel, double* host_out
     case 0: src = t->h_lb64; n = t->spec.n_Te; break;
     case 1: src = t->h_ls64; n = syn_count(t->spec); break;
     case 2: src = t->h_lc64; n = (long long)t->spec.n_Tc * t->spec.n_Tc; break;
+    case 3: {
+        // the paper's layout (made on first use), copied from the device
+        n = syn_count(t->spec);
+        if (count != n) return COOL_EINVAL;
+        cool_status st = table_qtotal(const_cast<cool_table*>(t));
+        if (st != COOL_OK) return st;
+        cudaError_t e = cudaMemcpy(host_out, t->d_lt64, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+    }
     default: return COOL_EINVAL;
     }
     if (count != n) return COOL_EINVAL;
@@ -680,6 +738,11 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
         return launch_step_tex(t, p, n_cells, (const float*)rho, (const float*)B, (const float*)H,
                                (const float*)u_e_in, (const float*)u_i_in, (float*)u_e_out, (float*)u_i_out,
                                (float*)q_cool_out, (float*)q_cc_out, counters, s);
+    }
+    if (p->path == COOL_PATH_QTOTAL) {
+        if (field_dtype != COOL_F32 || t->spec.dtype != COOL_F32) return COOL_EUNSUPPORTED;
+        st = table_qtotal(const_cast<cool_table*>(t));
+        if (st != COOL_OK) return st;
     }
     if (field_dtype == COOL_F32)
         return launch_step_f32(t, p, n_cells, (const float*)rho, (const float*)B, (const float*)H,

@@ -366,6 +366,27 @@ __global__ void k_build_syn(BuildArgs a, long long first, long long count, doubl
     }
 }
 
+// The paper's table layout (Sec. 3.1): log2 Q_total at every node of the
+// 4-D grid, the bridge of Eqs. 11-12 (sigma_SB) applied at the node's
+// (H, n_e, T_e) to the table's own FP64 brems and synchrotron values.
+__global__ void k_build_qtotal(BuildArgs a, const double* lb64, const double* ls64, double* out) {
+    const long long total = (long long)a.n[0] * a.n[1] * a.n[2] * a.n[3];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += stride) {
+        long long r = i;
+        const int t = (int)(r % a.n[3]); r /= a.n[3];
+        const int n = (int)(r % a.n[2]); r /= a.n[2];
+        r /= a.n[1];
+        const int h = (int)r;
+        const double Hc = a.x64[a.off[0] + h], ne = a.x64[a.off[2] + n], T = a.x64[a.off[3] + t];
+        const double qthin = ne * ne * exp2(lb64[t]) + exp2(ls64[i]);
+        const double T2 = T * T;
+        const double tau_abs = Hc * qthin / (4.0 * kSigSB * T2 * T2);
+        const double tau_sca = 2.0 * ne * kSigT * Hc;
+        out[i] = log2(qthin / (1.0 + tau_abs * (1.7320508075688772 + 1.5 * (tau_abs + tau_sca))));
+    }
+}
+
 __global__ void k_build_small(BuildArgs a, double* lb, double* lc) {
     int tid = blockIdx.x * blockDim.x + threadIdx.x;
     int nT = a.n[3], nC = a.n[4];
@@ -460,6 +481,25 @@ cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64
     return COOL_OK;
 }
 
+
+cool_status build_qtotal_fp64(const cool_table_spec& s, const double* d_axes64, const int* axis_off64,
+                              const double* d_lb64, const double* d_ls64, double* d_lt64, cudaStream_t st) {
+    BuildArgs a;
+    a.x64 = d_axes64;
+    int n[5] = {s.n_H, s.n_B, s.n_ne, s.n_Te, s.n_Tc};
+    for (int i = 0; i < 5; ++i) { a.off[i] = axis_off64[i]; a.n[i] = n[i]; }
+    a.k2_switch_T = s.k2_switch_T;
+    a.lnLambda = s.lnLambda;
+    a.theta_i_uses_mp = s.theta_i_uses_mp;
+    a.compton_literal = s.compton_literal;
+    const long long total = syn_count(s);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_build_qtotal<<<(int)blocks, 256, 0, st>>>(a, d_lb64, d_ls64, d_lt64);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+}
 
 cool_status launch_step_direct(const cool_table_spec& phys, const cool_params* p, long long n, const double* rho,
                                const double* B, const double* H, const double* ue, const double* ui, double* ue_o,

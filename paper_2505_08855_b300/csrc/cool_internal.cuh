@@ -51,6 +51,9 @@ struct DevTable {
     //   fmt 3/4 (BF16/FP16 block-scaled): float off, float scale, 12 16-bit
     //                          residuals r, value = off + scale r,   W = 12, S = 11
     const uint32_t* lsb;
+    // the paper's layout (COOL_PATH_QTOTAL, made on first use): log2 Q_total
+    // on the same grid, packed as fmt 0 blocks in the same row order
+    const uint32_t* lst;
     int fmt;
     int blk_stride;         // S
     int nblk;               // ceil((nT - 1) / S)
@@ -85,6 +88,10 @@ struct cool_table {
     // objects on it, point sampling and hardware linear filtering
     cudaArray_t tex_arr;
     unsigned long long tex_point, tex_linear;
+    // the paper's-layout channel (COOL_PATH_QTOTAL): FP64 natural layout and
+    // packed FP32 blocks, made on first use
+    void* d_lt64;
+    void* d_lst;
 };
 
 constexpr uint32_t kTableMagic = 0xC0011AB1u;
@@ -106,6 +113,13 @@ long long syn_count(const cool_table_spec& s);
 cool_status build_channels_fp64(const cool_table_spec& s, const double* d_axes64,
                                 const int* axis_off64, double* d_lb64, double* d_ls64,
                                 double* d_lc64, cudaStream_t st);
+// The paper's layout: log2 Q_total on the 4-D grid from the FP64 brems and
+// synchrotron channels (synchronous on st).
+cool_status build_qtotal_fp64(const cool_table_spec& s, const double* d_axes64, const int* axis_off64,
+                              const double* d_lb64, const double* d_ls64, double* d_lt64, cudaStream_t st);
+// Build (once, synchronously) and pack the paper's-layout channel of an FP32
+// table: t->d_lt64 (FP64, natural layout) and t->dev.lst (packed blocks).
+cool_status table_qtotal(cool_table* t);
 
 // Surrogate training samples (cool_build.cu): x [n][4] normalised coordinates,
 // y [n] log2(eta Q_syn) from the formulas; even samples sit on table nodes.

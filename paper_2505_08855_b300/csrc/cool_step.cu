@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                const Out o = step_cell<FMT, VAR & 7, false>(k, S, win, tile[j], tile[kWarpCells + j],
+                const Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, tile[j], tile[kWarpCells + j],
                                                              tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                              tile[4 * kWarpCells + j],
                                                              (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                 for (int c = 0; c < 4; ++c) {
                     if (!((redo >> c) & 1u)) continue;
                     const int j = c * 32 + lane;
-                    const Out o = step_cell<FMT, VAR & 7, true>(k, S, win, tile[j], tile[kWarpCells + j],
+                    const Out o = step_cell<FMT, (VAR & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
                                                                 tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                                 tile[4 * kWarpCells + j],
                                                                 (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float ri = (VAR & 4) ? rr[i] : 0.f;
-        Out o = step_cell<FMT, VAR & 7, false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
-        if (o.near) o = step_cell<FMT, VAR & 7, true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+        Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+        if (o.near) o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
@@ -294,9 +294,16 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     static const KFn disk_v[8] = {COOL_KD(true)};
     static const KFn disk_s[8] = {COOL_KD(false)};
 #undef COOL_KD
+    // the paper's table layout (template bit 4): explicit, FP32 table, no geometry
+    static const KFn tot_v[2] = {k_step_f32<true, 0, 16>, k_step_f32<true, 0, 24>};
+    static const KFn tot_s[2] = {k_step_f32<false, 0, 16>, k_step_f32<false, 0, 24>};
     if (disk && (fmt != 0 || !r)) return COOL_EUNSUPPORTED;
+    const bool tot = p->path == COOL_PATH_QTOTAL;
+    if (tot && (disk || fmt != 0 || p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical || !t->dev.lst))
+        return COOL_EUNSUPPORTED;
     const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0) | (cnt ? 4 : 0);
-    KFn fn = disk ? (vec ? disk_v[var] : disk_s[var]) : (vec ? table_v[fmt][var] : table_s[fmt][var]);
+    KFn fn = tot ? (vec ? tot_v[cnt ? 1 : 0] : tot_s[cnt ? 1 : 0])
+                 : disk ? (vec ? disk_v[var] : disk_s[var]) : (vec ? table_v[fmt][var] : table_s[fmt][var]);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;

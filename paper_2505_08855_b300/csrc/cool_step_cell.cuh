@@ -17,7 +17,8 @@ struct Out {
 
 // VAR: bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in,
 // bit 2 = disk geometry (radius r per cell: H_th from the state and the
-// temperature floor; Sec. 2.7, Sec. 3.2.3).  The explicit FP32 kernel carries
+// temperature floor; Sec. 2.7, Sec. 3.2.3), bit 4 = the paper's table layout
+// (COOL_PATH_QTOTAL: explicit, FP32 table, no geometry).  The explicit FP32 kernel carries
 // no solver code, no FP64 code and no geometry.  EXACT: every index by node
 // compares (select_axis); otherwise o.near asks for that when some key fell
 // near a node (see select_sub).
@@ -71,7 +72,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         c.oN = rowf;
         c.oB = rowf * T.n[2];
         c.oH = c.oB * T.n[1];
-        c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
+        c.row = ((VAR & 16) ? T.lst : T.lsb) + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
         c.wh = sh.w;
         c.wb = sb.w;
         c.wn = sn.w;
@@ -130,7 +131,8 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
             continue;
         }
         // ---- (ii) radiative cooling ----------------------------------------
-        const float q = cool_energy<FMT, EXACT>(k, S, c, cc, ue * inv_e, clamp);
+        const float q = (VAR & 16) ? cool_energy_total<EXACT>(k, S, c, cc, ue * inv_e, clamp)
+                                   : cool_energy<FMT, EXACT>(k, S, c, cc, ue * inv_e, clamp);
         float du = fminf(q, k.limiter * ue);
         if ((VAR & 1) && q > k.limiter * ue) {
             stiff = 1u;

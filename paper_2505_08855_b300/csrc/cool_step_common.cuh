@@ -367,6 +367,22 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     return ex2a(fminf(lq, 126.f));
 }
 
+// The same energy on the paper's table layout (Sec. 3.1): the total rate,
+// bridge included, interpolated from one 4-D table (c.row points into it):
+// q = 2^(L + log2(h / e_scale)).  FP32 table format only.
+template <bool EXACT>
+__device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
+                                                   float Te, unsigned& clamp) {
+    const int nT = k.tab.n[3];
+    const float* axT = S.ax + k.tab.axis_off[3];
+    const SelW s = select_sub<3, EXACT>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
+    const int j = s.j;
+    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<0>::S - 1)) gather<0>(c, j / Fmt<0>::S, cc);
+    const int o = j - cc.base;
+    const float L = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], s.w) + c.ls_off;
+    return ex2a(fminf(L, 126.f));
+}
+
 // Backward Euler u' = u0 - q(u') of a stiff cell (q(u0) > limiter u0) in
 // FP32.  Bracket [u0 2^-60, u0]: g(u0) = q(u0) > 0 and g(u0 2^-60) < 0 is
 // checked (false when it fails).  Illinois (modified regula falsi) first on

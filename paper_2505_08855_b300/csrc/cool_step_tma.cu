@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
-                const Out o = step_cell<FMT, VAR & 7, false>(k, S, win, tile[j], tile[kWarpCells + j],
+                const Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, tile[j], tile[kWarpCells + j],
                                                              tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                              tile[4 * kWarpCells + j], 0.f);
                 if (o.near) {
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
                 for (int c = 0; c < 4; ++c) {
                     if (!((redo >> c) & 1u)) continue;
                     const int j = c * 32 + lane;
-                    const Out o = step_cell<FMT, VAR & 7, true>(k, S, win, tile[j], tile[kWarpCells + j],
+                    const Out o = step_cell<FMT, (VAR & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
                                                                 tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                                 tile[4 * kWarpCells + j], 0.f);
                     tile[3 * kWarpCells + j] = o.ue;
@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
     const long long scalar_start = ntiles * kWarpCells;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Out o = step_cell<FMT, VAR & 7, false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
-        if (o.near) o = step_cell<FMT, VAR & 7, true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        if (o.near) o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;

@@ -123,6 +123,32 @@ def test_formats_on_the_shell(env, oracle):
     assert storage["BF16 row-scaled"] < storage["BF16"] and storage["FP16 row-scaled"] < storage["FP16"]
 
 
+def test_paper_layout_on_the_shell(env, oracle):
+    """The paper's table layout (one 4-D table of Q_total, the bridge folded
+    in at the nodes) against the factored layout (brems, synchrotron, bridge
+    at run time), both from the FP32 table, at the sampled cells against the
+    direct formulas (O1): what interpolating the bridged rate costs."""
+    cool, F, idx, sub, ospec, lazy, o1, o2 = env
+    n = F["rho"].size
+    tf = {k: torch.from_numpy(v).cuda() for k, v in F.items()}
+    t = cool.Table(cool.TableSpec(n=N5))
+    ti = torch.from_numpy(idx).cuda()
+    res = {}
+    for name, path in (("factored layout", cool.PATH_L2WINDOW), ("paper's layout (Q_total table)",
+                                                                 cool.PATH_QTOTAL)):
+        ue, ui, qc, cnt, ms = _gpu_step(cool, t, cool.Params(n_sub=8, path=path), tf)
+        got = [a[ti].cpu().numpy().astype(np.float64) for a in (ue, ui, qc)]
+        res[name] = _errs(got, o1, sub["ue"])
+        report({"suite": "precision", "case": f"FP32 table, explicit, {name}", "workload": "shell_448x192x192",
+                "cells": n, "ms_per_step": ms, "cell_updates_per_s": n / (ms * 1e-3), "vs_O1": res[name],
+                "sample": SAMPLE})
+    # both are the same method up to where the interpolation happens: their
+    # errors against O1 are of the same order (the table's interpolation error)
+    a, b = res["factored layout"]["u_e"], res["paper's layout (Q_total table)"]["u_e"]
+    assert b["median"] <= 10 * a["median"] + 1e-5 and a["median"] <= 10 * b["median"] + 1e-5
+    t.free()
+
+
 def test_fp64_options_on_the_shell(env, oracle):
     cool, F, idx, sub, ospec, lazy, o1, o2 = env
     n = F["rho"].size
