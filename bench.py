@@ -78,11 +78,13 @@ def traffic_per_launch():
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (kernel_source_sha); else None."""
     sha = kernel_source_sha()
-    for f in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
         if not f.endswith(".md"):
             continue
-        txt = open(os.path.join(ROOT, "profiles", f)).read()
-        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256_16:\s*([0-9a-f]+)\s+workload:\s*(\S+)", txt)
+        txt = open(os.path.join(pdir, f)).read()
+        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256_16:\s*([0-9a-f]+)"
+                      r"\s+workload:\s*(\S+)", txt)
         if m and m.group(2) == sha and m.group(3) == WORKLOAD:
             return float(m.group(1))
     return None

@@ -24,7 +24,8 @@ EXPORTS = (
     "cool_build_table", "cool_table_free", "cool_table_l2_persist", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
     "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
-    "cool_debug_gemm_bf16", "cool_debug_wait_timeout", "cool_fit_spec_default", "cool_surrogate_fit", "cool_surrogate_free",
+    "cool_debug_gemm_bf16", "cool_debug_wait_timeout", "cool_fit_spec_default", "cool_surrogate_fit",
+    "cool_surrogate_free",
     "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
     "cool_surrogate_eval", "cool_surrogate_mask", "cool_surrogate_set_mask", "cool_surrogate_infer",
     "cool_step_direct", "cool_step_host", "cool_radiation_te", "cool_step_disk",
