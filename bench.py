@@ -90,6 +90,24 @@ def traffic_per_launch():
     return None
 
 
+def ncu_utilisation():
+    """Utilisation of the units that bind the step kernel, from the committed
+    ncu summary of the current kernel sources (same keying as
+    traffic_per_launch): {"l1_data_pipe": f, "issue_active": f} as fractions
+    of their peaks, or None."""
+    sha = kernel_source_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not f.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, f)).read()
+        m = re.search(r"ncu_utilisation:\s*l1_data_pipe\s+([0-9.]+)\s+issue_active\s+([0-9.]+)"
+                      r"\s+source_sha256_16:\s*([0-9a-f]+)\s+workload:\s*(\S+)", txt)
+        if m and m.group(3) == sha and m.group(4) == WORKLOAD:
+            return {"l1_data_pipe": float(m.group(1)), "issue_active": float(m.group(2))}
+    return None
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -635,7 +653,9 @@ def main():
     achieved = BYTES_PER_CELL * n / (ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_per_launch(), "peak_source": peak_kind,
-            "kernel": "k_step_f32<true>", "bytes_per_cell": BYTES_PER_CELL}
+            "kernel": "k_step_f32<true>", "bytes_per_cell": BYTES_PER_CELL,
+            # what binds instead of HBM (ncu, fractions of each unit's peak)
+            "ncu_utilisation": ncu_utilisation()}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
