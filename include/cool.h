@@ -237,10 +237,16 @@ cool_status cool_table_save(const cool_table* t, const char* path);
 cool_status cool_table_load(const char* path, void* stream, cool_table** out);
 
 /* One cooling step over n_cells cells (Sec. 3.2): per cell, N_sub sub-cycles
- * of (i) Coulomb exchange (Eq. 16; FP64 inside the equilibrium band) and
- * (ii) radiative cooling from the table with the bridge of Eq. 11, applied
- * to u_e explicitly (min(h Q, limiter_frac u_e)) or, in mode IMPLICIT for
- * stiff cells (h Q > limiter_frac u_e), by backward Euler.
+ * of (i) Coulomb exchange (Eq. 16; the cancelling difference of T_i and T_e
+ * formed exactly in FP32, or FP64 inside the equilibrium band with
+ * fp64_critical) and (ii) radiative cooling from the table with the bridge
+ * of Eq. 11, applied to u_e explicitly (min(h Q, limiter_frac u_e)) or, in
+ * mode IMPLICIT for stiff cells (h Q > limiter_frac u_e), by backward Euler.
+ * FP32 fields: every table index equals the node-compare rule of
+ * cool_debug_lookup (axes 0..4); the step zeroes an 8-byte tile counter of
+ * `stream` before its kernel (one per device and stream, allocated on first
+ * use outside stream capture; a capture with none yet uses a fixed tile
+ * order, with the same results).
  *   field_dtype: COOL_F32 or COOL_F64 (all seven field arrays of that type).
  *   rho, B, H, u_e_in, u_i_in: device inputs, n_cells each.
  *   u_e_out, u_i_out: device outputs (may alias u_e_in / u_i_in).
