@@ -168,6 +168,7 @@ __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const doub
         } else {
             const DevTable& T = k.tab;
             Cell64 c;
+            c.jt = -1;
             c.ne = r * k.s_n;
             c.Hc = H * k.s_H;
             c.jh = select64(T, 0, c.Hc, c.wh, clamp);
@@ -194,19 +195,12 @@ __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const doub
                 double du;
                 if (k.mode == 1 && q > k.limiter * ue) {
                     stiff = 1u;
-                    double a = log2(ue) - 60.0, b = log2(ue);
-                    unsigned dummy = 0u;
-                    double ga = exp2(a) - ue + cool_q64(k, c, exp2(a), r, dummy);
-                    if (!(ga < 0.0)) {
+                    double u1;
+                    if (implicit_fp64(k, c, r, ue, u1)) {
+                        du = ue - u1;
+                    } else {
                         fail = 1u;
                         du = k.limiter * ue;
-                    } else {
-                        for (int it = 0; it < k.iters; ++it) {
-                            double m = 0.5 * (a + b);
-                            double um = exp2(m);
-                            if (um - ue + cool_q64(k, c, um, r, dummy) > 0.0) b = m; else a = m;
-                        }
-                        du = ue - exp2(0.5 * (a + b));
                     }
                 } else {
                     du = q < k.limiter * ue ? q : k.limiter * ue;

@@ -68,22 +68,33 @@ __device__ int select64(const DevTable& T, int a, double key, double& w, unsigne
 struct Cell64 {
     int jh, jb, jn;
     double wh, wb, wn, ne, Hc;
+    int jt;             // T_e interval of the cached collapse, -1 if none
+    double v0, v1;      // synchrotron log2 values at its two nodes, collapsed over H, B, n_e
 };
 
-__device__ double cool_q64(const StepK64& k, const Cell64& c, double ue, double rho, unsigned& clamp) {
+__device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, unsigned& clamp) {
     const DevTable& T = k.tab;
     double Te = k.s_Te * ue / rho;
     double wt;
     int jt = select64(T, 3, Te, wt, clamp);
-    const int nB = T.n[1], nN = T.n[2], nT = T.n[3];
-    double ls = 0.0;
-    for (int cidx = 0; cidx < 16; ++cidx) {
-        int bh = cidx & 1, bb = (cidx >> 1) & 1, bn = (cidx >> 2) & 1, bt = (cidx >> 3) & 1;
-        double wgt = (bh ? c.wh : 1.0 - c.wh) * (bb ? c.wb : 1.0 - c.wb) * (bn ? c.wn : 1.0 - c.wn) *
-                     (bt ? wt : 1.0 - wt);
-        long long idx = (((long long)(c.jh + bh) * nB + (c.jb + bb)) * nN + (c.jn + bn)) * nT + jt + bt;
-        ls += wgt * T.ls64[idx];
+    if (jt != c.jt) {
+        // the 8 (H, B, n_e) corners at the interval's two T_e nodes, collapsed
+        // once per visited interval (an implicit solve evaluates many T_e in few
+        // intervals)
+        const int nB = T.n[1], nN = T.n[2], nT = T.n[3];
+        double v0 = 0.0, v1 = 0.0;
+        for (int cidx = 0; cidx < 8; ++cidx) {
+            const int bh = cidx & 1, bb = (cidx >> 1) & 1, bn = (cidx >> 2) & 1;
+            const double wgt = (bh ? c.wh : 1.0 - c.wh) * (bb ? c.wb : 1.0 - c.wb) * (bn ? c.wn : 1.0 - c.wn);
+            const long long idx = (((long long)(c.jh + bh) * nB + (c.jb + bb)) * nN + (c.jn + bn)) * nT + jt;
+            v0 += wgt * T.ls64[idx];
+            v1 += wgt * T.ls64[idx + 1];
+        }
+        c.jt = jt;
+        c.v0 = v0;
+        c.v1 = v1;
     }
+    double ls = (1.0 - wt) * c.v0 + wt * c.v1;
     double lb = (1.0 - wt) * T.lb64[jt] + wt * T.lb64[jt + 1];
     double qthin = c.ne * c.ne * exp2(lb) + exp2(ls);
     double bb4 = 4.0 * kSigSB * Te * Te * Te * Te;
@@ -93,19 +104,50 @@ __device__ double cool_q64(const StepK64& k, const Cell64& c, double ue, double 
     return k.hs * Q / k.escale;
 }
 
-// Backward Euler of a stiff cell in FP64 on the FP64 table: bisection in
-// log2 u over [u0 2^-60, u0] (iters halvings).  Returns false when the
-// bracket has no sign change.
-__device__ __noinline__ bool implicit_fp64(const StepK64& k, const Cell64& c, double rho, double u0, double& u_out) {
+// Backward Euler of a stiff cell in FP64 on the FP64 table: the root of
+// g(x) = 2^x - u0 + q(2^x), x = log2 u, in the bracket [log2 u0 - 60,
+// log2 u0] (g < 0 at its low end is checked, g = q(u0) > 0 at its high end).
+// Illinois iterations (regula falsi with the value at the retained end
+// halved) first on G(x) = log2((2^x + q(2^x)) / u0), which is close to
+// piecewise linear over the 60 octaves, then on g itself once the bracket
+// is 1e-3 wide, until it is 1e-15 max(1, |x|) wide: the root the oracle's
+// bisection finds, to FP64 precision, in ~20 evaluations instead of 60; at
+// most iters evaluations.  Returns false when the bracket has no sign change.
+__device__ __noinline__ bool implicit_fp64(const StepK64& k, Cell64& c, double rho, double u0, double& u_out) {
     unsigned dummy = 0u;
-    double a = log2(u0) - 60.0, b = log2(u0);
-    if (!(exp2(a) - u0 + cool_q64(k, c, exp2(a), rho, dummy) < 0.0)) return false;
-    for (int it = 0; it < k.iters; ++it) {
-        double m = 0.5 * (a + b);
-        double um = exp2(m);
-        if (um - u0 + cool_q64(k, c, um, rho, dummy) > 0.0) b = m; else a = m;
+    double xa = log2(u0) - 60.0, xb = log2(u0);
+    double ua = exp2(xa), ub = exp2(xb);
+    double qa = cool_q64(k, c, ua, rho, dummy), qb = cool_q64(k, c, ub, rho, dummy);
+    if (!(ua - u0 + qa < 0.0) || !(ub - u0 + qb > 0.0)) return false;
+    int it = 2;
+    for (int phase = 0; phase < 2; ++phase) {
+        // phase 0: G in log space; phase 1: g in u
+        double fa = phase == 0 ? log2((ua + qa) / u0) : ua - u0 + qa;
+        double fb = phase == 0 ? log2((ub + qb) / u0) : ub - u0 + qb;
+        int side = 0;
+        for (; it < k.iters; ++it) {
+            const double width = xb - xa;
+            if (phase == 0 ? width <= 1e-3 : width <= 1e-15 * fmax(1.0, fabs(xb))) break;
+            double x = xb - fb * width / (fb - fa);
+            if (!(x > xa && x < xb)) x = 0.5 * (xa + xb);
+            const double u = exp2(x);
+            const double q = cool_q64(k, c, u, rho, dummy);
+            const double f = phase == 0 ? log2((u + q) / u0) : u - u0 + q;
+            if (f > 0.0) {
+                xb = x; ub = u; qb = q; fb = f;
+                if (side > 0) fa *= 0.5;
+                side = 1;
+            } else if (f < 0.0) {
+                xa = x; ua = u; qa = q; fa = f;
+                if (side < 0) fb *= 0.5;
+                side = -1;
+            } else {
+                xa = xb = x;
+                break;
+            }
+        }
     }
-    u_out = exp2(0.5 * (a + b));
+    u_out = exp2(0.5 * (xa + xb));
     return true;
 }
 
@@ -447,11 +489,12 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
 }
 
 // The same solve in FP64 on the FP64 table (fp64_critical): the cell's H, B,
-// n_e selections are redone with FP64 keys and implicit_fp64 bisects.
+// n_e selections are redone with FP64 keys and implicit_fp64 finds the root.
 __device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
                                                 float u0, float& u_out) {
     Cell64 c64;
     unsigned dummy = 0u;
+    c64.jt = -1;
     c64.ne = (double)rho * k.k64.s_n;
     c64.Hc = (double)H * k.k64.s_H;
     c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
