@@ -64,10 +64,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
     constexpr int NF = (VAR & 4) ? 6 : 5;   // staged input fields
     extern __shared__ float sm[];
     load_smem(k, sm);
-    Smem S;
-    S.ax = sm;
-    S.lb = sm + k.axes_floats;
-    S.lc = sm + k.axes_floats + k.tab.n[3];
+    const Smem S = smem_view(k, sm);
     constexpr int WR = Fmt<FMT>::W;                          // window rows of this format
     float* win = sm + smem_table_floats(k) + threadIdx.x;   // WR x kThreads window
     const int lane = threadIdx.x & 31;

@@ -205,10 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc) {
     extern __shared__ float sm[];
     load_smem(k, sm);
-    Smem S;
-    S.ax = sm;
-    S.lb = sm + k.axes_floats;
-    S.lc = sm + k.axes_floats + k.tab.n[3];
+    const Smem S = smem_view(k, sm);
     float* win = sm + smem_table_floats(k) + threadIdx.x;           // 8-row window (FP32 table)
     float* glb_s = sm + smem_table_floats(k) + Fmt<0>::W * kThreads;  // partial brems adjoints
     float* glc_s = glb_s + k.tab.n[3];                             // partial Coulomb adjoints

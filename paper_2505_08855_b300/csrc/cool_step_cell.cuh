@@ -161,7 +161,21 @@ __device__ __forceinline__ void load_smem(const StepK& k, float* sm) {
         const int r = i / nC;
         sm[na + nT + r * k.lc_stride + (i - r * nC)] = k.tab.lc[i];
     }
+    // the T_e interval records read by cool_energy
+    const float* axT = k.tab.axes + k.tab.axis_off[3];
+    float4* tn = reinterpret_cast<float4*>(sm + k.tn_off);
+    for (int j = threadIdx.x; j < nT - 1; j += blockDim.x)
+        tn[j] = make_float4(axT[nT + j], axT[2 * nT + j], k.tab.lb[j], k.tab.lb[j + 1]);
     __syncthreads();
+}
+
+__device__ __forceinline__ Smem smem_view(const StepK& k, const float* sm) {
+    Smem S;
+    S.ax = sm;
+    S.lb = sm + k.axes_floats;
+    S.lc = sm + k.axes_floats + k.tab.n[3];
+    S.tn = reinterpret_cast<const float4*>(sm + k.tn_off);
+    return S;
 }
 
 __device__ __forceinline__ void count_flags(unsigned f, cool_counters* cnt) {

@@ -31,6 +31,7 @@ struct Smem {
     const float* ax;   // concatenated axes (x, rx, lx per axis)
     const float* lb;
     const float* lc;
+    const float4* tn;  // per cooling T_e interval j: (1/x_j, log2 x_j, lb_j, lb_j+1)
 };
 
 // ---------------------------------------------------------------------------
@@ -165,8 +166,8 @@ struct StepK {
     float limiter, eq_band, clamp;
     int n_sub, mode, iters;
     int smem_floats;                  // floats of axes + lb + lc in shared memory
-    int lc_stride;                    // row stride of the Coulomb channel in shared memory: odd, so
-                                      // rows of one column fall in different banks
+    int lc_stride;                    // row stride of the Coulomb channel in shared memory (see fill_stepk)
+    int tn_off;                       // float offset (multiple of 4) of the T_e interval records (Smem::tn)
     int axes_floats;
     float spin, h_floor;              // disk geometry (the disk step): a, (H/R)_floor
     int h_from_state;                 // H_th = c_s / Omega_K replaces the H field
@@ -229,6 +230,27 @@ struct SelW {
 // a million) `near` is set and the caller redoes the cell with EXACT; the
 // values returned meanwhile are those of the guessed interval.  The clamp
 // flag compares the key with the end nodes exactly, as select_axis does.
+template <int A>
+__device__ __forceinline__ int select_guess(const StepK& k, float inv_dl, float key) {
+    float t = fmaf(lg2a(key), inv_dl, k.g_c0[A]);
+    t = fminf(fmaxf(t, 0.f), k.g_hi[A]);
+    return __float_as_int(__fadd_rn(t, 12582912.f)) - 0x4B400000;
+}
+
+template <int A>
+__device__ __forceinline__ SelW select_finish(const StepK& k, int j, float rxj, float inv_dl, float key,
+                                              unsigned& clamp, unsigned& near) {
+    SelW s;
+    s.j = j;
+    s.r = lg2a(key * rxj);
+    const float w = s.r * inv_dl;
+    const bool out = key < k.g_x0[A] || key > k.g_xn[A];
+    clamp |= out ? 1u : 0u;
+    near |= (!out && fabsf(w - 0.5f) > k.g_wb[A]) ? 1u : 0u;
+    s.w = __saturatef(w);
+    return s;
+}
+
 template <int A, bool EXACT>
 __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int n, float inv_dl, float key,
                                            unsigned& clamp, unsigned& near) {
@@ -240,17 +262,8 @@ __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int 
         s.w = __saturatef(e.r * inv_dl);
         return s;
     }
-    float t = fmaf(lg2a(key), inv_dl, k.g_c0[A]);
-    t = fminf(fmaxf(t, 0.f), k.g_hi[A]);
-    SelW s;
-    s.j = __float_as_int(__fadd_rn(t, 12582912.f)) - 0x4B400000;
-    s.r = lg2a(key * rx[s.j]);
-    float w = s.r * inv_dl;
-    const bool out = key < k.g_x0[A] || key > k.g_xn[A];
-    clamp |= out ? 1u : 0u;
-    near |= (!out && fabsf(w - 0.5f) > k.g_wb[A]) ? 1u : 0u;
-    s.w = __saturatef(w);
-    return s;
+    const int j = select_guess<A>(k, inv_dl, key);
+    return select_finish<A>(k, j, rx[j], inv_dl, key, clamp, near);
 }
 
 // Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
@@ -385,14 +398,23 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
                                              Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
     const float* axT = S.ax + k.tab.axis_off[3];
-    const SelW s = select_sub<3, EXACT>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
+    SelW s;
+    float4 nd;   // (1/x_j, log2 x_j, lb_j, lb_j+1): one 128-bit shared load on the step's path
+    if (EXACT) {
+        s = select_sub<3, true>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
+        nd = make_float4(0.f, axT[2 * nT + s.j], S.lb[s.j], S.lb[s.j + 1]);
+    } else {
+        const int jg = select_guess<3>(k, k.tab.inv_dl[3], Te);
+        nd = S.tn[jg];
+        s = select_finish<3>(k, jg, nd.x, k.tab.inv_dl[3], Te, clamp, cc.near);
+    }
     const int j = s.j;
     if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
     const int o = j - cc.base;
     const float w = s.w;
     const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
-    const float Lb = lerpf(S.lb[j], S.lb[j + 1], w) + c.lb_off;
-    const float lT = axT[2 * nT + j] + s.r;
+    const float Lb = lerpf(nd.z, nd.w, w) + c.lb_off;
+    const float lT = nd.y + s.r;
     const float M = fmaxf(Ls, Lb);
     const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
     const float Bb = fmaf(4.f, lT, c.lbb_off);
@@ -583,8 +605,18 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
         k.g_xn[a] = x[n - 1];
         k.g_wb[a] = (float)(0.5 - 1e-6 * (double)t->dev.inv_dl[a]);
     }
-    k.lc_stride = t->dev.n[4] | 1;
-    k.smem_floats = na + t->dev.n[3] + t->dev.n[4] * k.lc_stride;
+    // Row stride of the Coulomb channel in shared memory: the smallest one
+    // >= n that is 5 mod 32.  A warp's cells hold a few (T_i, T_e) rows and
+    // columns near each other; with the stride n + 1 (1 mod 32) corner (i, j)
+    // shares its bank with (i + 1, j - 1), (i + 2, j - 2), ..., so the four
+    // corner loads averaged 4.2 passes over the banks per warp on the 256^3
+    // two-region cells; 5 mod 32 separates such neighbours (2.2 passes).
+    {
+        const int nc = t->dev.n[4];
+        k.lc_stride = nc + (((5 - nc) % 32) + 32) % 32;
+    }
+    k.tn_off = (na + t->dev.n[3] + t->dev.n[4] * k.lc_stride + 3) & ~3;
+    k.smem_floats = k.tn_off + 4 * (t->dev.n[3] - 1);
     k.sched = nullptr;
 }
 

@@ -31,10 +31,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
     constexpr int TILE = 5 * kWarpCells;     // floats per buffer
     extern __shared__ __align__(16) float smt[];
     load_smem(k, smt);
-    Smem S;
-    S.ax = smt;
-    S.lb = smt + k.axes_floats;
-    S.lc = smt + k.axes_floats + k.tab.n[3];
+    const Smem S = smem_view(k, smt);
     float* win = smt + smem_table_floats(k) + threadIdx.x;   // W x kThreads window
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
