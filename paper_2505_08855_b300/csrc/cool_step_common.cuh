@@ -402,14 +402,18 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     float4 nd;   // (1/x_j, log2 x_j, lb_j, lb_j+1): one 128-bit shared load on the step's path
     if (EXACT) {
         s = select_sub<3, true>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
+        if ((unsigned)(s.j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, s.j / Fmt<FMT>::S, cc);
         nd = make_float4(0.f, axT[2 * nT + s.j], S.lb[s.j], S.lb[s.j + 1]);
     } else {
+        // the guess is the interval used (a doubtful one only flags the cell),
+        // so the window moves before the record is read: nothing is held
+        // across the gather
         const int jg = select_guess<3>(k, k.tab.inv_dl[3], Te);
+        if ((unsigned)(jg - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, jg / Fmt<FMT>::S, cc);
         nd = S.tn[jg];
         s = select_finish<3>(k, jg, nd.x, k.tab.inv_dl[3], Te, clamp, cc.near);
     }
     const int j = s.j;
-    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, j / Fmt<FMT>::S, cc);
     const int o = j - cc.base;
     const float w = s.w;
     const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;

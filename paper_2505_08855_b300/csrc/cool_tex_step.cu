@@ -167,7 +167,8 @@ cool_status launch_step_tex(const cool_table* t, const cool_params* p, long long
     if (n == 0) return COOL_OK;
     StepK k;
     fill_stepk(t, p, k);
-    const size_t smem = (size_t)k.smem_floats * sizeof(float);
+    // this kernel's own shared layout: axes, brems row, unpadded Coulomb channel
+    const size_t smem = (size_t)(k.axes_floats + k.tab.n[3] + k.tab.n[4] * k.tab.n[4]) * sizeof(float);
     const bool hw = p->path == COOL_PATH_TEXTURE_HWLERP;
     auto kern = hw ? k_step_tex<true> : k_step_tex<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
