@@ -17,6 +17,7 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int kMaxSub = 64;
 constexpr float kLn2 = 0.69314718056f;
+constexpr float kInvLn2 = 1.44269504089f;
 
 // Cooling energy q(u) and d ln q / d ln x for x = u, rho, B, H, plus
 // dq/dLs and dq/dLb for the table scatter (FP32 octet layout).
@@ -79,7 +80,7 @@ __device__ __forceinline__ QGrad cool_grad(const StepK& k, const Smem& S, const 
     const int j = s.j;
     const float wraw = s.r * T.inv_dl[3];
     const float wt = __saturatef(wraw);
-    const float cT = (wraw > 0.f && wraw < 1.f) ? T.inv_dl[3] / kLn2 : 0.f;   // dwt / d ln Te
+    const float cT = (wraw > 0.f && wraw < 1.f) ? T.inv_dl[3] * kInvLn2 : 0.f;   // dwt / d ln Te
     // corner values at nodes j, j+1 (octet layout: block j/7, offset j%7)
     if (gc.j != j) grad_corners(c, j, gc);
     const float* Sv = gc.Sv;
@@ -100,8 +101,9 @@ __device__ __forceinline__ QGrad cool_grad(const StepK& k, const Smem& S, const 
         const float tau = ex2a(lt);
         const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
         lq = A - lg2a(D);
-        kap = tau * (1.7320508f + 3.f * tau + 1.5f * c.tau_sca) / D;
-        ctau = 1.5f * tau / (D * kLn2);
+        const float rD = __fdividef(1.f, D);   // D >= 1
+        kap = tau * (1.7320508f + 3.f * tau + 1.5f * c.tau_sca) * rD;
+        ctau = (1.5f * kInvLn2) * tau * rD;
     } else {
         const float tau = ex2a(fminf(lt, 126.f));
         lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
@@ -145,7 +147,7 @@ struct XGrad {
     float wi, we;
 };
 
-__device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, float ue, float ui, float rho,
+__device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, float ue, float ui, float inv_rho,
                                               float inv_e, float inv_i, float kr, float lcc_off) {
     XGrad x;
     const DevTable& T = k.tab;
@@ -156,8 +158,8 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
     const Sel si = select_axis(axC, nC, T.inv_dl[4], ui * inv_i, dummy);
     const float re = se.r * T.inv_dl[4], ri = si.r * T.inv_dl[4];
     const float we = __saturatef(re), wi = __saturatef(ri);
-    const float ce_w = (re > 0.f && re < 1.f) ? T.inv_dl[4] / kLn2 : 0.f;
-    const float ci_w = (ri > 0.f && ri < 1.f) ? T.inv_dl[4] / kLn2 : 0.f;
+    const float ce_w = (re > 0.f && re < 1.f) ? T.inv_dl[4] * kInvLn2 : 0.f;
+    const float ci_w = (ri > 0.f && ri < 1.f) ? T.inv_dl[4] * kInvLn2 : 0.f;
     const int ls = k.lc_stride;
     const float* row = S.lc + si.j * ls + se.j;
     const float c00 = row[0], c01 = row[1], c10 = row[ls], c11 = row[ls + 1];
@@ -179,11 +181,11 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
         const float dlC_we = lerpf(c01 - c00, c11 - c10, wi);
         const float dlC_wi = lerpf(c10 - c00, c11 - c01, we);
         const float live = (lC + lcc_off) < 126.f ? 1.f : 0.f;
-        x.due = X * kLn2 * dlC_we * ce_w * live / ue - rate * kr * k.ce;
-        x.dui = X * kLn2 * dlC_wi * ci_w * live / ui + rate * kr * k.ci;
+        x.due = __fdividef(X * kLn2 * dlC_we * ce_w * live, ue) - rate * kr * k.ce;
+        x.dui = __fdividef(X * kLn2 * dlC_wi * ci_w * live, ui) + rate * kr * k.ci;
         // d ln X / d ln rho = ln2 dlC/d ln rho + 2 (n_e^2) - 1 (s_K/rho); a saturated
         // rate keeps only the -1
-        x.drho = live > 0.f ? X * (1.f - kLn2 * (dlC_we * ce_w + dlC_wi * ci_w)) / rho : -X / rho;
+        x.drho = live > 0.f ? X * (1.f - kLn2 * (dlC_we * ce_w + dlC_wi * ci_w)) * inv_rho : -X * inv_rho;
     }
     x.X = X;
     x.ji = si.j;
@@ -196,6 +198,7 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
 // SMS: the per-sub-cycle state lives in shared memory (n_sub <= kSmemSub,
 // column layout, conflict-free) instead of thread-local arrays.
 constexpr int kSmemSub = 8;
+constexpr int kStateFloats = 7;   // floats of per-sub-cycle state (ST_F)
 
 template <bool SMS>
 __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
@@ -214,15 +217,21 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
     __syncthreads();
     // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
-    // implicit root, and the branch taken (0 free, 1 limited, 2 implicit)
+    // implicit root, the exchange's partials dX/du_e, dX/du_i, dX/drho, and
+    // the branch taken (0 free, 1 limited, 2 implicit)
     float* sst = glc_s + ((nC * nC + 3) & ~3);
-    unsigned char* sbr = reinterpret_cast<unsigned char*>(sst + 4 * kSmemSub * kThreads);
-    float l_ue[SMS ? 1 : kMaxSub], l_ui[SMS ? 1 : kMaxSub], l_u1[SMS ? 1 : kMaxSub], l_us[SMS ? 1 : kMaxSub];
+    unsigned char* sbr = reinterpret_cast<unsigned char*>(sst + kStateFloats * kSmemSub * kThreads);
+    float l_st[SMS ? 1 : kStateFloats * kMaxSub];
     unsigned char l_br[SMS ? 1 : kMaxSub];
-#define ST_UE(sub) (*(SMS ? &sst[(4 * (sub) + 0) * kThreads + threadIdx.x] : &l_ue[(sub)]))
-#define ST_UI(sub) (*(SMS ? &sst[(4 * (sub) + 1) * kThreads + threadIdx.x] : &l_ui[(sub)]))
-#define ST_U1(sub) (*(SMS ? &sst[(4 * (sub) + 2) * kThreads + threadIdx.x] : &l_u1[(sub)]))
-#define ST_US(sub) (*(SMS ? &sst[(4 * (sub) + 3) * kThreads + threadIdx.x] : &l_us[(sub)]))
+#define ST_F(sub, f) (*(SMS ? &sst[(kStateFloats * (sub) + (f)) * kThreads + threadIdx.x] \
+                            : &l_st[kStateFloats * (sub) + (f)]))
+#define ST_UE(sub) ST_F(sub, 0)
+#define ST_UI(sub) ST_F(sub, 1)
+#define ST_U1(sub) ST_F(sub, 2)
+#define ST_US(sub) ST_F(sub, 3)
+#define ST_XE(sub) ST_F(sub, 4)
+#define ST_XI(sub) ST_F(sub, 5)
+#define ST_XR(sub) ST_F(sub, 6)
 #define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
     // cells in chunks of 32 (one per lane): each warp's first chunk by its
     // index in the grid, the next ones from the tile counter (k.sched) as
@@ -245,6 +254,9 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             unsigned clamp = 0u;
             const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
             const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
+            const float inv_rho = 1.f / rho;
+            const float inv_B = B > 0.f ? 1.f / B : 0.f;   // used only where dq/dB != 0 (B above the first node)
+            const float inv_H = H > 0.f ? 1.f / H : 0.f;
             CellC c;
             CellD cd;
             {
@@ -260,9 +272,9 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 c.wh = __saturatef(rh);
                 c.wb = __saturatef(rb);
                 c.wn = __saturatef(rn);
-                cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] / kLn2 : 0.f;
-                cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] / kLn2 : 0.f;
-                cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] / kLn2 : 0.f;
+                cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] * kInvLn2 : 0.f;
+                cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] * kInvLn2 : 0.f;
+                cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] * kInvLn2 : 0.f;
                 c.ls_off = k.l_hs_e;
                 c.lb_off = fmaf(2.f, lg2a(ne), k.l_hs_e);
                 c.lbb_off = k.l_bb - lg2a(Hc);
@@ -277,10 +289,13 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             for (int sub = 0; sub < k.n_sub; ++sub) {
                 ST_UE(sub) = ue;
                 ST_UI(sub) = ui;
-                const XGrad xg = coulomb_grad(k, S, ue, ui, rho, inv_e, inv_i, kr, lcc_off);
+                const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
                 ue += xg.X;
                 ui -= xg.X;
                 ST_U1(sub) = ue;
+                ST_XE(sub) = xg.due;
+                ST_XI(sub) = xg.dui;
+                ST_XR(sub) = xg.drho;
                 const float q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
                 float du = fminf(q, k.limiter * ue);
                 unsigned char br = q < k.limiter * ue ? 0 : 1;
@@ -307,19 +322,18 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 } else {
                     const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
                     const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
-                    const float qu = g.q * g.du / u;
+                    const float qu = __fdividef(g.q * g.du, u);
                     float sc;
                     if (br == 2) {
-                        const float den = 1.f + qu;
-                        ge1 = ge / den;
-                        sc = -ge / den;
+                        ge1 = __fdividef(ge, 1.f + qu);
+                        sc = -ge1;
                     } else {
                         ge1 = ge * (1.f - qu);
                         sc = -ge;
                     }
-                    grho += sc * g.q * g.drho / rho;
-                    if (g.dB != 0.f) gB += sc * g.q * g.dB / B;
-                    if (g.dH != 0.f) gH += sc * g.q * g.dH / H;
+                    grho += sc * g.q * g.drho * inv_rho;
+                    if (g.dB != 0.f) gB += sc * g.q * g.dB * inv_B;
+                    if (g.dH != 0.f) gH += sc * g.q * g.dH * inv_H;
                     if (g_ls) {
                         const float gs = sc * g.Gs;
                         const float wts[2] = {1.f - g.wt, g.wt};
@@ -344,12 +358,14 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                         atomicAdd(&glb_s[g.jt + 1], sc * g.Gb * g.wt);
                     }
                 }
-                const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), rho, inv_e, inv_i, kr, lcc_off);
                 const float gX = ge1 - gi;
-                ge = ge1 + gX * xg.due;
-                gi = gi + gX * xg.dui;
-                grho += gX * xg.drho;
-                if (g_lc && !xg.clamped) {
+                ge = ge1 + gX * ST_XE(sub);
+                gi = gi + gX * ST_XI(sub);
+                grho += gX * ST_XR(sub);
+                if (g_lc) {
+                    // the exchange's table adjoint needs its corners: recomputed
+                    const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), inv_rho, inv_e, inv_i, kr, lcc_off);
+                    if (xg.clamped) continue;
                     const float cl = gX * xg.X * kLn2;
                     atomicAdd(&glc_s[xg.ji * nC + xg.je], cl * (1.f - xg.wi) * (1.f - xg.we));
                     atomicAdd(&glc_s[xg.ji * nC + xg.je + 1], cl * (1.f - xg.wi) * xg.we);
@@ -372,10 +388,14 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             chunk += first;
         }
     }
+#undef ST_F
 #undef ST_UE
 #undef ST_UI
 #undef ST_U1
 #undef ST_US
+#undef ST_XE
+#undef ST_XI
+#undef ST_XR
 #undef ST_BR
     __syncthreads();
     if (g_lb)
@@ -399,7 +419,7 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     const bool sms = p->n_sub <= kSmemSub;
     size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads + t->dev.n[3] +
                            ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
-    if (sms) smem += (size_t)kSmemSub * kThreads * (4 * sizeof(float) + 1);
+    if (sms) smem += (size_t)kSmemSub * kThreads * (kStateFloats * sizeof(float) + 1);
     auto fn = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
