@@ -237,9 +237,12 @@ __global__ void k_debug_lookup(StepK k, int axis, long long n, const float* keys
             case 3: s = select_sub<3, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
             default: s = select_sub<4, false>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near); break;
             }
-            // near a node: node compares, as the step redoes such a cell (the
-            // EXACT form does not use the axis' constants, so A = 0 serves)
-            if (near) s = select_sub<0, true>(k, rx, T.n[a], T.inv_dl[a], keys[i], clamp, near);
+            // near a node: node compares, as the step redoes such a cell
+            if (near) {
+                const Sel e = select_axis(rx - T.n[a], T.n[a], T.inv_dl[a], keys[i], clamp);
+                s.j = e.j;
+                s.w = __saturatef(e.r * T.inv_dl[a]);
+            }
             idx[i] = s.j;
             w[i] = s.w;
         }

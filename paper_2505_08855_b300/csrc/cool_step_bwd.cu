@@ -76,10 +76,10 @@ __device__ __forceinline__ QGrad cool_grad(const StepK& k, const Smem& S, const 
     const float* axT = S.ax + T.axis_off[3];
     unsigned dummy = 0u;
     const float Te = u * inv_e;
-    const Sel s = select_axis(axT, nT, T.inv_dl[3], Te, dummy);
+    const SelW s = select_sub<3, true>(k, axT + nT, nT, T.inv_dl[3], Te, dummy, dummy);
     const int j = s.j;
     const float wraw = s.r * T.inv_dl[3];
-    const float wt = __saturatef(wraw);
+    const float wt = s.w;
     const float cT = (wraw > 0.f && wraw < 1.f) ? T.inv_dl[3] * kInvLn2 : 0.f;   // dwt / d ln Te
     // corner values at nodes j, j+1 (octet layout: block j/7, offset j%7)
     if (gc.j != j) grad_corners(c, j, gc);
@@ -154,10 +154,10 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
     const int nC = T.n[4];
     const float* axC = S.ax + T.axis_off[4];
     unsigned dummy = 0u;
-    const Sel se = select_axis(axC, nC, T.inv_dl[4], ue * inv_e, dummy);
-    const Sel si = select_axis(axC, nC, T.inv_dl[4], ui * inv_i, dummy);
+    const SelW se = select_sub<4, true>(k, axC + nC, nC, T.inv_dl[4], ue * inv_e, dummy, dummy);
+    const SelW si = select_sub<4, true>(k, axC + nC, nC, T.inv_dl[4], ui * inv_i, dummy, dummy);
     const float re = se.r * T.inv_dl[4], ri = si.r * T.inv_dl[4];
-    const float we = __saturatef(re), wi = __saturatef(ri);
+    const float we = se.w, wi = si.w;
     const float ce_w = (re > 0.f && re < 1.f) ? T.inv_dl[4] * kInvLn2 : 0.f;
     const float ci_w = (ri > 0.f && ri < 1.f) ? T.inv_dl[4] * kInvLn2 : 0.f;
     const int ls = k.lc_stride;
@@ -260,9 +260,13 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             CellC c;
             CellD cd;
             {
-                Sel sh = select_axis(S.ax + T.axis_off[0], T.n[0], T.inv_dl[0], Hc, clamp);
-                Sel sb = select_axis(S.ax + T.axis_off[1], T.n[1], T.inv_dl[1], Bg, clamp);
-                Sel sn = select_axis(S.ax + T.axis_off[2], T.n[2], T.inv_dl[2], ne, clamp);
+                unsigned unused = 0u;
+                const SelW sh = select_sub<0, true>(k, S.ax + T.axis_off[0] + T.n[0], T.n[0], T.inv_dl[0], Hc,
+                                                    clamp, unused);
+                const SelW sb = select_sub<1, true>(k, S.ax + T.axis_off[1] + T.n[1], T.n[1], T.inv_dl[1], Bg,
+                                                    clamp, unused);
+                const SelW sn = select_sub<2, true>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne,
+                                                    clamp, unused);
                 const int rowf = 8 * T.nblk;
                 c.oN = rowf;
                 c.oB = rowf * T.n[2];

@@ -251,18 +251,23 @@ __device__ __forceinline__ SelW select_finish(const StepK& k, int j, float rxj, 
     return s;
 }
 
+// EXACT: the guess where its weight confirms it, node compares (select_axis)
+// where it does not; the same j, r, w as select_axis in every case.
 template <int A, bool EXACT>
 __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int n, float inv_dl, float key,
                                            unsigned& clamp, unsigned& near) {
+    const int j = select_guess<A>(k, inv_dl, key);
     if (EXACT) {
-        const Sel e = select_axis(rx - n, n, inv_dl, key, clamp);
-        SelW s;
-        s.j = e.j;
-        s.r = e.r;
-        s.w = __saturatef(e.r * inv_dl);
+        unsigned doubt = 0u;
+        SelW s = select_finish<A>(k, j, rx[j], inv_dl, key, clamp, doubt);
+        if (doubt) {
+            const Sel e = select_axis(rx - n, n, inv_dl, key, clamp);
+            s.j = e.j;
+            s.r = e.r;
+            s.w = __saturatef(e.r * inv_dl);
+        }
         return s;
     }
-    const int j = select_guess<A>(k, inv_dl, key);
     return select_finish<A>(k, j, rx[j], inv_dl, key, clamp, near);
 }
 
