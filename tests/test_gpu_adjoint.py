@@ -118,3 +118,19 @@ def test_full_size_sampled_gradients(env, oracle):
         err = np.abs(g[k].cpu().numpy()[idx] - want[name]) * np.abs(sub[fld]) / np.maximum(L, 1e-30)
         bad |= err > 2e-4
     assert bad.sum() <= 5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_adjoint_mixed_axis_sizes(env, oracle, mode):
+    """A table whose axes all differ in size (and n_Tc != n_Te): every
+    selection of the recomputed forward and of the reverse sweep uses its
+    own axis' guess constants and node arrays."""
+    cool = env[0]
+    n5 = (6, 40, 9, 33, 24)
+    tab = cool.Table(cool.TableSpec(n=n5))
+    ospec = oracle.Spec(n=n5)
+    OT = oracle.build_tables(ospec, nthreads=0)
+    f = inputs.uniform(6000, seed=63, dtype=np.float32)
+    g, want, tg, bad, worst = _compare(cool, tab, oracle, ospec, OT, f, mode)
+    print(f"\nmixed axes, mode {mode}: cells beyond 2e-4: {bad.sum()} of {bad.size}; 99.5th pct {worst:.2e}")
+    assert bad.mean() <= 0.005

@@ -135,6 +135,53 @@ def test_debug_lookup_step_rule(cool, small, oracle):
         assert np.abs(gw.cpu().numpy() - ow).max() < 2e-7, a
 
 
+MIXED = (6, 40, 9, 33, 24)   # every axis a different size (and n_Tc != n_Te)
+
+
+@pytest.fixture(scope="module")
+def mixed(cool, oracle):
+    tab = cool.Table(cool.TableSpec(n=MIXED))
+    ospec = oracle.Spec(n=MIXED)
+    return tab, ospec, oracle.build_tables(ospec, nthreads=0)
+
+
+def test_mixed_axis_sizes_lookup(cool, mixed, oracle):
+    """Both selection rules (exact node compares, axes 0..4; the step's lg2
+    guess with its redo near a node, axes 5..9) on a table whose axes all
+    differ in size: each axis uses its own guess constants and arrays.
+    Indices bit-exact.  The weight is w = r / dl, r = log2(key * (1/x_j))
+    by lg2.approx: r carries 2^-22 max(1, r) from lg2.approx plus the two
+    FP32 roundings (1/x_j and the product, 2^-24 / ln 2 each in log2
+    units), so |dw| <= (2^-22 max(1, r) + 2^-23 / ln 2) / dl + 2^-24
+    <= 4.7e-7 max(1, 1/dl), 1/dl the nodes per octave (1.17 on the 40-node
+    B axis, where 2e-7 no longer bounds it)."""
+    tab, ospec, _ = mixed
+    rng = np.random.default_rng(11)
+    for a in range(5):
+        x32 = oracle.nodes(ospec, a)[2]
+        inv_dl = (MIXED[a] - 1) / np.log2(ospec.hi[a] / ospec.lo[a])
+        w_tol = 4.7e-7 * max(1.0, inv_dl)
+        keys = np.exp(rng.uniform(np.log(ospec.lo[a]) - 2, np.log(ospec.hi[a]) + 2, 200_000))
+        near = np.concatenate([x32, np.nextafter(x32, 0), np.nextafter(x32, np.inf),
+                               (x32 * (1 + rng.uniform(-1e-5, 1e-5, (200, x32.size)))).reshape(-1)])
+        keys = np.concatenate([keys, near]).astype(np.float32)
+        oi, ow = oracle.select_f32(ospec, a, keys)
+        for axis in (a, a + 5):
+            gi, gw = cool.debug_lookup(tab, axis, torch.from_numpy(keys).cuda())
+            assert np.array_equal(gi.cpu().numpy(), oi), axis
+            assert np.abs(gw.cpu().numpy() - ow).max() < w_tol, axis
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_mixed_axis_sizes_step(cool, mixed, oracle, mode):
+    tab, ospec, OT = mixed
+    f = inputs.subsample(inputs.make("uniform_32c", dtype=np.float32), np.arange(0, 32 ** 3, 7)[:4099])
+    want = oracle.step(ospec, OT, oracle.Params(n_sub=8, mode=mode), **f)
+    got = run_gpu(cool, tab, cool.Params(n_sub=8, mode=mode), to_dev(f, torch.float32))
+    for k in range(2):
+        assert rel(got[k], want[k]).max() <= TOL32, k
+
+
 # ---- step --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("mode", [0, 1])
