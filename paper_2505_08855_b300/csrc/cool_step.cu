@@ -21,8 +21,9 @@
 //     128-bit accesses, staged per warp in tiles of 128 cells, which warps
 //     take in a dynamic order from a per-stream counter;
 //   - node arrays, the 1-D bremsstrahlung and the 2-D Coulomb channels live
-//     in shared memory (loaded once per persistent block; Coulomb rows at an
-//     odd stride against bank conflicts);
+//     in shared memory (loaded once per persistent block; Coulomb rows at a
+//     stride of 5 mod 32 against bank conflicts, one 16-byte record per
+//     cooling T_e interval);
 //   - the 4-D synchrotron channel stays in global memory, L2-resident by its
 //     reuse: the step-invariant H, B, n_e axes are collapsed once per visited
 //     T_e block (8 corners x one 32-byte block of nodes, T_e fastest in
@@ -105,8 +106,9 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                 }
             }
             if (__any_sync(0xffffffffu, redo != 0u)) {
-                // a few cells in a million: every index by node compares,
-                // kept out of the loop above so that it leaves its code alone
+                // a few cells in a million: every index by the exact rule
+                // (node compares where the lg2 guess is in doubt), kept out of
+                // the loop above so that it leaves its code alone
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
                     if (!((redo >> c) & 1u)) continue;

@@ -12,16 +12,16 @@ namespace {
 struct Out {
     float ue, ui, qc, qx;
     unsigned flags;  // bit 0 clamped, 1 invalid, 2 stiff, 3 equilibrium band, 4 implicit fail, 6 floored
-    unsigned near;   // a key fell near a node: redo the cell with EXACT (select_sub)
+    unsigned near;   // a key fell near a node: redo the cell with EXACT
 };
 
 // VAR: bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in,
 // bit 2 = disk geometry (radius r per cell: H_th from the state and the
 // temperature floor; Sec. 2.7, Sec. 3.2.3), bit 4 = the paper's table layout
 // (COOL_PATH_QTOTAL: explicit, FP32 table, no geometry).  The explicit FP32 kernel carries
-// no solver code, no FP64 code and no geometry.  EXACT: every index by node
-// compares (select_axis); otherwise o.near asks for that when some key fell
-// near a node (see select_sub).
+// no solver code, no FP64 code and no geometry.  EXACT: every index by the
+// exact rule (select_sub<A, true>: node compares where the lg2 guess is in
+// doubt); otherwise o.near asks for that when some key fell near a node.
 template <int FMT, int VAR, bool EXACT>
 __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* win, float rho, float B,
                                          float H, float ue, float ui, float r) {
