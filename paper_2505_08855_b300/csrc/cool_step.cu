@@ -195,7 +195,7 @@ __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const doub
                 if (k.mode == 1 && q > k.limiter * ue) {
                     stiff = 1u;
                     double u1;
-                    if (implicit_fp64(k, c, r, ue, u1)) {
+                    if (implicit_fp64(k, c, r, ue, u1, nan64(), nan64())) {
                         du = ue - u1;
                     } else {
                         fail = 1u;

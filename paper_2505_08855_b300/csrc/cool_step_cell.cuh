@@ -137,8 +137,16 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         if ((VAR & 1) && q > k.limiter * ue) {
             stiff = 1u;
             float u1;
-            const bool ok = (VAR & 2) ? implicit_fp64_cell(k, T, rho, B, H, ue, u1)
-                                      : implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u1);
+            bool ok;
+            if (VAR & 2) {
+                // the FP32 solve's log-space bracket, refined in FP64
+                float xa = 0.f, xb = 0.f;
+                const bool br = implicit_fp32<FMT, EXACT, true>(k, S, c, cc, inv_e, ue, q, xa, &xb);
+                ok = implicit_fp64_cell(k, T, rho, B, H, ue, u1, br ? (double)xa : nan64(),
+                                        br ? (double)xb : nan64());
+            } else {
+                ok = implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u1);
+            }
             if (ok) du = ue - u1;
             else fail = 1u;
         }

@@ -26,6 +26,9 @@ __device__ __forceinline__ float lg2a(float x) {
 }
 
 
+// A quiet FP64 NaN (an absent argument).
+__device__ __forceinline__ double nan64() { return __longlong_as_double(0x7ff8000000000000ll); }
+
 // Shared-memory view of the small table parts.
 struct Smem {
     const float* ax;   // concatenated axes (x, rx, lx per axis)
@@ -114,13 +117,35 @@ __device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, u
 // is 1e-3 wide, until it is 1e-15 max(1, |x|) wide: the root the oracle's
 // bisection finds, to FP64 precision, in ~20 evaluations instead of 60; at
 // most iters evaluations.  Returns false when the bracket has no sign change.
-__device__ __noinline__ bool implicit_fp64(const StepK64& k, Cell64& c, double rho, double u0, double& u_out) {
+// xa0 < xb0: a narrower bracket from the FP32 solve (its log-space phase on
+// the FP32 table), used when g changes sign over it in FP64 (the FP32 and
+// FP64 functions differ by ~1e-6, the bracket is ~1e-3 wide), else the full
+// one; NaN: none.
+__device__ __noinline__ bool implicit_fp64(const StepK64& k, Cell64& c, double rho, double u0, double& u_out,
+                                           double xa0, double xb0) {
     unsigned dummy = 0u;
-    double xa = log2(u0) - 60.0, xb = log2(u0);
-    double ua = exp2(xa), ub = exp2(xb);
-    double qa = cool_q64(k, c, ua, rho, dummy), qb = cool_q64(k, c, ub, rho, dummy);
-    if (!(ua - u0 + qa < 0.0) || !(ub - u0 + qb > 0.0)) return false;
-    int it = 2;
+    double xa = xa0, xb = xb0, ua = 0.0, ub = 0.0, qa = 0.0, qb = 0.0;
+    int it = 0;
+    bool bracketed = false;
+    if (xa0 < xb0) {
+        // a bracket from the FP32 solve: kept if g changes sign over it in FP64
+        ua = exp2(xa);
+        ub = exp2(xb);
+        qa = cool_q64(k, c, ua, rho, dummy);
+        qb = cool_q64(k, c, ub, rho, dummy);
+        it = 2;
+        bracketed = ua - u0 + qa < 0.0 && ub - u0 + qb > 0.0;
+    }
+    if (!bracketed) {
+        xa = log2(u0) - 60.0;
+        xb = log2(u0);
+        ua = exp2(xa);
+        ub = exp2(xb);
+        qa = cool_q64(k, c, ua, rho, dummy);
+        qb = cool_q64(k, c, ub, rho, dummy);
+        it += 2;
+        if (!(ua - u0 + qa < 0.0) || !(ub - u0 + qb > 0.0)) return false;
+    }
     for (int phase = 0; phase < 2; ++phase) {
         // phase 0: G in log space; phase 1: g in u
         double fa = phase == 0 ? log2((ua + qa) / u0) : ua - u0 + qa;
@@ -463,9 +488,12 @@ __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S
 // linear over the 60 octaves, then on g(u) = u + q(u) - u0 in u once the
 // bracket is tight (FP32 x cannot resolve u to better than ~1e-6).  At most
 // implicit_iters evaluations.  Kept out of line: stiff cells are a minority.
-template <int FMT, bool EXACT>
+// BRACKET: stop after the log-space phase and return its bracket [xa, xb]
+// in log2 u (u_out = xa, *xb_out = xb): the start of the FP64 solve.
+template <int FMT, bool EXACT, bool BRACKET = false>
 __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
-                                           float inv_e, float u0, float q0, float& u_out) {
+                                           float inv_e, float u0, float q0, float& u_out,
+                                           float* xb_out = nullptr) {
     const float inv_u0 = 1.f / u0;
     unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
     float xb = lg2a(u0);
@@ -491,6 +519,11 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
             if (side == -1) Gb *= 0.5f;
             side = -1;
         }
+    }
+    if (BRACKET) {
+        u_out = xa;
+        *xb_out = xb;
+        return true;
     }
     float a = ex2a(xa), b = ex2a(xb);
     float ga = a - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, a * inv_e, trial);
@@ -522,7 +555,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
 // The same solve in FP64 on the FP64 table (fp64_critical): the cell's H, B,
 // n_e selections are redone with FP64 keys and implicit_fp64 finds the root.
 __device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
-                                                float u0, float& u_out) {
+                                                float u0, float& u_out, double xa0, double xb0) {
     Cell64 c64;
     unsigned dummy = 0u;
     c64.jt = -1;
@@ -532,7 +565,7 @@ __device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& 
     c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
     c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
     double u1;
-    if (!implicit_fp64(k.k64, c64, (double)rho, (double)u0, u1)) return false;
+    if (!implicit_fp64(k.k64, c64, (double)rho, (double)u0, u1, xa0, xb0)) return false;
     u_out = (float)u1;
     return true;
 }
