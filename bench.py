@@ -182,9 +182,12 @@ def cell_shard(n, rank, world):
     return first, base + (1 if rank < extra else 0)
 
 
-def cpu_oracle_rate(n_cells_sample, nthreads, seed_off=0, repeats=1):
+def cpu_oracle_rate(n_cells_sample, nthreads, seed_off=0, repeats=1, extra=None):
     """The FP64 oracle's step on a sample of the workload, host cores.  The
-    oracle builds its 64^4 table first (untimed, like the GPU table)."""
+    oracle builds its 64^4 table first (untimed, like the GPU table).  With
+    `extra` (a dict, filled in): the same O2 step on one thread over 65,536
+    of the cells, and the O1 step (every rate from the formulas, the paper's
+    analytic path) on all threads over 2,048 of them."""
     import oracle as O
     from paper_2505_08855_b300 import inputs
     spec = O.Spec(n=TABLE_N)
@@ -204,7 +207,27 @@ def cpu_oracle_rate(n_cells_sample, nthreads, seed_off=0, repeats=1):
         t0 = time.perf_counter()
         O.step(spec, T, p, **sub, nthreads=nthreads)
         times.append(time.perf_counter() - t0)
+    if extra is not None:
+        for key, m, threads, direct in (("o2_one_thread", 65536, 1, False), ("o1_direct", 2048, nthreads, True)):
+            idx = np.sort(rng.choice(F["rho"].size, m, replace=False))
+            part = inputs.subsample(F, idx)
+            t0 = time.perf_counter()
+            O.step(spec, T, p, **part, direct=direct, nthreads=threads)
+            dt = time.perf_counter() - t0
+            extra[key] = {"value": m / dt, "unit": UNIT, "threads": threads,
+                          "sample": f"{m} random cells, one 8-sub-cycle step ({dt:.2f} s)"}
     return n_cells_sample / min(times), t_build, times
+
+
+def host_cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def host_cores():
@@ -661,11 +684,13 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cores = host_cores()
         sample = n   # every cell of the workload: about 2 s per step on 16 cores
-        rate, t_build, times = cpu_oracle_rate(sample, cores, repeats=3)
+        more = {}
+        rate, t_build, times = cpu_oracle_rate(sample, cores, repeats=3, extra=more)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"all {sample} cells of the 256^3 workload, one 8-sub-cycle step, FP64 O2 "
                          f"oracle on {cores} threads (best of 3: {min(times):.1f} s, "
-                         f"{sum(times):.1f} s in all); its 64^4 table built once untimed ({t_build:.0f} s)"}
+                         f"{sum(times):.1f} s in all); its 64^4 table built once untimed ({t_build:.0f} s)",
+               "host": host_cpu_model(), **more}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
