@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     float* glc_s = glb_s + k.tab.n[3];                             // partial Coulomb adjoints
     const DevTable& T = k.tab;
     const int nT = T.n[3], nC = T.n[4];
+    const bool tbl = g_ls || g_lb || g_lc;   // table adjoints requested
     for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
     __syncthreads();
     // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
@@ -232,6 +233,12 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 #define ST_XE(sub) ST_F(sub, 4)
 #define ST_XI(sub) ST_F(sub, 5)
 #define ST_XR(sub) ST_F(sub, 6)
+// without table adjoints slots 0..3 hold the cooling's partials instead:
+// q dln q/dln u / u, q dln q/dln rho / rho, the same for B and H
+#define ST_QU(sub) ST_F(sub, 0)
+#define ST_QR(sub) ST_F(sub, 1)
+#define ST_QB(sub) ST_F(sub, 2)
+#define ST_QH(sub) ST_F(sub, 3)
 #define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
     // cells in chunks of 32 (one per lane): each warp's first chunk by its
     // index in the grid, the next ones from the tile counter (k.sched) as
@@ -289,40 +296,75 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             cc.base = -8;
             cc.win = win;
             cc.near = 0u;
+            GCache gc;
+            gc.j = -1;
             // ---- forward, recorded (the forward kernel's arithmetic) ----
+            // Without table adjoints the cooling energy comes from cool_grad
+            // (the same selection, corner collapse and bridge as cool_energy,
+            // hence the same q) with its partials, kept for the reverse sweep;
+            // with them the states are kept and the reverse sweep re-evaluates.
             for (int sub = 0; sub < k.n_sub; ++sub) {
-                ST_UE(sub) = ue;
-                ST_UI(sub) = ui;
+                if (tbl) {
+                    ST_UE(sub) = ue;
+                    ST_UI(sub) = ui;
+                }
                 const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
                 ue += xg.X;
                 ui -= xg.X;
-                ST_U1(sub) = ue;
+                if (tbl) ST_U1(sub) = ue;
                 ST_XE(sub) = xg.due;
                 ST_XI(sub) = xg.dui;
                 ST_XR(sub) = xg.drho;
-                const float q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
+                QGrad g;
+                float q;
+                if (tbl) {
+                    q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
+                } else {
+                    g = cool_grad(k, S, c, cd, gc, ue, inv_e);
+                    q = g.q;
+                }
                 float du = fminf(q, k.limiter * ue);
                 unsigned char br = q < k.limiter * ue ? 0 : 1;
+                float u_at = ue;   // where the cooling's partials are taken
                 if (k.mode == 1 && q > k.limiter * ue) {
                     float u1;
                     if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
                         du = ue - u1;
                         br = 2;
-                        ST_US(sub) = u1;
+                        u_at = u1;
+                        if (tbl) ST_US(sub) = u1;
+                        else g = cool_grad(k, S, c, cd, gc, u1, inv_e);
                     }
+                }
+                if (!tbl && br != 1) {
+                    ST_QU(sub) = __fdividef(g.q * g.du, u_at);
+                    ST_QR(sub) = g.q * g.drho * inv_rho;
+                    ST_QB(sub) = g.dB != 0.f ? g.q * g.dB * inv_B : 0.f;
+                    ST_QH(sub) = g.dH != 0.f ? g.q * g.dH * inv_H : 0.f;
                 }
                 ST_BR(sub) = br;
                 ue -= du;
             }
             // ---- reverse sweep ----
             float ge = ge_out, gi = gi_out, grho = 0.f, gB = 0.f, gH = 0.f;
-            GCache gc;
-            gc.j = -1;
             for (int sub = k.n_sub - 1; sub >= 0; --sub) {
                 float ge1;
                 const unsigned char br = ST_BR(sub);
                 if (br == 1) {
                     ge1 = (1.f - k.limiter) * ge;
+                } else if (!tbl) {
+                    const float qu = ST_QU(sub);
+                    float sc;
+                    if (br == 2) {
+                        ge1 = __fdividef(ge, 1.f + qu);
+                        sc = -ge1;
+                    } else {
+                        ge1 = ge * (1.f - qu);
+                        sc = -ge;
+                    }
+                    grho += sc * ST_QR(sub);
+                    gB += sc * ST_QB(sub);
+                    gH += sc * ST_QH(sub);
                 } else {
                     const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
                     const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
@@ -400,6 +442,10 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 #undef ST_XE
 #undef ST_XI
 #undef ST_XR
+#undef ST_QU
+#undef ST_QR
+#undef ST_QB
+#undef ST_QH
 #undef ST_BR
     __syncthreads();
     if (g_lb)
