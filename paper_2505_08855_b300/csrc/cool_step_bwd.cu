@@ -347,6 +347,23 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             }
             // ---- reverse sweep ----
             float ge = ge_out, gi = gi_out, grho = 0.f, gB = 0.f, gH = 0.f;
+            int ls_j = -1;                 // interval whose synchrotron adjoints are being summed
+            float ls_a0 = 0.f, ls_a1 = 0.f;
+            // add the summed adjoints of interval j to its 8 corner rows (natural layout)
+            auto flush_ls = [&](int j, float a0, float a1) {
+                if (j < 0) return;
+                const long long r0 = (long long)(c.row - T.lsb) / (8 * T.nblk);
+                const long long nN = T.n[2], nBN = (long long)T.n[1] * T.n[2];
+                const long long rows[8] = {r0, r0 + 1, r0 + nN, r0 + nN + 1,
+                                           r0 + nBN, r0 + nBN + 1, r0 + nBN + nN, r0 + nBN + nN + 1};
+                const float wh[2] = {1.f - c.wh, c.wh}, wb[2] = {1.f - c.wb, c.wb}, wn[2] = {1.f - c.wn, c.wn};
+#pragma unroll
+                for (int cidx = 0; cidx < 8; ++cidx) {
+                    const float wc = wh[cidx >> 2] * wb[(cidx >> 1) & 1] * wn[cidx & 1];
+                    atomicAdd(&g_ls[rows[cidx] * nT + j], wc * a0);
+                    atomicAdd(&g_ls[rows[cidx] * nT + j + 1], wc * a1);
+                }
+            };
             for (int sub = k.n_sub - 1; sub >= 0; --sub) {
                 float ge1;
                 const unsigned char br = ST_BR(sub);
@@ -381,23 +398,17 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                     if (g.dB != 0.f) gB += sc * g.q * g.dB * inv_B;
                     if (g.dH != 0.f) gH += sc * g.q * g.dH * inv_H;
                     if (g_ls) {
+                        // the 16 corner entries of interval jt receive w_corner x
+                        // (gs w_T): summed over the sub-cycles that stay in it
                         const float gs = sc * g.Gs;
-                        const float wts[2] = {1.f - g.wt, g.wt};
-                        const long long rowT = nT;
-                        // natural-layout row of corner (jh, jb, jn): rebuilt from the packed row offset
-                        const long long r0 = (long long)(c.row - T.lsb) / (8 * T.nblk);
-                        const long long rows[8] = {r0, r0 + 1, r0 + T.n[2], r0 + T.n[2] + 1,
-                                                   r0 + (long long)T.n[1] * T.n[2], r0 + (long long)T.n[1] * T.n[2] + 1,
-                                                   r0 + (long long)T.n[1] * T.n[2] + T.n[2],
-                                                   r0 + (long long)T.n[1] * T.n[2] + T.n[2] + 1};
-                        const float wh[2] = {1.f - c.wh, c.wh}, wb[2] = {1.f - c.wb, c.wb}, wn[2] = {1.f - c.wn, c.wn};
-    #pragma unroll
-                        for (int cidx = 0; cidx < 8; ++cidx) {
-                            const float wc = wh[cidx >> 2] * wb[(cidx >> 1) & 1] * wn[cidx & 1];
-    #pragma unroll
-                            for (int t = 0; t < 2; ++t)
-                                atomicAdd(&g_ls[rows[cidx] * rowT + g.jt + t], gs * wc * wts[t]);
+                        if (g.jt != ls_j) {
+                            flush_ls(ls_j, ls_a0, ls_a1);
+                            ls_j = g.jt;
+                            ls_a0 = 0.f;
+                            ls_a1 = 0.f;
                         }
+                        ls_a0 += gs * (1.f - g.wt);
+                        ls_a1 += gs * g.wt;
                     }
                     if (g_lb) {
                         atomicAdd(&glb_s[g.jt], sc * g.Gb * (1.f - g.wt));
@@ -419,6 +430,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                     atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je + 1], cl * xg.wi * xg.we);
                 }
             }
+            if (g_ls) flush_ls(ls_j, ls_a0, ls_a1);
             g_rho[i] = grho;
             g_B[i] = gB;
             g_H[i] = gH;
