@@ -200,7 +200,9 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
 constexpr int kSmemSub = 8;
 constexpr int kStateFloats = 7;   // floats of per-sub-cycle state (ST_F)
 
-template <bool SMS>
+// TBL: table adjoints requested (g_lb, g_ls or g_lc non-null); without,
+// the kernel carries no table-adjoint code.
+template <bool SMS, bool TBL>
 __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
     const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     float* glc_s = glb_s + k.tab.n[3];                             // partial Coulomb adjoints
     const DevTable& T = k.tab;
     const int nT = T.n[3], nC = T.n[4];
-    const bool tbl = g_ls || g_lb || g_lc;   // table adjoints requested
+    constexpr bool tbl = TBL;
     for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
     __syncthreads();
     // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
@@ -482,7 +484,9 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads + t->dev.n[3] +
                            ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
     if (sms) smem += (size_t)kSmemSub * kThreads * (kStateFloats * sizeof(float) + 1);
-    auto fn = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
+    const bool tbl = g_lb || g_ls || g_lc;
+    auto fn = sms ? (tbl ? k_step_bwd_f32<true, true> : k_step_bwd_f32<true, false>)
+                  : (tbl ? k_step_bwd_f32<false, true> : k_step_bwd_f32<false, false>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;
