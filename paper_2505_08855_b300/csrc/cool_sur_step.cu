@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kSurT) k_step_surrogate(StepK k, SurK m, long 
     S.ax = sms;
     S.lb = sms + k.axes_floats;
     S.lc = k.tab.lc;
+    S.tn = nullptr;   // the T_e interval records are not staged here (no cool_energy)
     unsigned char* W1s = reinterpret_cast<unsigned char*>(sms + sur_table_floats(k));
     unsigned char* W2s = W1s + 128 * 16 * 2;
     unsigned char* H1s = W2s + 128 * 128 * 2;
