@@ -193,6 +193,32 @@ def test_nu_c_root(oracle, pt):
         assert abs(lhs / rhs - 1) < 1e-11
 
 
+@pytest.mark.parametrize("pt", [(1e8, 1e3, 1e15, 1e9), (1e6, 1e5, 1e18, 3e10),
+                                (1e11, 10.0, 1e12, 2e8), (1e4, 1e8, 1e20, 1e11),
+                                (1e9, 1e2, 1e10, 5e7)])
+def test_nu_c_makes_qsyn_stationary(oracle, pt):
+    """Eq. 5 against Eq. 6.  With nu_c left free, Eq. 6 reads
+    Q(nu) = 2 pi k T nu^3/(3 c^2 H) + int_nu^inf eps_s dnu', so
+    dQ/dnu = 2 pi k T nu^2/(c^2 H) - eps_s(nu), which vanishes exactly where
+    H eps_s = 2 pi nu^2 k T/c^2: the root of Eq. 5 as read.  Q evaluated at
+    nu_c (1 +- delta) is then even in delta up to O(delta^3); a factor slip
+    on either side of Eq. 5 (2H for H, a doubled Rayleigh-Jeans term) makes
+    the odd part O(delta) times the Rayleigh-Jeans share of Q (here 0.04 to
+    0.86, so ~1e-5 and above).  The points cover both sides of the K2
+    switch (T_e = 5e7 K below it).  Neither side of Eq. 5 is written here."""
+    H, B, ne, T = pt
+    nuc, flag = oracle.nu_c(H, B, ne, T)
+    assert flag == 0 and nuc > 1.0
+    q0 = oracle.qsyn_nu(H, B, ne, T, nuc)
+    for d, tol in ((1e-3, 1e-6), (1e-4, 1e-9)):
+        qp = oracle.qsyn_nu(H, B, ne, T, nuc * (1 + d))
+        qm = oracle.qsyn_nu(H, B, ne, T, nuc * (1 - d))
+        odd = (qp - qm) / (2 * q0)
+        even = (qp + qm - 2 * q0) / (2 * q0)
+        assert abs(odd) < tol, (d, odd)
+        assert even > 0.0            # nu_c is where Q of Eq. 6 is smallest
+
+
 def test_qsyn_thin_limit_small_H(oracle):
     """H -> 0: nu_c -> 0 (nu_c ~ H^(6/7) since eps_s ~ nu^(1/3) there), the
     Rayleigh-Jeans part vanishes and Q_syn -> the whole thin integral,
@@ -309,6 +335,116 @@ def test_coulomb_vs_nrl_equilibration(oracle):
         q_nrl = 1.5 * ne * K_B * nu * (Ti - Te)
         q = oracle.coulomb_C(Ti, Te) * ne * ne * (Ti - Te)
         assert abs(q / q_nrl - 1) < 0.03
+
+
+def _landau_exchange_coefficient(Te, Ti, lnL=20.0):
+    """Electron heating rate per n_e n_i (T_i - T_e) for two Maxwell-Juettner
+    gases (electrons, protons) from the relativistic Landau collision
+    operator of Beliaev & Budker (1956), by quadrature.  This is the energy
+    moment the closed form of Eq. 16 (Stepney & Guilbert 1983) evaluates; it
+    is computed here without that closed form:
+
+    * Landau form C_a = 2 pi e^4 lnL d/dp_i int U_ij (f_b df_a/dp_j -
+      f_a df_b/dp'_j) d^3p' with the Beliaev-Budker kernel
+      U_ij = r^2/(g g' c (r^2-1)^(3/2)) [(r^2-1) d_ij - u_i u_j - u'_i u'_j
+      + r (u_i u'_j + u'_i u_j)], u = p/(m c) per species, g = sqrt(1+u^2),
+      r = g g' - u.u' (it reduces to (w^2 d_ij - w_i w_j)/w^3 at low speed
+      and annihilates the relative velocity u/g - u'/g');
+    * for Juettner distributions df/dp = -f v/(kT), so
+      dW_e/dt = 2 pi e^4 lnL n_e n_i (T_i - T_e)/(k T_e T_i) <v.U.v>, and
+      v.U.v = c r^2 (r_+ - r)(r - r_-)/(g g' (r^2-1)^(3/2)) with
+      r_+- = g g' +- |u||u'|;
+    * the angle between u and u' is traded for r, whose integral has the
+      closed form I(r_-, r_+) below (checked against direct quadrature in
+      test_landau_r_integral); the two energy integrals, in t = (g-1)/theta
+      per species, are done by adaptive quadrature split where the two
+      speeds are equal (I has a kink there);
+    * 2 pi e^4 = (3/4) sigma_T m_e^2 c^4 (e^2 = r_e m_e c^2, sigma_T =
+      8 pi r_e^2/3)."""
+    import scipy.integrate as si
+    the = K_B * Te / (M_E * C_LIGHT ** 2)
+    thi = K_B * Ti / (M_P * C_LIGHT ** 2)
+
+    def inner(te):
+        ge = 1 + the * te
+        ue = math.sqrt(the * te * (2 + the * te))
+        tstar = the * te / thi                   # ion kinetic variable with the electron's speed
+
+        def g(ti):
+            gi = 1 + thi * ti
+            ui = math.sqrt(thi * ti * (2 + thi * ti))
+            return math.exp(-ti) * _landau_r_integral(ge, gi, ue, ui)
+        return si.quad(g, 0, 80, points=[tstar] if tstar < 80 else None, epsabs=0, epsrel=1e-12,
+                       limit=400)[0]
+
+    pts = [thi * k / the for k in (1.0, 10.0, 80.0) if thi * k / the < 80]
+    j2 = si.quad(lambda te: math.exp(-te) * inner(te), 0, 80, points=pts or None, epsabs=0, epsrel=1e-11,
+                 limit=400)[0]
+    # <v.U.v> = 8 pi^2 c int int f_e f_i u u'/(g g') I du du'; with
+    # f = exp(-g/theta)/(4 pi theta K2(1/theta)) and du = g theta dt/u this is
+    # (c/2) j2 / (e^(1/theta_e) K2(1/theta_e) e^(1/theta_i) K2(1/theta_i))
+    vuv = 0.5 * C_LIGHT * j2 / (sp.kve(2, 1 / the) * sp.kve(2, 1 / thi))
+    return 0.75 * SIG_T * M_E ** 2 * C_LIGHT ** 4 * lnL * vuv / (K_B * Te * Ti)
+
+
+_GL_PHI = np.polynomial.legendre.leggauss(64)
+
+
+def _landau_r_integral(ge, gi, ue, ui):
+    """int_{r_-}^{r_+} r^2 (r_+ - r)(r - r_-)/(r^2 - 1)^(3/2) dr, r_+- = g g' +-
+    |u||u'|.  Where r_- - 1 exceeds the width r_+ - r_- the integrand is
+    smooth: r = g g' - |u||u'| cos(phi) turns it into
+    int_0^pi r^2 (|u||u'|)^3 sin^3(phi)/(r^2-1)^(3/2) dphi (64-point
+    Gauss-Legendre).  Closer to r = 1 (nearly equal speeds) the closed form
+    from the antiderivatives of r^n/(r^2-1)^(3/2), n = 2, 3, 4, is used, with
+    r - 1 formed without cancellation: (r_+ - 1)(r_- - 1) = (g - g')^2."""
+    rp1 = ge * gi - 1 + ue * ui
+    rm1 = (ge - gi) ** 2 / rp1
+    half = ue * ui
+    if rm1 > 2 * half:
+        x, w = _GL_PHI
+        phi = 0.5 * math.pi * (x + 1)
+        r1 = rm1 + half * (1 - np.cos(phi))          # r - 1
+        r = 1 + r1
+        f = r * r * half ** 3 * np.sin(phi) ** 3 / (r1 * (r + 1)) ** 1.5
+        return 0.5 * math.pi * float(np.dot(w, f))
+    rp, rm = 1 + rp1, 1 + rm1
+    sp_ = math.sqrt(rp1 * (rp + 1))
+    sm_ = math.sqrt(rm1 * (rm + 1))
+    ach = math.log1p(rp1 + sp_) - math.log1p(rm1 + sm_)
+    return sp_ * (0.5 * rp + 2 * rm) - sm_ * (2 * rp + 0.5 * rm) - (1.5 + rp * rm) * ach
+
+
+def test_landau_r_integral():
+    import scipy.integrate as si
+    for ge, gi in [(2.0, 1.001), (5.0, 1.3), (1.2, 1.19), (30.0, 1.00001), (1.0001, 1.00002),
+                   (1.5, 1.5000001), (3.0, 1.0 + 1e-7)]:
+        ue, ui = math.sqrt(ge * ge - 1), math.sqrt(gi * gi - 1)
+        rp, rm = ge * gi + ue * ui, ge * gi - ue * ui
+        rm1 = (ge - gi) ** 2 / (rp - 1)
+
+        def f(t):                           # r = r_- + t^2 lifts the (r - 1)^(-1/2) end
+            r1 = rm1 + t * t
+            r = 1 + r1
+            return 2 * t * r * r * (rp - r) * t * t / (r1 * (r + 1)) ** 1.5
+        tb = min(10 * math.sqrt(rm1), 0.5 * math.sqrt(rp - rm))   # the end's own scale
+        num = sum(si.quad(f, a, b, epsabs=0, epsrel=1e-13, limit=200)[0]
+                  for a, b in ((0, tb), (tb, math.sqrt(rp - rm))))
+        assert abs(_landau_r_integral(ge, gi, ue, ui) / num - 1) < 1e-8
+
+
+@pytest.mark.parametrize("Te,Ti", [(1e6, 1e7), (1e10, 1e9), (1e10, 1e11), (3e10, 1e12), (1e11, 1e8),
+                                   (3e10, 3e10), (1e11, 1e13), (2e9, 2e12), (1e12, 3e13)])
+def test_coulomb_vs_relativistic_landau_operator(oracle, Te, Ti):
+    """Eq. 16 (theta_i with m_p, lnL = 20) against the Beliaev-Budker energy
+    moment by quadrature, from theta_e = 1.7e-4 to 170 and theta_i = 1e-4 to
+    2.8: absolute agreement, so the prefactor, the (2(theta_e+theta_i)^2 +
+    1)/(theta_e+theta_i) K1 + 2 K0 bracket and the K2 K2 denominator are all
+    fixed, including their relativistic terms (a slip in 2(theta_e +
+    theta_i)^2 is an O(1) error at theta_e ~ 1 and above)."""
+    got = oracle.coulomb_C(Ti, Te)
+    want = _landau_exchange_coefficient(Te, Ti)
+    assert abs(got / want - 1) < 1e-9, (got, want)
 
 
 def test_coulomb_finite_and_smooth_over_range(oracle):
