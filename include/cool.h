@@ -122,7 +122,12 @@ typedef struct {
     double limiter_frac;      /* explicit cap on the electron energy removed per sub-cycle (0.3) */
     double eq_band;           /* equilibrium band |T_e - T_i| <= eq_band T_i (0.1), where T_i - T_e cancels */
     double coulomb_clamp;     /* the exchange may move at most this fraction of the way to T_e = T_i (1) */
-    int implicit_iters;       /* bisection halvings of the implicit solve, 1 .. 200 (60) */
+    int implicit_iters;       /* evaluations of q(u) allowed to the implicit solve of a stiff cell,
+                                 1 .. 200 (60).  The GPU solves backward Euler by Illinois (modified
+                                 regula falsi) iterations, first on log2((u + q(u))/u_e) in log2 u,
+                                 then on u + q(u) - u_e once the bracket is narrow, stopping at the
+                                 FP32 (or, with fp64_critical, FP64) resolution of the root or after
+                                 this many evaluations; the FP64 oracle bisects in log2 u instead. */
     cool_path path;           /* COOL_PATH_L2WINDOW (default), TMA_SMEM, TEXTURE_POINT, TEXTURE_HWLERP, QTOTAL */
     int fp64_critical;        /* FP32 fields only.  0 (default): the Coulomb difference
                                  (gamma_i-1) u_i - (gamma_e-1) u_e is formed with an error-free FP32
@@ -243,10 +248,15 @@ cool_status cool_table_load(const char* path, void* stream, cool_table** out);
  * of Eq. 11, applied to u_e explicitly (min(h Q, limiter_frac u_e)) or, in
  * mode IMPLICIT for stiff cells (h Q > limiter_frac u_e), by backward Euler.
  * FP32 fields: every table index equals the node-compare rule of
- * cool_debug_lookup (axes 0..4); the step zeroes an 8-byte tile counter of
- * `stream` before its kernel (one per device and stream, allocated on first
- * use outside stream capture; a capture with none yet uses a fixed tile
- * order, with the same results).
+ * cool_debug_lookup (axes 0..4).  Warps take tiles of cells from an 8-byte
+ * tile counter that the step zeroes on `stream` before its kernel: one
+ * counter per device and stream, keyed by the stream's unique id
+ * (cudaStreamGetId, so cudaStreamPerThread on two host threads gets two),
+ * allocated on first use.  Launches inside a stream capture never use the
+ * counter (they take a fixed tile order, with the same results), so a graph
+ * replayed on any stream cannot share it with a step running meanwhile.
+ * Launches on one stream run in order, so no two launches that overlap in
+ * time share a counter.
  *   field_dtype: COOL_F32 or COOL_F64 (all seven field arrays of that type).
  *   rho, B, H, u_e_in, u_i_in: device inputs, n_cells each.
  *   u_e_out, u_i_out: device outputs (may alias u_e_in / u_i_in).
@@ -284,10 +294,11 @@ cool_status cool_step(const cool_table* t, const cool_params* p, long long n_cel
  * process exits.  All calls share it and it keeps the last call's contents
  * (the counter is cleared at the start of each call), so calls whose work
  * overlaps on the GPU (different streams, or different host threads) race:
- * order them on one stream.  The first call on a device performs a
- * synchronous one-time set-up (it resolves the array's device address and
- * uploads the quadrature constants); make that first call before any stream
- * capture. */
+ * order them on one stream.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, with the caller's device current) and enqueues the
+ * quadrature constants on `stream` before its kernels; the first call on a
+ * device may also load the library's device code, so make that first call
+ * before any stream capture. */
 cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_out, double* ls_out,
                                         double* lc_out, void* stream);
 
@@ -469,6 +480,14 @@ cool_status cool_debug_gemm_bf16(const void* A, const void* B, float* C, int M, 
  * usable.  Errors: COOL_ENULL (err NULL), COOL_EINVAL (polls out of range).
  * Asynchronous on stream. */
 cool_status cool_debug_wait_timeout(int polls, unsigned* err, void* stream);
+
+/* Error word of the TMA_SMEM step path on the current device, read
+ * synchronously into *err_out (host): bit 0 is set when a bulk copy of a
+ * field tile never signalled completion within the kernel's bounded wait;
+ * that warp then wrote none of its remaining tiles' outputs.  clear = 1
+ * zeroes the word after reading it.  Errors: COOL_ENULL (err_out NULL),
+ * COOL_EINVAL (clear not 0 or 1), COOL_ECUDA. */
+cool_status cool_tma_error(unsigned* err_out, int clear);
 
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n).  axis 0..4 (H, B,

@@ -324,6 +324,14 @@ def debug_wait_timeout(polls, stream=None):
     return int(err.item())
 
 
+def tma_error(clear=True):
+    """cool_tma_error: the TMA_SMEM path's error word on the current device
+    (bit 0: a field copy that never completed).  Synchronous."""
+    v = C.c_uint(0)
+    _b.check(_b.lib().cool_tma_error(C.byref(v), 1 if clear else 0), "cool_tma_error")
+    return int(v.value)
+
+
 def debug_lookup(table, axis, keys, stream=None):
     """(idx int32, w float32) of the interpolation rule for FP32 keys."""
     import torch
@@ -335,14 +343,32 @@ def debug_lookup(table, axis, keys, stream=None):
     return idx, w
 
 
+def _check_noalloc_outputs(spec, lb_out, ls_out, lc_out):
+    """The library writes exactly n_Te, n_H n_B n_ne n_Te and n_Tc^2 doubles
+    through raw pointers: anything else (another dtype, a shorter tensor, a
+    tensor on another device) is refused here, before any launch."""
+    import torch
+    n_h, n_b, n_ne, n_te, n_tc = spec.n
+    want = (n_te, n_h * n_b * n_ne * n_te, n_tc * n_tc)
+    outs = list(zip(("lb_out", "ls_out", "lc_out"), (lb_out, ls_out, lc_out), want))
+    for name, t, m in outs:
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if t.numel() != m:
+            raise ValueError(f"{name} must hold exactly {m} elements, got {t.numel()}")
+    for name, t, _ in outs:
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must live on the current CUDA device")
+
+
 def build_channels_noalloc(spec, lb_out, ls_out, lc_out, stream=None):
     """cool_build_channels_noalloc: the table's FP64 log2 channels written into
     caller-allocated CUDA float64 tensors (sizes n_Te, n_H n_B n_ne n_Te,
     n_Tc^2); the library allocates no device memory for it."""
+    _check_noalloc_outputs(spec, lb_out, ls_out, lc_out)
     cs = spec.c()
-    for t in (lb_out, ls_out, lc_out):
-        if not t.is_cuda or not t.is_contiguous():
-            raise ValueError("outputs must be contiguous CUDA tensors")
     _b.check(_b.lib().cool_build_channels_noalloc(_b.ref(cs), _ptr(lb_out), _ptr(ls_out), _ptr(lc_out),
                                                   _stream_ptr(stream)), "cool_build_channels_noalloc")
 

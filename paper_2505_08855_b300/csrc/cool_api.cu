@@ -40,28 +40,36 @@ static bool unregister_table(const cool_table* t) {
     return live_tables().erase(t) == 1;
 }
 
+// Tile counter of the dynamic tile order, one per (device, stream id).  The
+// stream's unique id, not its handle, is the key: cudaStreamPerThread (and
+// the legacy stream under per-thread default streams) is one handle value
+// for many streams.  Inside a stream capture no counter is used (nullptr:
+// the static tile order), so a captured launch replayed on another stream
+// never shares a counter with a launch running at the same time; a counter
+// is only ever used by launches on its own stream, which run in order.
 unsigned long long* sched_counter(cudaStream_t st) {
     static std::mutex mu;
-    static std::map<std::pair<int, cudaStream_t>, unsigned long long*> counters;
+    static std::map<std::pair<int, unsigned long long>, unsigned long long*> counters;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    unsigned long long sid = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetId(st, &sid) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     std::lock_guard<std::mutex> g(mu);
-    auto it = counters.find({dev, st});
+    auto it = counters.find({dev, sid});
     if (it != counters.end()) return it->second;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
-        cudaGetLastError();
-        return nullptr;   // no allocation inside a capture
-    }
     unsigned long long* p = nullptr;
     if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    counters[{dev, st}] = p;
+    counters[{dev, sid}] = p;
     return p;
 }
 

@@ -16,7 +16,6 @@
 #include <stdint.h>
 #include <stdio.h>
 
-#include <mutex>
 
 #include "cool_internal.cuh"
 
@@ -551,7 +550,6 @@ cool_status launch_step_direct(const cool_table_spec& phys, const cool_params* p
 namespace {
 
 constexpr int kNoAllocAxisMax = 256;                     // nodes per axis the scratch holds
-constexpr int kNoAllocDevices = 64;
 constexpr size_t kNoAllocNodeBytes = sizeof(double) * 5 * 2 * kNoAllocAxisMax;   // 20 KiB
 constexpr size_t kNoAllocScratchBytes = kNoAllocNodeBytes + 256;                 // + flag word
 
@@ -560,13 +558,6 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocNodeBytes + 256;                
 // [a*2*256 + 256, (a+1)*2*256) = l_j; the flag counter at byte
 // kNoAllocNodeBytes.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-struct NoAllocDevice {
-    bool ready;
-    unsigned char* scratch;   // device address of g_noalloc_scratch on this device
-};
-static NoAllocDevice g_noalloc[kNoAllocDevices];
-static std::mutex g_noalloc_mu;
 
 // Node coordinates of the five axes into the scratch: l_j = l0 + j dl,
 // x_j = 2^l_j (the same node definition as the allocating build).
@@ -585,25 +576,22 @@ __global__ void k_noalloc_nodes(double* nodes, double l0_0, double l0_1, double 
     }
 }
 
-// First call on a device: resolve the device address of the scratch array
-// (its name is only a host-side stand-in in host code) and upload the
-// Gauss-Legendre constants.  Synchronous; must not run inside a capture.
-cool_status noalloc_setup(int dev, unsigned char** scratch) {
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (dev < 0 || dev >= kNoAllocDevices) return COOL_EUNSUPPORTED;
-    if (!g_noalloc[dev].ready) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return set_cuda_error(e);
-        double gx[16], gw[16];
-        gl16_host(gx, gw);
-        e = cudaMemcpyToSymbol(c_glx, gx, sizeof(gx));
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, gw, sizeof(gw));
-        if (e != cudaSuccess) return set_cuda_error(e);
-        g_noalloc[dev].scratch = (unsigned char*)ptr;
-        g_noalloc[dev].ready = true;
-    }
-    *scratch = g_noalloc[dev].scratch;
+// Per call, with the caller's device current: the device address of the
+// scratch array (in host code its name is only a host-side stand-in), looked
+// up every call so that a re-created context never sees a stale address,
+// and the Gauss-Legendre constants uploaded on the caller's stream, as the
+// allocating build does, so a context whose constant memory was reset
+// integrates with the right nodes.
+cool_status noalloc_setup(cudaStream_t st, unsigned char** scratch) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    double gx[16], gw[16];
+    gl16_host(gx, gw);
+    e = cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    *scratch = (unsigned char*)ptr;
     return COOL_OK;
 }
 
@@ -632,10 +620,10 @@ extern "C" cool_status cool_build_channels_noalloc(const cool_table_spec* spec, 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_cuda_error(e);
-    unsigned char* scratch = nullptr;
-    cool_status st = noalloc_setup(dev, &scratch);
-    if (st != COOL_OK) return st;
     cudaStream_t cs = (cudaStream_t)stream;
+    unsigned char* scratch = nullptr;
+    cool_status st = noalloc_setup(cs, &scratch);
+    if (st != COOL_OK) return st;
     double* nodes = (double*)scratch;
     unsigned int* flags = (unsigned int*)(scratch + kNoAllocNodeBytes);
     double l0[5], dl[5];

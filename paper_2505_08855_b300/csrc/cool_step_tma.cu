@@ -16,8 +16,10 @@ namespace {
 // start of the tile.  Outputs overwrite the inputs of their cell in the
 // buffer and leave by 128-bit streaming stores, as in k_step_f32.  The
 // window holds only the W nodes of the table format's block.  Waits are
-// bounded: a copy that does not complete sets *err bit 0 (the tile's
-// outputs are then not written).
+// bounded: a copy that does not complete sets g_tma_err bit 0 (read by the
+// host after the launch); the warp then issues no further copy, waits
+// (bounded) for those in flight and stops stepping tiles, so none of its
+// later tiles is computed from a partly filled buffer.
 __device__ unsigned g_tma_err;
 
 template <int FMT, int VAR>
@@ -72,16 +74,23 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
             mma::fence_async_smem();   // the other buffer's generic reads and writes are done (warp-synchronised)
             issue(nx, b ^ 1);
         }
-        const bool ok = mma::mbar_wait(mbar[b], phase[b], 1 << 22);
-        phase[b] ^= 1u;
+        // warp-uniform: every lane polls, and the tile is used only if all saw it land
+        const bool ok = __all_sync(0xffffffffu, mma::mbar_wait(mbar[b], phase[b], 1 << 22));
         if (!ok) {
+            // a copy did not complete: report it, issue nothing more, wait
+            // (bounded) for the copies still in flight into either buffer and
+            // leave the tile loop; no tile output is written after this
             if (lane == 0) atomicOr(&g_tma_err, 1u);
-            mma::mbar_wait(mbar[b], phase[b] ^ 1u, 1 << 16);
+            mma::mbar_wait(mbar[b], phase[b], 1 << 22);
+            if (nx < ntiles) mma::mbar_wait(mbar[b ^ 1], phase[b ^ 1], 1 << 22);
+            __syncwarp();
+            break;
         }
+        phase[b] ^= 1u;
         float* tile = bufs + b * TILE;
         float4* t4 = reinterpret_cast<float4*>(tile);
         const long long q = tw * 32 + lane;
-        if (ok) {
+        {
             unsigned redo = 0u;   // cells with a key near a node, redone below (as k_step_f32)
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
@@ -186,3 +195,17 @@ cool_status launch_step_tma(const cool_table* t, const cool_params* p, long long
 }
 
 }  // namespace cool
+
+// Error word of the TMA-staged step on the current device: bit 0 = a bulk
+// copy that never completed (see k_step_tma).  Synchronous.
+extern "C" cool_status cool_tma_error(unsigned* err_out, int clear) {
+    using namespace cool;
+    if (!err_out) return COOL_ENULL;
+    if (clear != 0 && clear != 1) return COOL_EINVAL;
+    cudaError_t e = cudaMemcpyFromSymbol(err_out, g_tma_err, sizeof(unsigned));
+    if (e == cudaSuccess && clear) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_tma_err, &zero, sizeof(unsigned));
+    }
+    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+}

@@ -115,3 +115,21 @@ def test_product_path_never_imports_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "cool_oracle" not in src and "liboracle" not in src, f
+
+
+def test_noalloc_wrapper_rejects_wrong_outputs_before_any_launch():
+    """build_channels_noalloc writes through raw pointers: a float32 tensor or
+    a short float64 tensor must be refused by the binding before the library
+    is called (CPU tensors suffice: dtype and size are checked first)."""
+    import torch
+    import paper_2505_08855_b300 as cool
+    spec = cool.TableSpec(n=(4, 5, 6, 7, 8))
+    good = [torch.zeros(m, dtype=torch.float64) for m in (7, 4 * 5 * 6 * 7, 64)]
+    bad32 = [good[0], good[1].float(), good[2]]
+    with pytest.raises(ValueError, match="float64"):
+        cool.build_channels_noalloc(spec, *bad32)
+    short = [good[0], good[1], torch.zeros(63, dtype=torch.float64)]
+    with pytest.raises(ValueError, match="exactly 64"):
+        cool.build_channels_noalloc(spec, *short)
+    with pytest.raises(ValueError, match="CUDA device"):
+        cool.build_channels_noalloc(spec, *good)     # right sizes, but host tensors

@@ -45,6 +45,7 @@ def test_tma_path_equals_default(env, dtype, scaled, mode, fp64):
     a, b = outs[_b.COOL_PATH_L2WINDOW], outs[_b.COOL_PATH_TMA_SMEM]
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+    assert cool.tma_error() == 0      # every bulk copy completed within its bounded wait
 
 
 def test_tma_path_needs_aligned_fields(env):

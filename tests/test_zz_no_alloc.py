@@ -7,8 +7,9 @@ inside the library.  Its channels must equal those of the allocating build
 (cool_build_table, read back through cool_table_export) within the table
 tolerance of the other GPU tests, on two calls in a row (the shared scratch
 keeps the previous call's contents, so the second call checks that nothing
-stale leaks through).  Collected last so that a failure here does not hide
-the other tests.
+stale leaks through), and equal the FP64 oracle's tables of the same spec
+within the same tolerance.  Collected last so that a failure here does not
+hide the other tests.
 """
 import ctypes as C
 
@@ -28,10 +29,13 @@ def test_noalloc_build_matches_allocating_build():
     from paper_2505_08855_b300 import binding as b, build
     build.build()
     L = b.lib()
+    import oracle as O
     for n in [(12, 10, 9, 17, 16), (16, 16, 16, 32, 24)]:
         spec = cool.TableSpec(n=n)
         ref = cool.Table(spec)
         want = [ref.export(ch) for ch in range(3)]
+        ot = O.build_tables(O.Spec(n=n))
+        orc = [ot["lb"], ot["ls"], np.asarray(ot["lc"]).reshape(-1)]
         sizes = [n[3], n[0] * n[1] * n[2] * n[3], n[4] * n[4]]
         for call in range(2):
             outs = [torch.full((m,), float("nan"), dtype=torch.float64, device="cuda") for m in sizes]
@@ -41,9 +45,10 @@ def test_noalloc_build_matches_allocating_build():
                                                C.c_void_p(torch.cuda.current_stream().cuda_stream))
             assert st == b.COOL_OK, L.cool_strerror(st)
             torch.cuda.synchronize()
-            for got, w in zip(outs, want):
+            for got, w, o in zip(outs, want, orc):
                 g = got.cpu().numpy()
                 assert np.all(np.abs(g - w) <= TOL * np.maximum(1.0, np.abs(w))), (n, call)
+                assert np.all(np.abs(g - o) <= TOL * np.maximum(1.0, np.abs(o))), (n, call, "oracle")
 
 
 def test_noalloc_rejects_axes_beyond_scratch():
