@@ -108,6 +108,34 @@ def ncu_utilisation():
     return None
 
 
+def issue_roofline(ms, n_cells, clk):
+    """The step kernel against its instruction-issue roof: warp instructions
+    per launch from the committed ncu summary of the current kernel sources
+    (same keying as traffic_per_launch) over the launch time, against 148 SMs
+    x 4 schedulers x 1 warp instruction per clock at the SM clock sampled
+    during the timed region (the maximum clock when no sample was taken)."""
+    sha = kernel_source_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    inst = tinst = None
+    for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not f.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, f)).read()
+        m = re.search(r"issue:\s*warp_instructions_per_launch\s+([0-9.eE+]+)\s+thread_instructions_per_launch\s+"
+                      r"([0-9.eE+]+)\s+source_sha256_16:\s*([0-9a-f]+)\s+workload:\s*(\S+)", txt)
+        if m and m.group(3) == sha and m.group(4) == WORKLOAD:
+            inst, tinst = float(m.group(1)), float(m.group(2))
+    if inst is None:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or 2032.0
+    peak = 148 * 4 * mhz * 1e6
+    achieved = inst / (ms * 1e-3)
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "sm_mhz": mhz, "warp_instructions_per_launch": inst,
+            "thread_instructions_per_cell": tinst / n_cells,
+            "source": "ncu smsp__inst_executed.sum / smsp__thread_inst_executed.sum of the committed capture"}
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -205,8 +233,11 @@ def cpu_oracle_rate(n_cells_sample, nthreads, seed_off=0, repeats=1, extra=None)
     times = []
     for _ in range(repeats):
         t0 = time.perf_counter()
-        O.step(spec, T, p, **sub, nthreads=nthreads)
+        out = O.step(spec, T, p, **sub, nthreads=nthreads)
         times.append(time.perf_counter() - t0)
+    if extra is not None:
+        extra["_outputs"] = (out[0], out[1])     # u_e, u_i of every sampled cell (for the error report)
+        extra["_tables"] = (spec, T)
     if extra is not None:
         for key, m, threads, direct in (("o2_one_thread", 65536, 1, False), ("o1_direct", 2048, nthreads, True)):
             idx = np.sort(rng.choice(F["rho"].size, m, replace=False))
@@ -217,6 +248,79 @@ def cpu_oracle_rate(n_cells_sample, nthreads, seed_off=0, repeats=1, extra=None)
             extra[key] = {"value": m / dt, "unit": UNIT, "threads": threads,
                           "sample": f"{m} random cells, one 8-sub-cycle step ({dt:.2f} s)"}
     return n_cells_sample / min(times), t_build, times
+
+
+def rel_err_report(got, want):
+    """Per-field error of the GPU against the FP64 oracle: max and 99.99th
+    percentile of |got - want| / |want|, and the cells beyond 1e-5."""
+    r = np.abs(got.astype(np.float64) - want) / np.abs(want)
+    return {"max": float(r.max()), "p9999": float(np.quantile(r, 0.9999)), "beyond_1e-5": int((r > 1e-5).sum())}
+
+
+FWD_BWD_WORKLOAD = "uniform_128c"
+FWD_BWD_BYTES_PER_CELL = 76   # forward 28 B + backward: read 5 fields + 2 output adjoints, write 5 (48 B)
+
+
+def fwd_bwd_gpu(torch, cool, inputs, dev, table, steps):
+    """Forward + adjoint (cool_step, cool_step_bwd) on the 128^3 uniform cells
+    with the 64^4 table, 8 sub-cycles, CUDA events on the launching stream:
+    returns the timing dict and the adjoint outputs of the last launch."""
+    G = inputs.make(FWD_BWD_WORKLOAD)
+    m = G["rho"].size
+    tg = {k: torch.from_numpy(v).to(dev) for k, v in G.items()}
+    gl = [tg[k] for k in ("rho", "B", "H", "ue", "ui")]
+    p = cool.Params(n_sub=N_SUB)
+    g_ue = torch.ones(m, device=dev)
+    g_ui = torch.full((m,), 0.5, device=dev)
+    nH, nB, nN, nT, nC = TABLE_N
+    tgr = {"lb": torch.zeros(nT, device=dev), "ls": torch.zeros(nH * nB * nN * nT, device=dev),
+           "lc": torch.zeros(nC * nC, device=dev)}
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def fwd():
+        cool.step(table, p, *gl)
+
+    def bwd():
+        out["g"] = cool.step_bwd(table, p, *gl, g_ue, g_ui)
+
+    def bwd_t():
+        cool.step_bwd(table, p, *gl, g_ue, g_ui, tgr)
+
+    ms_f = _timed(torch, fwd, steps, 3, stream)
+    ms_b = _timed(torch, bwd, steps, 3, stream)
+    ms_bt = _timed(torch, bwd_t, steps, 3, stream)
+    grads = [t.cpu().numpy() for t in out["g"]]
+    del tg, gl, g_ue, g_ui, tgr, out
+    torch.cuda.empty_cache()
+    return {"cells": m, "ms_fwd": ms_f, "ms_bwd": ms_b, "ms_bwd_with_table_adjoints": ms_bt}, grads, G
+
+
+def fwd_bwd_oracle(G, grads, spec, T, nthreads, n_sample=1024, seed=1003):
+    """The oracle's forward + adjoint on a seeded sample of the same cells
+    (the CPU baseline of the fwd+bwd metric) and the GPU adjoint's error on
+    it: |g_gpu - g_oracle| |x| / |L| per input (L = sum(u_e + u_i/2), the
+    loss whose adjoint the GPU launch computed; a scale-free measure, since
+    an adjoint can vanish)."""
+    import oracle as O
+    from paper_2505_08855_b300 import inputs
+    m = G["rho"].size
+    idx = np.sort(np.random.default_rng(seed).choice(m, n_sample, replace=False))
+    sub = inputs.subsample(G, idx)
+    t0 = time.perf_counter()
+    want = O.step_bwd(spec, T, O.Params(n_sub=N_SUB), **sub, g_ue=np.ones(n_sample), g_ui=np.full(n_sample, 0.5),
+                      nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    L = np.abs(want["ue"] + 0.5 * want["ui"])
+    err = {}
+    for k, (name, fld) in enumerate(zip(("g_rho", "g_B", "g_H", "g_ue", "g_ui"), ("rho", "B", "H", "ue", "ui"))):
+        e = np.abs(grads[k][idx] - want[name]) * np.abs(sub[fld]) / np.maximum(L, 1e-30)
+        err[name] = {"max": float(e.max()), "median": float(np.median(e)), "beyond_2e-4": int((e > 2e-4).sum())}
+    cpu = {"value": n_sample / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+           "sample": f"{n_sample} cells (seed {seed}) of the 128^3 uniform workload: the FP64 O2 oracle's forward "
+                     f"recomputation and adjoint of one 8-sub-cycle step ({dt:.2f} s)"}
+    return cpu, {"cells": n_sample, "measure": "|g_gpu - g_oracle| |x| / |L| per input, L = sum(u_e + u_i / 2)",
+                 **err}
 
 
 def host_cpu_model():
@@ -672,6 +776,11 @@ def main():
     ms_e2e = e0.elapsed_time(e1) / args.e2e_steps
     ms_e2e, e2e_value = job_rate(dist, world, ms_e2e, n, dev)
 
+    # forward + adjoint (rank 0 only: a secondary measurement of this line)
+    fb = None
+    if rank == 0:
+        fb_t, fb_grads, fb_G = fwd_bwd_gpu(torch, cool, inputs, dev, table, max(args.steps, 10))
+
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_CELL * n / (ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -686,6 +795,13 @@ def main():
         sample = n   # every cell of the workload: about 2 s per step on 16 cores
         more = {}
         rate, t_build, times = cpu_oracle_rate(sample, cores, repeats=3, extra=more)
+        o_ue, o_ui = more.pop("_outputs")
+        ospec, otab = more.pop("_tables")
+        max_err = {"u_e": rel_err_report(ue_o.cpu().numpy(), o_ue), "u_i": rel_err_report(ui_o.cpu().numpy(), o_ui),
+                   "cells": int(o_ue.size), "against": "FP64 O2 oracle, same cells, same table spec",
+                   "tolerance": 1e-5}
+        fb_cpu, fb_err = fwd_bwd_oracle(fb_G, fb_grads, ospec, otab, cores)
+        del o_ue, o_ui, otab
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"all {sample} cells of the 256^3 workload, one 8-sub-cycle step, FP64 O2 "
                          f"oracle on {cores} threads (best of 3: {min(times):.1f} s, "
@@ -693,13 +809,29 @@ def main():
                "host": host_cpu_model(), **more}
 
     if rank == 0:
+        ms_fb = fb_t["ms_fwd"] + fb_t["ms_bwd"]
+        m_fb = fb_t["cells"]
+        a_fb = FWD_BWD_BYTES_PER_CELL * m_fb / (ms_fb * 1e-3) / 1e9
+        ms_fbt = fb_t["ms_fwd"] + fb_t["ms_bwd_with_table_adjoints"]
+        fb = {"value": m_fb / (ms_fb * 1e-3), "unit": UNIT, "ms_per_step": ms_fb,
+              "workload": "128^3 uniform cells (synthetic, seeded), 64^4 FP32 table, 8 sub-cycles recomputed",
+              "ms_fwd": fb_t["ms_fwd"], "ms_bwd": fb_t["ms_bwd"],
+              "roofline": {"bound": "hbm", "achieved": a_fb, "peak": peak, "unit": "GB/s", "frac": a_fb / peak,
+                           "bytes_per_cell": FWD_BWD_BYTES_PER_CELL, "peak_source": peak_kind},
+              "with_table_adjoints": {"value": m_fb / (ms_fbt * 1e-3), "ms_per_step": ms_fbt,
+                                      "ms_bwd": fb_t["ms_bwd_with_table_adjoints"]}}
+        if cpu is not None:
+            fb["cpu_baseline"] = fb_cpu
+            fb["max_err"] = fb_err
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(n, world), "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
-                "gpu_launches": args.steps, "clocks": clk}
+                "gpu_launches": args.steps, "clocks": clk,
+                "fwd_bwd": fb, "max_rel_err": max_err if cpu is not None else None,
+                "issue_roofline": issue_roofline(ms, n, clk)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -134,7 +134,7 @@ def _declare(L):
         "orc_build_qtotal": (None, [_P, _P, _P, _P]),
         "orc_step_qtotal": (_i, [_P, _P, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i]),
         "orc_step_bwd": (_i, [_P, _P, _P, _P, _P, _ll, _P, _P, _P, _P, _P, _P, _P, _P,
-                              _P, _P, _P, _P, _P, _P, _i]),
+                              _P, _P, _P, _P, _P, _P, _i, _i]),
         "orc_step_surrogate": (_i, [_P, _P, _P, _P, _P, _d, _d, _P, _P, _d, _P, _i, _P, _ll,
                                     _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i]),
         "orc_net_eval": (_i, [_P, _d, _d, _d, _i, _ll, _P, _P]),
@@ -407,10 +407,12 @@ def step_qtotal(spec, tables, ltot, params, rho, B, H, ue, ui, nthreads=0):
     return outs[0], outs[1], outs[2], outs[3], dict(zip(COUNTER_NAMES, cnt.tolist()))
 
 
-def step_bwd(spec, tables, params, rho, B, H, ue, ui, g_ue, g_ui, table_grads=False, nthreads=0):
+def step_bwd(spec, tables, params, rho, B, H, ue, ui, g_ue, g_ui, table_grads=False, nthreads=0, lazy=False):
     """Adjoint of step(): returns dict with g_rho, g_B, g_H, g_ue, g_ui (per
     cell), the table adjoints g_lb, g_ls, g_lc (natural layouts) when asked,
-    sig (hash of each cell's discrete decisions) and the forward outputs."""
+    sig (hash of each cell's discrete decisions) and the forward outputs.
+    lazy: tables from build_tables(..., syn=False); the 4-D channel's nodes
+    are computed on first use (one thread)."""
     f = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (rho, B, H, ue, ui, g_ue, g_ui)]
     n = f[0].size
     grads = np.zeros((n, 5))
@@ -426,7 +428,7 @@ def step_bwd(spec, tables, params, rho, B, H, ue, ui, g_ue, g_ui, table_grads=Fa
     lc = np.ascontiguousarray(tables["lc"]).reshape(-1)
     rc = lib().orc_step_bwd(_ref(s), _ptr(tables["lb"]), _ptr(tables["ls"]), _ptr(lc), _ref(p), n,
                             *[_ptr(a) for a in f], _ptr(grads), _ptr(g_lb), _ptr(g_ls), _ptr(g_lc),
-                            _ptr(sig), _ptr(ue_o), _ptr(ui_o), int(nthreads))
+                            _ptr(sig), _ptr(ue_o), _ptr(ui_o), int(nthreads), 1 if lazy else 0)
     if rc != 0:
         raise RuntimeError(f"orc_step_bwd failed: {rc}")
     out = dict(g_rho=grads[:, 0], g_B=grads[:, 1], g_H=grads[:, 2], g_ue=grads[:, 3], g_ui=grads[:, 4],

@@ -1100,7 +1100,7 @@ static void q_dn(const orc_rates* R, const bwd_const* K, dn rho, dn B, dn H, dn 
             idx[a] = j[a] + bit;
             wt = dmul(wt, bit ? w[a] : dsub(dc(1.0), w[a]));
         }
-        lqs = dadd(lqs, dscale(wt, syn_at(R->s, R->ls, 0, idx[0], idx[1], idx[2], idx[3])));
+        lqs = dadd(lqs, dscale(wt, syn_at(R->s, R->ls, R->lazy, idx[0], idx[1], idx[2], idx[3])));
     }
     dn lqb = dadd(dscale(dsub(dc(1.0), w[3]), R->lb[j[3]]), dscale(w[3], R->lb[j[3] + 1]));
     dn qthin = dadd(dmul(dmul(ne, ne), dexp2(lqb)), dexp2(lqs));
@@ -1293,15 +1293,17 @@ static void cell_bwd(const orc_rates* R, const orc_params* p, double rho, double
  * u_e_in, u_i_in) for L = sum(g_ue_out u_e_out + g_ui_out u_i_out);
  * g_lb / g_ls / g_lc (nullable, natural table layouts) accumulate dL/d(table
  * log2 values); sig (nullable) receives a hash of each cell's discrete
- * decisions; ue_out / ui_out (nullable) the forward outputs. */
+ * decisions; ue_out / ui_out (nullable) the forward outputs.  lazy: the 4-D
+ * channel's NaN entries are computed on first use (one thread). */
 int orc_step_bwd(const orc_spec* s, const double* lb, double* ls, const double* lc, const orc_params* p,
                  long long n, const double* rho, const double* B, const double* H, const double* ue,
                  const double* ui, const double* g_ue_out, const double* g_ui_out, double* grads,
                  double* g_lb, double* g_ls, double* g_lc, unsigned long long* sig, double* ue_out,
-                 double* ui_out, int nthreads) {
+                 double* ui_out, int nthreads, int lazy) {
     orc_rates* R = (orc_rates*)malloc(sizeof(orc_rates));
     if (!R) return -1;
-    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = 0; R->direct = 0; R->lsp = NULL; R->net = NULL;
+    R->s = s; R->lb = lb; R->ls = ls; R->lc = lc; R->lazy = lazy; R->direct = 0; R->lsp = NULL; R->net = NULL;
+    if (lazy) nthreads = 1;
     R->ltot = NULL;
     for (int a = 0; a < 5; ++a) {
         if (s->n[a] < 2 || s->n[a] > ORC_MAXN) { free(R); return -2; }

@@ -336,3 +336,28 @@ def test_full_size_sampled_parity(cool, oracle):
     ei = rel(ui.cpu().numpy()[idx], want[1])
     print(f"\nfull-size sample: max rel u_e {eu.max():.2e}, u_i {ei.max():.2e}")
     assert eu.max() <= TOL32 and ei.max() <= TOL32
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_paper_size_table_sampled_parity(cool, oracle, mode):
+    """The paper's table size (100 nodes per axis, Sec. 2.6; 457 MB packed,
+    beyond L2) on the 256^3 two-region cells, 8 sub-cycles, explicit and
+    implicit, launched as the benchmark launches its step; 1024 sampled
+    cells against the oracle (lazy 100^4 table)."""
+    n = (100,) * 5
+    tab = cool.Table(cool.TableSpec(n=n))
+    F = inputs.make("two_region_256c")
+    tf = to_dev(F, torch.float32)
+    p = cool.Params(n_sub=8, mode=mode)
+    ue, ui = cool.step(tab, p, tf["rho"], tf["B"], tf["H"], tf["ue"], tf["ui"])
+    torch.cuda.synchronize()
+    tab.free()
+    idx = np.sort(np.random.default_rng(100 + mode).choice(F["rho"].size, 1024, replace=False))
+    sub = inputs.subsample(F, idx)
+    ospec = oracle.Spec(n=n)
+    OT = oracle.build_tables(ospec, syn=False)
+    want = oracle.step(ospec, OT, oracle.Params(n_sub=8, mode=mode), **sub, lazy=True)
+    eu = rel(ue.cpu().numpy()[idx], want[0])
+    ei = rel(ui.cpu().numpy()[idx], want[1])
+    print(f"\n100^4 table, mode {mode}: max rel u_e {eu.max():.2e}, u_i {ei.max():.2e}")
+    assert eu.max() <= TOL32 and ei.max() <= TOL32
