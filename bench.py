@@ -56,7 +56,7 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = ("cool_step.cu", "cool_step_cell.cuh", "cool_step_common.cuh")
+KERNEL_SOURCES = ("cool_step.cu", "cool_step_kernel.cuh", "cool_step_cell.cuh", "cool_step_common.cuh")
 
 
 def kernel_source_sha():
@@ -434,7 +434,7 @@ def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=Non
 
 
 SECTIONS = ("cfg2", "paper_size", "staging_bound", "l2_persist", "disk", "radiation", "scalar", "fp64", "adjoint",
-            "direct", "surrogate")
+            "direct", "surrogate", "placement")
 
 
 def run_suite_perf(args, torch, cool, inputs, dev):
@@ -640,6 +640,56 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         del d64
     if want & {"adjoint", "direct"}:
         del tg, gl
+        torch.cuda.empty_cache()
+
+    if "placement" in want:
+        # where the table lives, one short run per choice (1 untimed + 2
+        # timed launches each, so that one ncu capture of every k_step launch
+        # of this section covers all of them): the L2 block layout (default),
+        # the same with the persisting-L2 reservation, the two texture paths,
+        # the TMA-staged fields, the block-scaled BF16 table; then, on the
+        # 448 x 192 x 192 shell (spatially coherent cells), the bound on
+        # staging the table per tile: the same step with a 4-D channel of
+        # 2x2x2 corners x 64 T_e nodes (L1-resident) against the
+        # 128 x 128 x 64 x 64 table (302 MB).
+        F = inputs.make(WORKLOAD)
+        n = F["rho"].size
+        fl = [torch.from_numpy(F[k]).to(dev) for k in ("rho", "B", "H", "ue", "ui")]
+        uo, io = torch.empty_like(fl[3]), torch.empty_like(fl[4])
+        del F
+        p8 = cool.Params(n_sub=N_SUB)
+        t32 = cool.Table(cool.TableSpec(n=TABLE_N))
+        tbs = cool.Table(cool.TableSpec(n=TABLE_N, dtype=cool.BF16, row_scaled=1))
+        runs = [("L2 block layout (default)", t32, p8, False),
+                ("L2 block layout + persisting-L2 reservation", t32, p8, True),
+                ("texture, point fetches + FP32 lerp", t32, cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT),
+                 False),
+                ("texture, hardware trilinear filtering", t32,
+                 cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP), False),
+                ("TMA-staged field tiles", t32, cool.Params(n_sub=N_SUB, path=cool.PATH_TMA_SMEM), False),
+                ("BF16 block-scaled table", tbs, p8, False)]
+        for name, t, p, persist in runs:
+            t.l2_persist(persist)
+            ms = _timed(torch, lambda: cool.step(t, p, *fl, ue_out=uo, ui_out=io), 2, 1, stream)
+            t.l2_persist(False)
+            _suite_line(f"placement: {name}", WORKLOAD, n, ms, {"table_packed_bytes": t.packed_bytes()},
+                        BYTES_PER_CELL, peak)
+        t32.free()
+        tbs.free()
+        del fl, uo, io
+        S = inputs.make("shell_448x192x192")
+        sf = [torch.from_numpy(S[k]).to(dev) for k in ("rho", "B", "H", "ue", "ui")]
+        ns = sf[0].numel()
+        del S
+        so = (torch.empty_like(sf[3]), torch.empty_like(sf[4]))
+        for nn, label in (((128, 128, 64, 64, 64), "128x128x64x64 table (302 MB)"),
+                          ((2, 2, 2, 64, 64), "2x2x2x64 4-D channel (L1-resident)")):
+            tt = cool.Table(cool.TableSpec(n=nn))
+            ms = _timed(torch, lambda: cool.step(tt, p8, *sf, ue_out=so[0], ui_out=so[1]), 2, 1, stream)
+            _suite_line(f"placement: shell staging bound, {label}", "shell_448x192x192", ns, ms,
+                        {"table_packed_bytes": tt.packed_bytes()}, BYTES_PER_CELL, peak)
+            tt.free()
+        del sf, so
         torch.cuda.empty_cache()
 
     if "surrogate" in want:

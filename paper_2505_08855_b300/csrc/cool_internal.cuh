@@ -132,6 +132,11 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                             const float* ue, const float* ui, float* ue_o, float* ui_o,
                             float* qc, float* qx, cool_counters* cnt, cudaStream_t st,
                             const cool_disk* disk = nullptr, const float* r = nullptr);
+// Step kernels of the 16-bit table formats (cool_step_f16.cu: fmt 1, 2;
+// cool_step_f16s.cu: fmt 3, 4) for launch_step_f32: var = implicit |
+// fp64_critical << 1 | counters << 2; nullptr outside their formats.
+const void* step_kernel_f16(int fmt, bool vec, int var);
+const void* step_kernel_f16s(int fmt, bool vec, int var);
 cool_status launch_step_f64(const cool_table* t, const cool_params* p, long long n,
                             const double* rho, const double* B, const double* H,
                             const double* ue, const double* ui, double* ue_o, double* ui_o,

@@ -36,122 +36,11 @@
 //     over/underflows FP32 over the table's 60-decade range.
 #include <string.h>
 
-#include "cool_step_cell.cuh"
+#include "cool_step_kernel.cuh"
 
 namespace cool {
 namespace {
 
-// VAR: the step_cell variant bits (0 implicit, 1 fp64_critical, 2 disk
-// geometry) and bit 3, counters requested: without it no counter flag is
-// formed (the flag arithmetic of step_cell is dead code) and nothing is
-// counted.
-// VEC: all arrays 16-byte aligned.  Each warp walks tiles of 128 cells: its
-// first tile by its index in the grid, the next ones from a device counter
-// (k.sched) as it finishes, so the warps that draw cheap tiles take more of
-// them (static round-robin order when k.sched is null).  Per tile the five
-// input fields arrive by 128-bit streaming loads into the
-// warp's staging area, each lane steps cells lane, lane+32, lane+64, lane+96
-// (one cell's state in registers at a time), the outputs overwrite the
-// staging area and leave by 128-bit streaming stores.  Warps synchronise
-// only with themselves (__syncwarp), so a slow cell delays one warp, not the
-// block.  The remainder (and unaligned arrays) take a scalar loop.
-template <bool VEC, int FMT, int VAR>
-__global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_constant__ StepK k, long long n,
-                                                                  const float* __restrict__ rho,
-                                                         const float* __restrict__ Bf, const float* __restrict__ Hf,
-                                                         const float* ue_in, const float* ui_in, float* ue_out,
-                                                         float* ui_out, float* qc_out, float* qx_out,
-                                                         cool_counters* cnt, const float* __restrict__ rr) {
-    constexpr int NF = (VAR & 4) ? 6 : 5;   // staged input fields
-    extern __shared__ float sm[];
-    load_smem(k, sm);
-    const Smem S = smem_view(k, sm);
-    constexpr int WR = Fmt<FMT>::W;                          // window rows of this format
-    float* win = sm + smem_table_floats(k) + threadIdx.x;   // WR x kThreads window
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    long long scalar_start = 0;
-    if (VEC) {
-        float* tile = sm + smem_table_floats(k) + WR * kThreads + warp * NF * kWarpCells;
-        float4* t4 = reinterpret_cast<float4*>(tile);
-        const long long ntiles = n / kWarpCells;
-        const long long first = (long long)gridDim.x * kWarps;   // tiles taken statically
-        long long tw = (long long)blockIdx.x * kWarps + warp;
-        while (tw < ntiles) {
-            const long long q = tw * 32 + lane;  // float4 index of this lane
-            t4[0 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rho) + q);
-            t4[1 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(Bf) + q);
-            t4[2 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(Hf) + q);
-            t4[3 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ue_in) + q);
-            t4[4 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(ui_in) + q);
-            if (VAR & 4) t4[5 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rr) + q);
-            __syncwarp();
-            unsigned redo = 0u;   // cells with a key near a node, redone below
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                const int j = c * 32 + lane;
-                const Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, tile[j], tile[kWarpCells + j],
-                                                             tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
-                                                             tile[4 * kWarpCells + j],
-                                                             (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
-                if (o.near) {
-                    redo |= 1u << c;   // its inputs stay in the tile
-                } else {
-                    // inputs of cell j are consumed: outputs reuse its slots
-                    tile[3 * kWarpCells + j] = o.ue;
-                    tile[4 * kWarpCells + j] = o.ui;
-                    tile[0 * kWarpCells + j] = o.qc;
-                    tile[1 * kWarpCells + j] = o.qx;
-                    if (VAR & 8) count_flags(o.flags, cnt);
-                }
-            }
-            if (__any_sync(0xffffffffu, redo != 0u)) {
-                // a few cells in a million: every index by the exact rule
-                // (node compares where the lg2 guess is in doubt), kept out of
-                // the loop above so that it leaves its code alone
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    if (!((redo >> c) & 1u)) continue;
-                    const int j = c * 32 + lane;
-                    const Out o = step_cell<FMT, (VAR & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
-                                                                tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
-                                                                tile[4 * kWarpCells + j],
-                                                                (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
-                    tile[3 * kWarpCells + j] = o.ue;
-                    tile[4 * kWarpCells + j] = o.ui;
-                    tile[0 * kWarpCells + j] = o.qc;
-                    tile[1 * kWarpCells + j] = o.qx;
-                    if (VAR & 8) count_flags(o.flags, cnt);
-                }
-            }
-            __syncwarp();
-            __stcs(reinterpret_cast<float4*>(ue_out) + q, t4[3 * 32 + lane]);
-            __stcs(reinterpret_cast<float4*>(ui_out) + q, t4[4 * 32 + lane]);
-            if (qc_out) __stcs(reinterpret_cast<float4*>(qc_out) + q, t4[0 * 32 + lane]);
-            if (qx_out) __stcs(reinterpret_cast<float4*>(qx_out) + q, t4[1 * 32 + lane]);
-            __syncwarp();
-            if (k.sched) {
-                unsigned long long nt = 0;
-                if (lane == 0) nt = atomicAdd(k.sched, 1ull);
-                tw = first + (long long)__shfl_sync(0xffffffffu, nt, 0);
-            } else {
-                tw += first;
-            }
-        }
-        scalar_start = ntiles * kWarpCells;
-    }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float ri = (VAR & 4) ? rr[i] : 0.f;
-        Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
-        if (o.near) o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
-        ue_out[i] = o.ue;
-        ui_out[i] = o.ui;
-        if (qc_out) qc_out[i] = o.qc;
-        if (qx_out) qx_out[i] = o.qx;
-        if (VAR & 8) count_flags(o.flags, cnt);
-    }
-}
 
 __global__ void k_step_f64(StepK64 k, long long n, const double* rho, const double* Bf,
                            const double* Hf, const double* ue_in, const double* ui_in, double* ue_out,
@@ -272,34 +161,34 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     // shared memory: the table parts, the window (one row per node of a
     // block of this format) and the warps' field tiles
     size_t smem = (size_t)(smem_table_floats(k) + fmt_nodes(fmt) * kThreads) * sizeof(float);
-    if (vec) smem += (size_t)kWarps * (disk ? 6 : 5) * kWarpCells * sizeof(float);
-    using KFn = void (*)(StepK, long long, const float*, const float*, const float*, const float*, const float*,
-                         float*, float*, float*, float*, cool_counters*, const float*);
-    // the tables are indexed by implicit | fp64_critical << 1 | counters << 2
-    // (template bits 0, 1 and 3)
+    if (vec) smem += (size_t)kWarps * (disk ? 6 : 5) * kWarpCells * sizeof(float) + kWarps * kWarpCells;
+    // the kernels are indexed by implicit | fp64_critical << 1 | counters << 2
+    // (template bits 0, 1 and 3); 16-bit formats come from cool_step_f16.cu
+    // and cool_step_f16s.cu
 #define COOL_KV(V, F) k_step_f32<V, F, 0>, k_step_f32<V, F, 1>, k_step_f32<V, F, 2>, k_step_f32<V, F, 3>, \
                       k_step_f32<V, F, 8>, k_step_f32<V, F, 9>, k_step_f32<V, F, 10>, k_step_f32<V, F, 11>
-    static const KFn table_v[5][8] = {{COOL_KV(true, 0)}, {COOL_KV(true, 1)}, {COOL_KV(true, 2)},
-                                      {COOL_KV(true, 3)}, {COOL_KV(true, 4)}};
-    static const KFn table_s[5][8] = {{COOL_KV(false, 0)}, {COOL_KV(false, 1)}, {COOL_KV(false, 2)},
-                                      {COOL_KV(false, 3)}, {COOL_KV(false, 4)}};
+    static const StepKernelFn table_v[8] = {COOL_KV(true, 0)};
+    static const StepKernelFn table_s[8] = {COOL_KV(false, 0)};
 #undef COOL_KV
     // disk geometry (template bit 2): FP32 table only
 #define COOL_KD(V) k_step_f32<V, 0, 4>, k_step_f32<V, 0, 5>, k_step_f32<V, 0, 6>, k_step_f32<V, 0, 7>, \
                    k_step_f32<V, 0, 12>, k_step_f32<V, 0, 13>, k_step_f32<V, 0, 14>, k_step_f32<V, 0, 15>
-    static const KFn disk_v[8] = {COOL_KD(true)};
-    static const KFn disk_s[8] = {COOL_KD(false)};
+    static const StepKernelFn disk_v[8] = {COOL_KD(true)};
+    static const StepKernelFn disk_s[8] = {COOL_KD(false)};
 #undef COOL_KD
     // the paper's table layout (template bit 4): explicit, FP32 table, no geometry
-    static const KFn tot_v[2] = {k_step_f32<true, 0, 16>, k_step_f32<true, 0, 24>};
-    static const KFn tot_s[2] = {k_step_f32<false, 0, 16>, k_step_f32<false, 0, 24>};
+    static const StepKernelFn tot_v[2] = {k_step_f32<true, 0, 16>, k_step_f32<true, 0, 24>};
+    static const StepKernelFn tot_s[2] = {k_step_f32<false, 0, 16>, k_step_f32<false, 0, 24>};
     if (disk && (fmt != 0 || !r)) return COOL_EUNSUPPORTED;
     const bool tot = p->path == COOL_PATH_QTOTAL;
     if (tot && (disk || fmt != 0 || p->mode != COOL_EXPLICIT_LIMITED || p->fp64_critical || !t->dev.lst))
         return COOL_EUNSUPPORTED;
     const int var = (p->mode == COOL_IMPLICIT_STIFF ? 1 : 0) | (p->fp64_critical ? 2 : 0) | (cnt ? 4 : 0);
-    KFn fn = tot ? (vec ? tot_v[cnt ? 1 : 0] : tot_s[cnt ? 1 : 0])
-                 : disk ? (vec ? disk_v[var] : disk_s[var]) : (vec ? table_v[fmt][var] : table_s[fmt][var]);
+    const void* fn = tot    ? (const void*)(vec ? tot_v[cnt ? 1 : 0] : tot_s[cnt ? 1 : 0])
+                     : disk ? (const void*)(vec ? disk_v[var] : disk_s[var])
+                     : fmt == 0 ? (const void*)(vec ? table_v[var] : table_s[var])
+                     : (fmt <= 2 ? step_kernel_f16(fmt, vec, var) : step_kernel_f16s(fmt, vec, var));
+    if (!fn) return COOL_EUNSUPPORTED;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;
@@ -343,7 +232,8 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    e = cudaLaunchKernelEx(&cfg, fn, k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt, r);
+    void* args[] = {&k, &n, &rho, &B, &H, &ue, &ui, &ue_o, &ui_o, &qc, &qx, &cnt, &r};
+    e = cudaLaunchKernelExC(&cfg, fn, args);
     if (e != cudaSuccess) return set_cuda_error(e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);

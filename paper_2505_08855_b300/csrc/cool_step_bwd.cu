@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 c.oN = rowf;
                 c.oB = rowf * T.n[2];
                 c.oH = c.oB * T.n[1];
-                c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
+                c.rowi = (sh.j * T.n[1] + sb.j) * T.n[2] + sn.j;
+                c.row = T.lsb + (long long)c.rowi * rowf;
                 const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
                 c.wh = __saturatef(rh);
                 c.wb = __saturatef(rb);

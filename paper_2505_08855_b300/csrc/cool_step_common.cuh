@@ -7,6 +7,7 @@
 
 #include <cuda_fp16.h>
 #include <math.h>
+#include <string.h>
 
 #include "cool_internal.cuh"
 
@@ -117,10 +118,10 @@ __device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, u
 // is 1e-3 wide, until it is 1e-15 max(1, |x|) wide: the root the oracle's
 // bisection finds, to FP64 precision, in ~20 evaluations instead of 60; at
 // most iters evaluations.  Returns false when the bracket has no sign change.
-// xa0 < xb0: a narrower bracket from the FP32 solve (its log-space phase on
-// the FP32 table), used when g changes sign over it in FP64 (the FP32 and
-// FP64 functions differ by ~1e-6, the bracket is ~1e-3 wide), else the full
-// one; NaN: none.
+// xa0 < xb0: a narrower bracket around the FP32 solve's root (on the FP32
+// table), used when g changes sign over it in FP64 (the FP32 and FP64
+// functions differ by ~1e-6 relative, the bracket is 2^-13 wide in log2 u),
+// else the full one; NaN: none.
 __device__ __noinline__ bool implicit_fp64(const StepK64& k, Cell64& c, double rho, double u0, double& u_out,
                                            double xa0, double xb0) {
     unsigned dummy = 0u;
@@ -203,6 +204,10 @@ struct StepK {
     // tile counter of the vector step's dynamic tile order (zeroed on the
     // launch stream before the launch); nullptr: the static order
     unsigned long long* sched;
+    // 1 when the cooling T_e axis and the Coulomb T axis are the same node
+    // array (same n, same range, bitwise equal FP32 nodes): one cached T_e
+    // interval then serves both T_e lookups of a sub-cycle
+    int shared_T;
 };
 
 struct Sel {
@@ -298,7 +303,9 @@ __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int 
 
 // Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
 struct CellC {
-    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words
+    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words (16-bit gathers, adjoint,
+                          // surrogate step)
+    int rowi;           // its row index r = (jh n_B + jb) n_ne + jn (the FP32 gather)
     int oH, oB, oN;     // float offsets to the H+1, B+1, n_e+1 corner rows
     float wh, wb, wn;
     float lb_off;       // log2(h n_e^2 / e_scale)
@@ -357,27 +364,35 @@ __device__ __forceinline__ float dec(const uint32_t (&r)[8], int t) {
 // Read the 8 corner blocks of block kb (one 32-byte sector each) and collapse
 // the H, B, n_e axes: win[o] = trilinear value at T_e node S kb + o.
 template <int FMT>
-__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
+__device__ __forceinline__ void gather(const StepK& k, const uint32_t* tb, const CellC& c, int kb, Cache& cc) {
     constexpr int W = Fmt<FMT>::W;
-    const uint32_t* p = c.row + (long long)kb * 8;
+    // FP32: the table base tb and the corner rows' offsets are launch
+    // constants, read here so that no register holds them between gathers;
+    // the 16-bit formats (whose wider decode holds more registers inside the
+    // gather) keep the cell's row pointer and offsets (measured: fewer spills
+    // each way)
+    const int oN = FMT == 0 ? 8 * k.tab.nblk : c.oN;
+    const int oB = FMT == 0 ? oN * k.tab.n[2] : c.oB;
+    const int oH = FMT == 0 ? oB * k.tab.n[1] : c.oH;
+    const uint32_t* p = FMT == 0 ? tb + ((long long)c.rowi * oN + kb * 8) : c.row + (long long)kb * 8;
     if (FMT == 0) {
         // FP32: the four corners of one H plane in flight together (two L2
         // round trips per gather); the first plane's bilinear value waits in
         // the window while the second plane loads
         uint32_t a[8], b[8], d[8], e[8];
         ld8u(p, a);
-        ld8u(p + c.oN, b);
-        ld8u(p + c.oB, d);
-        ld8u(p + c.oB + c.oN, e);
+        ld8u(p + oN, b);
+        ld8u(p + oB, d);
+        ld8u(p + oB + oN, e);
 #pragma unroll
         for (int t = 0; t < 8; ++t)
             cc.win[t * kThreads] = lerpf(lerpf(dec<0>(a, t), dec<0>(b, t), c.wn),
                                          lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
-        const uint32_t* q = p + c.oH;
+        const uint32_t* q = p + oH;
         ld8u(q, a);
-        ld8u(q + c.oN, b);
-        ld8u(q + c.oB, d);
-        ld8u(q + c.oB + c.oN, e);
+        ld8u(q + oN, b);
+        ld8u(q + oB, d);
+        ld8u(q + oB + oN, e);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const float y = lerpf(lerpf(dec<0>(a, t), dec<0>(b, t), c.wn), lerpf(dec<0>(d, t), dec<0>(e, t), c.wn),
@@ -390,22 +405,22 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
         // in flight, as for FP32, measured slower for BF16)
         uint32_t r0[8], r1[8];
         ld8u(p, r0);
-        ld8u(p + c.oN, r1);
+        ld8u(p + oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t) cc.win[t * kThreads] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
-        ld8u(p + c.oB, r0);
-        ld8u(p + c.oB + c.oN, r1);
+        ld8u(p + oB, r0);
+        ld8u(p + oB + oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t)
             cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
-        const uint32_t* q = p + c.oH;
+        const uint32_t* q = p + oH;
         float hb[W];
         ld8u(q, r0);
-        ld8u(q + c.oN, r1);
+        ld8u(q + oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t) hb[t] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
-        ld8u(q + c.oB, r0);
-        ld8u(q + c.oB + c.oN, r1);
+        ld8u(q + oB, r0);
+        ld8u(q + oB + oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t) {
             const float h1 = lerpf(hb[t], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
@@ -413,6 +428,30 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
         }
     }
     cc.base = Fmt<FMT>::S * kb;
+}
+
+// The cooling energy of one sub-cycle from the interval's values: the
+// synchrotron channel's collapsed values v0, v1 at its two T_e nodes, its
+// record nd = (1/x_j, log2 x_j, lb_j, lb_j+1), r = log2(T_e/x_j) and the
+// weight w: the bridge of Eq. 11 in log2 space (see cool_energy below).
+__device__ __forceinline__ float bridge_energy(const CellC& c, float v0, float v1, float4 nd, float r, float w) {
+    const float Ls = lerpf(v0, v1, w) + c.ls_off;
+    const float Lb = lerpf(nd.z, nd.w, w) + c.lb_off;
+    const float lT = nd.y + r;
+    const float M = fmaxf(Ls, Lb);
+    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
+    const float Bb = fmaf(4.f, lT, c.lbb_off);
+    const float lt = A - Bb;  // log2 tau_abs
+    float lq;
+    if (lt <= 60.f) {
+        const float tau = ex2a(lt);
+        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
+        lq = A - lg2a(D);
+    } else {
+        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
+        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
+    }
+    return ex2a(fminf(lq, 126.f));
 }
 
 // Energy (code units) that cooling removes in one sub-cycle at T_e, with
@@ -432,41 +471,24 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     float4 nd;   // (1/x_j, log2 x_j, lb_j, lb_j+1): one 128-bit shared load on the step's path
     if (EXACT) {
         s = select_sub<3, true>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
-        if ((unsigned)(s.j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, s.j / Fmt<FMT>::S, cc);
+        if ((unsigned)(s.j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(k, k.tab.lsb, c, s.j / Fmt<FMT>::S, cc);
         nd = make_float4(0.f, axT[2 * nT + s.j], S.lb[s.j], S.lb[s.j + 1]);
     } else {
         // the guess is the interval used (a doubtful one only flags the cell),
         // so the window moves before the record is read: nothing is held
         // across the gather
         const int jg = select_guess<3>(k, k.tab.inv_dl[3], Te);
-        if ((unsigned)(jg - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, jg / Fmt<FMT>::S, cc);
+        if ((unsigned)(jg - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(k, k.tab.lsb, c, jg / Fmt<FMT>::S, cc);
         nd = S.tn[jg];
         s = select_finish<3>(k, jg, nd.x, k.tab.inv_dl[3], Te, clamp, cc.near);
     }
-    const int j = s.j;
-    const int o = j - cc.base;
-    const float w = s.w;
-    const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
-    const float Lb = lerpf(nd.z, nd.w, w) + c.lb_off;
-    const float lT = nd.y + s.r;
-    const float M = fmaxf(Ls, Lb);
-    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
-    const float Bb = fmaf(4.f, lT, c.lbb_off);
-    const float lt = A - Bb;  // log2 tau_abs
-    float lq;
-    if (lt <= 60.f) {
-        const float tau = ex2a(lt);
-        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
-        lq = A - lg2a(D);
-    } else {
-        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    }
-    return ex2a(fminf(lq, 126.f));
+    const int o = s.j - cc.base;
+    return bridge_energy(c, cc.win[o * kThreads], cc.win[(o + 1) * kThreads], nd, s.r, s.w);
 }
 
+
 // The same energy on the paper's table layout (Sec. 3.1): the total rate,
-// bridge included, interpolated from one 4-D table (c.row points into it):
+// bridge included, interpolated from one 4-D table (k.tab.lst, read by the gather):
 // q = 2^(L + log2(h / e_scale)).  FP32 table format only.
 template <bool EXACT>
 __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
@@ -475,7 +497,7 @@ __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S
     const float* axT = S.ax + k.tab.axis_off[3];
     const SelW s = select_sub<3, EXACT>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
     const int j = s.j;
-    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<0>::S - 1)) gather<0>(c, j / Fmt<0>::S, cc);
+    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<0>::S - 1)) gather<0>(k, k.tab.lst, c, j / Fmt<0>::S, cc);
     const int o = j - cc.base;
     const float L = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], s.w) + c.ls_off;
     return ex2a(fminf(L, 126.f));
@@ -487,13 +509,10 @@ __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S
 // G(x) = log2((2^x + q(2^x))/u0), x = log2 u, which is close to piecewise
 // linear over the 60 octaves, then on g(u) = u + q(u) - u0 in u once the
 // bracket is tight (FP32 x cannot resolve u to better than ~1e-6).  At most
-// implicit_iters evaluations.  Kept out of line: stiff cells are a minority.
-// BRACKET: stop after the log-space phase and return its bracket [xa, xb]
-// in log2 u (u_out = xa, *xb_out = xb): the start of the FP64 solve.
-template <int FMT, bool EXACT, bool BRACKET = false>
+// implicit_iters evaluations.
+template <int FMT, bool EXACT>
 __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
-                                           float inv_e, float u0, float q0, float& u_out,
-                                           float* xb_out = nullptr) {
+                                           float inv_e, float u0, float q0, float& u_out) {
     const float inv_u0 = 1.f / u0;
     unsigned trial = 0u;  // trial points of the solve do not count as clamped keys
     float xb = lg2a(u0);
@@ -519,11 +538,6 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
             if (side == -1) Gb *= 0.5f;
             side = -1;
         }
-    }
-    if (BRACKET) {
-        u_out = xa;
-        *xb_out = xb;
-        return true;
     }
     float a = ex2a(xa), b = ex2a(xb);
     float ga = a - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, a * inv_e, trial);
@@ -660,6 +674,13 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
     k.tn_off = (na + t->dev.n[3] + t->dev.n[4] * k.lc_stride + 3) & ~3;
     k.smem_floats = k.tn_off + 4 * (t->dev.n[3] - 1);
     k.sched = nullptr;
+    {
+        const int n3 = t->dev.n[3];
+        k.shared_T = n3 == t->dev.n[4] && t->dev.inv_dl[3] == t->dev.inv_dl[4] && k.g_c0[3] == k.g_c0[4] &&
+                     k.g_wb[3] == k.g_wb[4] && k.g_x0[3] == k.g_x0[4] && k.g_xn[3] == k.g_xn[4] &&
+                     memcmp(t->h_axes + t->dev.axis_off[3], t->h_axes + t->dev.axis_off[4],
+                            sizeof(float) * 3 * n3) == 0;
+    }
 }
 
 }  // namespace
