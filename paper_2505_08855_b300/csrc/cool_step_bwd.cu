@@ -280,8 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 c.oN = rowf;
                 c.oB = rowf * T.n[2];
                 c.oH = c.oB * T.n[1];
-                c.rowi = (sh.j * T.n[1] + sb.j) * T.n[2] + sn.j;
-                c.row = T.lsb + (long long)c.rowi * rowf;
+                c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
                 const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
                 c.wh = __saturatef(rh);
                 c.wb = __saturatef(rb);

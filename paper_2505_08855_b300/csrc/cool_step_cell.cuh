@@ -15,75 +15,6 @@ struct Out {
     unsigned near;   // a key fell near a node: redo the cell with EXACT
 };
 
-// Coulomb exchange of one sub-cycle (Eq. 16) from the interpolated log2 C:
-// X = h n_e^2 C (T_i - T_e) / e_scale moved from u_i to u_e, clamped so that
-// it does not cross T_e = T_i.  D = (gamma_i - 1) u_i - (gamma_e - 1) u_e;
-// T_i - T_e = (s_K/rho) D and the equilibrium point is X_eq = D / (ce + ci).
-// D cancels as T_e -> T_i: it is formed by an error-free transformation of
-// the product ce*u_e (p + e = ce*u_e exactly), so D carries ~1 ulp of its
-// own size; with fp64_critical (VAR bit 1) the band is evaluated in FP64.
-template <int VAR>
-__device__ __forceinline__ float exchange(const StepK& k, float lC, float lcc_off, float kr, float Te, float Ti,
-                                          float& ue, float& ui, unsigned& band) {
-    const float rate = ex2a(fminf(lC + lcc_off, 126.f));
-    const bool in_band = fabsf(Te - Ti) <= k.eq_band * Ti;
-    band |= in_band ? 1u : 0u;
-    float X;
-    if ((VAR & 2) && in_band) {
-        // literal FP64 evaluation inside the band
-        double D = k.ci64 * (double)ui - k.ce64 * (double)ue;
-        double Xd = (double)rate * ((double)kr * D);
-        double lim = (double)k.clamp * fabs(D * k.inv_cec64);
-        if (fabs(Xd) > lim) Xd = copysign(lim, Xd);
-        ue = (float)((double)ue + Xd);
-        ui = (float)((double)ui - Xd);
-        X = (float)Xd;
-    } else {
-        const float pe = k.ce * ue;
-        const float ee = fmaf(k.ce, ue, -pe);
-        const float D = fmaf(k.ci, ui, -pe) - ee;
-        X = rate * (kr * D);
-        const float lim = k.clamp * fabsf(D * k.inv_cec);
-        X = fabsf(X) > lim ? copysignf(lim, X) : X;
-        ue += X;
-        ui -= X;
-    }
-    return X;
-}
-
-// Electron energy removed by cooling in one sub-cycle, given q = the
-// cooling energy at the current u_e: the limited explicit step
-// min(q, limiter u_e), or in mode IMPLICIT (VAR bit 0) for a stiff cell the
-// backward-Euler step (FP32 Illinois, or with fp64_critical the FP64 solve
-// started from the FP32 solve's bracket).
-template <int FMT, int VAR, bool EXACT>
-__device__ __forceinline__ float cool_update(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
-                                             float inv_e, float rho, float B, float H, float ue, float q,
-                                             unsigned& stiff, unsigned& fail) {
-    float du = fminf(q, k.limiter * ue);
-    if ((VAR & 1) && q > k.limiter * ue) {
-        stiff = 1u;
-        if (VAR & 32) return du;   // flagged only: the cell is stepped again with the FP64 solve
-        float u1;
-        bool ok;
-        if (VAR & 2) {
-            // the FP32 root, refined in FP64 from a bracket of +-2^-14 in
-            // log2 u around it (the FP32 and FP64 functions differ by ~1e-6
-            // relative); implicit_fp64 checks the sign change in FP64 and
-            // takes the whole bracket when there is none
-            float u32 = 0.f;
-            const bool br = implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u32) && u32 > 0.f;
-            const double x32 = br ? log2((double)u32) : nan64();
-            ok = implicit_fp64_cell(k, k.tab, rho, B, H, ue, u1, x32 - 0x1p-14, x32 + 0x1p-14);
-        } else {
-            ok = implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u1);
-        }
-        if (ok) du = ue - u1;
-        else fail = 1u;
-    }
-    return du;
-}
-
 // VAR: bit 5 = the flagging pass of an fp64_critical kernel (a stiff cell
 // is flagged and takes the limited step: its result is discarded),
 // bit 0 = implicit mode compiled in, bit 1 = fp64_critical compiled in,
@@ -139,14 +70,11 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
                                              cc.near);
         const SelW sn = select_sub<2, EXACT>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne, clamp,
                                              cc.near);
-        c.rowi = (sh.j * T.n[1] + sb.j) * T.n[2] + sn.j;
-        if (FMT != 0) {
-            const int rowf = 8 * T.nblk;   // words per n_e row
-            c.oN = rowf;
-            c.oB = rowf * T.n[2];
-            c.oH = c.oB * T.n[1];
-            c.row = T.lsb + (long long)c.rowi * rowf;
-        }
+        const int rowf = 8 * T.nblk;                       // floats per n_e row
+        c.oN = rowf;
+        c.oB = rowf * T.n[2];
+        c.oH = c.oB * T.n[1];
+        c.row = ((VAR & 16) ? T.lst : T.lsb) + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
         c.wh = sh.w;
         c.wb = sb.w;
         c.wn = sn.w;
@@ -157,135 +85,77 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         c.tau_sca = k.two_sigT * ne * Hc;
     }
     const float lcc_off = c.lb_off;  // log2(h n_e^2 / e_scale)
+    const int nC = T.n[4];
+    const float* axC = S.ax + T.axis_off[4];
     float sum_q = 0.f, sum_x = 0.f;
-    if (!EXACT && FMT == 0 && !(VAR & (1 | 16)) && k.shared_T && k.n_sub >= 4) {
-        // The two T axes are one node array.  Keys move little between
-        // sub-cycles, so each lane keeps its current T_e interval (record,
-        // window values) and T_i interval (1/x_j) and the Coulomb corners of
-        // the pair, and tests a key against the held interval first: a
-        // weight r/dl = log2(key/x_j)/dl inside (1e-6/dl, 1 - 1e-6/dl) proves
-        // x_j < key < x_j+1 (the same proof that confirms the log2 guess in
-        // select_finish), so the held interval is the selection's index and
-        // the weight is the one the guess would give.  A key outside it takes
-        // the guess (select_guess / select_finish, flags as before).  One
-        // held T_e interval serves both T_e lookups of a sub-cycle (before
-        // and after the exchange).  Only the lanes whose key left their
-        // interval execute the re-selection; a warp skips it when none did.
-        // Kept for the FP32 table in explicit mode with N_sub >= 4, where it
-        // was measured faster (0.997 -> 0.973 ms per 256^3 step: thread
-        // instructions -22 %, shared-memory wavefronts -48 %, bitwise the
-        // same outputs); the 16-bit formats' wider gather and the implicit
-        // solve spill with the held intervals, and with one sub-cycle there
-        // is nothing to reuse, so those take the loop below.
-        const float inv_dl = T.inv_dl[3];
-        const float* axT = S.ax + T.axis_off[3];
-        const int nT = T.n[3];
+    for (int sub = 0; sub < k.n_sub; ++sub) {
+        // ---- (i) Coulomb exchange --------------------------------------------
+        const float Te = ue * inv_e;
+        const float Ti = ui * inv_i;
+        const SelW se = select_sub<4, EXACT>(k, axC + nC, nC, T.inv_dl[4], Te, clamp, cc.near);
+        const SelW si = select_sub<4, EXACT>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp, cc.near);
+        const float we = se.w;
+        const float wi = si.w;
         const int ls = k.lc_stride;
-        constexpr int SB = Fmt<FMT>::S;
-        int jT = 0;                                           // held T_e interval
-        float4 rec = make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, 0.f);  // its record (NaN: none held)
-        float v0 = 0.f, v1 = 0.f;                             // its window values
-        int jI = 0;                                           // held T_i interval
-        float rxI = __int_as_float(0x7fffffff);               // its 1/x_j (NaN: none held)
-        int cEI = -1;                                         // (T_e, T_i) intervals of the held corners
-        float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-        for (int sub = 0; sub < k.n_sub; ++sub) {
-            // ---- (i) Coulomb exchange ----------------------------------------
-            const float Te = ue * inv_e;
-            const float Ti = ui * inv_i;
-            float we = lg2a(Te * rec.x) * inv_dl;
-            if (!(fabsf(we - 0.5f) <= k.g_wb[4])) {
-                // a new T_e interval: the window moves first if it must (the
-                // T_i interval and the corners are let go across the gather,
-                // so that no register holds them there, and taken again
-                // below), then its record and window values
-                jT = select_guess<4>(k, inv_dl, Te);
-                if ((unsigned)(jT - cc.base) > (unsigned)(SB - 1)) {
-                    gather<FMT>(k, k.tab.lsb, c, jT / SB, cc);
-                    jI = 0;
-                    rxI = __int_as_float(0x7fffffff);
-                    cEI = -1;
-                    c00 = c01 = c10 = c11 = 0.f;
-                }
-                rec = S.tn[jT];
-                we = select_finish<4>(k, jT, rec.x, inv_dl, Te, clamp, cc.near).w;
-                v0 = cc.win[(jT - cc.base) * kThreads];
-                v1 = cc.win[(jT - cc.base + 1) * kThreads];
-            }
-            float wi = lg2a(Ti * rxI) * inv_dl;
-            if (!(fabsf(wi - 0.5f) <= k.g_wb[4])) {
-                jI = select_guess<4>(k, inv_dl, Ti);
-                rxI = axT[nT + jI];
-                wi = select_finish<4>(k, jI, rxI, inv_dl, Ti, clamp, cc.near).w;
-            }
-            if (jT + (jI << 16) != cEI) {
-                const float* row = S.lc + jI * ls + jT;
-                c00 = row[0];
-                c01 = row[1];
-                c10 = row[ls];
-                c11 = row[ls + 1];
-                cEI = jT + (jI << 16);
-            }
-            const float lC = lerpf(lerpf(c00, c01, we), lerpf(c10, c11, we), wi);
-            sum_x += exchange<VAR>(k, lC, lcc_off, kr, Te, Ti, ue, ui, band);
-            // ---- temperature floor: no cooling below T_floor -------------------
-            if ((VAR & 4) && fmaf(k.ce, ue, k.ci * ui) < t_floor * rho) {
-                floored = 1u;
-                continue;
-            }
-            // ---- (ii) radiative cooling ----------------------------------------
-            const float Tc = ue * inv_e;
-            float rc = lg2a(Tc * rec.x);
-            float wc = rc * inv_dl;
-            if (!(fabsf(wc - 0.5f) <= k.g_wb[3])) {
-                // as in cool_energy: the window moves before the record is read
-                jT = select_guess<3>(k, inv_dl, Tc);
-                if ((unsigned)(jT - cc.base) > (unsigned)(SB - 1)) {
-                    gather<FMT>(k, k.tab.lsb, c, jT / SB, cc);
-                    jI = 0;
-                    rxI = __int_as_float(0x7fffffff);
-                    cEI = -1;
-                    c00 = c01 = c10 = c11 = 0.f;
-                }
-                rec = S.tn[jT];
-                const SelW sc = select_finish<3>(k, jT, rec.x, inv_dl, Tc, clamp, cc.near);
-                rc = sc.r;
-                wc = sc.w;
-                v0 = cc.win[(jT - cc.base) * kThreads];
-                v1 = cc.win[(jT - cc.base + 1) * kThreads];
-            }
-            const float q = bridge_energy(c, v0, v1, rec, rc, wc);
-            const float du = cool_update<FMT, VAR, EXACT>(k, S, c, cc, inv_e, rho, B, H, ue, q, stiff, fail);
-            ue -= du;
-            sum_q += du;
+        const float* row = S.lc + si.j * ls + se.j;
+        const float lC = lerpf(lerpf(row[0], row[1], we), lerpf(row[ls], row[ls + 1], we), wi);
+        const float rate = ex2a(fminf(lC + lcc_off, 126.f));
+        // D = (gamma_i - 1) u_i - (gamma_e - 1) u_e; T_i - T_e = (s_K/rho) D and
+        // the equilibrium point is X_eq = D / (ce + ci).  D cancels as T_e -> T_i:
+        // it is formed by an error-free transformation of the product ce*u_e
+        // (p + e = ce*u_e exactly), so D carries ~1 ulp of its own size.
+        const bool in_band = fabsf(Te - Ti) <= k.eq_band * Ti;
+        band |= in_band ? 1u : 0u;
+        float X;
+        if ((VAR & 2) && in_band) {
+            // literal FP64 evaluation inside the band
+            double D = k.ci64 * (double)ui - k.ce64 * (double)ue;
+            double Xd = (double)rate * ((double)kr * D);
+            double lim = (double)k.clamp * fabs(D * k.inv_cec64);
+            if (fabs(Xd) > lim) Xd = copysign(lim, Xd);
+            ue = (float)((double)ue + Xd);
+            ui = (float)((double)ui - Xd);
+            X = (float)Xd;
+        } else {
+            const float pe = k.ce * ue;
+            const float ee = fmaf(k.ce, ue, -pe);
+            const float D = fmaf(k.ci, ui, -pe) - ee;
+            X = rate * (kr * D);
+            const float lim = k.clamp * fabsf(D * k.inv_cec);
+            X = fabsf(X) > lim ? copysignf(lim, X) : X;
+            ue += X;
+            ui -= X;
         }
-    } else {
-        const int nC = T.n[4];
-        const float* axC = S.ax + T.axis_off[4];
-        for (int sub = 0; sub < k.n_sub; ++sub) {
-            // ---- (i) Coulomb exchange --------------------------------------------
-            const float Te = ue * inv_e;
-            const float Ti = ui * inv_i;
-            const SelW se = select_sub<4, EXACT>(k, axC + nC, nC, T.inv_dl[4], Te, clamp, cc.near);
-            const SelW si = select_sub<4, EXACT>(k, axC + nC, nC, T.inv_dl[4], Ti, clamp, cc.near);
-            const float we = se.w;
-            const float wi = si.w;
-            const int ls = k.lc_stride;
-            const float* row = S.lc + si.j * ls + se.j;
-            const float lC = lerpf(lerpf(row[0], row[1], we), lerpf(row[ls], row[ls + 1], we), wi);
-            sum_x += exchange<VAR>(k, lC, lcc_off, kr, Te, Ti, ue, ui, band);
-            // ---- temperature floor: no cooling below T_floor -----------------------
-            if ((VAR & 4) && fmaf(k.ce, ue, k.ci * ui) < t_floor * rho) {
-                floored = 1u;
-                continue;
-            }
-            // ---- (ii) radiative cooling ----------------------------------------
-            const float q = (VAR & 16) ? cool_energy_total<EXACT>(k, S, c, cc, ue * inv_e, clamp)
-                                       : cool_energy<FMT, EXACT>(k, S, c, cc, ue * inv_e, clamp);
-            const float du = cool_update<FMT, VAR, EXACT>(k, S, c, cc, inv_e, rho, B, H, ue, q, stiff, fail);
-            ue -= du;
-            sum_q += du;
+        sum_x += X;
+        // ---- temperature floor: no cooling below T_floor -----------------------
+        if ((VAR & 4) && fmaf(k.ce, ue, k.ci * ui) < t_floor * rho) {
+            floored = 1u;
+            continue;
         }
+        // ---- (ii) radiative cooling ----------------------------------------
+        const float q = (VAR & 16) ? cool_energy_total<EXACT>(k, S, c, cc, ue * inv_e, clamp)
+                                   : cool_energy<FMT, EXACT>(k, S, c, cc, ue * inv_e, clamp);
+        float du = fminf(q, k.limiter * ue);
+        if ((VAR & 1) && q > k.limiter * ue) {
+            stiff = 1u;
+            if (!(VAR & 32)) {   // bit 5: flagged only, the cell is stepped again with the FP64 solve
+                float u1;
+                bool ok;
+                if (VAR & 2) {
+                    // the FP32 root, refined in FP64 (Newton from it, else a
+                    // bracketed solve around it or over the whole bracket)
+                    float u32 = 0.f;
+                    if (!implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u32)) u32 = 0.f;
+                    ok = implicit_fp64_cell(k, T, rho, B, H, ue, u1, u32);
+                } else {
+                    ok = implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u1);
+                }
+                if (ok) du = ue - u1;
+                else fail = 1u;
+            }
+        }
+        ue -= du;
+        sum_q += du;
     }
     o.ue = ue; o.ui = ui; o.qc = sum_q; o.qx = sum_x;
     o.flags = clamp | (stiff << 2) | (band << 3) | (fail << 4) | (floored << 6);

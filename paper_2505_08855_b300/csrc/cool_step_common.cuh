@@ -7,7 +7,6 @@
 
 #include <cuda_fp16.h>
 #include <math.h>
-#include <string.h>
 
 #include "cool_internal.cuh"
 
@@ -77,7 +76,10 @@ struct Cell64 {
     double v0, v1;      // synchrotron log2 values at its two nodes, collapsed over H, B, n_e
 };
 
-__device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, unsigned& clamp) {
+// dqdu (nullable): also dq/du of the same interpolation (the slopes of the
+// T_e interval and of the bridge; zero slope where the key is clamped).
+__device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, unsigned& clamp,
+                           double* dqdu = nullptr) {
     const DevTable& T = k.tab;
     double Te = k.s_Te * ue / rho;
     double wt;
@@ -101,11 +103,22 @@ __device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, u
     }
     double ls = (1.0 - wt) * c.v0 + wt * c.v1;
     double lb = (1.0 - wt) * T.lb64[jt] + wt * T.lb64[jt + 1];
-    double qthin = c.ne * c.ne * exp2(lb) + exp2(ls);
+    const double qb = c.ne * c.ne * exp2(lb), qs = exp2(ls);
+    double qthin = qb + qs;
     double bb4 = 4.0 * kSigSB * Te * Te * Te * Te;
     double tau_sca = 2.0 * c.ne * kSigT * c.Hc;
     double tau_abs = c.Hc * qthin / bb4;
-    double Q = qthin / (1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca)));
+    const double D = 1.0 + tau_abs * (sqrt(3.0) + 1.5 * (tau_abs + tau_sca));
+    double Q = qthin / D;
+    if (dqdu) {
+        // d/dln T_e: the weight moves by 1/(dl ln 2) inside the interval
+        const bool inside = wt > 0.0 && wt < 1.0;
+        const double dw = inside ? 1.0 / (T.dl64[3] * 0.6931471805599453) : 0.0;
+        const double dthin = 0.6931471805599453 * dw * (qb * (T.lb64[jt + 1] - T.lb64[jt]) + qs * (c.v1 - c.v0));
+        const double dtau = c.Hc * dthin / bb4 - 4.0 * tau_abs;
+        const double dD = (sqrt(3.0) + 3.0 * tau_abs + 1.5 * tau_sca) * dtau;
+        *dqdu = k.hs / k.escale * (dthin / D - qthin * dD / (D * D)) / ue;   // dln T_e/du = 1/u
+    }
     return k.hs * Q / k.escale;
 }
 
@@ -204,10 +217,6 @@ struct StepK {
     // tile counter of the vector step's dynamic tile order (zeroed on the
     // launch stream before the launch); nullptr: the static order
     unsigned long long* sched;
-    // 1 when the cooling T_e axis and the Coulomb T axis are the same node
-    // array (same n, same range, bitwise equal FP32 nodes): one cached T_e
-    // interval then serves both T_e lookups of a sub-cycle
-    int shared_T;
 };
 
 struct Sel {
@@ -303,9 +312,7 @@ __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int 
 
 // Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
 struct CellC {
-    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words (16-bit gathers, adjoint,
-                          // surrogate step)
-    int rowi;           // its row index r = (jh n_B + jb) n_ne + jn (the FP32 gather)
+    const uint32_t* row;  // block row of corner (jh, jb, jn): lsb + r nblk 8 words
     int oH, oB, oN;     // float offsets to the H+1, B+1, n_e+1 corner rows
     float wh, wb, wn;
     float lb_off;       // log2(h n_e^2 / e_scale)
@@ -364,35 +371,27 @@ __device__ __forceinline__ float dec(const uint32_t (&r)[8], int t) {
 // Read the 8 corner blocks of block kb (one 32-byte sector each) and collapse
 // the H, B, n_e axes: win[o] = trilinear value at T_e node S kb + o.
 template <int FMT>
-__device__ __forceinline__ void gather(const StepK& k, const uint32_t* tb, const CellC& c, int kb, Cache& cc) {
+__device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
     constexpr int W = Fmt<FMT>::W;
-    // FP32: the table base tb and the corner rows' offsets are launch
-    // constants, read here so that no register holds them between gathers;
-    // the 16-bit formats (whose wider decode holds more registers inside the
-    // gather) keep the cell's row pointer and offsets (measured: fewer spills
-    // each way)
-    const int oN = FMT == 0 ? 8 * k.tab.nblk : c.oN;
-    const int oB = FMT == 0 ? oN * k.tab.n[2] : c.oB;
-    const int oH = FMT == 0 ? oB * k.tab.n[1] : c.oH;
-    const uint32_t* p = FMT == 0 ? tb + ((long long)c.rowi * oN + kb * 8) : c.row + (long long)kb * 8;
+    const uint32_t* p = c.row + (long long)kb * 8;
     if (FMT == 0) {
         // FP32: the four corners of one H plane in flight together (two L2
         // round trips per gather); the first plane's bilinear value waits in
         // the window while the second plane loads
         uint32_t a[8], b[8], d[8], e[8];
         ld8u(p, a);
-        ld8u(p + oN, b);
-        ld8u(p + oB, d);
-        ld8u(p + oB + oN, e);
+        ld8u(p + c.oN, b);
+        ld8u(p + c.oB, d);
+        ld8u(p + c.oB + c.oN, e);
 #pragma unroll
         for (int t = 0; t < 8; ++t)
             cc.win[t * kThreads] = lerpf(lerpf(dec<0>(a, t), dec<0>(b, t), c.wn),
                                          lerpf(dec<0>(d, t), dec<0>(e, t), c.wn), c.wb);
-        const uint32_t* q = p + oH;
+        const uint32_t* q = p + c.oH;
         ld8u(q, a);
-        ld8u(q + oN, b);
-        ld8u(q + oB, d);
-        ld8u(q + oB + oN, e);
+        ld8u(q + c.oN, b);
+        ld8u(q + c.oB, d);
+        ld8u(q + c.oB + c.oN, e);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const float y = lerpf(lerpf(dec<0>(a, t), dec<0>(b, t), c.wn), lerpf(dec<0>(d, t), dec<0>(e, t), c.wn),
@@ -405,22 +404,22 @@ __device__ __forceinline__ void gather(const StepK& k, const uint32_t* tb, const
         // in flight, as for FP32, measured slower for BF16)
         uint32_t r0[8], r1[8];
         ld8u(p, r0);
-        ld8u(p + oN, r1);
+        ld8u(p + c.oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t) cc.win[t * kThreads] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
-        ld8u(p + oB, r0);
-        ld8u(p + oB + oN, r1);
+        ld8u(p + c.oB, r0);
+        ld8u(p + c.oB + c.oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t)
             cc.win[t * kThreads] = lerpf(cc.win[t * kThreads], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
-        const uint32_t* q = p + oH;
+        const uint32_t* q = p + c.oH;
         float hb[W];
         ld8u(q, r0);
-        ld8u(q + oN, r1);
+        ld8u(q + c.oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t) hb[t] = lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn);
-        ld8u(q + oB, r0);
-        ld8u(q + oB + oN, r1);
+        ld8u(q + c.oB, r0);
+        ld8u(q + c.oB + c.oN, r1);
 #pragma unroll
         for (int t = 0; t < W; ++t) {
             const float h1 = lerpf(hb[t], lerpf(dec<FMT>(r0, t), dec<FMT>(r1, t), c.wn), c.wb);
@@ -428,30 +427,6 @@ __device__ __forceinline__ void gather(const StepK& k, const uint32_t* tb, const
         }
     }
     cc.base = Fmt<FMT>::S * kb;
-}
-
-// The cooling energy of one sub-cycle from the interval's values: the
-// synchrotron channel's collapsed values v0, v1 at its two T_e nodes, its
-// record nd = (1/x_j, log2 x_j, lb_j, lb_j+1), r = log2(T_e/x_j) and the
-// weight w: the bridge of Eq. 11 in log2 space (see cool_energy below).
-__device__ __forceinline__ float bridge_energy(const CellC& c, float v0, float v1, float4 nd, float r, float w) {
-    const float Ls = lerpf(v0, v1, w) + c.ls_off;
-    const float Lb = lerpf(nd.z, nd.w, w) + c.lb_off;
-    const float lT = nd.y + r;
-    const float M = fmaxf(Ls, Lb);
-    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
-    const float Bb = fmaf(4.f, lT, c.lbb_off);
-    const float lt = A - Bb;  // log2 tau_abs
-    float lq;
-    if (lt <= 60.f) {
-        const float tau = ex2a(lt);
-        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
-        lq = A - lg2a(D);
-    } else {
-        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    }
-    return ex2a(fminf(lq, 126.f));
 }
 
 // Energy (code units) that cooling removes in one sub-cycle at T_e, with
@@ -471,24 +446,41 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     float4 nd;   // (1/x_j, log2 x_j, lb_j, lb_j+1): one 128-bit shared load on the step's path
     if (EXACT) {
         s = select_sub<3, true>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
-        if ((unsigned)(s.j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(k, k.tab.lsb, c, s.j / Fmt<FMT>::S, cc);
+        if ((unsigned)(s.j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, s.j / Fmt<FMT>::S, cc);
         nd = make_float4(0.f, axT[2 * nT + s.j], S.lb[s.j], S.lb[s.j + 1]);
     } else {
         // the guess is the interval used (a doubtful one only flags the cell),
         // so the window moves before the record is read: nothing is held
         // across the gather
         const int jg = select_guess<3>(k, k.tab.inv_dl[3], Te);
-        if ((unsigned)(jg - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(k, k.tab.lsb, c, jg / Fmt<FMT>::S, cc);
+        if ((unsigned)(jg - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, jg / Fmt<FMT>::S, cc);
         nd = S.tn[jg];
         s = select_finish<3>(k, jg, nd.x, k.tab.inv_dl[3], Te, clamp, cc.near);
     }
-    const int o = s.j - cc.base;
-    return bridge_energy(c, cc.win[o * kThreads], cc.win[(o + 1) * kThreads], nd, s.r, s.w);
+    const int j = s.j;
+    const int o = j - cc.base;
+    const float w = s.w;
+    const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
+    const float Lb = lerpf(nd.z, nd.w, w) + c.lb_off;
+    const float lT = nd.y + s.r;
+    const float M = fmaxf(Ls, Lb);
+    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
+    const float Bb = fmaf(4.f, lT, c.lbb_off);
+    const float lt = A - Bb;  // log2 tau_abs
+    float lq;
+    if (lt <= 60.f) {
+        const float tau = ex2a(lt);
+        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
+        lq = A - lg2a(D);
+    } else {
+        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
+        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
+    }
+    return ex2a(fminf(lq, 126.f));
 }
 
-
 // The same energy on the paper's table layout (Sec. 3.1): the total rate,
-// bridge included, interpolated from one 4-D table (k.tab.lst, read by the gather):
+// bridge included, interpolated from one 4-D table (c.row points into it):
 // q = 2^(L + log2(h / e_scale)).  FP32 table format only.
 template <bool EXACT>
 __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S, const CellC& c, Cache& cc,
@@ -497,7 +489,7 @@ __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S
     const float* axT = S.ax + k.tab.axis_off[3];
     const SelW s = select_sub<3, EXACT>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
     const int j = s.j;
-    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<0>::S - 1)) gather<0>(k, k.tab.lst, c, j / Fmt<0>::S, cc);
+    if ((unsigned)(j - cc.base) > (unsigned)(Fmt<0>::S - 1)) gather<0>(c, j / Fmt<0>::S, cc);
     const int o = j - cc.base;
     const float L = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], s.w) + c.ls_off;
     return ex2a(fminf(L, 126.f));
@@ -566,10 +558,18 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
     return true;
 }
 
-// The same solve in FP64 on the FP64 table (fp64_critical): the cell's H, B,
-// n_e selections are redone with FP64 keys and implicit_fp64 finds the root.
+// The same solve in FP64 on the FP64 table (fp64_critical, FP32 fields):
+// the cell's H, B, n_e selections are redone with FP64 keys.  From u32, the
+// FP32 solve's root (0: none), Newton steps on g(u) = u - u0 + q(u) with
+// g' = 1 + dq/du of the same interpolation: from the FP32 root's ~1e-6
+// relative error two steps reach FP64 rounding.  Accepted when a step falls
+// below 1e-14 u within 4 steps and every iterate stays within 2^-14 (in
+// log2 u) of u32; otherwise (a kink of the interpolation on the way, or no
+// FP32 root) implicit_fp64 solves from the bracket u32 2^+-(2^-14), or the
+// whole one when g does not change sign over it.  The result is rounded to
+// FP32.
 __device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
-                                                float u0, float& u_out, double xa0, double xb0) {
+                                                float u0, float& u_out, float u32) {
     Cell64 c64;
     unsigned dummy = 0u;
     c64.jt = -1;
@@ -578,8 +578,29 @@ __device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& 
     c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
     c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
     c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
+    const double U0 = (double)u0;
+    double x32 = nan64();
+    if (u32 > 0.f) {
+        const double ulo = (double)u32 * 0.9999576945484311, uhi = (double)u32 * 1.0000423072413958;
+        double u = (double)u32;
+        for (int it = 0; it < 4; ++it) {
+            double dq = 0.0;
+            const double q = cool_q64(k.k64, c64, u, (double)rho, dummy, &dq);
+            const double g = u - U0 + q, gp = 1.0 + dq;
+            if (!(gp > 0.0)) break;
+            const double step = g / gp;
+            const double un = u - step;
+            if (!(un > ulo && un < uhi)) break;
+            u = un;
+            if (fabs(step) <= 1e-14 * u) {
+                u_out = (float)u;
+                return true;
+            }
+        }
+        x32 = log2((double)u32);
+    }
     double u1;
-    if (!implicit_fp64(k.k64, c64, (double)rho, (double)u0, u1, xa0, xb0)) return false;
+    if (!implicit_fp64(k.k64, c64, (double)rho, U0, u1, x32 - 0x1p-14, x32 + 0x1p-14)) return false;
     u_out = (float)u1;
     return true;
 }
@@ -674,13 +695,6 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
     k.tn_off = (na + t->dev.n[3] + t->dev.n[4] * k.lc_stride + 3) & ~3;
     k.smem_floats = k.tn_off + 4 * (t->dev.n[3] - 1);
     k.sched = nullptr;
-    {
-        const int n3 = t->dev.n[3];
-        k.shared_T = n3 == t->dev.n[4] && t->dev.inv_dl[3] == t->dev.inv_dl[4] && k.g_c0[3] == k.g_c0[4] &&
-                     k.g_wb[3] == k.g_wb[4] && k.g_x0[3] == k.g_x0[4] && k.g_xn[3] == k.g_xn[4] &&
-                     memcmp(t->h_axes + t->dev.axis_off[3], t->h_axes + t->dev.axis_off[4],
-                            sizeof(float) * 3 * n3) == 0;
-    }
 }
 
 }  // namespace
