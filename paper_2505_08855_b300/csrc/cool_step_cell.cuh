@@ -85,6 +85,8 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         c.tau_sca = k.two_sigT * ne * Hc;
     }
     const float lcc_off = c.lb_off;  // log2(h n_e^2 / e_scale)
+    Cell64 c64;                      // fp64_critical implicit: the cell's FP64 selections, made when first stiff
+    c64.jt = -2;
     const int nC = T.n[4];
     const float* axC = S.ax + T.axis_off[4];
     float sum_q = 0.f, sum_x = 0.f;
@@ -146,7 +148,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
                     // bracketed solve around it or over the whole bracket)
                     float u32 = 0.f;
                     if (!implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u32)) u32 = 0.f;
-                    ok = implicit_fp64_cell(k, T, rho, B, H, ue, u1, u32);
+                    ok = implicit_fp64_cell(k, T, rho, B, H, ue, u1, u32, c64);
                 } else {
                     ok = implicit_fp32<FMT, EXACT>(k, S, c, cc, inv_e, ue, q, u1);
                 }

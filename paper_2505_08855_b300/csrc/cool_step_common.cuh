@@ -112,12 +112,13 @@ __device__ double cool_q64(const StepK64& k, Cell64& c, double ue, double rho, u
     double Q = qthin / D;
     if (dqdu) {
         // d/dln T_e: the weight moves by 1/(dl ln 2) inside the interval
+        // (FP64 divisions are slow on this part: one reciprocal of D serves)
         const bool inside = wt > 0.0 && wt < 1.0;
-        const double dw = inside ? 1.0 / (T.dl64[3] * 0.6931471805599453) : 0.0;
-        const double dthin = 0.6931471805599453 * dw * (qb * (T.lb64[jt + 1] - T.lb64[jt]) + qs * (c.v1 - c.v0));
-        const double dtau = c.Hc * dthin / bb4 - 4.0 * tau_abs;
+        const double dthin = inside ? (qb * (T.lb64[jt + 1] - T.lb64[jt]) + qs * (c.v1 - c.v0)) / T.dl64[3] : 0.0;
+        const double dtau = tau_abs * (dthin / qthin - 4.0);
         const double dD = (sqrt(3.0) + 3.0 * tau_abs + 1.5 * tau_sca) * dtau;
-        *dqdu = k.hs / k.escale * (dthin / D - qthin * dD / (D * D)) / ue;   // dln T_e/du = 1/u
+        const double rD = 1.0 / D;
+        *dqdu = k.hs * (dthin - Q * dD) * rD / (k.escale * ue);   // dln T_e/du = 1/u
     }
     return k.hs * Q / k.escale;
 }
@@ -559,7 +560,9 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
 }
 
 // The same solve in FP64 on the FP64 table (fp64_critical, FP32 fields):
-// the cell's H, B, n_e selections are redone with FP64 keys.  From u32, the
+// the cell's H, B, n_e selections with FP64 keys are made on its first
+// stiff sub-cycle (c64.jt == -2) and kept in c64 for the next ones, with
+// the collapse of the last T_e interval visited.  From u32, the
 // FP32 solve's root (0: none), Newton steps on g(u) = u - u0 + q(u) with
 // g' = 1 + dq/du of the same interpolation: from the FP32 root's ~1e-6
 // relative error two steps reach FP64 rounding.  Accepted when a step falls
@@ -569,15 +572,16 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
 // whole one when g does not change sign over it.  The result is rounded to
 // FP32.
 __device__ __noinline__ bool implicit_fp64_cell(const StepK& k, const DevTable& T, float rho, float B, float H,
-                                                float u0, float& u_out, float u32) {
-    Cell64 c64;
+                                                float u0, float& u_out, float u32, Cell64& c64) {
     unsigned dummy = 0u;
-    c64.jt = -1;
-    c64.ne = (double)rho * k.k64.s_n;
-    c64.Hc = (double)H * k.k64.s_H;
-    c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
-    c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
-    c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
+    if (c64.jt == -2) {
+        c64.jt = -1;
+        c64.ne = (double)rho * k.k64.s_n;
+        c64.Hc = (double)H * k.k64.s_H;
+        c64.jh = select64(T, 0, c64.Hc, c64.wh, dummy);
+        c64.jb = select64(T, 1, (double)B * k.k64.s_B, c64.wb, dummy);
+        c64.jn = select64(T, 2, c64.ne, c64.wn, dummy);
+    }
     const double U0 = (double)u0;
     double x32 = nan64();
     if (u32 > 0.f) {
