@@ -647,8 +647,9 @@ def run_suite_perf(args, torch, cool, inputs, dev):
         # timed launches each, so that one ncu capture of every k_step launch
         # of this section covers all of them): the L2 block layout (default),
         # the same with the persisting-L2 reservation, the two texture paths,
-        # the TMA-staged fields, the block-scaled BF16 table; then, on the
-        # 448 x 192 x 192 shell (spatially coherent cells), the bound on
+        # the TMA-staged fields, the block-scaled BF16 table; the paper-size
+        # 100^4 table (beyond L2) on the block layout and both texture paths;
+        # then, on the 448 x 192 x 192 shell (spatially coherent cells), the bound on
         # staging the table per tile: the same step with a 4-D channel of
         # 2x2x2 corners x 64 T_e nodes (L1-resident) against the
         # 128 x 128 x 64 x 64 table (302 MB).
@@ -676,6 +677,18 @@ def run_suite_perf(args, torch, cool, inputs, dev):
                         BYTES_PER_CELL, peak)
         t32.free()
         tbs.free()
+        # the paper's table size (100 nodes per axis; 457 MB packed, 3.6x L2):
+        # the block layout against both texture paths beyond L2
+        big = cool.Table(cool.TableSpec(n=(100,) * 5))
+        for name, p in (("100^4 table, L2 block layout", p8),
+                        ("100^4 table, texture, hardware trilinear filtering",
+                         cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_HWLERP)),
+                        ("100^4 table, texture, point fetches + FP32 lerp",
+                         cool.Params(n_sub=N_SUB, path=cool.PATH_TEXTURE_POINT))):
+            ms = _timed(torch, lambda: cool.step(big, p, *fl, ue_out=uo, ui_out=io), 2, 1, stream)
+            _suite_line(f"placement: {name}", WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()},
+                        BYTES_PER_CELL, peak)
+        big.free()
         del fl, uo, io
         S = inputs.make("shell_448x192x192")
         sf = [torch.from_numpy(S[k]).to(dev) for k in ("rho", "B", "H", "ue", "ui")]
