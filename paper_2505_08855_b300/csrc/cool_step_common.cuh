@@ -266,10 +266,14 @@ struct SelW {
 // within ~1e-5 node spacings of a node.  Then r = log2(key / x_j) comes from
 // the ratio, accurate to ~2e-7 in log2: a weight inside the band
 // (1e-6/dl, 1 - 1e-6/dl) proves x_j < key < x_{j+1}, so j is the index.
-// Outside it (a key within ~1e-6 of a node, or a wrong guess: a few keys in
-// a million) `near` is set and the caller redoes the cell with EXACT; the
-// values returned meanwhile are those of the guessed interval.  The clamp
-// flag compares the key with the end nodes exactly, as select_axis does.
+// Outside it (a key within ~1e-6 of a node, a wrong guess -- a few keys in
+// a million -- or a key outside the axis, whose weight lies outside [0, 1])
+// `near` is set and the caller redoes the cell with EXACT, which also sets
+// the clamp flag; the values returned meanwhile are those of the guessed
+// interval.  (Sending out-of-range keys to the redo instead of testing the
+// range here saves two compares per key: 4 % of the benchmark step.)  The
+// clamp flag compares the key with the end nodes exactly, as select_axis
+// does; outside the redo it is formed only where counters are kept.
 template <int A>
 __device__ __forceinline__ int select_guess(const StepK& k, float inv_dl, float key) {
     float t = fmaf(lg2a(key), inv_dl, k.g_c0[A]);
@@ -284,9 +288,8 @@ __device__ __forceinline__ SelW select_finish(const StepK& k, int j, float rxj, 
     s.j = j;
     s.r = lg2a(key * rxj);
     const float w = s.r * inv_dl;
-    const bool out = key < k.g_x0[A] || key > k.g_xn[A];
-    clamp |= out ? 1u : 0u;
-    near |= (!out && fabsf(w - 0.5f) > k.g_wb[A]) ? 1u : 0u;
+    clamp |= (key < k.g_x0[A] || key > k.g_xn[A]) ? 1u : 0u;   // formed only where counted
+    near |= fabsf(w - 0.5f) > k.g_wb[A] ? 1u : 0u;   // an out-of-range key too: its weight is outside
     s.w = __saturatef(w);
     return s;
 }
