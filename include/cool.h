@@ -311,7 +311,12 @@ cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_
  * additions is not deterministic).  The forward sub-cycles are recomputed,
  * not stored; explicit and limited sub-cycles are differentiated on the
  * branch taken, implicit ones by the implicit-function theorem at the root.
- * Invalid cells pass the output adjoints through.  The inputs must not alias
+ * Without table gradients (all three NULL) the chain rule runs in the
+ * forward order (the 2x5 Jacobian of the cell carried along the
+ * sub-cycles); with any of them, in the reverse order over the kept
+ * sub-cycle states.  The two give the same input gradients up to FP32
+ * rounding order (not bitwise).  Invalid cells pass the output adjoints
+ * through.  The inputs must not alias
  * the gradient outputs.  Device pointers, asynchronous on stream; n_sub <= 64. */
 cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
                           const float* B, const float* H, const float* u_e_in, const float* u_i_in,

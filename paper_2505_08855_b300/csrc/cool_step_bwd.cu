@@ -5,14 +5,16 @@ namespace cool {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Adjoint (cool_step_bwd).  Per cell: the forward sub-cycles are recomputed
-// with the forward kernel's own functions (same trajectory, same branches),
-// keeping each sub-cycle's state; then a reverse sweep applies, per
-// sub-cycle, the hand-derived partial derivatives of the cooling energy q
-// and of the Coulomb transfer X (below), the limiter's branch, and for an
-// implicit sub-cycle the implicit-function theorem at the root
-// (du*/du1 = 1/(1 + dq/du), du*/dtheta = -dq/dtheta / (1 + dq/du)).
-// Table adjoints go to the natural layouts: synchrotron [nH nB nN nT] with
+// Adjoint (cool_step_bwd).  Per cell the forward sub-cycles are recomputed
+// with the forward kernel's own functions (same trajectory, same branches)
+// and differentiated with the hand-derived partial derivatives of the
+// cooling energy q and of the Coulomb transfer X (below), the limiter's
+// branch, and for an implicit sub-cycle the implicit-function theorem at
+// the root (du*/du1 = 1/(1 + dq/du), du*/dtheta = -dq/dtheta / (1 + dq/du)).
+// Input gradients alone: forward tangents (k_step_tan_f32), the 2x5
+// Jacobian carried along the sub-cycles.  With table adjoints: each
+// sub-cycle's state is kept and a reverse sweep (k_step_bwd_f32) sends the
+// table adjoints to the natural layouts: synchrotron [nH nB nN nT] with
 // global atomics, brems and Coulomb through shared-memory partial sums.
 // ---------------------------------------------------------------------------
 constexpr int kMaxSub = 64;
@@ -195,14 +197,43 @@ __device__ __forceinline__ XGrad coulomb_grad(const StepK& k, const Smem& S, flo
     return x;
 }
 
+// The per-cell constants of both adjoint kernels, from (rho, B, H): the
+// (H, B, n_e) selection (exact rule) with its weights, the weights'
+// derivative constants, and the bridge's offsets.
+__device__ __forceinline__ void bwd_cell(const StepK& k, const Smem& S, float rho, float B, float H,
+                                         CellC& c, CellD& cd, unsigned& clamp) {
+    const DevTable& T = k.tab;
+    const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
+    unsigned unused = 0u;
+    const SelW sh = select_sub<0, true>(k, S.ax + T.axis_off[0] + T.n[0], T.n[0], T.inv_dl[0], Hc, clamp, unused);
+    const SelW sb = select_sub<1, true>(k, S.ax + T.axis_off[1] + T.n[1], T.n[1], T.inv_dl[1], Bg, clamp, unused);
+    const SelW sn = select_sub<2, true>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne, clamp, unused);
+    const int rowf = 8 * T.nblk;
+    c.oN = rowf;
+    c.oB = rowf * T.n[2];
+    c.oH = c.oB * T.n[1];
+    c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
+    const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
+    c.wh = __saturatef(rh);
+    c.wb = __saturatef(rb);
+    c.wn = __saturatef(rn);
+    cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] * kInvLn2 : 0.f;
+    cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] * kInvLn2 : 0.f;
+    cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] * kInvLn2 : 0.f;
+    c.ls_off = k.l_hs_e;
+    c.lb_off = fmaf(2.f, lg2a(ne), k.l_hs_e);
+    c.lbb_off = k.l_bb - lg2a(Hc);
+    c.tau_sca = k.two_sigT * ne * Hc;
+}
+
 // SMS: the per-sub-cycle state lives in shared memory (n_sub <= kSmemSub,
 // column layout, conflict-free) instead of thread-local arrays.
 constexpr int kSmemSub = 8;
 constexpr int kStateFloats = 7;   // floats of per-sub-cycle state (ST_F)
 
-// TBL: table adjoints requested (g_lb, g_ls or g_lc non-null); without,
-// the kernel carries no table-adjoint code.
-template <bool SMS, bool TBL>
+// With table adjoints requested (g_lb, g_ls or g_lc non-null); the input
+// gradients alone come from k_step_tan_f32.
+template <bool SMS>
 __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
     const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
@@ -216,7 +247,6 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     float* glc_s = glb_s + k.tab.n[3];                             // partial Coulomb adjoints
     const DevTable& T = k.tab;
     const int nT = T.n[3], nC = T.n[4];
-    constexpr bool tbl = TBL;
     for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
     __syncthreads();
     // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
@@ -235,12 +265,6 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 #define ST_XE(sub) ST_F(sub, 4)
 #define ST_XI(sub) ST_F(sub, 5)
 #define ST_XR(sub) ST_F(sub, 6)
-// without table adjoints slots 0..3 hold the cooling's partials instead:
-// q dln q/dln u / u, q dln q/dln rho / rho, the same for B and H
-#define ST_QU(sub) ST_F(sub, 0)
-#define ST_QR(sub) ST_F(sub, 1)
-#define ST_QB(sub) ST_F(sub, 2)
-#define ST_QH(sub) ST_F(sub, 3)
 #define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
     // cells in chunks of 32 (one per lane): each warp's first chunk by its
     // index in the grid, the next ones from the tile counter (k.sched) as
@@ -261,38 +285,13 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 goto next_chunk;
             }
             unsigned clamp = 0u;
-            const float ne = rho * k.s_n, Bg = B * k.s_B, Hc = H * k.s_H;
             const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
             const float inv_rho = 1.f / rho;
             const float inv_B = B > 0.f ? 1.f / B : 0.f;   // used only where dq/dB != 0 (B above the first node)
             const float inv_H = H > 0.f ? 1.f / H : 0.f;
             CellC c;
             CellD cd;
-            {
-                unsigned unused = 0u;
-                const SelW sh = select_sub<0, true>(k, S.ax + T.axis_off[0] + T.n[0], T.n[0], T.inv_dl[0], Hc,
-                                                    clamp, unused);
-                const SelW sb = select_sub<1, true>(k, S.ax + T.axis_off[1] + T.n[1], T.n[1], T.inv_dl[1], Bg,
-                                                    clamp, unused);
-                const SelW sn = select_sub<2, true>(k, S.ax + T.axis_off[2] + T.n[2], T.n[2], T.inv_dl[2], ne,
-                                                    clamp, unused);
-                const int rowf = 8 * T.nblk;
-                c.oN = rowf;
-                c.oB = rowf * T.n[2];
-                c.oH = c.oB * T.n[1];
-                c.row = T.lsb + (long long)((sh.j * T.n[1] + sb.j) * T.n[2] + sn.j) * rowf;
-                const float rh = sh.r * T.inv_dl[0], rb = sb.r * T.inv_dl[1], rn = sn.r * T.inv_dl[2];
-                c.wh = __saturatef(rh);
-                c.wb = __saturatef(rb);
-                c.wn = __saturatef(rn);
-                cd.cH = (rh > 0.f && rh < 1.f) ? T.inv_dl[0] * kInvLn2 : 0.f;
-                cd.cB = (rb > 0.f && rb < 1.f) ? T.inv_dl[1] * kInvLn2 : 0.f;
-                cd.cN = (rn > 0.f && rn < 1.f) ? T.inv_dl[2] * kInvLn2 : 0.f;
-                c.ls_off = k.l_hs_e;
-                c.lb_off = fmaf(2.f, lg2a(ne), k.l_hs_e);
-                c.lbb_off = k.l_bb - lg2a(Hc);
-                c.tau_sca = k.two_sigT * ne * Hc;
-            }
+            bwd_cell(k, S, rho, B, H, c, cd, clamp);
             const float lcc_off = c.lb_off;
             Cache cc;
             cc.base = -8;
@@ -301,48 +300,26 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             GCache gc;
             gc.j = -1;
             // ---- forward, recorded (the forward kernel's arithmetic) ----
-            // Without table adjoints the cooling energy comes from cool_grad
-            // (the same selection, corner collapse and bridge as cool_energy,
-            // hence the same q) with its partials, kept for the reverse sweep;
-            // with them the states are kept and the reverse sweep re-evaluates.
             for (int sub = 0; sub < k.n_sub; ++sub) {
-                if (tbl) {
-                    ST_UE(sub) = ue;
-                    ST_UI(sub) = ui;
-                }
+                ST_UE(sub) = ue;
+                ST_UI(sub) = ui;
                 const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
                 ue += xg.X;
                 ui -= xg.X;
-                if (tbl) ST_U1(sub) = ue;
+                ST_U1(sub) = ue;
                 ST_XE(sub) = xg.due;
                 ST_XI(sub) = xg.dui;
                 ST_XR(sub) = xg.drho;
-                QGrad g;
-                float q;
-                if (tbl) {
-                    q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
-                } else {
-                    g = cool_grad(k, S, c, cd, gc, ue, inv_e);
-                    q = g.q;
-                }
+                const float q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
                 float du = fminf(q, k.limiter * ue);
                 unsigned char br = q < k.limiter * ue ? 0 : 1;
-                float u_at = ue;   // where the cooling's partials are taken
                 if (k.mode == 1 && q > k.limiter * ue) {
                     float u1;
                     if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
                         du = ue - u1;
                         br = 2;
-                        u_at = u1;
-                        if (tbl) ST_US(sub) = u1;
-                        else g = cool_grad(k, S, c, cd, gc, u1, inv_e);
+                        ST_US(sub) = u1;
                     }
-                }
-                if (!tbl && br != 1) {
-                    ST_QU(sub) = __fdividef(g.q * g.du, u_at);
-                    ST_QR(sub) = g.q * g.drho * inv_rho;
-                    ST_QB(sub) = g.dB != 0.f ? g.q * g.dB * inv_B : 0.f;
-                    ST_QH(sub) = g.dH != 0.f ? g.q * g.dH * inv_H : 0.f;
                 }
                 ST_BR(sub) = br;
                 ue -= du;
@@ -371,19 +348,6 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 const unsigned char br = ST_BR(sub);
                 if (br == 1) {
                     ge1 = (1.f - k.limiter) * ge;
-                } else if (!tbl) {
-                    const float qu = ST_QU(sub);
-                    float sc;
-                    if (br == 2) {
-                        ge1 = __fdividef(ge, 1.f + qu);
-                        sc = -ge1;
-                    } else {
-                        ge1 = ge * (1.f - qu);
-                        sc = -ge;
-                    }
-                    grho += sc * ST_QR(sub);
-                    gB += sc * ST_QB(sub);
-                    gH += sc * ST_QH(sub);
                 } else {
                     const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
                     const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
@@ -456,10 +420,6 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 #undef ST_XE
 #undef ST_XI
 #undef ST_XR
-#undef ST_QU
-#undef ST_QR
-#undef ST_QB
-#undef ST_QH
 #undef ST_BR
     __syncthreads();
     if (g_lb)
@@ -470,6 +430,124 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             if (glc_s[i] != 0.f) atomicAdd(&g_lc[i], glc_s[i]);
 }
 
+// The input gradients without table adjoints, by forward tangents.  The
+// step maps five inputs (rho, B, H, u_e, u_i) to two outputs, so the 2x5
+// Jacobian d(u_e, u_i)/d(inputs) is carried through the sub-cycles in
+// registers -- the chain rule applied in the forward order, with the same
+// partials of X and q the reverse sweep uses -- and contracted with the
+// output gradients at the end.  The product is the reverse sweep's
+// (different FP32 rounding order), with no per-sub-cycle state.
+// IMPL: the implicit mode's solve is compiled in; the explicit-only kernel
+// fits 64 registers without spills, 4 blocks (32 warps) per SM.
+template <bool IMPL>
+__global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
+    StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
+    const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
+    const float* __restrict__ gue_out, const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
+    float* g_ue, float* g_ui) {
+    extern __shared__ float sm[];
+    load_smem(k, sm);
+    const Smem S = smem_view(k, sm);
+    float* win = sm + smem_table_floats(k) + threadIdx.x;           // 8-row window (FP32 table)
+    const int lane = threadIdx.x & 31;
+    const long long nchunks = (n + 31) / 32;
+    const long long first = (long long)gridDim.x * kWarps;
+    long long chunk = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    while (chunk < nchunks) {
+        const long long i = chunk * 32 + lane;
+        if (i < n) {
+            const float rho = rho_in[i], B = B_in[i], H = H_in[i];
+            float ue = ue_in[i], ui = ui_in[i];
+            const float ge_out = gue_out[i], gi_out = gui_out[i];
+            if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
+                !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
+                g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
+            } else {
+                unsigned clamp = 0u;
+                const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
+                const float inv_rho = 1.f / rho;
+                const float inv_B = B > 0.f ? 1.f / B : 0.f;
+                const float inv_H = H > 0.f ? 1.f / H : 0.f;
+                CellC c;
+                CellD cd;
+                bwd_cell(k, S, rho, B, H, c, cd, clamp);
+                const float lcc_off = c.lb_off;
+                Cache cc;
+                cc.base = -8;
+                cc.win = win;
+                cc.near = 0u;
+                GCache gc;
+                gc.j = -1;
+                // tangents: je[x] = d u_e / d x, ji[x] = d u_i / d x for
+                // x = rho, B, H, u_e(in), u_i(in)
+                float je[5] = {0.f, 0.f, 0.f, 1.f, 0.f};
+                float ji[5] = {0.f, 0.f, 0.f, 0.f, 1.f};
+                for (int sub = 0; sub < k.n_sub; ++sub) {
+                    // exchange: u_e += X, u_i -= X
+                    const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
+                    ue += xg.X;
+                    ui -= xg.X;
+#pragma unroll
+                    for (int x = 0; x < 5; ++x) {
+                        float dX = fmaf(xg.due, je[x], xg.dui * ji[x]);
+                        if (x == 0) dX += xg.drho;
+                        je[x] += dX;
+                        ji[x] -= dX;
+                    }
+                    // cooling: free, limited or implicit, as the forward step
+                    QGrad g = cool_grad(k, S, c, cd, gc, ue, inv_e);
+                    const float q = g.q;
+                    float du = fminf(q, k.limiter * ue);
+                    int br = q < k.limiter * ue ? 0 : 1;
+                    float u_at = ue;
+                    if (IMPL && q > k.limiter * ue) {
+                        float u1;
+                        if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
+                            du = ue - u1;
+                            br = 2;
+                            u_at = u1;
+                            g = cool_grad(k, S, c, cd, gc, u1, inv_e);
+                        }
+                    }
+                    if (br == 1) {
+                        const float f = 1.f - k.limiter;
+#pragma unroll
+                        for (int x = 0; x < 5; ++x) je[x] *= f;
+                    } else {
+                        // dq = qu du + q_rho drho + q_B dB + q_H dH
+                        const float qu = __fdividef(g.q * g.du, u_at);
+                        const float qx[3] = {g.q * g.drho * inv_rho, g.dB != 0.f ? g.q * g.dB * inv_B : 0.f,
+                                             g.dH != 0.f ? g.q * g.dH * inv_H : 0.f};
+                        if (br == 2) {
+                            // u* + q(u*) = u_e: du* = (du_e - q_x dx) / (1 + qu)
+                            const float r = __fdividef(1.f, 1.f + qu);
+#pragma unroll
+                            for (int x = 0; x < 5; ++x) je[x] = (x < 3 ? je[x] - qx[x < 3 ? x : 0] : je[x]) * r;
+                        } else {
+                            const float f = 1.f - qu;
+#pragma unroll
+                            for (int x = 0; x < 5; ++x) je[x] = x < 3 ? fmaf(je[x], f, -qx[x < 3 ? x : 0]) : je[x] * f;
+                        }
+                    }
+                    ue -= du;
+                }
+                g_rho[i] = fmaf(ge_out, je[0], gi_out * ji[0]);
+                g_B[i] = fmaf(ge_out, je[1], gi_out * ji[1]);
+                g_H[i] = fmaf(ge_out, je[2], gi_out * ji[2]);
+                g_ue[i] = fmaf(ge_out, je[3], gi_out * ji[3]);
+                g_ui[i] = fmaf(ge_out, je[4], gi_out * ji[4]);
+            }
+        }
+        if (k.sched) {
+            unsigned long long nt = 0;
+            if (lane == 0) nt = atomicAdd(k.sched, 1ull);
+            chunk = first + (long long)__shfl_sync(0xffffffffu, nt, 0);
+        } else {
+            chunk += first;
+        }
+    }
+}
+
 }  // namespace
 
 cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long long n, const float* rho,
@@ -477,16 +555,22 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
                                 const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
                                 float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st) {
     if (n == 0) return COOL_OK;
+    const bool tbl = g_lb || g_ls || g_lc;
     if (t->dev.fmt != 0 || p->fp64_critical || p->n_sub > kMaxSub) return COOL_EUNSUPPORTED;
     StepK k;
     fill_stepk(t, p, k);
     const bool sms = p->n_sub <= kSmemSub;
-    size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads + t->dev.n[3] +
-                           ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
-    if (sms) smem += (size_t)kSmemSub * kThreads * (kStateFloats * sizeof(float) + 1);
-    const bool tbl = g_lb || g_ls || g_lc;
-    auto fn = sms ? (tbl ? k_step_bwd_f32<true, true> : k_step_bwd_f32<true, false>)
-                  : (tbl ? k_step_bwd_f32<false, true> : k_step_bwd_f32<false, false>);
+    // without table adjoints: forward tangents (the table parts and the
+    // window in shared memory); with them: the recorded forward and the
+    // reverse sweep (plus the partial sums and the sub-cycles' state)
+    size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads) * sizeof(float);
+    if (tbl) {
+        smem += (size_t)(t->dev.n[3] + ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
+        if (sms) smem += (size_t)kSmemSub * kThreads * (kStateFloats * sizeof(float) + 1);
+    }
+    const bool impl = p->mode == COOL_IMPLICIT_STIFF;
+    const void* fn = !tbl ? (impl ? (const void*)k_step_tan_f32<true> : (const void*)k_step_tan_f32<false>)
+                     : sms ? (const void*)k_step_bwd_f32<true> : (const void*)k_step_bwd_f32<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_cuda_error(e);
     int per_sm = 0;
@@ -504,8 +588,13 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
             if (e != cudaSuccess) return set_cuda_error(e);
         }
     }
-    fn<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui, g_lb,
-                                            g_ls, g_lc);
+    if (tbl) {
+        auto fb = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
+        fb<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui,
+                                                g_lb, g_ls, g_lc);
+    } else
+        (impl ? k_step_tan_f32<true> : k_step_tan_f32<false>)<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
+                                                            g_ue, g_ui);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
