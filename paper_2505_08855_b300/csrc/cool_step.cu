@@ -162,7 +162,8 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
     // block of this format) and the warps' field tiles
     size_t smem = (size_t)(smem_table_floats(k) + fmt_nodes(fmt) * kThreads) * sizeof(float);
     if (vec) smem += (size_t)kWarps * (disk ? 6 : 5) * kWarpCells * sizeof(float);
-    if (vec && p->fp64_critical) smem += (size_t)kWarps * kWarpCells;   // the deferred cells' lists
+    if (vec && (p->fp64_critical || p->mode == COOL_IMPLICIT_STIFF))
+        smem += (size_t)kWarps * kWarpCells;   // the deferred cells' lists
     // the kernels are indexed by implicit | fp64_critical << 1 | counters << 2
     // (template bits 0, 1 and 3); 16-bit formats come from cool_step_f16.cu
     // and cool_step_f16s.cu

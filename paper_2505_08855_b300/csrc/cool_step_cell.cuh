@@ -140,7 +140,7 @@ __device__ __forceinline__ Out step_cell(const StepK& k, const Smem& S, float* w
         float du = fminf(q, k.limiter * ue);
         if ((VAR & 1) && q > k.limiter * ue) {
             stiff = 1u;
-            if (!(VAR & 32)) {   // bit 5: flagged only, the cell is stepped again with the FP64 solve
+            if (!(VAR & 32)) {   // bit 5: flagged only, the cell is stepped again with the solve
                 float u1;
                 bool ok;
                 if (VAR & 2) {

@@ -271,9 +271,14 @@ struct SelW {
 // `near` is set and the caller redoes the cell with EXACT, which also sets
 // the clamp flag; the values returned meanwhile are those of the guessed
 // interval.  (Sending out-of-range keys to the redo instead of testing the
-// range here saves two compares per key: 4 % of the benchmark step.)  The
-// clamp flag compares the key with the end nodes exactly, as select_axis
-// does; outside the redo it is formed only where counters are kept.
+// range here saves two compares per key: 4 % of the benchmark step.)
+// RANGE: the implicit solve's trial keys, which fall outside the axis in
+// most solves: there the range is tested and an out-of-range key does not
+// set `near`, since its guess is already select_axis's result (the guess
+// clamps to the end interval, the weight to 0 or 1, and both take r from
+// the same ratio).  The clamp flag compares the key with the end nodes
+// exactly, as select_axis does; outside the redo it is formed only where
+// counters are kept.
 template <int A>
 __device__ __forceinline__ int select_guess(const StepK& k, float inv_dl, float key) {
     float t = fmaf(lg2a(key), inv_dl, k.g_c0[A]);
@@ -281,28 +286,30 @@ __device__ __forceinline__ int select_guess(const StepK& k, float inv_dl, float 
     return __float_as_int(__fadd_rn(t, 12582912.f)) - 0x4B400000;
 }
 
-template <int A>
+template <int A, bool RANGE = false>
 __device__ __forceinline__ SelW select_finish(const StepK& k, int j, float rxj, float inv_dl, float key,
                                               unsigned& clamp, unsigned& near) {
     SelW s;
     s.j = j;
     s.r = lg2a(key * rxj);
     const float w = s.r * inv_dl;
-    clamp |= (key < k.g_x0[A] || key > k.g_xn[A]) ? 1u : 0u;   // formed only where counted
-    near |= fabsf(w - 0.5f) > k.g_wb[A] ? 1u : 0u;   // an out-of-range key too: its weight is outside
+    const bool out = key < k.g_x0[A] || key > k.g_xn[A];
+    clamp |= out ? 1u : 0u;   // formed only where counted
+    if (RANGE) near |= (fabsf(w - 0.5f) > k.g_wb[A] && !out) ? 1u : 0u;
+    else near |= fabsf(w - 0.5f) > k.g_wb[A] ? 1u : 0u;   // an out-of-range key too: its weight is outside
     s.w = __saturatef(w);
     return s;
 }
 
 // EXACT: the guess where its weight confirms it, node compares (select_axis)
 // where it does not; the same j, r, w as select_axis in every case.
-template <int A, bool EXACT>
+template <int A, bool EXACT, bool RANGE = false>
 __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int n, float inv_dl, float key,
                                            unsigned& clamp, unsigned& near) {
     const int j = select_guess<A>(k, inv_dl, key);
     if (EXACT) {
         unsigned doubt = 0u;
-        SelW s = select_finish<A>(k, j, rx[j], inv_dl, key, clamp, doubt);
+        SelW s = select_finish<A, RANGE>(k, j, rx[j], inv_dl, key, clamp, doubt);
         if (doubt) {
             const Sel e = select_axis(rx - n, n, inv_dl, key, clamp);
             s.j = e.j;
@@ -311,7 +318,7 @@ __device__ __forceinline__ SelW select_sub(const StepK& k, const float* rx, int 
         }
         return s;
     }
-    return select_finish<A>(k, j, rx[j], inv_dl, key, clamp, near);
+    return select_finish<A, RANGE>(k, j, rx[j], inv_dl, key, clamp, near);
 }
 
 // Per-cell, step-invariant part of the 4-D lookup and the cooling constants.
@@ -445,7 +452,8 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
 // The common path has no range branches: 2^d underflows to 0 where one
 // channel is negligible and tau_abs to 0 where the cell is thin; only
 // tau_abs > 2^60 (where tau_abs^2 would overflow) takes the asymptotic form.
-template <int FMT, bool EXACT>
+// RANGE: a trial key of the implicit solve (select_finish).
+template <int FMT, bool EXACT, bool RANGE = false>
 __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, const CellC& c,
                                              Cache& cc, float Te, unsigned& clamp) {
     const int nT = k.tab.n[3];
@@ -453,7 +461,7 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     SelW s;
     float4 nd;   // (1/x_j, log2 x_j, lb_j, lb_j+1): one 128-bit shared load on the step's path
     if (EXACT) {
-        s = select_sub<3, true>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
+        s = select_sub<3, true, RANGE>(k, axT + nT, nT, k.tab.inv_dl[3], Te, clamp, cc.near);
         if ((unsigned)(s.j - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, s.j / Fmt<FMT>::S, cc);
         nd = make_float4(0.f, axT[2 * nT + s.j], S.lb[s.j], S.lb[s.j + 1]);
     } else {
@@ -463,7 +471,7 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
         const int jg = select_guess<3>(k, k.tab.inv_dl[3], Te);
         if ((unsigned)(jg - cc.base) > (unsigned)(Fmt<FMT>::S - 1)) gather<FMT>(c, jg / Fmt<FMT>::S, cc);
         nd = S.tn[jg];
-        s = select_finish<3>(k, jg, nd.x, k.tab.inv_dl[3], Te, clamp, cc.near);
+        s = select_finish<3, RANGE>(k, jg, nd.x, k.tab.inv_dl[3], Te, clamp, cc.near);
     }
     const int j = s.j;
     const int o = j - cc.base;
@@ -518,7 +526,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
     float xb = lg2a(u0);
     float xa = xb - 60.f;
     const float ua0 = ex2a(xa);
-    const float qa0 = cool_energy<FMT, EXACT>(k, S, c, cc, ua0 * inv_e, trial);
+    const float qa0 = cool_energy<FMT, EXACT, true>(k, S, c, cc, ua0 * inv_e, trial);
     if (!(ua0 - u0 + qa0 < 0.f)) return false;
     float Gb = lg2a(fmaf(q0, inv_u0, 1.f));
     float Ga = lg2a((ua0 + qa0) * inv_u0);
@@ -528,7 +536,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
         float x = xb - Gb * (xb - xa) / (Gb - Ga);
         if (!(x > xa && x < xb)) x = 0.5f * (xa + xb);
         const float u = ex2a(x);
-        const float G = lg2a((u + cool_energy<FMT, EXACT>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
+        const float G = lg2a((u + cool_energy<FMT, EXACT, true>(k, S, c, cc, u * inv_e, trial)) * inv_u0);
         if (G > 0.f) {
             xb = x; Gb = G;
             if (side == 1) Ga *= 0.5f;
@@ -540,8 +548,8 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
         }
     }
     float a = ex2a(xa), b = ex2a(xb);
-    float ga = a - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, a * inv_e, trial);
-    float gb = b - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, b * inv_e, trial);
+    float ga = a - u0 + cool_energy<FMT, EXACT, true>(k, S, c, cc, a * inv_e, trial);
+    float gb = b - u0 + cool_energy<FMT, EXACT, true>(k, S, c, cc, b * inv_e, trial);
     // an end whose residual rounds to the wrong sign is the root to rounding
     float u = !(ga < 0.f) ? a : (!(gb > 0.f) ? b : 0.5f * (a + b));
     side = 0;
@@ -549,7 +557,7 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
         u = b - gb * (b - a) / (gb - ga);
         if (!(u > a && u < b)) u = 0.5f * (a + b);
         if (b - a <= 2.4e-7f * b) break;
-        const float g = u - u0 + cool_energy<FMT, EXACT>(k, S, c, cc, u * inv_e, trial);
+        const float g = u - u0 + cool_energy<FMT, EXACT, true>(k, S, c, cc, u * inv_e, trial);
         if (g > 0.f) {
             b = u; gb = g;
             if (side == 1) ga *= 0.5f;

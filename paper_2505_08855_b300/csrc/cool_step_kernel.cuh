@@ -14,7 +14,8 @@ namespace {
 // geometry) and bit 3, counters requested: without it no counter flag is
 // formed (the flag arithmetic of step_cell is dead code) and nothing is
 // counted.  Shared memory after the warps' staging tiles: one list of up to
-// 128 tile indices per warp (the cells deferred to the FP64 options).
+// 128 tile indices per warp (the deferred cells: stiff ones in implicit
+// mode, and with fp64_critical those entering the equilibrium band).
 // VEC: all arrays 16-byte aligned.  Each warp walks tiles of 128 cells: its
 // first tile by its index in the grid, the next ones from a device counter
 // (k.sched) as it finishes, so the warps that draw cheap tiles take more of
@@ -33,14 +34,17 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                                                          float* ui_out, float* qc_out, float* qx_out,
                                                          cool_counters* cnt, const float* __restrict__ rr) {
     constexpr int NF = (VAR & 4) ? 6 : 5;   // staged input fields
-    // the tile pass's variant: with fp64_critical (bit 1) every cell is first
-    // stepped in FP32 (bit 1 cleared; bit 5: a stiff cell takes the limited
-    // step instead of a solve) and only flagged when it enters the
-    // equilibrium band or, in implicit mode, turns stiff.  Up to that
-    // sub-cycle the FP32 and the FP64-option steps are the same arithmetic,
-    // so an unflagged cell's result is the FP64-option result; a flagged
-    // cell is stepped again below with the FP64 options.
-    constexpr int VF = (VAR & 2) ? ((VAR & ~(2 | 8)) | 32) : (VAR & ~8);
+    // the tile pass's variant: in implicit mode (bit 0) a stiff cell takes
+    // the limited step instead of a solve (bit 5) and is only flagged; with
+    // fp64_critical (bit 1) every cell is first stepped in FP32 (bit 1
+    // cleared) and also flagged when it enters the equilibrium band.  Up to
+    // that sub-cycle the tile pass and the full variant are the same
+    // arithmetic, so an unflagged cell's result is the full variant's; a
+    // flagged cell is stepped again below with the full variant, the
+    // deferred cells of the tile gathered onto consecutive lanes, so that
+    // the solves run side by side instead of one lane at a time in most
+    // passes of the tile.
+    constexpr int VF = (VAR & 2) ? ((VAR & ~(2 | 8)) | 32) : (VAR & 1) ? ((VAR & ~8) | 32) : (VAR & ~8);
     extern __shared__ float sm[];
     load_smem(k, sm);
     const Smem S = smem_view(k, sm);
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
             if (VAR & 4) t4[5 * 32 + lane] = __ldcs(reinterpret_cast<const float4*>(rr) + q);
             __syncwarp();
             unsigned redo = 0u;    // cells with a key near a node, redone below
-            unsigned defer = 0u;   // fp64_critical: cells redone below with the FP64 options
+            unsigned defer = 0u;   // cells redone below with the full variant
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int j = c * 32 + lane;
@@ -73,7 +77,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                                                         tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                         tile[4 * kWarpCells + j],
                                                         (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
-                if ((VAR & 2) && ((o.flags & 8u) || ((VAR & 1) && (o.flags & 4u)))) {
+                if (((VAR & 2) && (o.flags & 8u)) || ((VAR & 1) && (o.flags & 4u))) {
                     defer |= 1u << c;  // its inputs stay in the tile
                 } else if (o.near) {
                     redo |= 1u << c;   // its inputs stay in the tile
@@ -105,11 +109,11 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                     if (VAR & 8) count_flags(o.flags, cnt);
                 }
             }
-            if ((VAR & 2) && __any_sync(0xffffffffu, defer != 0u)) {
+            if ((VAR & 3) && __any_sync(0xffffffffu, defer != 0u)) {
                 // the deferred cells, gathered onto consecutive lanes (their
                 // tile indices in the warp's list), stepped again from their
-                // inputs with the FP64 options: one pass per 32 of them
-                // instead of FP64 code in most sub-cycles of every warp
+                // inputs with the full variant: one pass per 32 of them
+                // instead of a solve (or FP64 code) in most passes
                 unsigned char* list = reinterpret_cast<unsigned char*>(
                                           sm + smem_table_floats(k) + WR * kThreads + kWarps * NF * kWarpCells) +
                                       warp * kWarpCells;
