@@ -149,6 +149,10 @@ typedef struct {
                                             some sub-cycle */
     unsigned long long n_floor;          /* cool_step_disk: cooling skipped under the temperature floor in
                                             some sub-cycle */
+    unsigned long long n_exact_redo;     /* FP32 step: cells stepped a second time with the exact index
+                                            rule (node compares) because a key fell within ~1e-6 of a
+                                            node or its guessed interval was in doubt; the outputs are
+                                            the same, this counts the fast selection's extra work */
 } cool_counters;
 
 /* Disk geometry for cool_step_disk (Sec. 2.7 scale height, Sec. 3.2.3

@@ -181,12 +181,13 @@ def _ptr(t):
 
 
 def new_counters(device=None):
-    """A zeroed device counter block (int64 x 7) for step(..., counters=)."""
+    """A zeroed device counter block (int64 x 8, cool_counters) for step(..., counters=)."""
     import torch
-    return torch.zeros(7, dtype=torch.int64, device=device or "cuda")
+    return torch.zeros(len(COUNTER_NAMES), dtype=torch.int64, device=device or "cuda")
 
 
-COUNTER_NAMES = ("clamped", "nonfinite", "stiff", "fp64_coulomb", "implicit_fail", "fallback", "floor")
+COUNTER_NAMES = ("clamped", "nonfinite", "stiff", "fp64_coulomb", "implicit_fail", "fallback", "floor",
+                 "exact_redo")
 
 
 def counters_dict(c):

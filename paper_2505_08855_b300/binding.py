@@ -65,7 +65,8 @@ class cool_surrogate_stats(C.Structure):
 
 class cool_counters(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("n_clamped", "n_nonfinite", "n_stiff",
-                                              "n_fp64_coulomb", "n_implicit_fail", "n_fallback", "n_floor")]
+                                              "n_fp64_coulomb", "n_implicit_fail", "n_fallback", "n_floor",
+                                              "n_exact_redo")]
 
 
 class cool_disk(C.Structure):

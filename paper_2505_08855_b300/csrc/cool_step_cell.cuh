@@ -192,11 +192,14 @@ __device__ __forceinline__ Smem smem_view(const StepK& k, const float* sm) {
     return S;
 }
 
+// count_flags bit 7: the cell was stepped again with the exact index rule
+constexpr unsigned kFlagRedo = 1u << 7;
+
 __device__ __forceinline__ void count_flags(unsigned f, cool_counters* cnt) {
     // warp-aggregated counter updates
     const unsigned full = __activemask();
 #pragma unroll
-    for (int b = 0; b < 7; ++b) {
+    for (int b = 0; b < 8; ++b) {
         if (b == 5) continue;   // surrogate fallback: not set by this kernel
         unsigned m = __ballot_sync(full, (f >> b) & 1u);
         if (m && (threadIdx.x & 31) == (__ffs(full) - 1)) {
@@ -207,7 +210,8 @@ __device__ __forceinline__ void count_flags(unsigned f, cool_counters* cnt) {
             case 2: dst = &cnt->n_stiff; break;
             case 3: dst = &cnt->n_fp64_coulomb; break;
             case 4: dst = &cnt->n_implicit_fail; break;
-            default: dst = &cnt->n_floor; break;
+            case 6: dst = &cnt->n_floor; break;
+            default: dst = &cnt->n_exact_redo; break;
             }
             atomicAdd(dst, (unsigned long long)__popc(m));
         }

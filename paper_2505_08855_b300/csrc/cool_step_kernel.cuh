@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                     tile[4 * kWarpCells + j] = o.ui;
                     tile[0 * kWarpCells + j] = o.qc;
                     tile[1 * kWarpCells + j] = o.qx;
-                    if (VAR & 8) count_flags(o.flags, cnt);
+                    if (VAR & 8) count_flags(o.flags | kFlagRedo, cnt);
                 }
             }
             if ((VAR & 3) && __any_sync(0xffffffffu, defer != 0u)) {
@@ -134,16 +134,19 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                                                                   tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                                   tile[4 * kWarpCells + j],
                                                                   (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
-                        if (o.near)
+                        unsigned rf = 0u;
+                        if (o.near) {
                             o = step_cell<FMT, (VAR & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
                                                                  tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                                  tile[4 * kWarpCells + j],
                                                                  (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
+                            rf = kFlagRedo;
+                        }
                         tile[3 * kWarpCells + j] = o.ue;
                         tile[4 * kWarpCells + j] = o.ui;
                         tile[0 * kWarpCells + j] = o.qc;
                         tile[1 * kWarpCells + j] = o.qx;
-                        if (VAR & 8) count_flags(o.flags, cnt);
+                        if (VAR & 8) count_flags(o.flags | rf, cnt);
                     }
                 }
             }
@@ -167,12 +170,16 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float ri = (VAR & 4) ? rr[i] : 0.f;
         Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
-        if (o.near) o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+        unsigned rf = 0u;
+        if (o.near) {
+            o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+            rf = kFlagRedo;
+        }
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
         if (qx_out) qx_out[i] = o.qx;
-        if (VAR & 8) count_flags(o.flags, cnt);
+        if (VAR & 8) count_flags(o.flags | rf, cnt);
     }
 }
 

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
                     tile[4 * kWarpCells + j] = o.ui;
                     tile[0 * kWarpCells + j] = o.qc;
                     tile[1 * kWarpCells + j] = o.qx;
-                    if (VAR & 8) count_flags(o.flags, cnt);
+                    if (VAR & 8) count_flags(o.flags | kFlagRedo, cnt);
                 }
             }
             __syncwarp();
@@ -137,12 +137,16 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_tma(const __grid_c
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
-        if (o.near) o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+        unsigned rf = 0u;
+        if (o.near) {
+            o = step_cell<FMT, (VAR & ~8), true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], 0.f);
+            rf = kFlagRedo;
+        }
         ue_out[i] = o.ue;
         ui_out[i] = o.ui;
         if (qc_out) qc_out[i] = o.qc;
         if (qx_out) qx_out[i] = o.qx;
-        if (VAR & 8) count_flags(o.flags, cnt);
+        if (VAR & 8) count_flags(o.flags | rf, cnt);
     }
 }
 
