@@ -434,7 +434,7 @@ def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=Non
 
 
 SECTIONS = ("cfg2", "paper_size", "staging_bound", "l2_persist", "disk", "radiation", "scalar", "fp64", "adjoint",
-            "direct", "surrogate", "placement")
+            "direct", "surrogate", "placement", "host_link")
 
 
 def run_suite_perf(args, torch, cool, inputs, dev):
@@ -738,6 +738,47 @@ def run_suite_perf(args, torch, cool, inputs, dev):
                         {"fallback_cells": cd["fallback"], "fit_seconds": fit_s, "fit": info,
                          "network_tflops": flops / (ms * 1e-3) / 1e12}, BYTES_PER_CELL, peak)
         sur.free()
+    if "host_link" in want:
+        # the end-to-end step's floor: the benchmark's 5 input fields host ->
+        # device and its 2 outputs back, alone and at once, beside
+        # cool_step_host (pinned host memory, 256^3 cells)
+        F = inputs.make(WORKLOAD, seed=1002)
+        n = F["rho"].size
+        hin = {k: torch.from_numpy(v).pin_memory() for k, v in F.items()}
+        del F
+        hout = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(2)]
+        din = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in hin}
+        dout = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(2)]
+        side = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+
+        def h2d():
+            for k in hin:
+                din[k].copy_(hin[k], non_blocking=True)
+
+        def d2h():
+            for a in range(2):
+                hout[a].copy_(dout[a], non_blocking=True)
+
+        def both():
+            for st in side:
+                st.wait_stream(stream)
+            with torch.cuda.stream(side[0]):
+                h2d()
+            with torch.cuda.stream(side[1]):
+                d2h()
+            for st in side:
+                stream.wait_stream(st)
+
+        t = table()
+        p = cool.Params(n_sub=N_SUB)
+        res = {"h2d_ms": _timed(torch, h2d, steps, warm, stream), "d2h_ms": _timed(torch, d2h, steps, warm, stream),
+               "both_at_once_ms": _timed(torch, both, steps, warm, stream),
+               "step_host_ms": _timed(torch, lambda: cool.step_host(t, p, hin["rho"], hin["B"], hin["H"], hin["ue"],
+                                                                    hin["ui"], hout[0], hout[1]), steps, warm, stream)}
+        res["h2d_GBps"] = 20.0 * n / res["h2d_ms"] / 1e6
+        res["d2h_GBps"] = 8.0 * n / res["d2h_ms"] / 1e6
+        _suite_line("end to end through cool_step_host, and the host link alone", WORKLOAD, n, res["step_host_ms"],
+                    res)
     return 0
 
 
