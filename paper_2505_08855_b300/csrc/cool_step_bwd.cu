@@ -438,13 +438,109 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 // output gradients at the end.  The product is the reverse sweep's
 // (different FP32 rounding order), with no per-sub-cycle state.
 // IMPL: the implicit mode's solve is compiled in; the explicit-only kernel
-// fits 64 registers without spills, 4 blocks (32 warps) per SM.
-template <bool IMPL>
+// fits 64 registers without spills, 4 blocks (32 warps) per SM.  DEFER
+// (implicit mode, without IMPL): a cell that turns stiff stops, writes
+// nothing and returns false; its index goes to a list that
+// k_step_tan_list_f32 steps with the solve, the listed cells side by side
+// on consecutive lanes instead of one solving lane holding its warp.
+template <bool IMPL, bool DEFER>
+__device__ __forceinline__ bool tan_cell(const StepK& k, const Smem& S, float* win, long long i,
+                                         const float* __restrict__ rho_in, const float* __restrict__ B_in,
+                                         const float* __restrict__ H_in, const float* __restrict__ ue_in,
+                                         const float* __restrict__ ui_in, const float* __restrict__ gue_out,
+                                         const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
+                                         float* g_ue, float* g_ui) {
+    const float rho = rho_in[i], B = B_in[i], H = H_in[i];
+    float ue = ue_in[i], ui = ui_in[i];
+    const float ge_out = gue_out[i], gi_out = gui_out[i];
+    if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
+        !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
+        g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
+    } else {
+        unsigned clamp = 0u;
+        const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
+        const float inv_rho = 1.f / rho;
+        const float inv_B = B > 0.f ? 1.f / B : 0.f;
+        const float inv_H = H > 0.f ? 1.f / H : 0.f;
+        CellC c;
+        CellD cd;
+        bwd_cell(k, S, rho, B, H, c, cd, clamp);
+        const float lcc_off = c.lb_off;
+        Cache cc;
+        cc.base = -8;
+        cc.win = win;
+        cc.near = 0u;
+        GCache gc;
+        gc.j = -1;
+        // tangents: je[x] = d u_e / d x, ji[x] = d u_i / d x for
+        // x = rho, B, H, u_e(in), u_i(in)
+        float je[5] = {0.f, 0.f, 0.f, 1.f, 0.f};
+        float ji[5] = {0.f, 0.f, 0.f, 0.f, 1.f};
+        for (int sub = 0; sub < k.n_sub; ++sub) {
+            // exchange: u_e += X, u_i -= X
+            const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
+            ue += xg.X;
+            ui -= xg.X;
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+                float dX = fmaf(xg.due, je[x], xg.dui * ji[x]);
+                if (x == 0) dX += xg.drho;
+                je[x] += dX;
+                ji[x] -= dX;
+            }
+            // cooling: free, limited or implicit, as the forward step
+            QGrad g = cool_grad(k, S, c, cd, gc, ue, inv_e);
+            const float q = g.q;
+            if (DEFER && q > k.limiter * ue) return false;   // stiff: the list kernel steps it
+            float du = fminf(q, k.limiter * ue);
+            int br = q < k.limiter * ue ? 0 : 1;
+            float u_at = ue;
+            if (IMPL && q > k.limiter * ue) {
+                float u1;
+                if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
+                    du = ue - u1;
+                    br = 2;
+                    u_at = u1;
+                    g = cool_grad(k, S, c, cd, gc, u1, inv_e);
+                }
+            }
+            if (br == 1) {
+                const float f = 1.f - k.limiter;
+#pragma unroll
+                for (int x = 0; x < 5; ++x) je[x] *= f;
+            } else {
+                // dq = qu du + q_rho drho + q_B dB + q_H dH
+                const float qu = __fdividef(g.q * g.du, u_at);
+                const float qx[3] = {g.q * g.drho * inv_rho, g.dB != 0.f ? g.q * g.dB * inv_B : 0.f,
+                                     g.dH != 0.f ? g.q * g.dH * inv_H : 0.f};
+                if (br == 2) {
+                    // u* + q(u*) = u_e: du* = (du_e - q_x dx) / (1 + qu)
+                    const float r = __fdividef(1.f, 1.f + qu);
+#pragma unroll
+                    for (int x = 0; x < 5; ++x) je[x] = (x < 3 ? je[x] - qx[x < 3 ? x : 0] : je[x]) * r;
+                } else {
+                    const float f = 1.f - qu;
+#pragma unroll
+                    for (int x = 0; x < 5; ++x) je[x] = x < 3 ? fmaf(je[x], f, -qx[x < 3 ? x : 0]) : je[x] * f;
+                }
+            }
+            ue -= du;
+        }
+        g_rho[i] = fmaf(ge_out, je[0], gi_out * ji[0]);
+        g_B[i] = fmaf(ge_out, je[1], gi_out * ji[1]);
+        g_H[i] = fmaf(ge_out, je[2], gi_out * ji[2]);
+        g_ue[i] = fmaf(ge_out, je[3], gi_out * ji[3]);
+        g_ui[i] = fmaf(ge_out, je[4], gi_out * ji[4]);
+    }
+    return true;
+}
+
+template <bool IMPL, bool DEFER>
 __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
     const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
     const float* __restrict__ gue_out, const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
-    float* g_ue, float* g_ui) {
+    float* g_ue, float* g_ui, unsigned* n_list, unsigned* list) {
     extern __shared__ float sm[];
     load_smem(k, sm);
     const Smem S = smem_view(k, sm);
@@ -455,87 +551,18 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
     long long chunk = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     while (chunk < nchunks) {
         const long long i = chunk * 32 + lane;
-        if (i < n) {
-            const float rho = rho_in[i], B = B_in[i], H = H_in[i];
-            float ue = ue_in[i], ui = ui_in[i];
-            const float ge_out = gue_out[i], gi_out = gui_out[i];
-            if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
-                !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
-                g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
-            } else {
-                unsigned clamp = 0u;
-                const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
-                const float inv_rho = 1.f / rho;
-                const float inv_B = B > 0.f ? 1.f / B : 0.f;
-                const float inv_H = H > 0.f ? 1.f / H : 0.f;
-                CellC c;
-                CellD cd;
-                bwd_cell(k, S, rho, B, H, c, cd, clamp);
-                const float lcc_off = c.lb_off;
-                Cache cc;
-                cc.base = -8;
-                cc.win = win;
-                cc.near = 0u;
-                GCache gc;
-                gc.j = -1;
-                // tangents: je[x] = d u_e / d x, ji[x] = d u_i / d x for
-                // x = rho, B, H, u_e(in), u_i(in)
-                float je[5] = {0.f, 0.f, 0.f, 1.f, 0.f};
-                float ji[5] = {0.f, 0.f, 0.f, 0.f, 1.f};
-                for (int sub = 0; sub < k.n_sub; ++sub) {
-                    // exchange: u_e += X, u_i -= X
-                    const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
-                    ue += xg.X;
-                    ui -= xg.X;
-#pragma unroll
-                    for (int x = 0; x < 5; ++x) {
-                        float dX = fmaf(xg.due, je[x], xg.dui * ji[x]);
-                        if (x == 0) dX += xg.drho;
-                        je[x] += dX;
-                        ji[x] -= dX;
-                    }
-                    // cooling: free, limited or implicit, as the forward step
-                    QGrad g = cool_grad(k, S, c, cd, gc, ue, inv_e);
-                    const float q = g.q;
-                    float du = fminf(q, k.limiter * ue);
-                    int br = q < k.limiter * ue ? 0 : 1;
-                    float u_at = ue;
-                    if (IMPL && q > k.limiter * ue) {
-                        float u1;
-                        if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
-                            du = ue - u1;
-                            br = 2;
-                            u_at = u1;
-                            g = cool_grad(k, S, c, cd, gc, u1, inv_e);
-                        }
-                    }
-                    if (br == 1) {
-                        const float f = 1.f - k.limiter;
-#pragma unroll
-                        for (int x = 0; x < 5; ++x) je[x] *= f;
-                    } else {
-                        // dq = qu du + q_rho drho + q_B dB + q_H dH
-                        const float qu = __fdividef(g.q * g.du, u_at);
-                        const float qx[3] = {g.q * g.drho * inv_rho, g.dB != 0.f ? g.q * g.dB * inv_B : 0.f,
-                                             g.dH != 0.f ? g.q * g.dH * inv_H : 0.f};
-                        if (br == 2) {
-                            // u* + q(u*) = u_e: du* = (du_e - q_x dx) / (1 + qu)
-                            const float r = __fdividef(1.f, 1.f + qu);
-#pragma unroll
-                            for (int x = 0; x < 5; ++x) je[x] = (x < 3 ? je[x] - qx[x < 3 ? x : 0] : je[x]) * r;
-                        } else {
-                            const float f = 1.f - qu;
-#pragma unroll
-                            for (int x = 0; x < 5; ++x) je[x] = x < 3 ? fmaf(je[x], f, -qx[x < 3 ? x : 0]) : je[x] * f;
-                        }
-                    }
-                    ue -= du;
-                }
-                g_rho[i] = fmaf(ge_out, je[0], gi_out * ji[0]);
-                g_B[i] = fmaf(ge_out, je[1], gi_out * ji[1]);
-                g_H[i] = fmaf(ge_out, je[2], gi_out * ji[2]);
-                g_ue[i] = fmaf(ge_out, je[3], gi_out * ji[3]);
-                g_ui[i] = fmaf(ge_out, je[4], gi_out * ji[4]);
+        bool deferred = false;
+        if (i < n)
+            deferred = !tan_cell<IMPL, DEFER>(k, S, win, i, rho_in, B_in, H_in, ue_in, ui_in, gue_out, gui_out,
+                                              g_rho, g_B, g_H, g_ue, g_ui);
+        if (DEFER) {
+            // the warp's deferred cells, appended with one atomic
+            const unsigned bal = __ballot_sync(0xffffffffu, deferred);
+            if (bal) {
+                unsigned base = 0u;
+                if (lane == 0) base = atomicAdd(n_list, (unsigned)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (deferred) list[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned)i;
             }
         }
         if (k.sched) {
@@ -546,6 +573,74 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
             chunk += first;
         }
     }
+}
+
+// The cells k_step_tan_f32<false, true> deferred, by index, with the solve
+// compiled in: consecutive list entries on consecutive lanes.
+__global__ void __launch_bounds__(kThreads, 2) k_step_tan_list_f32(
+    StepK k, const unsigned* __restrict__ n_list, const unsigned* __restrict__ list,
+    const float* __restrict__ rho_in, const float* __restrict__ B_in, const float* __restrict__ H_in,
+    const float* __restrict__ ue_in, const float* __restrict__ ui_in, const float* __restrict__ gue_out,
+    const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H, float* g_ue, float* g_ui) {
+    extern __shared__ float sm[];
+    load_smem(k, sm);
+    const Smem S = smem_view(k, sm);
+    float* win = sm + smem_table_floats(k) + threadIdx.x;
+    const long long m = *n_list;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (long long)gridDim.x * blockDim.x)
+        tan_cell<true, false>(k, S, win, (long long)list[t], rho_in, B_in, H_in, ue_in, ui_in, gue_out, gui_out,
+                              g_rho, g_B, g_H, g_ue, g_ui);
+}
+
+// The launches of one cool_step_bwd call: fn over the cells (persistent
+// grid, dynamic chunk order), then, with a deferral list, the list kernel.
+using TanFn = decltype(&k_step_tan_f32<false, false>);
+
+cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, bool tbl, bool sms, size_t smem,
+                       unsigned* scratch, const float* rho, const float* B, const float* H, const float* ue,
+                       const float* ui, const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
+                       float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long work = (n + kThreads - 1) / kThreads;
+    long long cap = (long long)sm_count() * per_sm;
+    long long blocks = work < cap ? work : cap;
+    if ((n + 31) / 32 > blocks * kWarps) {
+        // more chunks than warps: the dynamic order
+        k.sched = sched_counter(st);
+        if (k.sched) {
+            e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (tbl) {
+        auto fb = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
+        fb<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui,
+                                                g_lb, g_ls, g_lc);
+        return cudaGetLastError();
+    }
+    unsigned* list = scratch ? scratch + 1 : nullptr;
+    tf<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui, scratch,
+                                            list);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !scratch) return e;
+    const void* fl = (const void*)k_step_tan_list_f32;
+    e = cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fl, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    // the list's length is on the device: one resident wave strides over it
+    long long bl = (long long)sm_count() * per_sm;
+    if (bl > work) bl = work;
+    k_step_tan_list_f32<<<(int)bl, kThreads, smem, st>>>(k, scratch, list, rho, B, H, ue, ui, gue, gui, g_rho, g_B,
+                                                         g_H, g_ue, g_ui);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -569,33 +664,31 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
         if (sms) smem += (size_t)kSmemSub * kThreads * (kStateFloats * sizeof(float) + 1);
     }
     const bool impl = p->mode == COOL_IMPLICIT_STIFF;
-    const void* fn = !tbl ? (impl ? (const void*)k_step_tan_f32<true> : (const void*)k_step_tan_f32<false>)
-                     : sms ? (const void*)k_step_bwd_f32<true> : (const void*)k_step_bwd_f32<false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    if (per_sm < 1) per_sm = 1;
-    long long work = (n + kThreads - 1) / kThreads;
-    long long cap = (long long)sm_count() * per_sm;
-    long long blocks = work < cap ? work : cap;
-    if ((n + 31) / 32 > blocks * kWarps) {
-        // more chunks than warps: the dynamic order
-        k.sched = sched_counter(st);
-        if (k.sched) {
-            e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
-            if (e != cudaSuccess) return set_cuda_error(e);
+    // implicit mode without table adjoints: stiff cells deferred to a list
+    // (a stream-ordered scratch of n + 1 words: the count, then the
+    // indices); where it cannot be had, every lane solves its own cells
+    unsigned* scratch = nullptr;
+    if (!tbl && impl && n < 0xffffffffll) {
+        if (cudaMallocAsync(&scratch, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            scratch = nullptr;
+        } else {
+            cudaError_t em = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+            if (em != cudaSuccess) {
+                cudaFreeAsync(scratch, st);
+                return set_cuda_error(em);
+            }
         }
     }
-    if (tbl) {
-        auto fb = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
-        fb<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui,
-                                                g_lb, g_ls, g_lc);
-    } else
-        (impl ? k_step_tan_f32<true> : k_step_tan_f32<false>)<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
-                                                            g_ue, g_ui);
-    e = cudaGetLastError();
+    const bool defer = scratch != nullptr;
+    const TanFn tf = !impl ? k_step_tan_f32<false, false> : defer ? k_step_tan_f32<false, true> : k_step_tan_f32<true, false>;
+    const void* fn = !tbl ? (const void*)tf : sms ? (const void*)k_step_bwd_f32<true> : (const void*)k_step_bwd_f32<false>;
+    cudaError_t e = launch_bwd(k, n, fn, tf, tbl, sms, smem, scratch, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
+                               g_ue, g_ui, g_lb, g_ls, g_lc, st);
+    if (scratch) {
+        cudaError_t ef = cudaFreeAsync(scratch, st);
+        if (e == cudaSuccess) e = ef;
+    }
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
 }
