@@ -260,7 +260,12 @@ cool_status cool_table_load(const char* path, void* stream, cool_table** out);
  * counter (they take a fixed tile order, with the same results), so a graph
  * replayed on any stream cannot share it with a step running meanwhile.
  * Launches on one stream run in order, so no two launches that overlap in
- * time share a counter.
+ * time share a counter.  In mode IMPLICIT or with fp64_critical (FP32
+ * fields, FP32 table, 16-byte aligned arrays, n_cells < 2^32 - 1) the
+ * cells that turn stiff or enter the equilibrium band are listed in
+ * stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on `stream`,
+ * 4 (n_cells + 1) bytes) and stepped by a second kernel; where that
+ * allocation fails each warp steps its own (bitwise the same results).
  *   field_dtype: COOL_F32 or COOL_F64 (all seven field arrays of that type).
  *   rho, B, H, u_e_in, u_i_in: device inputs, n_cells each.
  *   u_e_out, u_i_out: device outputs (may alias u_e_in / u_i_in).

@@ -170,6 +170,14 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
 #define COOL_KV(V, F) k_step_f32<V, F, 0>, k_step_f32<V, F, 1>, k_step_f32<V, F, 2>, k_step_f32<V, F, 3>, \
                       k_step_f32<V, F, 8>, k_step_f32<V, F, 9>, k_step_f32<V, F, 10>, k_step_f32<V, F, 11>
     static const StepKernelFn table_v[8] = {COOL_KV(true, 0)};
+    // implicit / fp64_critical with the flagged cells listed (template bit 6)
+    // and the list kernels that step them
+    static const StepKernelFn table_lv[8] = {nullptr, k_step_f32<true, 0, 65>, k_step_f32<true, 0, 66>,
+                                             k_step_f32<true, 0, 67>, nullptr, k_step_f32<true, 0, 73>,
+                                             k_step_f32<true, 0, 74>, k_step_f32<true, 0, 75>};
+    static const StepKernelFn list_v[8] = {nullptr, k_step_list_f32<0, 1>, k_step_list_f32<0, 2>,
+                                           k_step_list_f32<0, 3>, nullptr, k_step_list_f32<0, 9>,
+                                           k_step_list_f32<0, 10>, k_step_list_f32<0, 11>};
     static const StepKernelFn table_s[8] = {COOL_KV(false, 0)};
 #undef COOL_KV
     // disk geometry (template bit 2): FP32 table only
@@ -191,53 +199,96 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                      : fmt == 0 ? (const void*)(vec ? table_v[var] : table_s[var])
                      : (fmt <= 2 ? step_kernel_f16(fmt, vec, var) : step_kernel_f16s(fmt, vec, var));
     if (!fn) return COOL_EUNSUPPORTED;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    if (per_sm < 1) per_sm = 1;
-    long long work = vec ? (n + kWarps * kWarpCells - 1) / (kWarps * kWarpCells) : (n + kThreads - 1) / kThreads;
-    long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
-    long long blocks = work < cap ? work : cap;
-    if (blocks < 1) blocks = 1;
-    if (vec && n / kWarpCells > blocks * kWarps) {
-        // more tiles than warps: the dynamic tile order (a no-op otherwise)
-        k.sched = sched_counter(st);
-        if (k.sched) {
-            e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
-            if (e != cudaSuccess) return set_cuda_error(e);
+    // implicit mode and fp64_critical on the FP32 table with aligned fields:
+    // the flagged cells go to a list in stream-ordered scratch (n + 1
+    // words: the count, then the indices), stepped by k_step_list_f32 after
+    // the tile pass; where the scratch cannot be had, each warp steps its own
+    unsigned* scratch = nullptr;
+    if (vec && !tot && !disk && fmt == 0 && (var & 3) && n < 0xffffffffll) {
+        if (cudaMallocAsync(&scratch, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            scratch = nullptr;
+        } else {
+            const cudaError_t em = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+            if (em != cudaSuccess) {
+                cudaFreeAsync(scratch, st);
+                return set_cuda_error(em);
+            }
+            fn = (const void*)table_lv[var];
+            k.dlist = scratch;
         }
     }
-    // with cool_table_l2_persist on: the packed 4-D channel as a persisting
-    // L2 access-policy window of this launch (the stream's own attributes are
-    // left alone)
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    int max_win = 0;
-    size_t limit = 0;
-    if (t->l2_persist && t->ls_bytes > 0 &&
-        cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device) == cudaSuccess &&
-        max_win > 0 && cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize) == cudaSuccess && limit > 0) {
-        const size_t win = t->ls_bytes < (size_t)max_win ? t->ls_bytes : (size_t)max_win;
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = (void*)t->dev.lsb;
-        attr[0].val.accessPolicyWindow.num_bytes = win;
-        attr[0].val.accessPolicyWindow.hitRatio = limit >= win ? 1.f : (float)limit / (float)win;
-        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+    auto tile_pass = [&]() -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        long long work = vec ? (n + kWarps * kWarpCells - 1) / (kWarps * kWarpCells) : (n + kThreads - 1) / kThreads;
+        long long cap = (long long)sm_count() * per_sm;  // one resident wave, persistent blocks
+        long long blocks = work < cap ? work : cap;
+        if (blocks < 1) blocks = 1;
+        if (vec && n / kWarpCells > blocks * kWarps) {
+            // more tiles than warps: the dynamic tile order (a no-op otherwise)
+            k.sched = sched_counter(st);
+            if (k.sched) {
+                e = cudaMemsetAsync(k.sched, 0, sizeof(unsigned long long), st);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        // with cool_table_l2_persist on: the packed 4-D channel as a persisting
+        // L2 access-policy window of this launch (the stream's own attributes are
+        // left alone)
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        int max_win = 0;
+        size_t limit = 0;
+        if (t->l2_persist && t->ls_bytes > 0 &&
+            cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device) == cudaSuccess &&
+            max_win > 0 && cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize) == cudaSuccess && limit > 0) {
+            const size_t win = t->ls_bytes < (size_t)max_win ? t->ls_bytes : (size_t)max_win;
+            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+            attr[0].val.accessPolicyWindow.base_ptr = (void*)t->dev.lsb;
+            attr[0].val.accessPolicyWindow.num_bytes = win;
+            attr[0].val.accessPolicyWindow.hitRatio = limit >= win ? 1.f : (float)limit / (float)win;
+            attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+            attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+        }
+        void* args[] = {&k, &n, &rho, &B, &H, &ue, &ui, &ue_o, &ui_o, &qc, &qx, &cnt, &r};
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    };
+    cudaError_t e = tile_pass();
+    if (scratch) {
+        if (e == cudaSuccess) {
+            // the listed cells: one resident wave strides over the list,
+            // whose length is on the device
+            const StepKernelFn fl = list_v[var];
+            const size_t sl = (size_t)(smem_table_floats(k) + fmt_nodes(fmt) * kThreads) * sizeof(float);
+            e = cudaFuncSetAttribute((const void*)fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+            int pl = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl, (const void*)fl, kThreads, sl);
+            if (e == cudaSuccess) {
+                if (pl < 1) pl = 1;
+                long long bl = (long long)sm_count() * pl;
+                const long long need = (n + kThreads - 1) / kThreads;
+                if (bl > need) bl = need;
+                fl<<<(int)bl, kThreads, sl, st>>>(k, n, rho, B, H, ue, ui, ue_o, ui_o, qc, qx, cnt, r);
+                e = cudaGetLastError();
+            }
+        }
+        const cudaError_t ef = cudaFreeAsync(scratch, st);
+        if (e == cudaSuccess) e = ef;
     }
-    void* args[] = {&k, &n, &rho, &B, &H, &ue, &ui, &ue_o, &ui_o, &qc, &qx, &cnt, &r};
-    e = cudaLaunchKernelExC(&cfg, fn, args);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
 }

@@ -218,6 +218,7 @@ struct StepK {
     // tile counter of the vector step's dynamic tile order (zeroed on the
     // launch stream before the launch); nullptr: the static order
     unsigned long long* sched;
+    unsigned* dlist;                  // deferred cells: [0] the count, then their indices (k_step_list_f32)
 };
 
 struct Sel {
@@ -714,6 +715,7 @@ void fill_stepk(const cool_table* t, const cool_params* p, StepK& k) {
     k.tn_off = (na + t->dev.n[3] + t->dev.n[4] * k.lc_stride + 3) & ~3;
     k.smem_floats = k.tn_off + 4 * (t->dev.n[3] - 1);
     k.sched = nullptr;
+    k.dlist = nullptr;
 }
 
 }  // namespace

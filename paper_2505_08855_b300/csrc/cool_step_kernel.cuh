@@ -26,6 +26,13 @@ namespace {
 // staging area and leave by 128-bit streaming stores.  Warps synchronise
 // only with themselves (__syncwarp), so a slow cell delays one warp, not the
 // block.  The remainder (and unaligned arrays) take a scalar loop.
+// A tile-pass result that defers the cell: it entered the equilibrium band
+// (fp64_critical) or turned stiff (implicit mode).
+template <int VAR>
+__device__ __forceinline__ bool deferred_flags(unsigned f) {
+    return ((VAR & 2) && (f & 8u)) || ((VAR & 1) && (f & 4u));
+}
+
 template <bool VEC, int FMT, int VAR>
 __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_constant__ StepK k, long long n,
                                                                   const float* __restrict__ rho,
@@ -44,7 +51,11 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
     // deferred cells of the tile gathered onto consecutive lanes, so that
     // the solves run side by side instead of one lane at a time in most
     // passes of the tile.
-    constexpr int VF = (VAR & 2) ? ((VAR & ~(2 | 8)) | 32) : (VAR & 1) ? ((VAR & ~8) | 32) : (VAR & ~8);
+    // bit 6 (LIST): the flagged cells go to the list k.dlist, stepped by
+    // k_step_list_f32 after this kernel, instead of the warp's own pass
+    constexpr bool LIST = (VAR & 64) != 0;
+    constexpr int V = VAR & ~64;
+    constexpr int VF = (V & 2) ? ((V & ~(2 | 8)) | 32) : (V & 1) ? ((V & ~8) | 32) : (V & ~8);
     extern __shared__ float sm[];
     load_smem(k, sm);
     const Smem S = smem_view(k, sm);
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                                                         tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                         tile[4 * kWarpCells + j],
                                                         (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
-                if (((VAR & 2) && (o.flags & 8u)) || ((VAR & 1) && (o.flags & 4u))) {
+                if (deferred_flags<VAR>(o.flags)) {
                     defer |= 1u << c;  // its inputs stay in the tile
                 } else if (o.near) {
                     redo |= 1u << c;   // its inputs stay in the tile
@@ -98,10 +109,17 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                 for (int c = 0; c < 4; ++c) {
                     if (!((redo >> c) & 1u)) continue;
                     const int j = c * 32 + lane;
-                    const Out o = step_cell<FMT, (VAR & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
-                                                                tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
-                                                                tile[4 * kWarpCells + j],
-                                                                (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
+                    // with LIST the flag-only variant: a cell that turns stiff
+                    // (or enters the band) on the exact trajectory is listed
+                    constexpr int VR = LIST ? VF : (V & ~8);
+                    const Out o = step_cell<FMT, VR, true>(k, S, win, tile[j], tile[kWarpCells + j],
+                                                           tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
+                                                           tile[4 * kWarpCells + j],
+                                                           (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
+                    if (LIST && deferred_flags<VAR>(o.flags)) {
+                        k.dlist[1 + atomicAdd(k.dlist, 1u)] = (unsigned)(tw * kWarpCells + j);
+                        continue;   // its slots keep the inputs
+                    }
                     tile[3 * kWarpCells + j] = o.ue;
                     tile[4 * kWarpCells + j] = o.ui;
                     tile[0 * kWarpCells + j] = o.qc;
@@ -109,7 +127,29 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                     if (VAR & 8) count_flags(o.flags | kFlagRedo, cnt);
                 }
             }
-            if ((VAR & 3) && __any_sync(0xffffffffu, defer != 0u)) {
+            if (LIST) {
+                // the tile's flagged cells, appended with one atomic; their
+                // slots keep the inputs, which the stores below write out and
+                // k_step_list_f32 overwrites
+                unsigned bal[4], tot = 0u;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    bal[c] = __ballot_sync(0xffffffffu, (defer >> c) & 1u);
+                    tot += __popc(bal[c]);
+                }
+                if (tot) {
+                    unsigned base = 0u;
+                    if (lane == 0) base = atomicAdd(k.dlist, tot);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if ((defer >> c) & 1u)
+                            k.dlist[1 + base + __popc(bal[c] & ((1u << lane) - 1u))] =
+                                (unsigned)(tw * kWarpCells + c * 32 + lane);
+                        base += __popc(bal[c]);
+                    }
+                }
+            } else if ((VAR & 3) && __any_sync(0xffffffffu, defer != 0u)) {
                 // the deferred cells, gathered onto consecutive lanes (their
                 // tile indices in the warp's list), stepped again from their
                 // inputs with the full variant: one pass per 32 of them
@@ -130,13 +170,13 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
                 for (int b = 0; b < m; b += 32) {
                     if (b + lane < m) {
                         const int j = list[b + lane];
-                        Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, tile[j], tile[kWarpCells + j],
+                        Out o = step_cell<FMT, (V & ~8), false>(k, S, win, tile[j], tile[kWarpCells + j],
                                                                   tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                                   tile[4 * kWarpCells + j],
                                                                   (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
                         unsigned rf = 0u;
                         if (o.near) {
-                            o = step_cell<FMT, (VAR & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
+                            o = step_cell<FMT, (V & ~8), true>(k, S, win, tile[j], tile[kWarpCells + j],
                                                                  tile[2 * kWarpCells + j], tile[3 * kWarpCells + j],
                                                                  tile[4 * kWarpCells + j],
                                                                  (VAR & 4) ? tile[5 * kWarpCells + j] : 0.f);
@@ -168,6 +208,46 @@ __global__ void __launch_bounds__(kThreads, COOL_MINB) k_step_f32(const __grid_c
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = scalar_start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float ri = (VAR & 4) ? rr[i] : 0.f;
+        // with LIST the flag-only variant, a flagged cell listed
+        constexpr int VS = LIST ? VF : (V & ~8);
+        Out o = step_cell<FMT, VS, false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+        unsigned rf = 0u;
+        if (o.near && !(LIST && deferred_flags<VAR>(o.flags))) {
+            o = step_cell<FMT, VS, true>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
+            rf = kFlagRedo;
+        }
+        if (LIST && deferred_flags<VAR>(o.flags)) {
+            k.dlist[1 + atomicAdd(k.dlist, 1u)] = (unsigned)i;
+            continue;
+        }
+        ue_out[i] = o.ue;
+        ui_out[i] = o.ui;
+        if (qc_out) qc_out[i] = o.qc;
+        if (qx_out) qx_out[i] = o.qx;
+        if (VAR & 8) count_flags(o.flags | rf, cnt);
+    }
+}
+
+// The cells a LIST tile pass listed in k.dlist, stepped from their inputs
+// with the full variant VAR (the solve, the FP64 options): consecutive list
+// entries on consecutive lanes, so that the solves run side by side.
+template <int FMT, int VAR>
+__global__ void __launch_bounds__(kThreads, 2) k_step_list_f32(const __grid_constant__ StepK k, long long n,
+                                                               const float* __restrict__ rho,
+                                                               const float* __restrict__ Bf,
+                                                               const float* __restrict__ Hf, const float* ue_in,
+                                                               const float* ui_in, float* ue_out, float* ui_out,
+                                                               float* qc_out, float* qx_out, cool_counters* cnt,
+                                                               const float* __restrict__ rr) {
+    extern __shared__ float sm[];
+    load_smem(k, sm);
+    const Smem S = smem_view(k, sm);
+    float* win = sm + smem_table_floats(k) + threadIdx.x;   // window rows of this format x kThreads
+    const long long m = k.dlist[0];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = k.dlist[1 + t];
         const float ri = (VAR & 4) ? rr[i] : 0.f;
         Out o = step_cell<FMT, (VAR & ~8), false>(k, S, win, rho[i], Bf[i], Hf[i], ue_in[i], ui_in[i], ri);
         unsigned rf = 0u;
