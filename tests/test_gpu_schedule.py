@@ -4,8 +4,10 @@ which warp steps it or when, so every schedule gives the same bits.
 * Steps on two streams at once (each stream has its own tile counter)
   equal the same steps run one after the other.
 * A step captured in a CUDA graph on a stream with no counter yet (the
-  static order: nothing is allocated inside a capture) and replayed equals
-  the plain step.
+  static order: no tile counter is allocated inside a capture) and
+  replayed equals the plain step, in every mode (implicit mode and
+  fp64_critical allocate their list of flagged cells stream-ordered, which
+  a graph holds as allocation nodes); so does the captured adjoint.
 """
 import numpy as np
 import pytest
@@ -55,9 +57,12 @@ def test_concurrent_streams_equal_serial(env):
             assert torch.equal(x, y)
 
 
-def test_graph_capture_equals_plain_step(env):
+@pytest.mark.parametrize("mode,fp64", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_graph_capture_equals_plain_step(env, mode, fp64):
+    """Implicit mode and fp64_critical also list their flagged cells in
+    stream-ordered scratch: allocated and freed inside the graph."""
     cool, tab, tf = env
-    p = cool.Params(n_sub=8)
+    p = cool.Params(n_sub=8, mode=mode, fp64_critical=fp64)
     want = [t.clone() for t in cool.step(tab, p, *tf)]
     ue_o, ui_o = torch.empty_like(tf[3]), torch.empty_like(tf[4])
     torch.cuda.synchronize()
@@ -69,6 +74,28 @@ def test_graph_capture_equals_plain_step(env):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(ue_o, want[0]) and torch.equal(ui_o, want[1])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_capture_of_the_adjoint(env, mode):
+    """The input gradients captured and replayed equal the plain call
+    (implicit mode: the stiff cells' list in stream-ordered scratch)."""
+    cool, tab, tf = env
+    p = cool.Params(n_sub=8, mode=mode)
+    n = tf[0].numel()
+    a = torch.ones(n, device="cuda")
+    b = torch.full((n,), -0.5, device="cuda")
+    want = [t.clone() for t in cool.step_bwd(tab, p, *tf, a, b)]
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        got = cool.step_bwd(tab, p, *tf, a, b)
+    for t in got:
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(got, want):
+        assert torch.equal(x, y)
 
 
 def test_graph_replayed_on_another_stream_while_a_step_runs(env, oracle):
