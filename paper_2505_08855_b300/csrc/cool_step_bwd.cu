@@ -229,12 +229,13 @@ __device__ __forceinline__ void bwd_cell(const StepK& k, const Smem& S, float rh
 // SMS: the per-sub-cycle state lives in shared memory (n_sub <= kSmemSub,
 // column layout, conflict-free) instead of thread-local arrays.
 constexpr int kSmemSub = 8;
-constexpr int kStateFloats = 7;   // floats of per-sub-cycle state (ST_F)
+constexpr int kStateFloats = 3;   // floats of per-sub-cycle state (ST_F) with the implicit root; 2 without
 
 // With table adjoints requested (g_lb, g_ls or g_lc non-null); the input
-// gradients alone come from k_step_tan_f32.
-template <bool SMS>
-__global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
+// gradients alone come from k_step_tan_f32.  IMPL: the implicit mode's
+// solve compiled in (and its root kept per sub-cycle).
+template <bool SMS, bool IMPL>
+__global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
     const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
     const float* __restrict__ gue_out, const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
@@ -249,22 +250,21 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
     const int nT = T.n[3], nC = T.n[4];
     for (int i = threadIdx.x; i < nT + nC * nC; i += blockDim.x) glb_s[i] = 0.f;
     __syncthreads();
-    // per-sub-cycle state: u_e, u_i before the exchange, u_e after it, the
-    // implicit root, the exchange's partials dX/du_e, dX/du_i, dX/drho, and
-    // the branch taken (0 free, 1 limited, 2 implicit)
+    // per-sub-cycle state: u_e, u_i before the exchange, the implicit root
+    // (IMPL) and the branch taken (0 free, 1 limited, 2 implicit); the
+    // exchange (its X and partials, u_e after it) is evaluated again from
+    // u_e, u_i in the reverse sweep, which needs its corners for the
+    // Coulomb adjoint anyway
+    constexpr int NSF = IMPL ? kStateFloats : kStateFloats - 1;
     float* sst = glc_s + ((nC * nC + 3) & ~3);
-    unsigned char* sbr = reinterpret_cast<unsigned char*>(sst + kStateFloats * kSmemSub * kThreads);
-    float l_st[SMS ? 1 : kStateFloats * kMaxSub];
+    unsigned char* sbr = reinterpret_cast<unsigned char*>(sst + NSF * kSmemSub * kThreads);
+    float l_st[SMS ? 1 : NSF * kMaxSub];
     unsigned char l_br[SMS ? 1 : kMaxSub];
-#define ST_F(sub, f) (*(SMS ? &sst[(kStateFloats * (sub) + (f)) * kThreads + threadIdx.x] \
-                            : &l_st[kStateFloats * (sub) + (f)]))
+#define ST_F(sub, f) (*(SMS ? &sst[(NSF * (sub) + (f)) * kThreads + threadIdx.x] \
+                            : &l_st[NSF * (sub) + (f)]))
 #define ST_UE(sub) ST_F(sub, 0)
 #define ST_UI(sub) ST_F(sub, 1)
-#define ST_U1(sub) ST_F(sub, 2)
-#define ST_US(sub) ST_F(sub, 3)
-#define ST_XE(sub) ST_F(sub, 4)
-#define ST_XI(sub) ST_F(sub, 5)
-#define ST_XR(sub) ST_F(sub, 6)
+#define ST_US(sub) ST_F(sub, 2)
 #define ST_BR(sub) (*(SMS ? &sbr[(sub) * kThreads + threadIdx.x] : &l_br[(sub)]))
     // cells in chunks of 32 (one per lane): each warp's first chunk by its
     // index in the grid, the next ones from the tile counter (k.sched) as
@@ -306,14 +306,10 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                 const XGrad xg = coulomb_grad(k, S, ue, ui, inv_rho, inv_e, inv_i, kr, lcc_off);
                 ue += xg.X;
                 ui -= xg.X;
-                ST_U1(sub) = ue;
-                ST_XE(sub) = xg.due;
-                ST_XI(sub) = xg.dui;
-                ST_XR(sub) = xg.drho;
                 const float q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
                 float du = fminf(q, k.limiter * ue);
                 unsigned char br = q < k.limiter * ue ? 0 : 1;
-                if (k.mode == 1 && q > k.limiter * ue) {
+                if (IMPL && q > k.limiter * ue) {
                     float u1;
                     if (implicit_fp32<0, true>(k, S, c, cc, inv_e, ue, q, u1)) {
                         du = ue - u1;
@@ -345,11 +341,14 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
             };
             for (int sub = k.n_sub - 1; sub >= 0; --sub) {
                 float ge1;
+                // the exchange of this sub-cycle again (the forward's arithmetic:
+                // the same X, so the same u_e after it)
+                const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), inv_rho, inv_e, inv_i, kr, lcc_off);
                 const unsigned char br = ST_BR(sub);
                 if (br == 1) {
                     ge1 = (1.f - k.limiter) * ge;
                 } else {
-                    const float u = br == 2 ? ST_US(sub) : ST_U1(sub);
+                    const float u = (IMPL && br == 2) ? ST_US(sub) : ST_UE(sub) + xg.X;
                     const QGrad g = cool_grad(k, S, c, cd, gc, u, inv_e);
                     const float qu = __fdividef(g.q * g.du, u);
                     float sc;
@@ -382,12 +381,10 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
                     }
                 }
                 const float gX = ge1 - gi;
-                ge = ge1 + gX * ST_XE(sub);
-                gi = gi + gX * ST_XI(sub);
-                grho += gX * ST_XR(sub);
+                ge = ge1 + gX * xg.due;
+                gi = gi + gX * xg.dui;
+                grho += gX * xg.drho;
                 if (g_lc) {
-                    // the exchange's table adjoint needs its corners: recomputed
-                    const XGrad xg = coulomb_grad(k, S, ST_UE(sub), ST_UI(sub), inv_rho, inv_e, inv_i, kr, lcc_off);
                     if (xg.clamped) continue;
                     const float cl = gX * xg.X * kLn2;
                     atomicAdd(&glc_s[xg.ji * nC + xg.je], cl * (1.f - xg.wi) * (1.f - xg.we));
@@ -415,11 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_step_bwd_f32(
 #undef ST_F
 #undef ST_UE
 #undef ST_UI
-#undef ST_U1
 #undef ST_US
-#undef ST_XE
-#undef ST_XI
-#undef ST_XR
 #undef ST_BR
     __syncthreads();
     if (g_lb)
@@ -596,8 +589,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_step_tan_list_f32(
 // The launches of one cool_step_bwd call: fn over the cells (persistent
 // grid, dynamic chunk order), then, with a deferral list, the list kernel.
 using TanFn = decltype(&k_step_tan_f32<false, false>);
+using BwdFn = decltype(&k_step_bwd_f32<true, true>);
 
-cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, bool tbl, bool sms, size_t smem,
+cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, BwdFn fb, bool tbl, size_t smem,
                        unsigned* scratch, const float* rho, const float* B, const float* H, const float* ue,
                        const float* ui, const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
                        float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st) {
@@ -619,7 +613,6 @@ cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, bool tbl
         }
     }
     if (tbl) {
-        auto fb = sms ? k_step_bwd_f32<true> : k_step_bwd_f32<false>;
         fb<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui,
                                                 g_lb, g_ls, g_lc);
         return cudaGetLastError();
@@ -661,7 +654,8 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads) * sizeof(float);
     if (tbl) {
         smem += (size_t)(t->dev.n[3] + ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
-        if (sms) smem += (size_t)kSmemSub * kThreads * (kStateFloats * sizeof(float) + 1);
+        const int nsf = p->mode == COOL_IMPLICIT_STIFF ? kStateFloats : kStateFloats - 1;
+        if (sms) smem += (size_t)kSmemSub * kThreads * (nsf * sizeof(float) + 1);
     }
     const bool impl = p->mode == COOL_IMPLICIT_STIFF;
     // implicit mode without table adjoints: stiff cells deferred to a list
@@ -682,8 +676,10 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     }
     const bool defer = scratch != nullptr;
     const TanFn tf = !impl ? k_step_tan_f32<false, false> : defer ? k_step_tan_f32<false, true> : k_step_tan_f32<true, false>;
-    const void* fn = !tbl ? (const void*)tf : sms ? (const void*)k_step_bwd_f32<true> : (const void*)k_step_bwd_f32<false>;
-    cudaError_t e = launch_bwd(k, n, fn, tf, tbl, sms, smem, scratch, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
+    const BwdFn fb = sms ? (impl ? k_step_bwd_f32<true, true> : k_step_bwd_f32<true, false>)
+                         : (impl ? k_step_bwd_f32<false, true> : k_step_bwd_f32<false, false>);
+    const void* fn = !tbl ? (const void*)tf : (const void*)fb;
+    cudaError_t e = launch_bwd(k, n, fn, tf, fb, tbl, smem, scratch, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
                                g_ue, g_ui, g_lb, g_ls, g_lc, st);
     if (scratch) {
         cudaError_t ef = cudaFreeAsync(scratch, st);

@@ -66,11 +66,12 @@ def test_adjoint_matches_oracle(env, oracle, mode, n_sub):
     assert bad.mean() <= 0.005
 
 
-@pytest.mark.parametrize("mode,n_sub", [(0, 8), (1, 8), (0, 12)])
+@pytest.mark.parametrize("mode,n_sub", [(0, 8), (1, 8), (0, 12), (1, 12)])
 def test_table_adjoints_match_oracle(env, oracle, mode, n_sub):
     """With table adjoints: the recorded forward and the reverse sweep; n_sub
     <= 8 keeps the per-sub-cycle state in shared memory, more in
-    thread-local arrays: both layouts are covered."""
+    thread-local arrays, each with and without the implicit root: all four
+    layouts are covered."""
     cool, tab, ospec, OT = env
     f = inputs.uniform(4000, seed=61, dtype=np.float32)
     g, want, tg, bad, worst = _compare(cool, tab, oracle, ospec, OT, f, mode, n_sub=n_sub, table=True)
