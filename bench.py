@@ -856,6 +856,17 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
     ms, value = job_rate(dist, world, ms, n, dev)
+    # each step on its own (events around every step, after the timed
+    # region): the median and the spread of single steps beside the mean
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for s_i in range(args.steps):
+        one()
+        ev[s_i + 1].record(stream)
+    torch.cuda.synchronize()
+    singles = sorted(ev[s_i].elapsed_time(ev[s_i + 1]) for s_i in range(args.steps))
+    per_step = {"median": singles[len(singles) // 2], "min": singles[0], "max": singles[-1],
+                "total_ms": ms * args.steps}
 
     # end to end through the public API with host buffers (cool_step_host):
     # every step copies the five input fields from pinned host memory and
@@ -928,7 +939,8 @@ def main():
             fb["cpu_baseline"] = fb_cpu
             fb["max_err"] = fb_err
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms, "per_step_ms": per_step,
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(n, world), "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

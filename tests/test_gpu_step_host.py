@@ -23,11 +23,14 @@ def env():
     return cool, tab, {k: np.ascontiguousarray(v[:n]) for k, v in f.items()}
 
 
-@pytest.mark.parametrize("pinned,chunk", [(True, 0), (True, 65536), (False, 100_000)])
-def test_host_step_equals_device_step(env, pinned, chunk):
+@pytest.mark.parametrize("pinned,chunk,mode,fp64", [(True, 0, 0, 0), (True, 65536, 0, 0), (False, 100_000, 0, 0),
+                                                  (True, 65536, 1, 0), (True, 100_000, 1, 1)])
+def test_host_step_equals_device_step(env, pinned, chunk, mode, fp64):
+    """Implicit mode and fp64_critical: each chunk lists and steps its own
+    flagged cells; the results and the counters are those of one step."""
     cool, tab, f = env
     n = f["rho"].size
-    p = cool.Params(n_sub=8)
+    p = cool.Params(n_sub=8, mode=mode, fp64_critical=fp64)
     host = {k: torch.from_numpy(v) for k, v in f.items()}
     if pinned:
         host = {k: v.pin_memory() for k, v in host.items()}
