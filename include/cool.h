@@ -324,11 +324,11 @@ cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_
  * forward order (the 2x5 Jacobian of the cell carried along the
  * sub-cycles); with any of them, in the reverse order over the kept
  * sub-cycle states.  The two give the same input gradients up to FP32
- * rounding order (not bitwise).  In implicit mode without table gradients
- * the stiff cells are deferred to a second kernel through a list held in
- * stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on `stream`,
- * 4 (n_cells + 1) bytes); where that allocation fails every cell is solved
- * in place (the same gradients to FP32 rounding).  Invalid cells pass the output adjoints
+ * rounding order (not bitwise).  In implicit mode (with table gradients:
+ * when n_sub <= 8) the stiff cells are deferred to a second kernel through
+ * a list held in stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on
+ * `stream`, 4 (n_cells + 1) bytes); where that allocation fails every cell
+ * is solved in place (the same gradients to FP32 rounding).  Invalid cells pass the output adjoints
  * through.  The inputs must not alias
  * the gradient outputs.  Device pointers, asynchronous on stream; n_sub <= 64. */
 cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,

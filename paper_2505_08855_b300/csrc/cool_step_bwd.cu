@@ -234,12 +234,16 @@ constexpr int kStateFloats = 3;   // floats of per-sub-cycle state (ST_F) with t
 // With table adjoints requested (g_lb, g_ls or g_lc non-null); the input
 // gradients alone come from k_step_tan_f32.  IMPL: the implicit mode's
 // solve compiled in (and its root kept per sub-cycle).
-template <bool SMS, bool IMPL>
+// PASS 1 (implicit mode, without IMPL): a cell that turns stiff stops
+// before any write and its index goes to the list dl ([0] the count, then
+// the indices); PASS 2 (with IMPL) steps the listed cells, consecutive
+// entries on consecutive lanes, instead of a solving lane holding its warp.
+template <bool SMS, bool IMPL, int PASS = 0>
 __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
     const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
     const float* __restrict__ gue_out, const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
-    float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc) {
+    float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, unsigned* dl) {
     extern __shared__ float sm[];
     load_smem(k, sm);
     const Smem S = smem_view(k, sm);
@@ -270,12 +274,14 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
     // index in the grid, the next ones from the tile counter (k.sched) as
     // it finishes, or round-robin without one
     const int lane = threadIdx.x & 31;
-    const long long nchunks = (n + 31) / 32;
+    const long long nitems = PASS == 2 ? (long long)dl[0] : n;
+    const long long nchunks = (nitems + 31) / 32;
     const long long first = (long long)gridDim.x * kWarps;
     long long chunk = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     while (chunk < nchunks) {
-        const long long i = chunk * 32 + lane;
-        if (i < n) {
+        const long long t = chunk * 32 + lane;
+        if (t < nitems) {
+            const long long i = PASS == 2 ? (long long)dl[1 + t] : t;
             const float rho = rho_in[i], B = B_in[i], H = H_in[i];
             float ue = ue_in[i], ui = ui_in[i];
             const float ge_out = gue_out[i], gi_out = gui_out[i];
@@ -307,6 +313,11 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
                 ue += xg.X;
                 ui -= xg.X;
                 const float q = cool_energy<0, true>(k, S, c, cc, ue * inv_e, clamp);
+                if (PASS == 1 && q > k.limiter * ue) {
+                    // stiff: listed for PASS 2, nothing written or added here
+                    dl[1 + atomicAdd(dl, 1u)] = (unsigned)i;
+                    goto next_chunk;
+                }
                 float du = fminf(q, k.limiter * ue);
                 unsigned char br = q < k.limiter * ue ? 0 : 1;
                 if (IMPL && q > k.limiter * ue) {
@@ -589,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step_tan_list_f32(
 // The launches of one cool_step_bwd call: fn over the cells (persistent
 // grid, dynamic chunk order), then, with a deferral list, the list kernel.
 using TanFn = decltype(&k_step_tan_f32<false, false>);
-using BwdFn = decltype(&k_step_bwd_f32<true, true>);
+using BwdFn = decltype(&k_step_bwd_f32<true, true, 0>);
 
 cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, BwdFn fb, bool tbl, size_t smem,
                        unsigned* scratch, const float* rho, const float* B, const float* H, const float* ue,
@@ -614,7 +625,23 @@ cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, BwdFn fb
     }
     if (tbl) {
         fb<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui,
-                                                g_lb, g_ls, g_lc);
+                                                g_lb, g_ls, g_lc, scratch);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || !scratch) return e;
+        // the listed stiff cells, with the solve (and its root in the state)
+        const void* fl = (const void*)k_step_bwd_f32<true, true, 2>;
+        const size_t sl = smem + (size_t)kSmemSub * kThreads * sizeof(float);
+        e = cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fl, kThreads, sl);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        long long bl = (long long)sm_count() * per_sm;
+        if (bl > work) bl = work;
+        StepK kl = k;
+        kl.sched = nullptr;   // the list in its fixed order
+        k_step_bwd_f32<true, true, 2><<<(int)bl, kThreads, sl, st>>>(kl, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B,
+                                                                       g_H, g_ue, g_ui, g_lb, g_ls, g_lc, scratch);
         return cudaGetLastError();
     }
     unsigned* list = scratch ? scratch + 1 : nullptr;
@@ -648,21 +675,14 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     StepK k;
     fill_stepk(t, p, k);
     const bool sms = p->n_sub <= kSmemSub;
-    // without table adjoints: forward tangents (the table parts and the
-    // window in shared memory); with them: the recorded forward and the
-    // reverse sweep (plus the partial sums and the sub-cycles' state)
-    size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads) * sizeof(float);
-    if (tbl) {
-        smem += (size_t)(t->dev.n[3] + ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
-        const int nsf = p->mode == COOL_IMPLICIT_STIFF ? kStateFloats : kStateFloats - 1;
-        if (sms) smem += (size_t)kSmemSub * kThreads * (nsf * sizeof(float) + 1);
-    }
     const bool impl = p->mode == COOL_IMPLICIT_STIFF;
-    // implicit mode without table adjoints: stiff cells deferred to a list
-    // (a stream-ordered scratch of n + 1 words: the count, then the
-    // indices); where it cannot be had, every lane solves its own cells
+    // implicit mode: stiff cells deferred to a list (a stream-ordered
+    // scratch of n + 1 words: the count, then the indices) stepped by a
+    // second pass with the solve -- for the input gradients, and for the
+    // table adjoints with the state in shared memory (n_sub <= 8); where
+    // the scratch cannot be had, every lane solves its own cells
     unsigned* scratch = nullptr;
-    if (!tbl && impl && n < 0xffffffffll) {
+    if (impl && (!tbl || sms) && n < 0xffffffffll) {
         if (cudaMallocAsync(&scratch, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess) {
             (void)cudaGetLastError();
             scratch = nullptr;
@@ -675,9 +695,21 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
         }
     }
     const bool defer = scratch != nullptr;
+    // without table adjoints: forward tangents (the table parts and the
+    // window in shared memory); with them: the recorded forward and the
+    // reverse sweep (plus the partial sums and the sub-cycles' state: the
+    // implicit root too where this pass solves)
+    const bool solves = impl && !defer;
+    size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads) * sizeof(float);
+    if (tbl) {
+        smem += (size_t)(t->dev.n[3] + ((t->dev.n[4] * t->dev.n[4] + 3) & ~3)) * sizeof(float);
+        const int nsf = solves ? kStateFloats : kStateFloats - 1;
+        if (sms) smem += (size_t)kSmemSub * kThreads * (nsf * sizeof(float) + 1);
+    }
     const TanFn tf = !impl ? k_step_tan_f32<false, false> : defer ? k_step_tan_f32<false, true> : k_step_tan_f32<true, false>;
-    const BwdFn fb = sms ? (impl ? k_step_bwd_f32<true, true> : k_step_bwd_f32<true, false>)
-                         : (impl ? k_step_bwd_f32<false, true> : k_step_bwd_f32<false, false>);
+    const BwdFn fb = sms ? (!impl ? k_step_bwd_f32<true, false, 0>
+                            : defer ? k_step_bwd_f32<true, false, 1> : k_step_bwd_f32<true, true, 0>)
+                         : (impl ? k_step_bwd_f32<false, true, 0> : k_step_bwd_f32<false, false, 0>);
     const void* fn = !tbl ? (const void*)tf : (const void*)fb;
     cudaError_t e = launch_bwd(k, n, fn, tf, fb, tbl, smem, scratch, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
                                g_ue, g_ui, g_lb, g_ls, g_lc, st);
