@@ -185,6 +185,12 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                    k_step_f32<V, 0, 12>, k_step_f32<V, 0, 13>, k_step_f32<V, 0, 14>, k_step_f32<V, 0, 15>
     static const StepKernelFn disk_v[8] = {COOL_KD(true)};
     static const StepKernelFn disk_s[8] = {COOL_KD(false)};
+    static const StepKernelFn disk_lv[8] = {nullptr, k_step_f32<true, 0, 69>, k_step_f32<true, 0, 70>,
+                                            k_step_f32<true, 0, 71>, nullptr, k_step_f32<true, 0, 77>,
+                                            k_step_f32<true, 0, 78>, k_step_f32<true, 0, 79>};
+    static const StepKernelFn disk_list_v[8] = {nullptr, k_step_list_f32<0, 5>, k_step_list_f32<0, 6>,
+                                                k_step_list_f32<0, 7>, nullptr, k_step_list_f32<0, 13>,
+                                                k_step_list_f32<0, 14>, k_step_list_f32<0, 15>};
 #undef COOL_KD
     // the paper's table layout (template bit 4): explicit, FP32 table, no geometry
     static const StepKernelFn tot_v[2] = {k_step_f32<true, 0, 16>, k_step_f32<true, 0, 24>};
@@ -199,12 +205,13 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                      : fmt == 0 ? (const void*)(vec ? table_v[var] : table_s[var])
                      : (fmt <= 2 ? step_kernel_f16(fmt, vec, var) : step_kernel_f16s(fmt, vec, var));
     if (!fn) return COOL_EUNSUPPORTED;
-    // implicit mode and fp64_critical on the FP32 table with aligned fields:
+    // implicit mode and fp64_critical on the FP32 table with aligned fields
+    // (with or without the disk geometry):
     // the flagged cells go to a list in stream-ordered scratch (n + 1
     // words: the count, then the indices), stepped by k_step_list_f32 after
     // the tile pass; where the scratch cannot be had, each warp steps its own
     unsigned* scratch = nullptr;
-    if (vec && !tot && !disk && fmt == 0 && (var & 3) && n < 0xffffffffll) {
+    if (vec && !tot && fmt == 0 && (var & 3) && n < 0xffffffffll) {
         if (cudaMallocAsync(&scratch, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess) {
             (void)cudaGetLastError();
             scratch = nullptr;
@@ -214,7 +221,7 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                 cudaFreeAsync(scratch, st);
                 return set_cuda_error(em);
             }
-            fn = (const void*)table_lv[var];
+            fn = (const void*)(disk ? disk_lv[var] : table_lv[var]);
             k.dlist = scratch;
         }
     }
@@ -272,7 +279,7 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
         if (e == cudaSuccess) {
             // the listed cells: one resident wave strides over the list,
             // whose length is on the device
-            const StepKernelFn fl = list_v[var];
+            const StepKernelFn fl = disk ? disk_list_v[var] : list_v[var];
             const size_t sl = (size_t)(smem_table_floats(k) + fmt_nodes(fmt) * kThreads) * sizeof(float);
             e = cudaFuncSetAttribute((const void*)fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
             int pl = 0;
