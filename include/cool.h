@@ -262,10 +262,12 @@ cool_status cool_table_load(const char* path, void* stream, cool_table** out);
  * Launches on one stream run in order, so no two launches that overlap in
  * time share a counter.  In mode IMPLICIT or with fp64_critical (FP32
  * fields, FP32 table, 16-byte aligned arrays, n_cells < 2^32 - 1) the
- * cells that turn stiff or enter the equilibrium band are listed in
- * stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on `stream`,
- * 4 (n_cells + 1) bytes) and stepped by a second kernel; where that
- * allocation fails each warp steps its own (bitwise the same results).
+ * cells that turn stiff or enter the equilibrium band are listed in scratch
+ * (4 (n_cells + 1) bytes) and stepped by a second kernel: device memory
+ * kept per device and stream between calls and grown as needed (see
+ * cool_release_scratch), or inside a stream capture stream-ordered memory
+ * (cudaMallocAsync/cudaFreeAsync on `stream`) that the graph owns; where
+ * it cannot be had each warp steps its own (bitwise the same results).
  *   field_dtype: COOL_F32 or COOL_F64 (all seven field arrays of that type).
  *   rho, B, H, u_e_in, u_i_in: device inputs, n_cells each.
  *   u_e_out, u_i_out: device outputs (may alias u_e_in / u_i_in).
@@ -326,9 +328,10 @@ cool_status cool_build_channels_noalloc(const cool_table_spec* spec, double* lb_
  * sub-cycle states.  The two give the same input gradients up to FP32
  * rounding order (not bitwise).  In implicit mode (with table gradients:
  * when n_sub <= 8) the stiff cells are deferred to a second kernel through
- * a list held in stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on
- * `stream`, 4 (n_cells + 1) bytes); where that allocation fails every cell
- * is solved in place (the same gradients to FP32 rounding).  Invalid cells pass the output adjoints
+ * a list in the scratch cool_step uses for its own (4 (n_cells + 1) bytes,
+ * kept per device and stream; stream-ordered inside a capture); where it
+ * cannot be had every cell is solved in place (the same gradients to FP32
+ * rounding).  Invalid cells pass the output adjoints
  * through.  The inputs must not alias
  * the gradient outputs.  Device pointers, asynchronous on stream; n_sub <= 64. */
 cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
@@ -506,6 +509,15 @@ cool_status cool_debug_wait_timeout(int polls, unsigned* err, void* stream);
  * zeroes the word after reading it.  Errors: COOL_ENULL (err_out NULL),
  * COOL_EINVAL (clear not 0 or 1), COOL_ECUDA. */
 cool_status cool_tma_error(unsigned* err_out, int clear);
+
+/* Free the scratch the library keeps for the deferral lists of cool_step,
+ * cool_step_disk and cool_step_bwd (implicit mode, fp64_critical) on the
+ * current device: one buffer per stream that ran such a step, 4 bytes per
+ * cell of its largest call, plus any it outgrew.  Waits for the device
+ * (cudaDeviceSynchronize) first, so no launch can still use them; the next
+ * call that needs a list allocates again.  Not part of the paper's method.
+ * COOL_ECUDA if the device cannot be synchronised. */
+cool_status cool_release_scratch(void);
 
 /* Index/weight selection of the table interpolation on one axis, for FP32
  * keys in the axis' physical unit (device arrays of n).  axis 0..4 (H, B,

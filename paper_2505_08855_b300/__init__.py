@@ -333,6 +333,12 @@ def tma_error(clear=True):
     return int(v.value)
 
 
+def release_scratch():
+    """cool_release_scratch: free the deferral-list scratch kept for the
+    current device's streams (after synchronising the device)."""
+    _b.check(_b.lib().cool_release_scratch(), "cool_release_scratch")
+
+
 def debug_lookup(table, axis, keys, stream=None):
     """(idx int32, w float32) of the interpolation rule for FP32 keys."""
     import torch

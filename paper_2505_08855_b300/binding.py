@@ -29,6 +29,7 @@ EXPORTS = (
     "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
     "cool_surrogate_eval", "cool_surrogate_mask", "cool_surrogate_set_mask", "cool_surrogate_infer",
     "cool_step_direct", "cool_step_host", "cool_radiation_te", "cool_step_disk", "cool_tma_error",
+    "cool_release_scratch",
 )
 
 
@@ -138,6 +139,7 @@ def lib():
             "cool_surrogate_infer": (I, [P, P, P, LL, P, P, P, P, P, P, P, P, P, P, P]),
             "cool_table_export_packed": (I, [P, P, LL]),
             "cool_tma_error": (I, [P, I]),
+            "cool_release_scratch": (I, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

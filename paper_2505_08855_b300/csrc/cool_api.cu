@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_set>
+#include <vector>
 #include <utility>
 
 #include "cool_internal.cuh"
@@ -70,6 +71,87 @@ unsigned long long* sched_counter(cudaStream_t st) {
         return nullptr;
     }
     counters[{dev, sid}] = p;
+    return p;
+}
+
+// Scratch of the deferral lists (the flagged cells of the implicit mode and
+// of fp64_critical, stepped by the list kernels): at least `words` 32-bit
+// words, one buffer per (device, stream id), kept between calls so that a
+// caller who synchronises after every step does not hand the memory back
+// and map it again on every call.  A call that needs more grows it to at
+// least twice its size; the superseded buffer is kept (a launch another
+// host thread already enqueued on the same stream may still read it) until
+// cool_release_scratch.  Inside a stream capture: nullptr with *capturing
+// set (the caller allocates stream-ordered scratch inside the graph, which
+// a replay on any stream owns alone); nullptr on an allocation failure.
+namespace {
+struct ListBuf {
+    unsigned* p = nullptr;
+    size_t words = 0;
+};
+std::mutex g_list_mu;
+std::map<std::pair<int, unsigned long long>, ListBuf>& list_bufs() {
+    static std::map<std::pair<int, unsigned long long>, ListBuf> m;
+    return m;
+}
+std::vector<std::pair<int, unsigned*>>& list_superseded() {
+    static std::vector<std::pair<int, unsigned*>> v;
+    return v;
+}
+}  // namespace
+
+unsigned* list_scratch(cudaStream_t st, size_t words, bool* capturing) {
+    *capturing = false;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cap != cudaStreamCaptureStatusNone) {
+        *capturing = true;
+        return nullptr;
+    }
+    int dev = 0;
+    unsigned long long sid = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetId(st, &sid) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(g_list_mu);
+    ListBuf& b = list_bufs()[{dev, sid}];
+    if (b.words >= words) return b.p;
+    const size_t want = words > 2 * b.words ? words : 2 * b.words;
+    unsigned* p = nullptr;
+    if (cudaMalloc(&p, want * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.p) list_superseded().push_back({dev, b.p});
+    b.p = p;
+    b.words = want;
+    return p;
+}
+
+unsigned* list_for_call(cudaStream_t st, long long n, bool* owned, cudaError_t* err) {
+    *owned = false;
+    *err = cudaSuccess;
+    bool cap = false;
+    unsigned* p = list_scratch(st, (size_t)n + 1, &cap);
+    if (!p && cap) {
+        if (cudaMallocAsync(&p, sizeof(unsigned) * ((size_t)n + 1), st) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        *owned = true;
+    }
+    if (!p) return nullptr;
+    const cudaError_t e = cudaMemsetAsync(p, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) {
+        if (*owned) cudaFreeAsync(p, st);
+        *owned = false;
+        *err = e;
+        return nullptr;
+    }
     return p;
 }
 
@@ -474,6 +556,35 @@ cool_status table_qtotal(cool_table* t) {
 using namespace cool;
 
 extern "C" {
+
+cool_status cool_release_scratch(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_cuda_error(e);
+    std::lock_guard<std::mutex> g(g_list_mu);
+    auto& m = list_bufs();
+    for (auto it = m.begin(); it != m.end();) {
+        if (it->first.first == dev) {
+            if (it->second.p) cudaFree(it->second.p);
+            it = m.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    auto& v = list_superseded();
+    for (size_t k = 0; k < v.size();) {
+        if (v[k].first == dev) {
+            cudaFree(v[k].second);
+            v[k] = v.back();
+            v.pop_back();
+        } else {
+            ++k;
+        }
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? COOL_OK : set_cuda_error(e);
+}
 
 const char* cool_strerror(cool_status s) {
     switch (s) {

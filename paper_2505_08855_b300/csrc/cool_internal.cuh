@@ -105,6 +105,16 @@ namespace cool {
 // one; nullptr if it cannot be created (first use inside stream capture, or
 // an allocation failure), and the step then takes its static tile order.
 unsigned long long* sched_counter(cudaStream_t st);
+// Scratch for a deferral list of `words` 32-bit words, kept per (device,
+// stream) between calls and grown as needed; nullptr inside a stream
+// capture (*capturing set: allocate stream-ordered scratch in the graph
+// instead) or on an allocation failure (step without the list).
+unsigned* list_scratch(cudaStream_t st, size_t words, bool* capturing);
+// The deferral list of one call over n cells (n + 1 words: the count,
+// zeroed on `st`, then the indices): the per-stream scratch, or inside a
+// capture stream-ordered scratch the caller frees with cudaFreeAsync after
+// its launches (*owned).  nullptr: no list (*err set if the zeroing failed).
+unsigned* list_for_call(cudaStream_t st, long long n, bool* owned, cudaError_t* err);
 cool_status set_cuda_error(cudaError_t e);
 bool table_ok(const cool_table* t);
 long long syn_count(const cool_table_spec& s);

@@ -206,21 +206,16 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                      : (fmt <= 2 ? step_kernel_f16(fmt, vec, var) : step_kernel_f16s(fmt, vec, var));
     if (!fn) return COOL_EUNSUPPORTED;
     // implicit mode and fp64_critical on the FP32 table with aligned fields
-    // (with or without the disk geometry):
-    // the flagged cells go to a list in stream-ordered scratch (n + 1
-    // words: the count, then the indices), stepped by k_step_list_f32 after
-    // the tile pass; where the scratch cannot be had, each warp steps its own
+    // (with or without the disk geometry): the flagged cells go to a list
+    // (n + 1 words: the count, then the indices), stepped by k_step_list_f32
+    // after the tile pass; without a list each warp steps its own
     unsigned* scratch = nullptr;
+    bool owned = false;
     if (vec && !tot && fmt == 0 && (var & 3) && n < 0xffffffffll) {
-        if (cudaMallocAsync(&scratch, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess) {
-            (void)cudaGetLastError();
-            scratch = nullptr;
-        } else {
-            const cudaError_t em = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
-            if (em != cudaSuccess) {
-                cudaFreeAsync(scratch, st);
-                return set_cuda_error(em);
-            }
+        cudaError_t em = cudaSuccess;
+        scratch = list_for_call(st, n, &owned, &em);
+        if (em != cudaSuccess) return set_cuda_error(em);
+        if (scratch) {
             fn = (const void*)(disk ? disk_lv[var] : table_lv[var]);
             k.dlist = scratch;
         }
@@ -293,8 +288,10 @@ cool_status launch_step_f32(const cool_table* t, const cool_params* p, long long
                 e = cudaGetLastError();
             }
         }
-        const cudaError_t ef = cudaFreeAsync(scratch, st);
-        if (e == cudaSuccess) e = ef;
+        if (owned) {
+            const cudaError_t ef = cudaFreeAsync(scratch, st);
+            if (e == cudaSuccess) e = ef;
+        }
     }
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;

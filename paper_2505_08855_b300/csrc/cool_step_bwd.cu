@@ -676,23 +676,16 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     fill_stepk(t, p, k);
     const bool sms = p->n_sub <= kSmemSub;
     const bool impl = p->mode == COOL_IMPLICIT_STIFF;
-    // implicit mode: stiff cells deferred to a list (a stream-ordered
-    // scratch of n + 1 words: the count, then the indices) stepped by a
-    // second pass with the solve -- for the input gradients, and for the
-    // table adjoints with the state in shared memory (n_sub <= 8); where
-    // the scratch cannot be had, every lane solves its own cells
+    // implicit mode: stiff cells deferred to a list (n + 1 words: the
+    // count, then the indices) stepped by a second pass with the solve --
+    // for the input gradients, and for the table adjoints with the state in
+    // shared memory (n_sub <= 8); without a list every lane solves its own
     unsigned* scratch = nullptr;
+    bool owned = false;
     if (impl && (!tbl || sms) && n < 0xffffffffll) {
-        if (cudaMallocAsync(&scratch, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess) {
-            (void)cudaGetLastError();
-            scratch = nullptr;
-        } else {
-            cudaError_t em = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
-            if (em != cudaSuccess) {
-                cudaFreeAsync(scratch, st);
-                return set_cuda_error(em);
-            }
-        }
+        cudaError_t em = cudaSuccess;
+        scratch = list_for_call(st, n, &owned, &em);
+        if (em != cudaSuccess) return set_cuda_error(em);
     }
     const bool defer = scratch != nullptr;
     // without table adjoints: forward tangents (the table parts and the
@@ -713,7 +706,7 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
     const void* fn = !tbl ? (const void*)tf : (const void*)fb;
     cudaError_t e = launch_bwd(k, n, fn, tf, fb, tbl, smem, scratch, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
                                g_ue, g_ui, g_lb, g_ls, g_lc, st);
-    if (scratch) {
+    if (owned) {
         cudaError_t ef = cudaFreeAsync(scratch, st);
         if (e == cudaSuccess) e = ef;
     }

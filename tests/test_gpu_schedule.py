@@ -136,3 +136,26 @@ def test_graph_replayed_on_another_stream_while_a_step_runs(env, oracle):
     for got, r in ((ue_g, ref[0]), (ui_g, ref[1])):
         err = np.abs(got.cpu().double().numpy()[idx] - r) / np.abs(r)
         assert err.max() <= 1e-5
+
+
+def test_list_scratch_grows_and_is_released(env):
+    """Implicit steps keep their list of stiff cells in scratch kept per
+    stream: a small call, a larger one (the scratch grows), the small one
+    again, then after cool_release_scratch (allocated again): every result
+    equals the first of its size, and the stiff counts agree."""
+    cool, tab, tf = env
+    p = cool.Params(n_sub=8, mode=1)
+    small = [t[:5000] for t in tf]
+    first_small = [x.clone() for x in cool.step(tab, p, *small)]
+    first_big = [x.clone() for x in cool.step(tab, p, *tf)]
+    again_small = cool.step(tab, p, *small)
+    torch.cuda.synchronize()
+    cool.release_scratch()
+    c = cool.new_counters()
+    after = cool.step(tab, p, *tf, counters=c)
+    torch.cuda.synchronize()
+    for x, y in zip(again_small, first_small):
+        assert torch.equal(x, y)
+    for x, y in zip(after, first_big):
+        assert torch.equal(x, y)
+    assert cool.counters_dict(c)["stiff"] > 0
