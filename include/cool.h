@@ -514,8 +514,10 @@ cool_status cool_tma_error(unsigned* err_out, int clear);
  * cool_step_disk and cool_step_bwd (implicit mode, fp64_critical) on the
  * current device: one buffer per stream that ran such a step, 4 bytes per
  * cell of its largest call, plus any it outgrew.  Waits for the device
- * (cudaDeviceSynchronize) first, so no launch can still use them; the next
- * call that needs a list allocates again.  Not part of the paper's method.
+ * (cudaDeviceSynchronize) first, so no launch can still use them; call it
+ * while no other host thread is inside a step call on this device.  The
+ * next call that needs a list allocates again.  Not part of the paper's
+ * method.
  * COOL_ECUDA if the device cannot be synchronised. */
 cool_status cool_release_scratch(void);
 
