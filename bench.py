@@ -434,7 +434,7 @@ def _suite_line(case, workload, n, ms, extra=None, bytes_per_cell=None, peak=Non
 
 
 SECTIONS = ("cfg2", "paper_size", "staging_bound", "l2_persist", "disk", "radiation", "scalar", "fp64", "adjoint",
-            "direct", "surrogate", "placement", "host_link")
+            "direct", "surrogate", "placement", "host_link", "nsub")
 
 
 def run_suite_perf(args, torch, cool, inputs, dev):
@@ -738,6 +738,19 @@ def run_suite_perf(args, torch, cool, inputs, dev):
                         {"fallback_cells": cd["fallback"], "fit_seconds": fit_s, "fit": info,
                          "network_tflops": flops / (ms * 1e-3) / 1e12}, BYTES_PER_CELL, peak)
         sur.free()
+    if "nsub" in want:
+        # the step's time against the number of sub-cycles (the benchmark's
+        # cells and table): the per-cell part and the cost of one sub-cycle
+        F = inputs.make(WORKLOAD)
+        n = F["rho"].size
+        fl = [torch.from_numpy(F[k]).to(dev) for k in ("rho", "B", "H", "ue", "ui")]
+        del F
+        uo, io = torch.empty_like(fl[3]), torch.empty_like(fl[4])
+        for ns in (1, 2, 4, 8, 16, 32):
+            p = cool.Params(n_sub=ns)
+            ms = _timed(torch, lambda: cool.step(table(), p, *fl, ue_out=uo, ui_out=io), steps, warm, stream)
+            _suite_line(f"explicit, N_sub = {ns}", WORKLOAD, n, ms, None, BYTES_PER_CELL, peak)
+        del fl, uo, io
     if "host_link" in want:
         # the end-to-end step's floor: the benchmark's 5 input fields host ->
         # device and its 2 outputs back, alone and at once, beside
