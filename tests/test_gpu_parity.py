@@ -221,14 +221,18 @@ def test_step_fp32_parity(cool, oracle, cfg1, mode, n_sub, fp64_critical):
     assert abs(got[4]["stiff"] - want[4]["stiff"]) <= 2 + want[4]["stiff"] // 1000
 
 
-def test_ragged_unaligned_inplace_bitwise(cool, cfg1):
+@pytest.mark.parametrize("mode,fp64", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_ragged_unaligned_inplace_bitwise(cool, cfg1, mode, fp64):
     """The 128-bit path, the scalar tail and the unaligned scalar path give
-    bit-identical cells; in-place output equals out-of-place."""
+    bit-identical cells; in-place output equals out-of-place.  In implicit
+    mode and with fp64_critical the aligned call lists its flagged cells
+    (from its tiles and its ragged tail) for the list kernel, the unaligned
+    one steps every cell on its own lane: the same bits."""
     tab, _, _ = cfg1
     n = 4 * 1000 + 3
     f = inputs.uniform(n + 1, seed=21, dtype=np.float32)
     tf = to_dev(f, torch.float32)
-    p = cool.Params(n_sub=8)
+    p = cool.Params(n_sub=8, mode=mode, fp64_critical=fp64)
     full = {k: v[:n].contiguous() for k, v in tf.items()}
     ue_a, ui_a = cool.step(tab, p, full["rho"], full["B"], full["H"], full["ue"], full["ui"])
     off = {k: v[1:n + 1] for k, v in {k: torch.cat([v[:1], v[:n]]) for k, v in tf.items()}.items()}
