@@ -506,6 +506,18 @@ def run_suite_perf(args, torch, cool, inputs, dev):
             _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
         big.free()
         del big
+        # the 16-bit storage formats at that size: half the table bytes (still
+        # beyond L2), so fewer of the gathers' sectors miss L2
+        for name, dt, sc in (("paper-size 100^4 table, BF16", cool.BF16, 0),
+                             ("paper-size 100^4 table, FP16", cool.F16, 0),
+                             ("paper-size 100^4 table, BF16 block-scaled", cool.BF16, 1),
+                             ("paper-size 100^4 table, FP16 block-scaled", cool.F16, 1)):
+            big = cool.Table(cool.TableSpec(n=(100,) * 5, dtype=dt, row_scaled=sc))
+            p = cool.Params(n_sub=N_SUB)
+            ms = _timed(torch, lambda: cool.step(big, p, *fl, ue_out=ue_o, ui_out=ui_o), steps, warm, stream)
+            _suite_line(name, WORKLOAD, n, ms, {"table_packed_bytes": big.packed_bytes()}, BYTES_PER_CELL, peak)
+            big.free()
+            del big
     if "staging_bound" in want:
         # what staging the 4-D channel on chip could gain at most: the same
         # step with a 4-D channel of 2x2x2 (H, B, n_e) corners x 64 T_e nodes
