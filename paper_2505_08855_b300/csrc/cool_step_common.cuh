@@ -445,6 +445,25 @@ __device__ __forceinline__ void gather(const CellC& c, int kb, Cache& cc) {
     cc.base = Fmt<FMT>::S * kb;
 }
 
+// The bridge of Eq. 11 (see cool_energy below) from Ls = log2 q_syn,
+// Lb = log2 q_brem (code units) and lT = log2 T_e.
+__device__ __forceinline__ float energy_from_logs(const CellC& c, float Ls, float Lb, float lT) {
+    const float M = fmaxf(Ls, Lb);
+    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
+    const float Bb = fmaf(4.f, lT, c.lbb_off);
+    const float lt = A - Bb;  // log2 tau_abs
+    float lq;
+    if (lt <= 60.f) {
+        const float tau = ex2a(lt);
+        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
+        lq = A - lg2a(D);
+    } else {
+        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
+        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
+    }
+    return ex2a(fminf(lq, 126.f));
+}
+
 // Energy (code units) that cooling removes in one sub-cycle at T_e, with
 // the bridge of Eq. 11 evaluated in log2 space:
 //   A = log2 q_thin = log2(q_brem + q_syn), B = log2 q_bb with
@@ -479,21 +498,7 @@ __device__ __forceinline__ float cool_energy(const StepK& k, const Smem& S, cons
     const float w = s.w;
     const float Ls = lerpf(cc.win[o * kThreads], cc.win[(o + 1) * kThreads], w) + c.ls_off;
     const float Lb = lerpf(nd.z, nd.w, w) + c.lb_off;
-    const float lT = nd.y + s.r;
-    const float M = fmaxf(Ls, Lb);
-    const float A = M + lg2a(1.f + ex2a(fminf(Ls, Lb) - M));
-    const float Bb = fmaf(4.f, lT, c.lbb_off);
-    const float lt = A - Bb;  // log2 tau_abs
-    float lq;
-    if (lt <= 60.f) {
-        const float tau = ex2a(lt);
-        const float D = fmaf(tau, fmaf(1.5f, tau + c.tau_sca, 1.7320508f), 1.f);
-        lq = A - lg2a(D);
-    } else {
-        // q = q_bb / (1.5 (tau_abs + tau_sca)) up to 2^-59 relative
-        lq = Bb - 0.5849625f - (lt + lg2a(1.f + c.tau_sca * ex2a(-lt)));
-    }
-    return ex2a(fminf(lq, 126.f));
+    return energy_from_logs(c, Ls, Lb, nd.y + s.r);
 }
 
 // The same energy on the paper's table layout (Sec. 3.1): the total rate,
@@ -512,6 +517,34 @@ __device__ __forceinline__ float cool_energy_total(const StepK& k, const Smem& S
     return ex2a(fminf(L, 126.f));
 }
 
+// Node 0 of T_e block 0 of a corner row (the words that hold it, read with
+// plain loads; the same decoding as dec<FMT>(r, 0)).
+template <int FMT>
+__device__ __forceinline__ float node0(const uint32_t* p) {
+    if (FMT == 0) return __uint_as_float(__ldg(p));
+    if (FMT == 1 || FMT == 2) return half_bits(__ldg(p) & 0xffffu, FMT == 2);
+    return fmaf(__uint_as_float(__ldg(p + 1)), half_bits(__ldg(p + 2) & 0xffffu, FMT == 4), __uint_as_float(__ldg(p)));
+}
+
+// cool_energy at a key below half the first T_e node: the selection there
+// is interval 0 with weight 0 (in EXACT mode too), so the synchrotron value
+// is node 0 collapsed over the H, B, n_e corners -- computed here from the
+// eight corners' node-0 words in the order gather uses, without moving the
+// window -- and the result is the one cool_energy returns, bit for bit.
+template <int FMT>
+__device__ __forceinline__ float cool_energy_below(const StepK& k, const Smem& S, const CellC& c, float Te) {
+    const int nT = k.tab.n[3];
+    const float* axT = S.ax + k.tab.axis_off[3];
+    const uint32_t* p = c.row;
+    const uint32_t* q = p + c.oH;
+    const float v0 = lerpf(lerpf(node0<FMT>(p), node0<FMT>(p + c.oN), c.wn),
+                           lerpf(node0<FMT>(p + c.oB), node0<FMT>(p + c.oB + c.oN), c.wn), c.wb);
+    const float v1 = lerpf(lerpf(node0<FMT>(q), node0<FMT>(q + c.oN), c.wn),
+                           lerpf(node0<FMT>(q + c.oB), node0<FMT>(q + c.oB + c.oN), c.wn), c.wb);
+    const float r = lg2a(Te * axT[nT]);   // log2(T_e / x_0), as select_finish forms it
+    return energy_from_logs(c, lerpf(v0, v1, c.wh) + c.ls_off, S.lb[0] + c.lb_off, axT[2 * nT] + r);
+}
+
 // Backward Euler u' = u0 - q(u') of a stiff cell (q(u0) > limiter u0) in
 // FP32.  Bracket [u0 2^-60, u0]: g(u0) = q(u0) > 0 and g(u0 2^-60) < 0 is
 // checked (false when it fails).  Illinois (modified regula falsi) first on
@@ -527,7 +560,12 @@ __device__ __forceinline__ bool implicit_fp32(const StepK& k, const Smem& S, con
     float xb = lg2a(u0);
     float xa = xb - 60.f;
     const float ua0 = ex2a(xa);
-    const float qa0 = cool_energy<FMT, EXACT, true>(k, S, c, cc, ua0 * inv_e, trial);
+    // the lower end lies 60 octaves below u0, far below the T_e axis: its
+    // energy comes from node 0 without moving the window, which keeps the
+    // block the next trial points (near the root) need
+    const float ta0 = ua0 * inv_e;
+    const float qa0 = ta0 < 0.5f * k.g_x0[3] ? cool_energy_below<FMT>(k, S, c, ta0)
+                                             : cool_energy<FMT, EXACT, true>(k, S, c, cc, ta0, trial);
     if (!(ua0 - u0 + qa0 < 0.f)) return false;
     float Gb = lg2a(fmaf(q0, inv_u0, 1.f));
     float Ga = lg2a((ua0 + qa0) * inv_u0);
