@@ -287,13 +287,28 @@ def fwd_bwd_gpu(torch, cool, inputs, dev, table, steps):
     def bwd_t():
         cool.step_bwd(table, p, *gl, g_ue, g_ui, tgr)
 
+    # the autograd path: the forward keeps each cell's 2x5 Jacobian, the
+    # backward contracts it with the output adjoints
+    uo, vo = torch.empty_like(gl[3]), torch.empty_like(gl[4])
+    J = torch.empty((10, m), device=dev)
+
+    def fwd_jac():
+        cool.step_fwd_jac(table, p, *gl, ue_out=uo, ui_out=vo, jac=J)
+
+    def bwd_jac():
+        out["gj"] = cool.step_bwd_jac(J, g_ue, g_ui)
+
     ms_f = _timed(torch, fwd, steps, 3, stream)
     ms_b = _timed(torch, bwd, steps, 3, stream)
     ms_bt = _timed(torch, bwd_t, steps, 3, stream)
-    grads = [t.cpu().numpy() for t in out["g"]]
-    del tg, gl, g_ue, g_ui, tgr, out
+    ms_fj = _timed(torch, fwd_jac, steps, 3, stream)
+    ms_bj = _timed(torch, bwd_jac, steps, 3, stream)
+    grads = [t.cpu().numpy() for t in out["gj"]]
+    same = all(torch.equal(a, b) for a, b in zip(out["gj"], out["g"]))
+    del tg, gl, g_ue, g_ui, tgr, out, uo, vo, J
     torch.cuda.empty_cache()
-    return {"cells": m, "ms_fwd": ms_f, "ms_bwd": ms_b, "ms_bwd_with_table_adjoints": ms_bt}, grads, G
+    return {"cells": m, "ms_fwd": ms_f, "ms_bwd": ms_b, "ms_bwd_with_table_adjoints": ms_bt,
+            "ms_fwd_jac": ms_fj, "ms_bwd_jac": ms_bj, "jac_grads_equal_step_bwd": same}, grads, G
 
 
 def fwd_bwd_oracle(G, grads, spec, T, nthreads, n_sample=1024, seed=1003):
@@ -640,7 +655,18 @@ def run_suite_perf(args, torch, cool, inputs, dev):
                     peak)
         _suite_line("forward + adjoint (inputs and table), 128^3 uniform", "uniform_128c", m, ms_f + ms_bt, None,
                     76, peak)
-        del g_ue, g_ui, tgr
+        # the autograd path: the forward keeps each cell's Jacobian, the
+        # backward contracts it (explicit and implicit mode)
+        uo, vo = torch.empty_like(gl[3]), torch.empty_like(gl[4])
+        J = torch.empty((10, m), device=dev)
+        for mode, label in ((cool.EXPLICIT, ""), (cool.IMPLICIT, ", implicit mode")):
+            pm = cool.Params(n_sub=N_SUB, mode=mode)
+            ms_fj = _timed(torch, lambda: cool.step_fwd_jac(T, pm, *gl, ue_out=uo, ui_out=vo, jac=J), steps * 5,
+                           warm, stream)
+            ms_bj = _timed(torch, lambda: cool.step_bwd_jac(J, g_ue, g_ui), steps * 5, warm, stream)
+            _suite_line(f"forward with Jacobian + its contraction{label}, 128^3 uniform", "uniform_128c", m,
+                        ms_fj + ms_bj, {"ms_fwd_jac": ms_fj, "ms_bwd_jac": ms_bj}, 76, peak)
+        del g_ue, g_ui, tgr, uo, vo, J
     if "direct" in want:
         # the paper's analytic-versus-table comparison: every rate from the
         # formulas (FP64), on the first 2^18 of these cells
@@ -949,15 +975,24 @@ def main():
                "host": host_cpu_model(), **more}
 
     if rank == 0:
-        ms_fb = fb_t["ms_fwd"] + fb_t["ms_bwd"]
+        # the library's autograd path (cool_step_fn): cool_step_fwd_jac, then
+        # cool_step_bwd_jac; beside it cool_step + cool_step_bwd (the
+        # sub-cycles recomputed in the backward), and with table adjoints
+        ms_fb = fb_t["ms_fwd_jac"] + fb_t["ms_bwd_jac"]
+        ms_fr = fb_t["ms_fwd"] + fb_t["ms_bwd"]
         m_fb = fb_t["cells"]
         a_fb = FWD_BWD_BYTES_PER_CELL * m_fb / (ms_fb * 1e-3) / 1e9
         ms_fbt = fb_t["ms_fwd"] + fb_t["ms_bwd_with_table_adjoints"]
         fb = {"value": m_fb / (ms_fb * 1e-3), "unit": UNIT, "ms_per_step": ms_fb,
-              "workload": "128^3 uniform cells (synthetic, seeded), 64^4 FP32 table, 8 sub-cycles recomputed",
-              "ms_fwd": fb_t["ms_fwd"], "ms_bwd": fb_t["ms_bwd"],
+              "workload": "128^3 uniform cells (synthetic, seeded), 64^4 FP32 table, 8 sub-cycles",
+              "path": "cool_step_fwd_jac (outputs + each cell's 2x5 Jacobian, 40 B/cell kept) + "
+                      "cool_step_bwd_jac (the contraction with the output adjoints)",
+              "ms_fwd": fb_t["ms_fwd_jac"], "ms_bwd": fb_t["ms_bwd_jac"],
+              "grads_equal_step_bwd": fb_t["jac_grads_equal_step_bwd"],
               "roofline": {"bound": "hbm", "achieved": a_fb, "peak": peak, "unit": "GB/s", "frac": a_fb / peak,
                            "bytes_per_cell": FWD_BWD_BYTES_PER_CELL, "peak_source": peak_kind},
+              "recomputed": {"value": m_fb / (ms_fr * 1e-3), "ms_per_step": ms_fr, "ms_fwd": fb_t["ms_fwd"],
+                             "ms_bwd": fb_t["ms_bwd"], "path": "cool_step + cool_step_bwd (sub-cycles recomputed)"},
               "with_table_adjoints": {"value": m_fb / (ms_fbt * 1e-3), "ms_per_step": ms_fbt,
                                       "ms_bwd": fb_t["ms_bwd_with_table_adjoints"]}}
         if cpu is not None:

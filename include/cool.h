@@ -339,6 +339,35 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                           const float* g_u_e_out, const float* g_u_i_out, float* g_rho, float* g_B, float* g_H,
                           float* g_u_e_in, float* g_u_i_in, float* g_lb, float* g_ls, float* g_lc, void* stream);
 
+/* Forward step and its Jacobian in one pass (the adjoint of cool_step_bwd
+ * split at the cell's Jacobian; Sec. 3.2's step, differentiated by the chain
+ * rule in the forward order).  Writes u_e_out, u_i_out -- cool_step's
+ * outputs for the same table, params and inputs, bit for bit -- and the
+ * Jacobian of each cell's outputs with respect to its inputs, so that
+ * cool_step_bwd_jac can later form the input gradients for any output
+ * adjoints without stepping again.  jac: 10 n_cells floats (device,
+ * caller-owned), ten rows of n_cells: row x = d u_e_out / d in_x and row
+ * 5 + x = d u_i_out / d in_x, for in = (rho, B, H, u_e_in, u_i_in), x = 0..4.
+ * Invalid cells pass through with the identity on (u_e, u_i).  The outputs
+ * may overwrite u_e_in, u_i_in (each cell reads its inputs first); jac must
+ * not alias the fields.  FP32 fields, an FP32 table, the L2WINDOW path,
+ * explicit or implicit mode (stiff cells through the list scratch of
+ * cool_step_bwd); fp64_critical: COOL_EUNSUPPORTED.  Device pointers,
+ * asynchronous on stream; n_sub <= 64. */
+cool_status cool_step_fwd_jac(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
+                              const float* B, const float* H, const float* u_e_in, const float* u_i_in,
+                              float* u_e_out, float* u_i_out, float* jac, void* stream);
+
+/* Input gradients from a Jacobian of cool_step_fwd_jac (same layout, same
+ * n_cells) and the output adjoints g_u_e_out, g_u_i_out:
+ * g_x = g_u_e_out d u_e_out/d x + g_u_i_out d u_i_out/d x for x = rho, B,
+ * H, u_e_in, u_i_in.  These are cool_step_bwd's input gradients (without
+ * table gradients) bit for bit: the same Jacobian, contracted by the same
+ * expression.  Device pointers, asynchronous on stream; the gradients must
+ * not alias jac or the adjoints. */
+cool_status cool_step_bwd_jac(long long n_cells, const float* jac, const float* g_u_e_out, const float* g_u_i_out,
+                              float* g_rho, float* g_B, float* g_H, float* g_u_e_in, float* g_u_i_in, void* stream);
+
 /* cool_step with the disk geometry of each cell: r (radius in r_g per
  * cell, FP32 device array, > 0) and `disk` (spin, optional H_th from the
  * state, optional temperature floor).  H may be NULL when

@@ -400,23 +400,80 @@ def step_bwd(table, params, rho, B, H, ue, ui, g_ue_out, g_ui_out, table_grads=N
     return tuple(outs)
 
 
+def step_fwd_jac(table, params, rho, B, H, ue, ui, ue_out=None, ui_out=None, jac=None, stream=None):
+    """cool_step_fwd_jac for FP32 fields: returns (ue_out, ui_out, jac), jac
+    a float32 [10, n] tensor (rows d u_e_out/d(rho, B, H, u_e, u_i), then
+    d u_i_out/d(the same))."""
+    import torch
+    n = rho.numel()
+    for f in (rho, B, H, ue, ui):
+        if f.dtype != torch.float32 or f.numel() != n or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("step_fwd_jac takes contiguous float32 CUDA tensors of one size")
+    ue_out = torch.empty_like(ue) if ue_out is None else ue_out
+    ui_out = torch.empty_like(ui) if ui_out is None else ui_out
+    jac = torch.empty((10, n), dtype=torch.float32, device=rho.device) if jac is None else jac
+    for f, m in ((ue_out, n), (ui_out, n), (jac, 10 * n)):
+        if f.dtype != torch.float32 or f.numel() != m or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("step_fwd_jac: outputs must be contiguous float32 CUDA tensors (jac: 10 n)")
+    p = params.c()
+    st = _b.lib().cool_step_fwd_jac(table.handle, _b.ref(p), n, *[_ptr(f) for f in (rho, B, H, ue, ui)],
+                                    _ptr(ue_out), _ptr(ui_out), _ptr(jac), _stream_ptr(stream))
+    _b.check(st, "cool_step_fwd_jac")
+    return ue_out, ui_out, jac
+
+
+def step_bwd_jac(jac, g_ue_out, g_ui_out, stream=None):
+    """cool_step_bwd_jac: the input gradients (g_rho, g_B, g_H, g_ue_in,
+    g_ui_in) from a Jacobian of step_fwd_jac and the output adjoints."""
+    import torch
+    n = g_ue_out.numel()
+    for f, m in ((jac, 10 * n), (g_ue_out, n), (g_ui_out, n)):
+        if f.dtype != torch.float32 or f.numel() != m or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("step_bwd_jac takes contiguous float32 CUDA tensors (jac: 10 n)")
+    outs = [torch.empty_like(g_ue_out) for _ in range(5)]
+    st = _b.lib().cool_step_bwd_jac(n, _ptr(jac), _ptr(g_ue_out), _ptr(g_ui_out), *[_ptr(o) for o in outs],
+                                    _stream_ptr(stream))
+    _b.check(st, "cool_step_bwd_jac")
+    return tuple(outs)
+
+
 def _make_autograd():
     import torch
 
     class CoolStepFn(torch.autograd.Function):
-        """u_e_out, u_i_out = cool_step(rho, B, H, u_e, u_i) with the adjoint
-        of cool_step_bwd; the forward keeps only its inputs (the backward
-        recomputes the sub-cycles)."""
+        """u_e_out, u_i_out = cool_step(rho, B, H, u_e, u_i) with its adjoint.
+        Without table gradients the forward is cool_step_fwd_jac: the same
+        outputs, plus each cell's 2x5 Jacobian (40 bytes per cell, kept for
+        the backward), and the backward is cool_step_bwd_jac, which contracts
+        it with the output adjoints; the gradients are cool_step_bwd's bit
+        for bit.  Where that is unsupported (fp64_critical) or table
+        gradients are asked for, the forward is cool_step, keeps only its
+        inputs, and the backward is cool_step_bwd (the sub-cycles recomputed)."""
 
         @staticmethod
         def forward(ctx, rho, B, H, ue, ui, table, params, table_grads=None):
-            ue_o, ui_o = step(table, params, rho.detach(), B.detach(), H.detach(), ue.detach(), ui.detach())
-            ctx.save_for_backward(rho, B, H, ue, ui)
             ctx.table, ctx.params, ctx.table_grads = table, params, table_grads
+            ins = [t.detach() for t in (rho, B, H, ue, ui)]
+            if table_grads is None and not params.fp64_critical and table.spec.dtype == F32:
+                ue_o, ui_o, jac = step_fwd_jac(table, params, *ins)
+                ctx.save_for_backward(jac)
+                ctx.jac = True
+            else:
+                ue_o, ui_o = step(table, params, *ins)
+                ctx.save_for_backward(rho, B, H, ue, ui)
+                ctx.jac = False
             return ue_o, ui_o
 
         @staticmethod
         def backward(ctx, g_ue, g_ui):
+            if ctx.jac:
+                (jac,) = ctx.saved_tensors
+                n = jac.shape[1]
+                z = None
+                g_ue = torch.zeros(n, device=jac.device) if g_ue is None else g_ue.contiguous()
+                g_ui = torch.zeros(n, device=jac.device) if g_ui is None else g_ui.contiguous()
+                g = step_bwd_jac(jac, g_ue, g_ui)
+                return g[0], g[1], g[2], g[3], g[4], z, z, z
             rho, B, H, ue, ui = ctx.saved_tensors
             g_ue = torch.zeros_like(ue) if g_ue is None else g_ue.contiguous()
             g_ui = torch.zeros_like(ui) if g_ui is None else g_ui.contiguous()

@@ -24,6 +24,7 @@ EXPORTS = (
     "cool_build_table", "cool_table_free", "cool_table_l2_persist", "cool_table_get_spec", "cool_table_export",
     "cool_table_nodes", "cool_table_save", "cool_table_load", "cool_step", "cool_debug_lookup",
     "cool_build_channels_noalloc", "cool_table_packed_bytes", "cool_table_export_packed", "cool_step_bwd",
+    "cool_step_fwd_jac", "cool_step_bwd_jac",
     "cool_debug_gemm_bf16", "cool_debug_wait_timeout", "cool_fit_spec_default", "cool_surrogate_fit",
     "cool_surrogate_free",
     "cool_surrogate_info", "cool_surrogate_get_params", "cool_surrogate_set_params", "cool_surrogate_grads",
@@ -120,6 +121,8 @@ def lib():
             "cool_build_channels_noalloc": (I, [P, P, P, P, P]),
             "cool_table_packed_bytes": (I, [P, P]),
             "cool_step_bwd": (I, [P, P, LL] + [P] * 15 + [P]),
+            "cool_step_fwd_jac": (I, [P, P, LL] + [P] * 8 + [P]),
+            "cool_step_bwd_jac": (I, [LL] + [P] * 8 + [P]),
             "cool_debug_gemm_bf16": (I, [P, P, P, I, I, I, P, P]),
             "cool_debug_wait_timeout": (I, [I, P, P]),
             "cool_fit_spec_default": (I, [P]),

@@ -1048,6 +1048,41 @@ cool_status cool_step_bwd(const cool_table* t, const cool_params* p, long long n
                                g_u_e_in, g_u_i_in, g_lb, g_ls, g_lc, (cudaStream_t)stream);
 }
 
+cool_status cool_step_fwd_jac(const cool_table* t, const cool_params* p, long long n_cells, const float* rho,
+                              const float* B, const float* H, const float* u_e_in, const float* u_i_in,
+                              float* u_e_out, float* u_i_out, float* jac, void* stream) {
+    if (!t || !p) return COOL_ENULL;
+    if (!table_ok(t)) return COOL_ESTATE;
+    cool_status st = validate_params(p);
+    if (st != COOL_OK) return st;
+    if (p->path != COOL_PATH_L2WINDOW) return COOL_EUNSUPPORTED;
+    if (n_cells < 0) return COOL_EINVAL;
+    if (n_cells == 0) return COOL_OK;
+    const void* req[] = {rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, jac};
+    for (const void* q : req)
+        if (!q) return COOL_ENULL;
+    for (const void* q : req)
+        if ((uintptr_t)q % 4 != 0) return COOL_EALIGN;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return COOL_ESTATE;
+    return launch_step_fwd_jac_f32(t, p, n_cells, rho, B, H, u_e_in, u_i_in, u_e_out, u_i_out, jac,
+                                   (cudaStream_t)stream);
+}
+
+cool_status cool_step_bwd_jac(long long n_cells, const float* jac, const float* g_u_e_out, const float* g_u_i_out,
+                              float* g_rho, float* g_B, float* g_H, float* g_u_e_in, float* g_u_i_in, void* stream) {
+    if (n_cells < 0) return COOL_EINVAL;
+    if (n_cells == 0) return COOL_OK;
+    const void* req[] = {jac, g_u_e_out, g_u_i_out, g_rho, g_B, g_H, g_u_e_in, g_u_i_in};
+    for (const void* q : req)
+        if (!q) return COOL_ENULL;
+    for (const void* q : req)
+        if ((uintptr_t)q % 4 != 0) return COOL_EALIGN;
+    return launch_jac_contract_f32(n_cells, jac, g_u_e_out, g_u_i_out, g_rho, g_B, g_H, g_u_e_in, g_u_i_in,
+                                   (cudaStream_t)stream);
+}
+
 cool_status cool_debug_lookup(const cool_table* t, int axis, long long n, const float* keys, int* idx,
                               float* w, void* stream) {
     if (!t) return COOL_ENULL;

@@ -155,6 +155,11 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
                                 const float* B, const float* H, const float* ue, const float* ui,
                                 const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
                                 float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st);
+cool_status launch_step_fwd_jac_f32(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                                    const float* B, const float* H, const float* ue, const float* ui, float* ue_out,
+                                    float* ui_out, float* jac, cudaStream_t st);
+cool_status launch_jac_contract_f32(long long n, const float* jac, const float* gue, const float* gui, float* g_rho,
+                                    float* g_B, float* g_H, float* g_ue, float* g_ui, cudaStream_t st);
 cool_status validate_params(const cool_params* p);
 cool_status table_textures(cool_table* t);
 cool_status launch_step_tma(const cool_table* t, const cool_params* p, long long n, const float* rho,

@@ -434,6 +434,13 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
             if (glc_s[i] != 0.f) atomicAdd(&g_lc[i], glc_s[i]);
 }
 
+// One input gradient from the output adjoints and a column of the
+// Jacobian; the same expression in tan_cell and k_jac_contract, so the
+// gradients of cool_step_bwd_jac are cool_step_bwd's bit for bit.
+__device__ __forceinline__ float jac_contract(float ge, float gi, float je, float ji) {
+    return fmaf(ge, je, gi * ji);
+}
+
 // The input gradients without table adjoints, by forward tangents.  The
 // step maps five inputs (rho, B, H, u_e, u_i) to two outputs, so the 2x5
 // Jacobian d(u_e, u_i)/d(inputs) is carried through the sub-cycles in
@@ -447,19 +454,43 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
 // nothing and returns false; its index goes to a list that
 // k_step_tan_list_f32 steps with the solve, the listed cells side by side
 // on consecutive lanes instead of one solving lane holding its warp.
-template <bool IMPL, bool DEFER>
+// JAC (cool_step_fwd_jac): instead of the contraction, the cell's outputs
+// u_e, u_i (the forward step's, bit for bit: the same selections, exchange,
+// bridge and solve) and its Jacobian go to jo, the Jacobian as ten SoA rows
+// of jo.n floats: row x = d u_e / d in_x, row 5 + x = d u_i / d in_x for
+// in = (rho, B, H, u_e, u_i).  The inputs are read before anything is
+// written, so the outputs may overwrite them.
+struct JacOut {
+    float* ue;
+    float* ui;
+    float* jac;
+    long long n;
+};
+
+template <bool IMPL, bool DEFER, bool JAC>
 __device__ __forceinline__ bool tan_cell(const StepK& k, const Smem& S, float* win, long long i,
                                          const float* __restrict__ rho_in, const float* __restrict__ B_in,
-                                         const float* __restrict__ H_in, const float* __restrict__ ue_in,
-                                         const float* __restrict__ ui_in, const float* __restrict__ gue_out,
+                                         const float* __restrict__ H_in, const float* ue_in,
+                                         const float* ui_in, const float* __restrict__ gue_out,
                                          const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
-                                         float* g_ue, float* g_ui) {
+                                         float* g_ue, float* g_ui, const JacOut& jo) {
     const float rho = rho_in[i], B = B_in[i], H = H_in[i];
     float ue = ue_in[i], ui = ui_in[i];
-    const float ge_out = gue_out[i], gi_out = gui_out[i];
+    const float ge_out = JAC ? 0.f : gue_out[i], gi_out = JAC ? 0.f : gui_out[i];
     if (!(isfinite(rho) && isfinite(B) && isfinite(H) && isfinite(ue) && isfinite(ui)) ||
         !(rho > 0.f) || !(ue > 0.f) || !(ui > 0.f) || B < 0.f || H < 0.f) {
-        g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
+        if (JAC) {
+            // passed through: the identity on (u_e, u_i)
+            jo.ue[i] = ue;
+            jo.ui[i] = ui;
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+                jo.jac[x * jo.n + i] = x == 3 ? 1.f : 0.f;
+                jo.jac[(5 + x) * jo.n + i] = x == 4 ? 1.f : 0.f;
+            }
+        } else {
+            g_rho[i] = 0.f; g_B[i] = 0.f; g_H[i] = 0.f; g_ue[i] = ge_out; g_ui[i] = gi_out;
+        }
     } else {
         unsigned clamp = 0u;
         const float inv_e = k.s_Te / rho, inv_i = k.s_Ti / rho, kr = k.s_K / rho;
@@ -530,21 +561,31 @@ __device__ __forceinline__ bool tan_cell(const StepK& k, const Smem& S, float* w
             }
             ue -= du;
         }
-        g_rho[i] = fmaf(ge_out, je[0], gi_out * ji[0]);
-        g_B[i] = fmaf(ge_out, je[1], gi_out * ji[1]);
-        g_H[i] = fmaf(ge_out, je[2], gi_out * ji[2]);
-        g_ue[i] = fmaf(ge_out, je[3], gi_out * ji[3]);
-        g_ui[i] = fmaf(ge_out, je[4], gi_out * ji[4]);
+        if (JAC) {
+            jo.ue[i] = ue;
+            jo.ui[i] = ui;
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+                jo.jac[x * jo.n + i] = je[x];
+                jo.jac[(5 + x) * jo.n + i] = ji[x];
+            }
+        } else {
+            g_rho[i] = jac_contract(ge_out, gi_out, je[0], ji[0]);
+            g_B[i] = jac_contract(ge_out, gi_out, je[1], ji[1]);
+            g_H[i] = jac_contract(ge_out, gi_out, je[2], ji[2]);
+            g_ue[i] = jac_contract(ge_out, gi_out, je[3], ji[3]);
+            g_ui[i] = jac_contract(ge_out, gi_out, je[4], ji[4]);
+        }
     }
     return true;
 }
 
-template <bool IMPL, bool DEFER>
+template <bool IMPL, bool DEFER, bool JAC>
 __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
     StepK k, long long n, const float* __restrict__ rho_in, const float* __restrict__ B_in,
-    const float* __restrict__ H_in, const float* __restrict__ ue_in, const float* __restrict__ ui_in,
+    const float* __restrict__ H_in, const float* ue_in, const float* ui_in,
     const float* __restrict__ gue_out, const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H,
-    float* g_ue, float* g_ui, unsigned* n_list, unsigned* list) {
+    float* g_ue, float* g_ui, unsigned* n_list, unsigned* list, JacOut jo) {
     extern __shared__ float sm[];
     load_smem(k, sm);
     const Smem S = smem_view(k, sm);
@@ -557,8 +598,8 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
         const long long i = chunk * 32 + lane;
         bool deferred = false;
         if (i < n)
-            deferred = !tan_cell<IMPL, DEFER>(k, S, win, i, rho_in, B_in, H_in, ue_in, ui_in, gue_out, gui_out,
-                                              g_rho, g_B, g_H, g_ue, g_ui);
+            deferred = !tan_cell<IMPL, DEFER, JAC>(k, S, win, i, rho_in, B_in, H_in, ue_in, ui_in, gue_out, gui_out,
+                                                   g_rho, g_B, g_H, g_ue, g_ui, jo);
         if (DEFER) {
             // the warp's deferred cells, appended with one atomic
             const unsigned bal = __ballot_sync(0xffffffffu, deferred);
@@ -579,13 +620,14 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 4) k_step_tan_f32(
     }
 }
 
-// The cells k_step_tan_f32<false, true> deferred, by index, with the solve
-// compiled in: consecutive list entries on consecutive lanes.
+// The cells k_step_tan_f32<false, true, JAC> deferred, by index, with the
+// solve compiled in: consecutive list entries on consecutive lanes.
+template <bool JAC>
 __global__ void __launch_bounds__(kThreads, 2) k_step_tan_list_f32(
     StepK k, const unsigned* __restrict__ n_list, const unsigned* __restrict__ list,
     const float* __restrict__ rho_in, const float* __restrict__ B_in, const float* __restrict__ H_in,
-    const float* __restrict__ ue_in, const float* __restrict__ ui_in, const float* __restrict__ gue_out,
-    const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H, float* g_ue, float* g_ui) {
+    const float* ue_in, const float* ui_in, const float* __restrict__ gue_out,
+    const float* __restrict__ gui_out, float* g_rho, float* g_B, float* g_H, float* g_ue, float* g_ui, JacOut jo) {
     extern __shared__ float sm[];
     load_smem(k, sm);
     const Smem S = smem_view(k, sm);
@@ -593,19 +635,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_step_tan_list_f32(
     const long long m = *n_list;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < m;
          t += (long long)gridDim.x * blockDim.x)
-        tan_cell<true, false>(k, S, win, (long long)list[t], rho_in, B_in, H_in, ue_in, ui_in, gue_out, gui_out,
-                              g_rho, g_B, g_H, g_ue, g_ui);
+        tan_cell<true, false, JAC>(k, S, win, (long long)list[t], rho_in, B_in, H_in, ue_in, ui_in, gue_out,
+                                   gui_out, g_rho, g_B, g_H, g_ue, g_ui, jo);
+}
+
+// cool_step_bwd_jac: the input gradients from a stored Jacobian (the layout
+// of JacOut) and the output adjoints.
+__global__ void k_jac_contract(long long n, const float* __restrict__ jac, const float* __restrict__ gue,
+                               const float* __restrict__ gui, float* g_rho, float* g_B, float* g_H, float* g_ue,
+                               float* g_ui) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float ge = gue[i], gi = gui[i];
+        g_rho[i] = jac_contract(ge, gi, jac[i], jac[5 * n + i]);
+        g_B[i] = jac_contract(ge, gi, jac[n + i], jac[6 * n + i]);
+        g_H[i] = jac_contract(ge, gi, jac[2 * n + i], jac[7 * n + i]);
+        g_ue[i] = jac_contract(ge, gi, jac[3 * n + i], jac[8 * n + i]);
+        g_ui[i] = jac_contract(ge, gi, jac[4 * n + i], jac[9 * n + i]);
+    }
 }
 
 // The launches of one cool_step_bwd call: fn over the cells (persistent
 // grid, dynamic chunk order), then, with a deferral list, the list kernel.
-using TanFn = decltype(&k_step_tan_f32<false, false>);
+using TanFn = decltype(&k_step_tan_f32<false, false, false>);
 using BwdFn = decltype(&k_step_bwd_f32<true, true, 0>);
 
 cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, BwdFn fb, bool tbl, size_t smem,
                        unsigned* scratch, const float* rho, const float* B, const float* H, const float* ue,
                        const float* ui, const float* gue, const float* gui, float* g_rho, float* g_B, float* g_H,
-                       float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, cudaStream_t st) {
+                       float* g_ue, float* g_ui, float* g_lb, float* g_ls, float* g_lc, const JacOut& jo,
+                       cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -646,10 +705,11 @@ cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, BwdFn fb
     }
     unsigned* list = scratch ? scratch + 1 : nullptr;
     tf<<<(int)blocks, kThreads, smem, st>>>(k, n, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui, scratch,
-                                            list);
+                                            list, jo);
     e = cudaGetLastError();
     if (e != cudaSuccess || !scratch) return e;
-    const void* fl = (const void*)k_step_tan_list_f32;
+    const auto lf = jo.jac ? k_step_tan_list_f32<true> : k_step_tan_list_f32<false>;
+    const void* fl = (const void*)lf;
     e = cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fl, kThreads, smem);
@@ -658,8 +718,8 @@ cudaError_t launch_bwd(StepK& k, long long n, const void* fn, TanFn tf, BwdFn fb
     // the list's length is on the device: one resident wave strides over it
     long long bl = (long long)sm_count() * per_sm;
     if (bl > work) bl = work;
-    k_step_tan_list_f32<<<(int)bl, kThreads, smem, st>>>(k, scratch, list, rho, B, H, ue, ui, gue, gui, g_rho, g_B,
-                                                         g_H, g_ue, g_ui);
+    lf<<<(int)bl, kThreads, smem, st>>>(k, scratch, list, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H, g_ue, g_ui,
+                                        jo);
     return cudaGetLastError();
 }
 
@@ -699,17 +759,64 @@ cool_status launch_step_bwd_f32(const cool_table* t, const cool_params* p, long 
         const int nsf = solves ? kStateFloats : kStateFloats - 1;
         if (sms) smem += (size_t)kSmemSub * kThreads * (nsf * sizeof(float) + 1);
     }
-    const TanFn tf = !impl ? k_step_tan_f32<false, false> : defer ? k_step_tan_f32<false, true> : k_step_tan_f32<true, false>;
+    const TanFn tf = !impl  ? k_step_tan_f32<false, false, false>
+                     : defer ? k_step_tan_f32<false, true, false>
+                             : k_step_tan_f32<true, false, false>;
     const BwdFn fb = sms ? (!impl ? k_step_bwd_f32<true, false, 0>
                             : defer ? k_step_bwd_f32<true, false, 1> : k_step_bwd_f32<true, true, 0>)
                          : (impl ? k_step_bwd_f32<false, true, 0> : k_step_bwd_f32<false, false, 0>);
     const void* fn = !tbl ? (const void*)tf : (const void*)fb;
+    const JacOut none{nullptr, nullptr, nullptr, 0};
     cudaError_t e = launch_bwd(k, n, fn, tf, fb, tbl, smem, scratch, rho, B, H, ue, ui, gue, gui, g_rho, g_B, g_H,
-                               g_ue, g_ui, g_lb, g_ls, g_lc, st);
+                               g_ue, g_ui, g_lb, g_ls, g_lc, none, st);
     if (owned) {
         cudaError_t ef = cudaFreeAsync(scratch, st);
         if (e == cudaSuccess) e = ef;
     }
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return COOL_OK;
+}
+
+cool_status launch_step_fwd_jac_f32(const cool_table* t, const cool_params* p, long long n, const float* rho,
+                                    const float* B, const float* H, const float* ue, const float* ui, float* ue_out,
+                                    float* ui_out, float* jac, cudaStream_t st) {
+    if (n == 0) return COOL_OK;
+    if (t->dev.fmt != 0 || p->fp64_critical || p->n_sub > kMaxSub) return COOL_EUNSUPPORTED;
+    StepK k;
+    fill_stepk(t, p, k);
+    const bool impl = p->mode == COOL_IMPLICIT_STIFF;
+    // implicit mode: stiff cells deferred to the list kernel, as in cool_step_bwd
+    unsigned* scratch = nullptr;
+    bool owned = false;
+    if (impl && n < 0xffffffffll) {
+        cudaError_t em = cudaSuccess;
+        scratch = list_for_call(st, n, &owned, &em);
+        if (em != cudaSuccess) return set_cuda_error(em);
+    }
+    const bool defer = scratch != nullptr;
+    const size_t smem = (size_t)(smem_table_floats(k) + Fmt<0>::W * kThreads) * sizeof(float);
+    const TanFn tf = !impl  ? k_step_tan_f32<false, false, true>
+                     : defer ? k_step_tan_f32<false, true, true>
+                             : k_step_tan_f32<true, false, true>;
+    const JacOut jo{ue_out, ui_out, jac, n};
+    cudaError_t e = launch_bwd(k, n, (const void*)tf, tf, nullptr, false, smem, scratch, rho, B, H, ue, ui, nullptr,
+                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, jo, st);
+    if (owned) {
+        cudaError_t ef = cudaFreeAsync(scratch, st);
+        if (e == cudaSuccess) e = ef;
+    }
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return COOL_OK;
+}
+
+cool_status launch_jac_contract_f32(long long n, const float* jac, const float* gue, const float* gui, float* g_rho,
+                                    float* g_B, float* g_H, float* g_ue, float* g_ui, cudaStream_t st) {
+    if (n == 0) return COOL_OK;
+    long long blocks = (n + kThreads - 1) / kThreads;
+    const long long cap = (long long)sm_count() * 8;   // streaming: a few waves of 256 threads per SM
+    if (blocks > cap) blocks = cap;
+    k_jac_contract<<<(int)blocks, kThreads, 0, st>>>(n, jac, gue, gui, g_rho, g_B, g_H, g_ue, g_ui);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(e);
     return COOL_OK;
 }

@@ -138,6 +138,80 @@ def test_autograd_function(env):
     assert torch.equal(ue.detach(), ref[0]) and torch.equal(ui.detach(), ref[1])
 
 
+def _same_bits(x, y):
+    return torch.equal(x.view(torch.int32), y.view(torch.int32))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fwd_jac_is_step_and_bwd_jac_is_step_bwd(env, mode):
+    """cool_step_fwd_jac's outputs are cool_step's and cool_step_bwd_jac's
+    gradients cool_step_bwd's, bit for bit (the same trajectory and Jacobian,
+    contracted by the same expression), on cells that include invalid ones
+    (passed through with the identity Jacobian), in explicit and implicit
+    mode; the outputs may overwrite the inputs."""
+    cool, tab, _, _ = env
+    f = inputs.uniform(40000, seed=65, dtype=np.float32)
+    f["ue"][:7] = np.array([0.0, -1.0, np.nan, np.inf, 1e-3, 1e-3, 1e-3], np.float32)
+    f["rho"][4] = 0.0
+    f["B"][5] = -1.0
+    n = f["rho"].size
+    tf = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
+    args = [tf[k] for k in ("rho", "B", "H", "ue", "ui")]
+    rng = np.random.default_rng(79)
+    a = torch.from_numpy(rng.uniform(0.5, 1.5, n).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.uniform(-1.0, 1.0, n).astype(np.float32)).cuda()
+    p = cool.Params(n_sub=8, mode=mode)
+    ue_ref, ui_ref = cool.step(tab, p, *args)
+    g_ref = cool.step_bwd(tab, p, *args, a, b)
+    ue, ui, jac = cool.step_fwd_jac(tab, p, *args)
+    g = cool.step_bwd_jac(jac, a, b)
+    torch.cuda.synchronize()
+    assert _same_bits(ue, ue_ref) and _same_bits(ui, ui_ref)   # NaN inputs pass through as NaN
+    for k in range(5):
+        assert torch.equal(g[k], g_ref[k]), k
+    J = jac.cpu().numpy()
+    bad = np.arange(6)
+    identity = np.array([0, 0, 0, 1, 0, 0, 0, 0, 0, 1], np.float32)   # d u_e/d u_e and d u_i/d u_i
+    assert np.array_equal(J[:, bad], np.repeat(identity[:, None], bad.size, 1))
+    # in place: the outputs overwrite u_e, u_i
+    ue_in, ui_in = tf["ue"].clone(), tf["ui"].clone()
+    _, _, jac2 = cool.step_fwd_jac(tab, p, tf["rho"], tf["B"], tf["H"], ue_in, ui_in, ue_out=ue_in, ui_out=ui_in)
+    torch.cuda.synchronize()
+    assert _same_bits(ue_in, ue_ref) and _same_bits(ui_in, ui_ref) and torch.equal(jac2, jac)
+
+
+def test_fwd_jac_errors(env):
+    from paper_2505_08855_b300 import binding as _b
+    cool, tab, _, _ = env
+    f = inputs.uniform(100, seed=66, dtype=np.float32)
+    args = [torch.from_numpy(f[k]).cuda() for k in ("rho", "B", "H", "ue", "ui")]
+    with pytest.raises(_b.CoolError) as e:
+        cool.step_fwd_jac(tab, cool.Params(n_sub=8, fp64_critical=1), *args)
+    assert e.value.status == _b.COOL_EUNSUPPORTED
+    L = _b.lib()
+    assert L.cool_step_bwd_jac(-1, None, None, None, None, None, None, None, None, None) == _b.COOL_EINVAL
+    assert L.cool_step_bwd_jac(0, None, None, None, None, None, None, None, None, None) == _b.COOL_OK
+    assert L.cool_step_bwd_jac(5, None, None, None, None, None, None, None, None, None) == _b.COOL_ENULL
+
+
+def test_autograd_implicit_mode(env):
+    """The autograd path (cool_step_fwd_jac + cool_step_bwd_jac) in implicit
+    mode equals cool_step and cool_step_bwd bit for bit; with table
+    gradients it falls back to cool_step + the reverse sweep."""
+    cool, tab, _, _ = env
+    f = inputs.uniform(20000, seed=67, dtype=np.float32)
+    t = {k: torch.from_numpy(v).cuda().requires_grad_(True) for k, v in f.items()}
+    p = cool.Params(n_sub=8, mode=1)
+    ue, ui = cool.cool_step_fn(t["rho"], t["B"], t["H"], t["ue"], t["ui"], tab, p)
+    (ue.sum() * 1.5 - ui.sum() * 0.25).backward()
+    det = [t[k].detach() for k in ("rho", "B", "H", "ue", "ui")]
+    ref = cool.step(tab, p, *det)
+    assert torch.equal(ue.detach(), ref[0]) and torch.equal(ui.detach(), ref[1])
+    g = cool.step_bwd(tab, p, *det, torch.full_like(ue, 1.5), torch.full_like(ui, -0.25))
+    for k, name in enumerate(("rho", "B", "H", "ue", "ui")):
+        assert torch.equal(t[name].grad, g[k]), name
+
+
 def test_full_size_sampled_gradients(env, oracle):
     """128^3 cells (2.1M), full-table-size run on the GPU; 1024 sampled cells
     (seed 1003) against the oracle adjoint."""
