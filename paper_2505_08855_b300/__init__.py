@@ -446,15 +446,18 @@ def _make_autograd():
         outputs, plus each cell's 2x5 Jacobian (40 bytes per cell, kept for
         the backward), and the backward is cool_step_bwd_jac, which contracts
         it with the output adjoints; the gradients are cool_step_bwd's bit
-        for bit.  Where that is unsupported (fp64_critical) or table
-        gradients are asked for, the forward is cool_step, keeps only its
-        inputs, and the backward is cool_step_bwd (the sub-cycles recomputed)."""
+        for bit.  Where that is unsupported (fp64_critical, a 16-bit table,
+        another table path) or table gradients are asked for, the forward is
+        cool_step, keeps only its inputs, and the backward is cool_step_bwd
+        (the sub-cycles recomputed); when no input needs a gradient the
+        forward is cool_step alone."""
 
         @staticmethod
         def forward(ctx, rho, B, H, ue, ui, table, params, table_grads=None):
             ctx.table, ctx.params, ctx.table_grads = table, params, table_grads
             ins = [t.detach() for t in (rho, B, H, ue, ui)]
-            if table_grads is None and not params.fp64_critical and table.spec.dtype == F32:
+            if (table_grads is None and any(ctx.needs_input_grad[:5]) and not params.fp64_critical
+                    and table.spec.dtype == F32 and params.path == _b.COOL_PATH_L2WINDOW):
                 ue_o, ui_o, jac = step_fwd_jac(table, params, *ins)
                 ctx.save_for_backward(jac)
                 ctx.jac = True

@@ -297,3 +297,24 @@ def test_sampled_gradients_on_64_table(env, oracle):
           f"excused and not flagged {(bad & ~kink).sum()}")
     assert bad.sum() <= 5
     assert not np.any(bad & ~kink)
+
+
+def test_autograd_falls_back_where_the_jacobian_pair_does_not_apply(env):
+    """Inputs that need no gradient: the forward is cool_step alone; a
+    texture-path table read: the forward is cool_step (the adjoint itself
+    is defined on the L2 block layout only, so its backward reports that)."""
+    from paper_2505_08855_b300 import binding as _b
+    cool, tab, _, _ = env
+    f = inputs.uniform(2000, seed=68, dtype=np.float32)
+    t = [torch.from_numpy(f[k]).cuda() for k in ("rho", "B", "H", "ue", "ui")]
+    p = cool.Params(n_sub=8)
+    ue, ui = cool.cool_step_fn(*t, tab, p)
+    ref = cool.step(tab, p, *t)
+    assert torch.equal(ue, ref[0]) and torch.equal(ui, ref[1])
+    pt = cool.Params(n_sub=8, path=_b.COOL_PATH_TEXTURE_POINT)
+    tg = [x.clone().requires_grad_(True) for x in t]
+    ue, ui = cool.cool_step_fn(*tg, tab, pt)
+    ref = cool.step(tab, pt, *t)
+    assert torch.equal(ue.detach(), ref[0]) and torch.equal(ui.detach(), ref[1])
+    with pytest.raises(_b.CoolError):
+        ue.sum().backward()
