@@ -350,6 +350,26 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
                     atomicAdd(&g_ls[rows[cidx] * nT + j + 1], wc * a1);
                 }
             };
+            // the brems and Coulomb adjoints likewise summed in registers while
+            // the sweep stays in one interval (brems: the synchrotron's T_e
+            // interval) or one Coulomb cell, then added to the block's
+            // shared partial sums
+            int lb_j = -1;
+            float lb_a0 = 0.f, lb_a1 = 0.f;
+            int lc_k = -1;                 // i nC + j of the Coulomb cell being summed
+            float lc00 = 0.f, lc01 = 0.f, lc10 = 0.f, lc11 = 0.f;
+            auto flush_lb = [&]() {
+                if (lb_j < 0) return;
+                atomicAdd(&glb_s[lb_j], lb_a0);
+                atomicAdd(&glb_s[lb_j + 1], lb_a1);
+            };
+            auto flush_lc = [&]() {
+                if (lc_k < 0) return;
+                atomicAdd(&glc_s[lc_k], lc00);
+                atomicAdd(&glc_s[lc_k + 1], lc01);
+                atomicAdd(&glc_s[lc_k + nC], lc10);
+                atomicAdd(&glc_s[lc_k + nC + 1], lc11);
+            };
             for (int sub = k.n_sub - 1; sub >= 0; --sub) {
                 float ge1;
                 // the exchange of this sub-cycle again (the forward's arithmetic:
@@ -387,8 +407,14 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
                         ls_a1 += gs * g.wt;
                     }
                     if (g_lb) {
-                        atomicAdd(&glb_s[g.jt], sc * g.Gb * (1.f - g.wt));
-                        atomicAdd(&glb_s[g.jt + 1], sc * g.Gb * g.wt);
+                        if (g.jt != lb_j) {
+                            flush_lb();
+                            lb_j = g.jt;
+                            lb_a0 = 0.f;
+                            lb_a1 = 0.f;
+                        }
+                        lb_a0 += sc * g.Gb * (1.f - g.wt);
+                        lb_a1 += sc * g.Gb * g.wt;
                     }
                 }
                 const float gX = ge1 - gi;
@@ -398,13 +424,21 @@ __global__ void __launch_bounds__(kThreads, IMPL ? 2 : 3) k_step_bwd_f32(
                 if (g_lc) {
                     if (xg.clamped) continue;
                     const float cl = gX * xg.X * kLn2;
-                    atomicAdd(&glc_s[xg.ji * nC + xg.je], cl * (1.f - xg.wi) * (1.f - xg.we));
-                    atomicAdd(&glc_s[xg.ji * nC + xg.je + 1], cl * (1.f - xg.wi) * xg.we);
-                    atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je], cl * xg.wi * (1.f - xg.we));
-                    atomicAdd(&glc_s[(xg.ji + 1) * nC + xg.je + 1], cl * xg.wi * xg.we);
+                    const int key = xg.ji * nC + xg.je;
+                    if (key != lc_k) {
+                        flush_lc();
+                        lc_k = key;
+                        lc00 = lc01 = lc10 = lc11 = 0.f;
+                    }
+                    lc00 += cl * (1.f - xg.wi) * (1.f - xg.we);
+                    lc01 += cl * (1.f - xg.wi) * xg.we;
+                    lc10 += cl * xg.wi * (1.f - xg.we);
+                    lc11 += cl * xg.wi * xg.we;
                 }
             }
             if (g_ls) flush_ls(ls_j, ls_a0, ls_a1);
+            if (g_lb) flush_lb();
+            if (g_lc) flush_lc();
             g_rho[i] = grho;
             g_B[i] = gB;
             g_H[i] = gH;
