@@ -318,3 +318,29 @@ def test_autograd_falls_back_where_the_jacobian_pair_does_not_apply(env):
     assert torch.equal(ue.detach(), ref[0]) and torch.equal(ui.detach(), ref[1])
     with pytest.raises(_b.CoolError):
         ue.sum().backward()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_jacobian_rows_match_oracle(env, oracle, mode):
+    """The stored Jacobian itself against the oracle adjoint (pinned by
+    finite differences): its u_e row is the oracle's gradient of u_e_out
+    alone, its u_i row that of u_i_out alone, each entry within
+    |dJ| |x| / |out| <= 2e-4 on all but cells at a kink of the step (at most
+    0.5 %, the allowance of the other oracle comparisons)."""
+    cool, tab, ospec, OT = env
+    f = inputs.uniform(6000, seed=69, dtype=np.float32)
+    n = f["rho"].size
+    tf = [torch.from_numpy(f[k]).cuda() for k in ("rho", "B", "H", "ue", "ui")]
+    _, _, jac = cool.step_fwd_jac(tab, cool.Params(n_sub=8, mode=mode), *tf)
+    J = jac.cpu().numpy().astype(np.float64)
+    op = oracle.Params(n_sub=8, mode=mode)
+    one, zero = np.ones(n, np.float32), np.zeros(n, np.float32)
+    bad = np.zeros(n, bool)
+    for row, (a, b, out) in enumerate(((one, zero, "ue"), (zero, one, "ui"))):
+        want = oracle.step_bwd(ospec, OT, op, **f, g_ue=a, g_ui=b)
+        scale = np.maximum(np.abs(want[out]), 1e-30)
+        for x, (name, fld) in enumerate(zip(["g_rho", "g_B", "g_H", "g_ue", "g_ui"], ["rho", "B", "H", "ue", "ui"])):
+            err = np.abs(J[5 * row + x] - want[name]) * np.abs(f[fld]) / scale
+            bad |= err > 2e-4
+    print(f"\nmode {mode}: cells with a Jacobian entry beyond 2e-4: {bad.sum()} of {n}")
+    assert bad.mean() <= 0.005
