@@ -133,3 +133,22 @@ def test_noalloc_wrapper_rejects_wrong_outputs_before_any_launch():
         cool.build_channels_noalloc(spec, *short)
     with pytest.raises(ValueError, match="CUDA device"):
         cool.build_channels_noalloc(spec, *good)     # right sizes, but host tensors
+
+
+def test_jacobian_wrappers_reject_wrong_tensors_before_any_launch():
+    """step_fwd_jac and step_bwd_jac write through raw pointers: wrong dtypes,
+    sizes (the Jacobian is 10 n floats) or host tensors are refused by the
+    binding before the library is called."""
+    import torch
+    import paper_2505_08855_b300 as cool
+    n = 16
+    f = [torch.ones(n) for _ in range(5)]
+    with pytest.raises(ValueError, match="step_fwd_jac"):
+        cool.step_fwd_jac(None, cool.Params(), *f)                       # host tensors
+    with pytest.raises(ValueError, match="step_fwd_jac"):
+        cool.step_fwd_jac(None, cool.Params(), *[x.double() for x in f])  # float64
+    g = torch.ones(n)
+    with pytest.raises(ValueError, match="step_bwd_jac"):
+        cool.step_bwd_jac(torch.ones(9 * n), g, g)                       # short Jacobian
+    with pytest.raises(ValueError, match="step_bwd_jac"):
+        cool.step_bwd_jac(torch.ones(10 * n), g, g)                      # host tensors
