@@ -98,6 +98,32 @@ def test_graph_capture_of_the_adjoint(env, mode):
         assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_capture_of_the_jacobian_pair(env, mode):
+    """cool_step_fwd_jac + cool_step_bwd_jac captured in one graph and
+    replayed equal the plain calls (implicit mode: the stiff cells' list in
+    stream-ordered scratch inside the graph)."""
+    cool, tab, tf = env
+    p = cool.Params(n_sub=8, mode=mode)
+    n = tf[0].numel()
+    a = torch.ones(n, device="cuda")
+    b = torch.full((n,), -0.5, device="cuda")
+    ue, ui, jac = cool.step_fwd_jac(tab, p, *tf)
+    want = [t.clone() for t in (ue, ui, *cool.step_bwd_jac(jac, a, b))]
+    torch.cuda.synchronize()
+    uo, vo, J = torch.empty_like(ue), torch.empty_like(ui), torch.empty_like(jac)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cool.step_fwd_jac(tab, p, *tf, ue_out=uo, ui_out=vo, jac=J)
+        grads = cool.step_bwd_jac(J, a, b)
+    for t in (uo, vo, J, *grads):
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for x, y in zip((uo, vo, *grads), want):
+        assert torch.equal(x, y)
+
+
 def test_graph_replayed_on_another_stream_while_a_step_runs(env, oracle):
     """A step captured on stream s1 after s1 already owns a tile counter, and
     replayed on stream s2 while s1 runs a plain step: a capture never uses a
